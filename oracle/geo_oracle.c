@@ -1,0 +1,601 @@
+/*
+ * geo_oracle.c -- TEST INFRASTRUCTURE. Plain, slow, scalar FP64 CPU oracle for
+ * the vector navigator of "Vectorising the detector geometry to optimize
+ * particle transport" (Apostolakis, Brun, Carminati, Gheata, Wenzel).
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load this library.  It shares no code, header, table or constant with
+ * the CUDA path; it is compiled with -O2 -ffp-contract=off (no implicit FMA,
+ * no fast-math) so it gives the same bits on every host.
+ *
+ * What it computes (Sec. 3, Fig. 1 and Sec. 3.1):
+ *   - DistFromOutside / DistFromInside of Box, Tube, Cone (Sec. 3.1, Fig. 2)
+ *   - Contains (inside/outside check) and Safety (Sec. 3.1)
+ *   - the navigator of Fig. 1: mother DistFromInside, then for every daughter
+ *     master->local transform + DistFromOutside, then min and hit index
+ *     (Sec. 3, Sec. 3.1 "coordinate transformations ... min/max algorithms")
+ *   - the adjoint of the navigator step (not in the paper; implicit-function
+ *     rule on the winning surface).
+ *
+ * Method: every distance is the plain set definition written out.  For the
+ * line x + s*u the oracle builds the exact set S = { s in R : x + s*u in solid }
+ * as a sorted list of closed intervals (intersection of one slab and up to
+ * two quadratic constraints) and reads
+ *     DistFromOutside = inf (S intersect [0, inf))          (+inf if empty)
+ *     DistFromInside  = sup of the component of S intersect [0, inf) holding 0
+ *                       (0 if x is outside).
+ * Solids are closed sets; no tolerance enters a definition.
+ *
+ * Readings where the paper is silent (the paper defers shapes to ROOT):
+ *   Box  params (dx,dy,dz) half-lengths.
+ *   Tube params (rmin,rmax,dz); solid when rmin == 0.
+ *   Cone params (dz,rmin1,rmax1,rmin2,rmax2), index 1 at z=-dz, 2 at z=+dz.
+ *   Placement p_mother = R p_local + t, R row-major.
+ *   Miss = +inf.  Ties: mother first, then lowest daughter index.
+ *   Track outside the mother: step 0, hit -2.  Zero/non-finite input: NaN, -2.
+ *   Safety is the exact Euclidean distance to the nearest boundary.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define K_BOX 0
+#define K_TUBE 1
+#define K_CONE 2
+
+/* Surface (face) tags carried on interval endpoints.  Box faces 0..5 are
+ * -x,+x,-y,+y,-z,+z; tubes and cones use 4/5 for -z/+z, 6 outer, 7 inner. */
+#define F_NONE (-1)
+#define F_ZM 4
+#define F_ZP 5
+#define F_OUT 6
+#define F_IN 7
+
+typedef struct {
+    double lo, hi;
+    int flo, fhi;     /* surface tag of each endpoint                      */
+    double clo, chi;  /* half-chord sqrt(D)/|A| of a quadratic endpoint
+                         (+inf for planes): conditioning of that endpoint */
+} ivl;
+
+#define MAXI 8
+typedef struct { int n; ivl v[MAXI]; } iset;
+
+static void set_all(iset *s) {
+    s->n = 1;
+    s->v[0].lo = -INFINITY; s->v[0].hi = INFINITY;
+    s->v[0].flo = s->v[0].fhi = F_NONE;
+    s->v[0].clo = s->v[0].chi = INFINITY;
+}
+static void set_empty(iset *s) { s->n = 0; }
+
+static void set_one(iset *s, double lo, int flo, double clo, double hi, int fhi, double chi) {
+    s->n = 1;
+    s->v[0].lo = lo; s->v[0].flo = flo; s->v[0].clo = clo;
+    s->v[0].hi = hi; s->v[0].fhi = fhi; s->v[0].chi = chi;
+}
+
+/* a <- a intersect b, both sorted lists of disjoint closed intervals. */
+static void set_and(iset *a, const iset *b) {
+    iset r; r.n = 0;
+    int i = 0, j = 0;
+    while (i < a->n && j < b->n) {
+        const ivl *x = &a->v[i], *y = &b->v[j];
+        ivl z;
+        if (x->lo >= y->lo) { z.lo = x->lo; z.flo = x->flo; z.clo = x->clo; }
+        else                { z.lo = y->lo; z.flo = y->flo; z.clo = y->clo; }
+        if (x->hi <= y->hi) { z.hi = x->hi; z.fhi = x->fhi; z.chi = x->chi; }
+        else                { z.hi = y->hi; z.fhi = y->fhi; z.chi = y->chi; }
+        if (z.lo <= z.hi) {
+            if (r.n >= MAXI) abort();
+            r.v[r.n++] = z;
+        }
+        if (x->hi < y->hi) i++; else j++;
+    }
+    *a = r;
+}
+
+/* { s : |c + s*w| <= h } for a slab; faces fm (at -h) and fp (at +h). */
+static void slab_set(double c, double w, double h, int fm, int fp, iset *s) {
+    if (w == 0.0) {
+        if (fabs(c) <= h) set_all(s); else set_empty(s);
+        return;
+    }
+    double a = (-h - c) / w;   /* where c + s w = -h */
+    double b = (h - c) / w;    /* where c + s w = +h */
+    if (w > 0.0) set_one(s, a, fm, INFINITY, b, fp, INFINITY);
+    else         set_one(s, b, fp, INFINITY, a, fm, INFINITY);
+}
+
+/* Discriminant B*B - A*C with error-free products (W. Kahan, "On the Cost of
+ * Floating-Point Computation Without Extra-Precise Arithmetic", 2004: the
+ * rounding errors of both products are recovered with a fused multiply-add
+ * and added back). */
+static double disc_kahan(double A, double B, double C) {
+    double p = B * B;
+    double dp = fma(B, B, -p);
+    double q = A * C;
+    double dq = fma(A, C, -q);
+    return (p - q) + (dp - dq);
+}
+
+/* { s : A s^2 + 2 B s + C <= 0 }, endpoints tagged with surface f. */
+static void quad_le0(double A, double B, double C, int f, iset *s) {
+    if (A == 0.0) {
+        if (B == 0.0) {
+            if (C <= 0.0) set_all(s); else set_empty(s);
+            return;
+        }
+        double r = -C / (2.0 * B);
+        if (B > 0.0) set_one(s, -INFINITY, F_NONE, INFINITY, r, f, INFINITY);
+        else         set_one(s, r, f, INFINITY, INFINITY, F_NONE, INFINITY);
+        return;
+    }
+    double D = disc_kahan(A, B, C);
+    if (D < 0.0) {
+        if (A > 0.0) set_empty(s); else set_all(s);
+        return;
+    }
+    double sq = sqrt(D);
+    double half = sq / fabs(A);
+    double q = -(B + copysign(sq, B));
+    double r1, r2;
+    if (q == 0.0) { r1 = 0.0; r2 = 0.0; }
+    else { r1 = q / A; r2 = C / q; }
+    double lo = r1 < r2 ? r1 : r2;
+    double hi = r1 < r2 ? r2 : r1;
+    if (A > 0.0) {
+        set_one(s, lo, f, half, hi, f, half);
+    } else if (!(lo < hi)) {
+        set_all(s);          /* double root of a downward parabola: <= 0 everywhere */
+    } else {
+        s->n = 2;
+        s->v[0].lo = -INFINITY; s->v[0].flo = F_NONE; s->v[0].clo = INFINITY;
+        s->v[0].hi = lo; s->v[0].fhi = f; s->v[0].chi = half;
+        s->v[1].lo = hi; s->v[1].flo = f; s->v[1].clo = half;
+        s->v[1].hi = INFINITY; s->v[1].fhi = F_NONE; s->v[1].chi = INFINITY;
+    }
+}
+
+/* Cone radius line R(z) = a + b z through (r1 at -dz) and (r2 at +dz). */
+static void cone_line(double dz, double r1, double r2, double *a, double *b) {
+    *a = 0.5 * (r1 + r2);
+    *b = (r2 - r1) / (2.0 * dz);
+}
+
+/* The exact line set S for a solid in its local frame. */
+static void line_set(int kind, const double *p, const double *x, const double *u, iset *S) {
+    iset t;
+    if (kind == K_BOX) {
+        slab_set(x[0], u[0], p[0], 0, 1, S);
+        slab_set(x[1], u[1], p[1], 2, 3, &t); set_and(S, &t);
+        slab_set(x[2], u[2], p[2], 4, 5, &t); set_and(S, &t);
+        return;
+    }
+    double A = u[0] * u[0] + u[1] * u[1];
+    double B = x[0] * u[0] + x[1] * u[1];
+    double C = x[0] * x[0] + x[1] * x[1];
+    if (kind == K_TUBE) {
+        double rmin = p[0], rmax = p[1], dz = p[2];
+        slab_set(x[2], u[2], dz, F_ZM, F_ZP, S);
+        quad_le0(A, B, C - rmax * rmax, F_OUT, &t); set_and(S, &t);
+        if (rmin > 0.0) {
+            /* rho^2 >= rmin^2  <=>  -(rho^2 - rmin^2) <= 0 */
+            quad_le0(-A, -B, -(C - rmin * rmin), F_IN, &t); set_and(S, &t);
+        }
+        return;
+    }
+    /* cone: rho <= Rmax(z) and rho >= Rmin(z) inside |z| <= dz; both radius
+     * lines are non-negative on the slab, so squaring is exact as a set
+     * statement there. */
+    double dz = p[0], a, b;
+    slab_set(x[2], u[2], dz, F_ZM, F_ZP, S);
+    cone_line(dz, p[2], p[4], &a, &b);
+    {
+        double R0 = a + b * x[2], Rs = b * u[2];
+        quad_le0(A - Rs * Rs, B - R0 * Rs, C - R0 * R0, F_OUT, &t); set_and(S, &t);
+    }
+    if (p[1] > 0.0 || p[3] > 0.0) {
+        cone_line(dz, p[1], p[3], &a, &b);
+        double R0 = a + b * x[2], Rs = b * u[2];
+        quad_le0(-(A - Rs * Rs), -(B - R0 * Rs), -(C - R0 * R0), F_IN, &t); set_and(S, &t);
+    }
+}
+
+typedef struct { double s; int face; double chord; } hitinfo;
+
+static hitinfo dist_out_info(int kind, const double *p, const double *x, const double *u) {
+    iset S; line_set(kind, p, x, u, &S);
+    hitinfo h = { INFINITY, F_NONE, INFINITY };
+    for (int i = 0; i < S.n; i++) {
+        if (S.v[i].hi >= 0.0) {
+            if (S.v[i].lo > 0.0) { h.s = S.v[i].lo; h.face = S.v[i].flo; h.chord = S.v[i].clo; }
+            else { h.s = 0.0; h.face = F_NONE; h.chord = INFINITY; }
+            return h;
+        }
+    }
+    return h;
+}
+
+static hitinfo dist_in_info(int kind, const double *p, const double *x, const double *u) {
+    iset S; line_set(kind, p, x, u, &S);
+    hitinfo h = { 0.0, F_NONE, INFINITY };
+    for (int i = 0; i < S.n; i++) {
+        if (S.v[i].lo <= 0.0 && S.v[i].hi >= 0.0) {
+            h.s = S.v[i].hi; h.face = S.v[i].fhi; h.chord = S.v[i].chi;
+            return h;
+        }
+    }
+    return h;
+}
+
+double orc_dist_out(int kind, const double *p, const double *x, const double *u) {
+    return dist_out_info(kind, p, x, u).s;
+}
+double orc_dist_in(int kind, const double *p, const double *x, const double *u) {
+    return dist_in_info(kind, p, x, u).s;
+}
+
+/* Closed-solid membership, straight from the definitions. */
+int orc_contains(int kind, const double *p, const double *x) {
+    if (kind == K_BOX)
+        return fabs(x[0]) <= p[0] && fabs(x[1]) <= p[1] && fabs(x[2]) <= p[2];
+    double r2 = x[0] * x[0] + x[1] * x[1];
+    if (kind == K_TUBE) {
+        if (fabs(x[2]) > p[2]) return 0;
+        return r2 <= p[1] * p[1] && r2 >= p[0] * p[0];
+    }
+    double dz = p[0];
+    if (fabs(x[2]) > dz) return 0;
+    double f = (x[2] + dz) / (2.0 * dz);
+    double rmin = p[1] + (p[3] - p[1]) * f;
+    double rmax = p[2] + (p[4] - p[2]) * f;
+    return r2 <= rmax * rmax && r2 >= rmin * rmin;
+}
+
+/* Euclidean distance from (px,pz) to the segment (ax,az)-(bx,bz). */
+static double seg_dist(double px, double pz, double ax, double az, double bx, double bz) {
+    double ex = bx - ax, ez = bz - az;
+    double wx = px - ax, wz = pz - az;
+    double L2 = ex * ex + ez * ez;
+    double t = 0.0;
+    if (L2 > 0.0) {
+        t = (wx * ex + wz * ez) / L2;
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+    }
+    double cx = ax + t * ex - px, cz = az + t * ez - pz;
+    return sqrt(cx * cx + cz * cz);
+}
+
+/* Safety: exact distance to the nearest boundary point.  inside=1 gives the
+ * distance for a point inside the solid, inside=0 for a point outside
+ * (0 when the point is in fact on the other side). */
+double orc_safety(int kind, const double *p, const double *x, int inside) {
+    int in = orc_contains(kind, p, x);
+    if (inside != in) return 0.0;
+    if (kind == K_BOX) {
+        if (in) {
+            double s = p[0] - fabs(x[0]);
+            double s1 = p[1] - fabs(x[1]), s2 = p[2] - fabs(x[2]);
+            if (s1 < s) s = s1;
+            if (s2 < s) s = s2;
+            return s;
+        }
+        double a = fabs(x[0]) - p[0], b = fabs(x[1]) - p[1], c = fabs(x[2]) - p[2];
+        if (a < 0.0) a = 0.0;
+        if (b < 0.0) b = 0.0;
+        if (c < 0.0) c = 0.0;
+        return sqrt(a * a + b * b + c * c);
+    }
+    /* Solids of revolution: the distance is the 2-D distance in the meridian
+     * half-plane (rho, z) to the cross-section polygon
+     * (rmin1,-dz) (rmax1,-dz) (rmax2,dz) (rmin2,dz). */
+    double dz, rmin1, rmax1, rmin2, rmax2;
+    if (kind == K_TUBE) { rmin1 = rmin2 = p[0]; rmax1 = rmax2 = p[1]; dz = p[2]; }
+    else { dz = p[0]; rmin1 = p[1]; rmax1 = p[2]; rmin2 = p[3]; rmax2 = p[4]; }
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]), z = x[2];
+    double d = seg_dist(rho, z, rmin1, -dz, rmax1, -dz);
+    double e = seg_dist(rho, z, rmax1, -dz, rmax2, dz);  if (e < d) d = e;
+    e = seg_dist(rho, z, rmax2, dz, rmin2, dz);          if (e < d) d = e;
+    /* the edge on the axis is no surface when both inner radii are 0 */
+    if (!in || rmin1 > 0.0 || rmin2 > 0.0) {
+        e = seg_dist(rho, z, rmin2, dz, rmin1, -dz);     if (e < d) d = e;
+    }
+    return d;
+}
+
+/* ------------------------------------------------------------------ */
+/* the navigator (Fig. 1)                                               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int mkind; const double *mparams;
+    int nd; const int32_t *kinds; const double *params, *rot, *trans;
+} orc_scene;
+
+/* x = R^T (p - t), u = R^T d: master -> local (Sec. 3.1). */
+static void to_local(const orc_scene *sc, int j, const double *pw, const double *dw,
+                     double *x, double *u) {
+    const double *R = sc->rot + 9 * j, *t = sc->trans + 3 * j;
+    double w0 = pw[0] - t[0], w1 = pw[1] - t[1], w2 = pw[2] - t[2];
+    for (int k = 0; k < 3; k++) {
+        x[k] = R[0 + k] * w0 + R[3 + k] * w1 + R[6 + k] * w2;
+        u[k] = R[0 + k] * dw[0] + R[3 + k] * dw[1] + R[6 + k] * dw[2];
+    }
+}
+
+static int bad_input(const double *pw, const double *dw) {
+    for (int k = 0; k < 3; k++)
+        if (!isfinite(pw[k]) || !isfinite(dw[k])) return 1;
+    return dw[0] == 0.0 && dw[1] == 0.0 && dw[2] == 0.0;
+}
+
+static double shape_scale(int kind, const double *p) {
+    if (kind == K_BOX) { double m = p[0]; if (p[1] > m) m = p[1]; if (p[2] > m) m = p[2]; return m; }
+    if (kind == K_TUBE) return p[1] > p[2] ? p[1] : p[2];
+    double m = p[0]; if (p[2] > m) m = p[2]; if (p[4] > m) m = p[4]; return m;
+}
+
+typedef struct {
+    double step;   int hit;
+    double second; /* second-smallest candidate (mother included)              */
+    int face;      /* surface of the winner                                   */
+    double err;    /* a-priori FP64 error bound of the step                      */
+} navres;
+
+static navres navigate_one(const orc_scene *sc, const double *pw, const double *dw) {
+    navres r;
+    r.second = INFINITY; r.face = F_NONE; r.err = 0.0;
+    if (bad_input(pw, dw)) { r.step = NAN; r.hit = -2; return r; }
+    if (!orc_contains(sc->mkind, sc->mparams, pw)) { r.step = 0.0; r.hit = -2; return r; }
+    hitinfo m = dist_in_info(sc->mkind, sc->mparams, pw, dw);
+    double best = m.s, chord = m.chord, tnorm = 0.0, scale = shape_scale(sc->mkind, sc->mparams);
+    int hit = -1, face = m.face;
+    double second = INFINITY;
+    for (int j = 0; j < sc->nd; j++) {
+        double x[3], u[3];
+        to_local(sc, j, pw, dw, x, u);
+        hitinfo h = dist_out_info(sc->kinds[j], sc->params + 5 * j, x, u);
+        if (h.s < best) {
+            second = best;
+            best = h.s; hit = j; face = h.face; chord = h.chord;
+            const double *t = sc->trans + 3 * j;
+            tnorm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+            scale = shape_scale(sc->kinds[j], sc->params + 5 * j);
+        } else if (h.s < second) {
+            second = h.s;
+        }
+    }
+    r.step = best; r.hit = hit; r.second = second; r.face = face;
+    {
+        /* E = 8 eps (|p| + |t_j| + s) (1 + L / l), eps = 2^-53 (c12 reading) */
+        double pn = sqrt(pw[0] * pw[0] + pw[1] * pw[1] + pw[2] * pw[2]);
+        double dn = sqrt(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+        double cond = isinf(chord) ? 1.0 : 1.0 + scale / (chord * dn);
+        r.err = 8.0 * ldexp(1.0, -53) * (pn + tnorm + best * dn) * cond;
+    }
+    return r;
+}
+
+static int contains_nav(const orc_scene *sc, const double *pw) {
+    if (!orc_contains(sc->mkind, sc->mparams, pw)) return -2;
+    for (int j = 0; j < sc->nd; j++) {
+        double x[3], u[3], zero[3] = { 0, 0, 0 };
+        to_local(sc, j, pw, zero, x, u);
+        if (orc_contains(sc->kinds[j], sc->params + 5 * j, x)) return j;
+    }
+    return -1;
+}
+
+static double safety_nav(const orc_scene *sc, const double *pw) {
+    if (!orc_contains(sc->mkind, sc->mparams, pw)) return 0.0;
+    double s = orc_safety(sc->mkind, sc->mparams, pw, 1);
+    for (int j = 0; j < sc->nd; j++) {
+        double x[3], u[3], zero[3] = { 0, 0, 0 };
+        to_local(sc, j, pw, zero, x, u);
+        double d = orc_safety(sc->kinds[j], sc->params + 5 * j, x, 0);
+        if (d < s) s = d;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------ */
+/* adjoint of the step (implicit function rule on the winning surface)  */
+/* ------------------------------------------------------------------ */
+
+/* For the winner hitting F(x; theta) = 0 at x* = x + s u (local frame):
+ *   ds/dp = -R g/den, ds/dt = +R g/den, ds/dd = -s R g/den,
+ *   ds/dtheta = -(dF/dtheta)(x*)/den,   g = grad_x F(x*), den = g . u.
+ * Returns 0 when the surface or denominator is undefined. */
+static int adjoint_one(const orc_scene *sc, const double *pw, const double *dw,
+                       double *gp, double *gd, int *jout, double *gt, double *gprm) {
+    navres nr = navigate_one(sc, pw, dw);
+    *jout = nr.hit;
+    for (int k = 0; k < 3; k++) { gp[k] = gd[k] = gt[k] = 0.0; }
+    for (int k = 0; k < 5; k++) gprm[k] = 0.0;
+    if (nr.hit < -1 || nr.face == F_NONE || !isfinite(nr.step)) return 0;
+    int kind; const double *p; double x[3], u[3];
+    const double *R = NULL;
+    if (nr.hit == -1) {
+        kind = sc->mkind; p = sc->mparams;
+        for (int k = 0; k < 3; k++) { x[k] = pw[k]; u[k] = dw[k]; }
+    } else {
+        kind = sc->kinds[nr.hit]; p = sc->params + 5 * nr.hit;
+        to_local(sc, nr.hit, pw, dw, x, u);
+        R = sc->rot + 9 * nr.hit;
+    }
+    double s = nr.step;
+    double xs[3] = { x[0] + s * u[0], x[1] + s * u[1], x[2] + s * u[2] };
+    double g[3] = { 0, 0, 0 }, dF[5] = { 0, 0, 0, 0, 0 };
+    int f = nr.face;
+    if (kind == K_BOX) {
+        int ax = f / 2; double sg = (f % 2) ? 1.0 : -1.0;
+        g[ax] = sg;                  /* F = sg*x_ax - h_ax */
+        dF[ax] = -1.0;
+    } else {
+        double dz = (kind == K_TUBE) ? p[2] : p[0];
+        int dzi = (kind == K_TUBE) ? 2 : 0;
+        if (f == F_ZM || f == F_ZP) {
+            double sg = (f == F_ZP) ? 1.0 : -1.0;
+            g[2] = sg; dF[dzi] = -1.0;  /* F = sg*z - dz */
+        } else if (kind == K_TUBE) {
+            double r = (f == F_OUT) ? p[1] : p[0];
+            double sg = (f == F_OUT) ? 1.0 : -1.0;   /* outside of the solid is F > 0 */
+            g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
+            dF[(f == F_OUT) ? 1 : 0] = sg * (-2.0 * r);
+        } else {
+            int outer = (f == F_OUT);
+            double r1 = outer ? p[2] : p[1], r2 = outer ? p[4] : p[3];
+            double sg = outer ? 1.0 : -1.0;
+            double w2 = (xs[2] + dz) / (2.0 * dz);    /* weight of r2 */
+            double Rz = r1 + (r2 - r1) * w2;
+            double dRdz = (r2 - r1) / (2.0 * dz);
+            /* F = sg (x^2 + y^2 - R(z)^2) */
+            g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
+            g[2] = sg * (-2.0 * Rz * dRdz);
+            double dRdr1 = 1.0 - w2, dRdr2 = w2;
+            /* dR/d(dz) at fixed z: w2 = (z+dz)/(2dz) -> dw2/ddz = -z/(2 dz^2) */
+            double dRddz = (r2 - r1) * (-xs[2] / (2.0 * dz * dz));
+            dF[outer ? 2 : 1] = sg * (-2.0 * Rz * dRdr1);
+            dF[outer ? 4 : 3] = sg * (-2.0 * Rz * dRdr2);
+            dF[0] = sg * (-2.0 * Rz * dRddz);
+        }
+    }
+    double den = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+    if (den == 0.0 || !isfinite(den)) return 0;
+    double Rg[3];
+    if (R) {
+        for (int k = 0; k < 3; k++) Rg[k] = R[3 * k] * g[0] + R[3 * k + 1] * g[1] + R[3 * k + 2] * g[2];
+    } else {
+        Rg[0] = g[0]; Rg[1] = g[1]; Rg[2] = g[2];
+    }
+    for (int k = 0; k < 3; k++) {
+        gp[k] = -Rg[k] / den;
+        gd[k] = -s * Rg[k] / den;
+        gt[k] = (nr.hit >= 0) ? Rg[k] / den : 0.0;
+    }
+    for (int k = 0; k < 5; k++) gprm[k] = -dF[k] / den;
+    return 1;
+}
+
+/* ------------------------------------------------------------------ */
+/* batch entry points (ctypes)                                           */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const orc_scene *sc;
+    const double *px, *py, *pz, *dx, *dy, *dz;
+    int64_t a, b;
+    double *step, *second, *err; int32_t *hit, *face;
+    double *safety; int32_t *where;
+    int what;
+} job;
+
+static void *run_job(void *arg) {
+    job *J = (job *)arg;
+    for (int64_t i = J->a; i < J->b; i++) {
+        double pw[3] = { J->px[i], J->py[i], J->pz[i] };
+        if (J->what == 0) {
+            double dw[3] = { J->dx[i], J->dy[i], J->dz[i] };
+            navres r = navigate_one(J->sc, pw, dw);
+            J->step[i] = r.step; J->hit[i] = r.hit;
+            if (J->second) J->second[i] = r.second;
+            if (J->err) J->err[i] = r.err;
+            if (J->face) J->face[i] = r.face;
+        } else if (J->what == 1) {
+            J->where[i] = contains_nav(J->sc, pw);
+        } else {
+            J->safety[i] = safety_nav(J->sc, pw);
+        }
+    }
+    return NULL;
+}
+
+static void run_threads(job *base, int64_t n, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (nthreads == 1 || n < 2 * nthreads) {
+        base->a = 0; base->b = n; run_job(base);
+        return;
+    }
+    pthread_t th[256];
+    job jobs[256];
+    int64_t chunk = (n + nthreads - 1) / nthreads;
+    int started = 0;
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t] = *base;
+        jobs[t].a = t * chunk;
+        jobs[t].b = (t + 1) * chunk < n ? (t + 1) * chunk : n;
+        if (jobs[t].a >= jobs[t].b) break;
+        if (pthread_create(&th[t], NULL, run_job, &jobs[t]) != 0) { run_job(&jobs[t]); continue; }
+        started = t + 1;
+    }
+    for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+}
+
+#define SCENE_ARGS int mkind, const double *mparams, int nd, const int32_t *kinds, \
+                   const double *params, const double *rot, const double *trans
+#define MAKE_SCENE orc_scene sc = { mkind, mparams, nd, kinds, params, rot, trans }
+
+void orc_navigate(SCENE_ARGS, int64_t n,
+                  const double *px, const double *py, const double *pz,
+                  const double *dx, const double *dy, const double *dz,
+                  double *step, int32_t *hit, double *second, double *err, int32_t *face,
+                  int nthreads) {
+    MAKE_SCENE;
+    job J; memset(&J, 0, sizeof J);
+    J.sc = &sc; J.px = px; J.py = py; J.pz = pz; J.dx = dx; J.dy = dy; J.dz = dz;
+    J.step = step; J.hit = hit; J.second = second; J.err = err; J.face = face; J.what = 0;
+    run_threads(&J, n, nthreads);
+}
+
+void orc_contains_nav(SCENE_ARGS, int64_t n, const double *px, const double *py,
+                      const double *pz, int32_t *where, int nthreads) {
+    MAKE_SCENE;
+    job J; memset(&J, 0, sizeof J);
+    J.sc = &sc; J.px = px; J.py = py; J.pz = pz; J.where = where; J.what = 1;
+    run_threads(&J, n, nthreads);
+}
+
+void orc_safety_nav(SCENE_ARGS, int64_t n, const double *px, const double *py,
+                    const double *pz, double *safety, int nthreads) {
+    MAKE_SCENE;
+    job J; memset(&J, 0, sizeof J);
+    J.sc = &sc; J.px = px; J.py = py; J.pz = pz; J.safety = safety; J.what = 2;
+    run_threads(&J, n, nthreads);
+}
+
+/* Per-track adjoint of step(p, d): gp, gd (3n each, SoA), the winner index,
+ * and that winner's ds/dt (3n) and ds/dparams (5n).  ok[i] = 0 where the
+ * winning surface is undefined (inside a daughter, outside the mother). */
+void orc_adjoint(SCENE_ARGS, int64_t n,
+                 const double *px, const double *py, const double *pz,
+                 const double *dx, const double *dy, const double *dz,
+                 double *gp, double *gd, int32_t *winner, double *gt, double *gprm, int32_t *ok) {
+    MAKE_SCENE;
+    for (int64_t i = 0; i < n; i++) {
+        double pw[3] = { px[i], py[i], pz[i] }, dw[3] = { dx[i], dy[i], dz[i] };
+        double a[3], b[3], c[3], e[5];
+        int j;
+        ok[i] = adjoint_one(&sc, pw, dw, a, b, &j, c, e);
+        winner[i] = j;
+        for (int k = 0; k < 3; k++) { gp[k * n + i] = a[k]; gd[k * n + i] = b[k]; gt[k * n + i] = c[k]; }
+        for (int k = 0; k < 5; k++) gprm[k * n + i] = e[k];
+    }
+}
+
+/* Single-shape batch calls for the shape-level tests. */
+void orc_shape_batch(int kind, const double *p, int64_t n, const double *x, const double *u,
+                     int what, double *out, int32_t *face) {
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i, *ui = u + 3 * i;
+        if (what == 0) { hitinfo h = dist_out_info(kind, p, xi, ui); out[i] = h.s; if (face) face[i] = h.face; }
+        else if (what == 1) { hitinfo h = dist_in_info(kind, p, xi, ui); out[i] = h.s; if (face) face[i] = h.face; }
+        else if (what == 2) out[i] = (double)orc_contains(kind, p, xi);
+        else if (what == 3) out[i] = orc_safety(kind, p, xi, 0);
+        else out[i] = orc_safety(kind, p, xi, 1);
+    }
+}

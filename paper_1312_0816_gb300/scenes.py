@@ -1,0 +1,465 @@
+"""Seeded synthetic workloads: detector volumes and track baskets.
+
+This module only *constructs* inputs. It holds none of the navigator's
+arithmetic (no distance, safety, transform-of-tracks or reduction code): it
+places shapes, draws rotations, and samples track positions and directions.
+Both the CUDA path and the CPU oracle consume its arrays, so neither side ever
+generates the other's inputs.
+
+Shape parameter conventions (ROOT-style, the paper defers all shape details to
+the ROOT geometry library, Sec. 3.1):
+
+* Box  (kind 0): params = (dx, dy, dz, 0, 0)            half-lengths
+* Tube (kind 1): params = (rmin, rmax, dz, 0, 0)        radii and half-z
+* Cone (kind 2): params = (dz, rmin1, rmax1, rmin2, rmax2), radii 1 at -dz, 2 at +dz
+
+A daughter is placed by a rotation R (row-major 3x3, local -> mother) and a
+translation t: p_mother = R p_local + t.
+
+Track pools follow the toy-detector protocol of Sec. 3.2: positions fill the
+exclusive part of the mother (here: the mother minus a keep-out envelope around
+every daughter), directions are isotropic unit vectors.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BOX, TUBE, CONE = 0, 1, 2
+KIND_NAMES = {BOX: "box", TUBE: "tube", CONE: "cone"}
+
+
+@dataclasses.dataclass
+class Scene:
+    """One logical volume: a mother shape and its placed daughters."""
+
+    name: str
+    mother_kind: int
+    mother_params: np.ndarray           # (5,) float64
+    kinds: np.ndarray                   # (nd,) int32
+    params: np.ndarray                  # (nd, 5) float64
+    rot: np.ndarray                     # (nd, 9) float64, row-major local->mother
+    trans: np.ndarray                   # (nd, 3) float64
+
+    @property
+    def n_daughters(self) -> int:
+        return int(self.kinds.shape[0])
+
+    def identity_mask(self) -> np.ndarray:
+        eye = np.eye(3).reshape(9)
+        return np.all(self.rot == eye[None, :], axis=1)
+
+    def bounding_radius(self) -> np.ndarray:
+        """Radius of a sphere about each daughter's origin enclosing it."""
+        p = self.params
+        r = np.empty(self.n_daughters)
+        for j, k in enumerate(self.kinds):
+            if k == BOX:
+                r[j] = math.sqrt(p[j, 0] ** 2 + p[j, 1] ** 2 + p[j, 2] ** 2)
+            elif k == TUBE:
+                r[j] = math.sqrt(p[j, 1] ** 2 + p[j, 2] ** 2)
+            else:
+                r[j] = math.sqrt(max(p[j, 2], p[j, 4]) ** 2 + p[j, 0] ** 2)
+        return r
+
+
+@dataclasses.dataclass
+class Tracks:
+    """A basket in structure-of-arrays form (Sec. 2: contiguous per-field vectors)."""
+
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    dx: np.ndarray
+    dy: np.ndarray
+    dz: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def fields(self):
+        return (self.x, self.y, self.z, self.dx, self.dy, self.dz)
+
+    def slice(self, a: int, b: int) -> "Tracks":
+        return Tracks(*(f[a:b] for f in self.fields()))
+
+
+# --------------------------------------------------------------------------
+# rotations
+# --------------------------------------------------------------------------
+
+def euler_zxz(phi: float, theta: float, psi: float) -> np.ndarray:
+    """R = Rz(phi) Rx(theta) Rz(psi), row-major (9,)."""
+    c1, s1 = math.cos(phi), math.sin(phi)
+    c2, s2 = math.cos(theta), math.sin(theta)
+    c3, s3 = math.cos(psi), math.sin(psi)
+    rz1 = np.array([[c1, -s1, 0.0], [s1, c1, 0.0], [0.0, 0.0, 1.0]])
+    rx = np.array([[1.0, 0.0, 0.0], [0.0, c2, -s2], [0.0, s2, c2]])
+    rz2 = np.array([[c3, -s3, 0.0], [s3, c3, 0.0], [0.0, 0.0, 1.0]])
+    return (rz1 @ rx @ rz2).reshape(9)
+
+
+def haar_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform (Haar) random rotation from ZXZ Euler angles with cos(theta) uniform."""
+    phi = rng.uniform(0.0, 2.0 * math.pi)
+    psi = rng.uniform(0.0, 2.0 * math.pi)
+    theta = math.acos(rng.uniform(-1.0, 1.0))
+    return euler_zxz(phi, theta, psi)
+
+
+_EYE = np.eye(3).reshape(9)
+
+
+def _scene(name, mkind, mparams, rows):
+    kinds = np.array([r[0] for r in rows], dtype=np.int32)
+    params = np.zeros((len(rows), 5))
+    for j, r in enumerate(rows):
+        params[j, : len(r[1])] = r[1]
+    rot = np.array([r[2] for r in rows], dtype=np.float64).reshape(len(rows), 9)
+    trans = np.array([r[3] for r in rows], dtype=np.float64).reshape(len(rows), 3)
+    mp = np.zeros(5)
+    mp[: len(mparams)] = mparams
+    return Scene(name, int(mkind), mp, kinds, params, rot, trans)
+
+
+# --------------------------------------------------------------------------
+# the workloads
+# --------------------------------------------------------------------------
+
+def box4(seed: int = 0) -> Scene:
+    """Box mother (half 100 mm) with four axis-aligned boxes at (+-50, +-50, 0),
+    half-lengths U[10, 20] per axis: the 1024-track basket case."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for cx, cy in ((-50.0, -50.0), (50.0, -50.0), (-50.0, 50.0), (50.0, 50.0)):
+        h = rng.uniform(10.0, 20.0, size=3)
+        rows.append((BOX, h, _EYE, (cx, cy, 0.0)))
+    return _scene("box4", BOX, (100.0, 100.0, 100.0), rows)
+
+
+def toy40(seed: int = 1) -> Scene:
+    """Toy detector after Sec. 3.2 (tube mother, beam-pipe/shield tubes, plates,
+    endcap cones) grown to 40 daughters: 8 coaxial tube shells, 24 rotated boxes
+    on a ring, 8 coaxial endcap cones."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for k in range(8):
+        rmin = 40.0 + 60.0 * k
+        rows.append((TUBE, (rmin, rmin + 30.0, 1000.0), _EYE, (0.0, 0.0, 0.0)))
+    for zc in (-600.0, 0.0, 600.0):
+        for m in range(8):
+            ph = math.radians(45.0 * m)
+            h = rng.uniform(10.0, 60.0, size=3)
+            rows.append((BOX, h, haar_rotation(rng), (750.0 * math.cos(ph), 750.0 * math.sin(ph), zc)))
+    for zc in (-1400.0, -1300.0, -1200.0, -1100.0, 1100.0, 1200.0, 1300.0, 1400.0):
+        rows.append((CONE, (40.0, 100.0, 800.0, 150.0, 900.0), _EYE, (0.0, 0.0, zc)))
+    return _scene("toy40", TUBE, (0.0, 1000.0, 1500.0), rows)
+
+
+def toy8(seed: int = 1) -> Scene:
+    """The paper's own toy-detector composition (Sec. 3.2): tube mother, two tubes,
+    four boxes, two cones."""
+    rng = np.random.default_rng(seed)
+    rows = [(TUBE, (40.0, 70.0, 1000.0), _EYE, (0.0, 0.0, 0.0)),
+            (TUBE, (100.0, 130.0, 1000.0), _EYE, (0.0, 0.0, 0.0))]
+    for m in range(4):
+        ph = math.radians(90.0 * m)
+        h = rng.uniform(10.0, 60.0, size=3)
+        rows.append((BOX, h, haar_rotation(rng), (750.0 * math.cos(ph), 750.0 * math.sin(ph), 0.0)))
+    for zc in (-1300.0, 1300.0):
+        rows.append((CONE, (40.0, 100.0, 800.0, 150.0, 900.0), _EYE, (0.0, 0.0, zc)))
+    return _scene("toy8", TUBE, (0.0, 1000.0, 1500.0), rows)
+
+
+def diff3() -> Scene:
+    """Box mother with one rotated box, tube and cone: exercises every shape-parameter
+    gradient of the adjoint."""
+    rows = [
+        (BOX, (15.0, 10.0, 12.0), euler_zxz(0.3, 0.7, 1.1), (-50.0, 40.0, 10.0)),
+        (TUBE, (5.0, 20.0, 25.0), euler_zxz(1.3, 0.4, 0.2), (50.0, 40.0, -10.0)),
+        (CONE, (20.0, 0.0, 15.0, 5.0, 25.0), euler_zxz(2.1, 1.2, 0.5), (0.0, -50.0, 0.0)),
+    ]
+    return _scene("diff3", BOX, (100.0, 100.0, 100.0), rows)
+
+
+def grid512(seed: int = 5) -> Scene:
+    """Box mother (half 800 mm) with 512 daughters on an 8x8x8 grid (pitch 200 mm):
+    boxes or tubes by a seeded coin, random rotations."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for i in range(8):
+        for j in range(8):
+            for k in range(8):
+                c = (-700.0 + 200.0 * i, -700.0 + 200.0 * j, -700.0 + 200.0 * k)
+                if rng.uniform() < 0.5:
+                    rows.append((BOX, rng.uniform(20.0, 50.0, size=3), haar_rotation(rng), c))
+                else:
+                    rmin = rng.uniform(0.0, 20.0)
+                    rows.append((TUBE, (rmin, rng.uniform(30.0, 60.0), rng.uniform(20.0, 60.0)),
+                                 haar_rotation(rng), c))
+    return _scene("grid512", BOX, (800.0, 800.0, 800.0), rows)
+
+
+def cell_volume(seed: int, nd: int, mother_box: bool) -> Scene:
+    """One logical volume of the batched workload: nd mixed daughters, one per
+    cell of a g^3 grid inscribed in the mother, random kinds and rotations."""
+    rng = np.random.default_rng(seed)
+    if mother_box:
+        mk, mp, half = BOX, (600.0, 600.0, 600.0), 590.0
+    else:
+        mk, mp, half = TUBE, (0.0, 700.0, 700.0), 700.0 / math.sqrt(2.0) - 5.0
+    g = int(math.ceil(nd ** (1.0 / 3.0) - 1e-9))
+    while g ** 3 < nd:
+        g += 1
+    pitch = 2.0 * half / g
+    cells = rng.permutation(g ** 3)[:nd]
+    rows = []
+    for c in cells:
+        i, j, k = c // (g * g), (c // g) % g, c % g
+        ctr = (-half + pitch * (i + 0.5), -half + pitch * (j + 0.5), -half + pitch * (k + 0.5))
+        kind = int(rng.integers(0, 3))
+        if kind == BOX:
+            prm = rng.uniform(0.1, 0.25, size=3) * pitch
+        elif kind == TUBE:
+            rmax = rng.uniform(0.15, 0.3) * pitch
+            prm = (rng.uniform(0.0, 0.6) * rmax, rmax, rng.uniform(0.1, 0.3) * pitch)
+        else:
+            r1, r2 = rng.uniform(0.05, 0.3, size=2) * pitch
+            prm = (rng.uniform(0.1, 0.3) * pitch, rng.uniform(0.0, 0.6) * r1, r1,
+                   rng.uniform(0.0, 0.6) * r2, r2)
+        rows.append((kind, prm, haar_rotation(rng), ctr))
+    return _scene(f"cell{nd}", mk, mp, rows)
+
+
+def batched64(seed: int = 3, n_volumes: int = 64, total: int = 1 << 22):
+    """64 logical volumes (box / tube mothers alternately, 4..200 daughters each)
+    and a list of baskets (volume, size) with sizes log-uniform in [16, 65536],
+    drawn until the total reaches `total` tracks."""
+    rng = np.random.default_rng(seed)
+    counts = rng.integers(4, 201, size=n_volumes)
+    vols = [cell_volume(seed * 1000 + v, int(counts[v]), v % 2 == 0) for v in range(n_volumes)]
+    baskets = []
+    acc = 0
+    while acc < total:
+        v = int(rng.integers(0, n_volumes))
+        size = int(round(math.exp(rng.uniform(math.log(16.0), math.log(65536.0)))))
+        size = min(size, total - acc)
+        baskets.append((v, size))
+        acc += size
+    return vols, baskets
+
+
+SCENES = {"box4": box4, "toy40": toy40, "toy8": toy8, "diff3": diff3, "grid512": grid512}
+
+
+# --------------------------------------------------------------------------
+# track sampling
+# --------------------------------------------------------------------------
+
+def isotropic(rng: np.random.Generator, n: int):
+    cz = rng.uniform(-1.0, 1.0, size=n)
+    ph = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    st = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
+    return st * np.cos(ph), st * np.sin(ph), cz
+
+
+def _sample_mother(rng, scene: Scene, n: int):
+    """Uniform points in the mother's interior, by construction (no test)."""
+    mp = scene.mother_params
+    if scene.mother_kind == BOX:
+        return (rng.uniform(-mp[0], mp[0], n), rng.uniform(-mp[1], mp[1], n),
+                rng.uniform(-mp[2], mp[2], n))
+    if scene.mother_kind == TUBE:
+        rmin, rmax, dz = mp[0], mp[1], mp[2]
+        r = np.sqrt(rng.uniform(rmin * rmin, rmax * rmax, n))
+        ph = rng.uniform(0.0, 2.0 * math.pi, n)
+        return r * np.cos(ph), r * np.sin(ph), rng.uniform(-dz, dz, n)
+    raise ValueError("track sampling supports box and tube mothers")
+
+
+def keepout_mask(scene: Scene, x, y, z, margin: float = 1e-6) -> np.ndarray:
+    """True where a point lies in the keep-out envelope of some daughter.
+
+    Envelopes are deliberately coarse: an axis-aligned box for unrotated boxes,
+    an axis-aligned annulus slab for unrotated tubes/cones, and the bounding
+    sphere for every rotated daughter.  The pool therefore covers the exclusive
+    part of the mother minus a thin shell around rotated daughters."""
+    from scipy.spatial import cKDTree
+
+    n = x.shape[0]
+    out = np.zeros(n, dtype=bool)
+    ident = scene.identity_mask()
+    p = scene.params
+    t = scene.trans
+    rad = scene.bounding_radius()
+    for j in np.nonzero(ident)[0]:
+        lx, ly, lz = x - t[j, 0], y - t[j, 1], z - t[j, 2]
+        k = scene.kinds[j]
+        if k == BOX:
+            m = (np.abs(lx) <= p[j, 0] + margin) & (np.abs(ly) <= p[j, 1] + margin) & \
+                (np.abs(lz) <= p[j, 2] + margin)
+        else:
+            if k == TUBE:
+                rlo, rhi, hz = p[j, 0], p[j, 1], p[j, 2]
+            else:
+                rlo, rhi, hz = min(p[j, 1], p[j, 3]), max(p[j, 2], p[j, 4]), p[j, 0]
+            rr = lx * lx + ly * ly
+            lo = max(rlo - margin, 0.0)
+            m = (np.abs(lz) <= hz + margin) & (rr <= (rhi + margin) ** 2) & (rr >= lo * lo)
+            if rlo - margin <= 0.0:
+                m = (np.abs(lz) <= hz + margin) & (rr <= (rhi + margin) ** 2)
+        out |= m
+    rot_idx = np.nonzero(~ident)[0]
+    if rot_idx.size:
+        tree = cKDTree(t[rot_idx])
+        rmax = float(rad[rot_idx].max()) + margin
+        kq = min(8, rot_idx.size)
+        pts = np.stack([x, y, z], axis=1)
+        dist, idx = tree.query(pts, k=kq, distance_upper_bound=rmax)
+        if kq == 1:
+            dist, idx = dist[:, None], idx[:, None]
+        valid = idx < rot_idx.size
+        safe_idx = np.where(valid, idx, 0)
+        rj = rad[rot_idx][safe_idx] + margin
+        out |= np.any(valid & (dist <= rj), axis=1)
+    return out
+
+
+def sample_tracks(scene: Scene, n: int, seed: int, exclusive: bool = True) -> Tracks:
+    """n tracks uniform in the mother (minus daughter keep-out envelopes when
+    `exclusive`), isotropic unit directions."""
+    rng = np.random.default_rng(seed)
+    xs, ys, zs = [], [], []
+    have = 0
+    while have < n:
+        m = max(1024, int((n - have) * 1.5))
+        x, y, z = _sample_mother(rng, scene, m)
+        if exclusive and scene.n_daughters:
+            keep = ~keepout_mask(scene, x, y, z)
+            x, y, z = x[keep], y[keep], z[keep]
+        xs.append(x)
+        ys.append(y)
+        zs.append(z)
+        have += x.shape[0]
+    x = np.concatenate(xs)[:n]
+    y = np.concatenate(ys)[:n]
+    z = np.concatenate(zs)[:n]
+    dx, dy, dz = isotropic(rng, n)
+    return Tracks(x.copy(), y.copy(), z.copy(), dx, dy, dz)
+
+
+def pool_baskets(pool_n: int, basket: int, repeats: int, seed: int):
+    """The benchmark protocol of Sec. 3.2: `repeats` baskets of `basket`
+    consecutive tracks, each starting at a random offset in a pool."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, pool_n - basket + 1, size=repeats)
+
+
+def batched_tracks(vols, baskets, seed: int):
+    """Concatenated SoA tracks for a basket list; returns Tracks and an int64
+    array of (volume, offset, count) rows."""
+    parts = []
+    rows = []
+    off = 0
+    for b, (v, size) in enumerate(baskets):
+        parts.append(sample_tracks(vols[v], size, seed * 100003 + b))
+        rows.append((v, off, size))
+        off += size
+    fields = [np.concatenate([getattr(p, f) for p in parts]) for f in ("x", "y", "z", "dx", "dy", "dz")]
+    return Tracks(*fields), np.array(rows, dtype=np.int64)
+
+
+# --------------------------------------------------------------------------
+# adversarial rays: grazing, edge and corner hits on a chosen daughter
+# --------------------------------------------------------------------------
+
+def _place(scene: Scene, j: int, q):
+    r = scene.rot[j].reshape(3, 3)
+    return r @ np.asarray(q) + scene.trans[j]
+
+
+def _dir_world(scene: Scene, j: int, v):
+    return scene.rot[j].reshape(3, 3) @ np.asarray(v)
+
+
+def _inside_mother_construct(scene: Scene, p) -> bool:
+    mp = scene.mother_params
+    if scene.mother_kind == BOX:
+        return bool(np.all(np.abs(p) < mp[:3] * 0.999))
+    return bool(p[0] ** 2 + p[1] ** 2 < (0.999 * mp[1]) ** 2 and abs(p[2]) < 0.999 * mp[2])
+
+
+def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) -> Tracks:
+    """Rays aimed at feature points of randomly chosen daughters: tangent to
+    cylinders and cones, at box edges and corners, along faces.  The target is a
+    constructed point on the feature (plus a relative jitter of about `jitter`
+    mm), the start is backed off along the ray by a random distance and kept
+    only if it lies well inside the mother and outside every keep-out envelope."""
+    rng = np.random.default_rng(seed)
+    xs = []
+    tries = 0
+    while len(xs) < n and tries < 50 * n:
+        tries += 1
+        j = int(rng.integers(0, scene.n_daughters))
+        k = scene.kinds[j]
+        p = scene.params[j]
+        mode = int(rng.integers(0, 3))
+        if k == BOX:
+            h = p[:3]
+            s = rng.choice([-1.0, 1.0], size=3)
+            q = s * h
+            if mode == 1:   # edge: free one coordinate
+                a = int(rng.integers(0, 3))
+                q[a] = rng.uniform(-h[a], h[a])
+            elif mode == 2:  # face: free two coordinates
+                a = int(rng.integers(0, 3))
+                for b in range(3):
+                    if b != a:
+                        q[b] = rng.uniform(-h[b], h[b])
+            v = np.array(isotropic(rng, 1)).reshape(3)
+            if mode == 2:  # nearly parallel to the face
+                a_ax = [b for b in range(3) if abs(q[b]) == h[b]]
+                for b in a_ax:
+                    v[b] *= 1e-6
+        else:
+            if k == TUBE:
+                rmin, rmax, hz = p[0], p[1], p[2]
+                zc = rng.uniform(-hz, hz) if mode != 2 else rng.choice([-hz, hz])
+                r = rmax if (rmin == 0.0 or rng.uniform() < 0.6) else rmin
+                slope = 0.0
+            else:
+                hz = p[0]
+                zc = rng.uniform(-hz, hz) if mode != 2 else rng.choice([-hz, hz])
+                outer = p[1] + p[3] == 0.0 or rng.uniform() < 0.6
+                r1, r2 = (p[2], p[4]) if outer else (p[1], p[3])
+                r = r1 + (r2 - r1) * (zc + hz) / (2.0 * hz)
+                slope = (r2 - r1) / (2.0 * hz)
+            ph = rng.uniform(0.0, 2.0 * math.pi)
+            radial = np.array([math.cos(ph), math.sin(ph), 0.0])
+            tang = np.array([-math.sin(ph), math.cos(ph), 0.0])
+            q = radial * r + np.array([0.0, 0.0, zc])
+            if mode == 0:   # tangent line to the surface at q (along the tangent plane)
+                gen = np.array([slope * radial[0], slope * radial[1], 1.0])
+                gen /= np.linalg.norm(gen)
+                a = rng.uniform(-1.0, 1.0)
+                v = tang * math.sqrt(max(0.0, 1.0 - a * a)) + gen * a
+            else:           # rim: any direction through the edge point
+                v = np.array(isotropic(rng, 1)).reshape(3)
+        q = np.asarray(q, dtype=np.float64) * (1.0 + jitter * rng.uniform(-1.0, 1.0, size=3))
+        v = v / np.linalg.norm(v)
+        qw = _place(scene, j, q)
+        vw = _dir_world(scene, j, v)
+        back = rng.uniform(1.0, 200.0)
+        start = qw - back * vw
+        if not _inside_mother_construct(scene, start):
+            continue
+        if keepout_mask(scene, start[0:1], start[1:2], start[2:3])[0]:
+            continue
+        xs.append((start, vw))
+    if len(xs) < n:
+        raise RuntimeError("adversarial sampler could not place enough rays")
+    arr = np.array([np.concatenate(a) for a in xs])
+    return Tracks(*(arr[:, c].copy() for c in range(6)))
