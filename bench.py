@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the vector navigator step (distance to the next boundary for a
+basket of tracks in one mother volume, Fig. 1 of the paper) on the GPU.
+
+Workload: the toy detector (tube mother r 1000 mm, half-z 1500 mm, 40
+daughters: 8 coaxial tube shells, 24 rotated boxes, 8 endcap cones), a basket
+of 2^20 tracks uniform in the mother's exclusive part with isotropic
+directions.  One step = one geo_dist_to_boundary call over the basket in
+GEO_FP32_REFINE mode; the plain FP64 mode is timed beside it.
+
+Prints one JSON line (rank 0).  Run `python bench.py --impl reference` for the
+CPU oracle timed on the host cores (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_TRACKS = 1 << 20
+N_COPIES = 8          # rotating basket copies: 8 x 60 MB > 2 x 129 MB L2
+METRIC = "tracks/s dist-to-boundary, FP32+FP64-refine vs plain FP64 on GPU; % roofline"
+WORKLOAD = "toy detector: tube mother r0-1000 half-z 1500 mm, 40 daughters (8 tube shells, 24 rotated boxes, " \
+           "8 cones), 2^20 tracks uniform in the mother's exclusive part, isotropic, seed 1"
+
+# Nominal peaks derived from unit counts and clocks (GB300: 152 SMs, 2070 MHz
+# max SM clock): FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
+# nominal 1.25 TFLOP/s of the part.  Flops count an FMA as 2.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+# FP64 pipe instructions of one evaluation of each routine (counted from
+# shapes64.cuh): (plain FP64 instructions, square roots, divisions).
+FP64_OPS = {
+    ("out", 0): (18, 0, 6), ("out", 1): (31, 2, 3), ("out", 2): (40, 2, 3),
+    ("in", 0): (9, 0, 3), ("in", 1): (12, 1, 2), ("in", 2): (20, 2, 3),
+}
+FP64_TRANSFORM = 21
+FP64_BPOINT = 3
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def algorithmic_ops(sc, hit):
+    """Algorithmic work per track of the step (shared by both modes):
+    HBM bytes 48 in + 12 out; FP64 = one evaluation of the winning solid (its
+    transform and DistFromOutside, or the mother's DistFromInside) and the
+    boundary point; FP32 (filter) = one bound per daughter whose bounding
+    sphere the track's line meets, plus the sphere tests."""
+    kinds = sc.kinds
+    w = hit[hit >= -1]
+    m = (w == -1).mean()
+    ops_d = {}
+    for k in (0, 1, 2):
+        ops_d[k] = ((w >= 0) & (np.where(w >= 0, kinds[np.maximum(w, 0)], -1) == k)).mean()
+    return m, ops_d
+
+
+def fp64_ops_per_track(sc, frac_mother, frac_kind, q_sqrt, q_div):
+    def cost(key):
+        a, s, d = FP64_OPS[key]
+        return a + s * q_sqrt + d * q_div
+
+    ops = frac_mother * cost(("in", sc.mother_kind))
+    for k, f in frac_kind.items():
+        ops += f * (FP64_TRANSFORM + cost(("out", k)))
+    return ops + FP64_BPOINT
+
+
+def fp32_visits(sc, tr, sample=20000):
+    """Mean number of daughters whose bounding sphere meets the track's line
+    ahead of it (the filter's algorithmic work), on a sample."""
+    rng = np.random.default_rng(0)
+    idx = rng.choice(tr.n, min(sample, tr.n), replace=False)
+    p = np.stack([tr.x[idx], tr.y[idx], tr.z[idx]], 1)
+    d = np.stack([tr.dx[idx], tr.dy[idx], tr.dz[idx]], 1)
+    rad = sc.bounding_radius()
+    w = sc.trans[None, :, :] - p[:, None, :]
+    proj = np.einsum("nkc,nc->nk", w, d)
+    perp2 = np.einsum("nkc,nkc->nk", w, w) - proj ** 2
+    hitsph = (perp2 <= rad[None, :] ** 2) & (proj + rad[None, :] >= 0)
+    return float(hitsph.sum(1).mean())
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores (reference arm)."""
+    import oracle
+    from paper_1312_0816_gb300 import scenes
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = len(os.sched_getaffinity(0))
+    sc = scenes.toy40(1)
+    sample = 1 << 15
+    tr = scenes.sample_tracks(sc, sample, 1)
+    for _ in range(args.warmup):
+        oracle.navigate(sc, tr.slice(0, 1024), nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.navigate(sc, tr, nthreads=cores)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = sample / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_tracks": sample},
+            "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} tracks of the toy-detector basket per step"},
+            "e2e": {"value": value, "unit": "tracks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(sc, tr):
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    sample = 1 << 16
+    sub = tr.slice(0, sample)
+    t0 = time.perf_counter()
+    oracle.navigate(sc, sub, nthreads=cores)
+    dt = time.perf_counter() - t0
+    one = tr.slice(0, 4096)
+    t1 = time.perf_counter()
+    oracle.navigate(sc, one, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    return {"value": sample / dt, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} tracks of the 2^20 basket, {cores} threads",
+            "single_thread_value": 4096 / dt1}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_TRACKS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as tdist
+
+    import paper_1312_0816_gb300 as pkg
+    from paper_1312_0816_gb300 import scenes
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            tdist.barrier()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    sc = scenes.toy40(1)
+    n = args.n
+    tr = scenes.sample_tracks(sc, n, 1 + rank)
+    vol = pkg.geo_build_volume(sc)
+    base = [torch.from_numpy(f).cuda() for f in tr.fields()]
+    copies = [base]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1234 + rank)
+    for _ in range(N_COPIES - 1):
+        perm = torch.randperm(n, device="cuda", generator=g)
+        copies.append([f[perm].contiguous() for f in base])
+    outs = [(torch.empty(n, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
+            for _ in range(N_COPIES)]
+    stream = torch.cuda.current_stream()
+
+    def step(k, mode):
+        c = copies[k % N_COPIES]
+        o = outs[k % N_COPIES]
+        pkg.geo_dist_to_boundary(vol, *c, mode=mode, step=o[0], hit=o[1])
+
+    def timed(mode, steps, warmup, clocks=None):
+        for k in range(warmup):
+            step(k, mode)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            step(k, mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        clk = clocks.stop() if clocks else None
+        return max_over_ranks(ms), clk
+
+    # correctness guard: both modes agree before anything is timed
+    step(0, 1)
+    s1, h1 = outs[0][0].clone(), outs[0][1].clone()
+    step(0, 0)
+    torch.cuda.synchronize()
+    agree = bool(torch.equal(s1, outs[0][0]) and torch.equal(h1, outs[0][1]))
+    pkg.geo_check_device_status(vol)
+
+    clocks = Clocks(local)
+    ms_ref, clk = timed(1, args.steps, args.warmup, clocks)
+    ms_f64, _ = timed(0, max(3, args.steps // 5), 3)
+    pkg.geo_check_device_status(vol)
+
+    # statistics of the refine stage
+    st_s, st_h, nref = pkg.geo_dist_to_boundary_stats(vol, *copies[0])
+    torch.cuda.synchronize()
+    nref = nref.cpu().numpy()
+    hit = st_h.cpu().numpy()
+    fallback = int((nref >= 1000).sum())
+    evals = float(np.where(nref >= 1000, nref - 1000, nref).mean())
+
+    # pipe rates for the roofline (measured) and the nominal peaks
+    r_f32 = pkg.geo_probe_pipe(0, 1 << 15)
+    r_f64 = pkg.geo_probe_pipe(1, 1 << 12)
+    r_div = pkg.geo_probe_pipe(2, 1 << 9)
+    r_sqrt = pkg.geo_probe_pipe(3, 1 << 9)
+    q_div, q_sqrt = r_f64 / r_div, r_f64 / r_sqrt
+
+    hit0 = np.asarray(hit)
+    fm, fk = algorithmic_ops(sc, hit0)
+    ops64 = fp64_ops_per_track(sc, fm, fk, q_sqrt, q_div)        # FP64 instructions per track
+    visits = fp32_visits(sc, tr)
+    ops32 = 16 * sc.n_daughters + visits * 70                     # FP32 instructions per track
+    hbm_bytes = 60.0
+    peak_hbm = 6760.9
+    try:
+        peak_hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    t_hbm = n * hbm_bytes / (peak_hbm * 1e9)
+    t_f64 = n * ops64 * 2 / (PEAK_FP64_TFLOPS * 1e12)
+    t_f32 = n * ops32 * 2 / (PEAK_FP32_TFLOPS * 1e12)
+    t_roof = max(t_hbm, t_f64, t_f32)
+    launch_s = ms_ref * 1e-3
+    achieved64 = n * ops64 * 2 / launch_s / 1e12
+    roof = {"bound": "alu", "achieved": achieved64, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved64 / PEAK_FP64_TFLOPS, "traffic": None,
+            "pipe": "fp64", "peak_source": "nominal 1.25 TFLOP/s FP64 (unit counts x clock), not measured",
+            "algorithmic_per_track": {"hbm_bytes": hbm_bytes, "fp64_instr": ops64, "fp32_instr": ops32},
+            "t_roof_us": {"hbm": t_hbm * 1e6, "fp64": t_f64 * 1e6, "fp32": t_f32 * 1e6},
+            "roof_frac_of_time": t_roof / launch_s,
+            "measured_rates": {"fp32_fma_tflops": 2 * r_f32 / 1e12, "fp64_fma_tflops": 2 * r_f64 / 1e12,
+                               "fp64_div_per_s": r_div, "fp64_sqrt_per_s": r_sqrt,
+                               "div_in_dfma": q_div, "sqrt_in_dfma": q_sqrt}}
+
+    # end to end through the host-memory entry point (pinned buffers)
+    pinned = [torch.from_numpy(f).pin_memory() for f in tr.fields()]
+    hs = torch.empty(n, dtype=torch.float64).pin_memory()
+    hh = torch.empty(n, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=n)
+    k_e2e = max(3, args.steps // 5)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=n)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, tr)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ws * n / (ms_ref * 1e-3), "unit": "tracks/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ref, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tracks_per_gpu": n, "mode": "GEO_FP32_REFINE",
+                       "l2": f"{N_COPIES} rotating basket copies ({N_COPIES * n * 60 / 1e6:.0f} MB > L2)",
+                       "parallelism": f"replicas x{ws}"},
+            "fp64_plain": {"value": ws * n / (ms_f64 * 1e-3), "unit": "tracks/s", "ms_per_step": ms_f64,
+                           "speedup_of_refine": ms_f64 / ms_ref},
+            "modes_bit_identical": agree,
+            "refine": {"fp64_evals_per_track": evals, "fallback_tracks": fallback},
+            "roofline": roof,
+            "e2e": {"value": ws * n / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": 48 * n,
+                    "d2h_bytes_per_step": 12 * n, "api": "geo_dist_to_boundary_host (pinned host buffers)"},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    vol.close()
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * geo.h -- C ABI of the GB300 vector navigator.
+ *
+ * The operations are those of the vector geometry navigator of "Vectorising
+ * the detector geometry to optimize particle transport" (Apostolakis, Brun,
+ * Carminati, Gheata, Wenzel):
+ *   - Sec. 3 / Fig. 1: for a basket of tracks inside one mother volume, the
+ *     geometrical step to the next boundary along the line of flight and the
+ *     volume hit (mother DistFromInside, then per daughter a master->local
+ *     transform and DistFromOutside, then min + index).
+ *   - Sec. 3.1: the shape queries distance-to-enter, distance-to-leave,
+ *     safety (minimum distance to any boundary) and inside/outside check for
+ *     Box, Tube and Cone, and the coordinate transformation and min/max
+ *     algorithms the navigator needs.
+ *   - Sec. 2: tracks arrive as a "basket", a structure of contiguous arrays.
+ *
+ * Conventions (the paper defers all shape details to the ROOT geometry
+ * library; these are the readings this library implements):
+ *   - Units are mm.  Solids are closed sets.  Directions are NOT renormalised:
+ *     steps are in units of |d|.
+ *   - Box  p = (dx, dy, dz, -, -)               half-lengths
+ *     Tube p = (rmin, rmax, dz, -, -)           rmin = 0 is a solid cylinder
+ *     Cone p = (dz, rmin1, rmax1, rmin2, rmax2)  radii "1" at z=-dz, "2" at +dz
+ *   - A daughter is placed by a rotation R (row-major, local -> mother) and a
+ *     translation t:  p_mother = R p_local + t.  The mother's frame is the
+ *     frame of the tracks (its rot must be the identity and trans zero).
+ *   - Miss = +inf.  Ties between equal steps: the mother wins, then the lowest
+ *     daughter index (the order of the sequential algorithm of Fig. 1a).
+ *   - Track outside the mother: step 0, hit -2.  Non-finite position or
+ *     direction, or a zero direction: step NaN, hit -2.
+ *   - Safety is the exact Euclidean distance to the nearest boundary of the
+ *     mother's exclusive region; 0 inside a daughter or outside the mother.
+ *
+ * Memory and streams:
+ *   - Every basket and output pointer is DEVICE memory owned by the caller
+ *     (e.g. torch.Tensor.data_ptr()), in structure-of-arrays layout, one FP64
+ *     (or int32) element per track, no stride.  Host pointers are rejected
+ *     with GEO_ERR_INVALID_ARG (except in geo_dist_to_boundary_host).
+ *   - The library owns a volume's device tables from geo_build_volume until
+ *     geo_destroy_volume.  Query calls allocate nothing.
+ *   - Query calls are asynchronous on `stream` (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream) and never synchronise the host.
+ *   - n == 0 returns GEO_OK and launches nothing.
+ *   - Nothing throws across this boundary; every call returns a geo_status.
+ *     geo_status_string() gives a static description.
+ */
+#ifndef GEONAV_GEO_H
+#define GEONAV_GEO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GEO_OK = 0,
+    GEO_ERR_INVALID_ARG = 1,    /* null/host pointer, n < 0, bad mode, bad kind     */
+    GEO_ERR_SHAPE_PARAMS = 2,   /* non-finite or inconsistent shape / placement     */
+    GEO_ERR_OOM = 3,            /* device allocation failed (builder only)          */
+    GEO_ERR_CUDA = 4,           /* a CUDA runtime call failed                       */
+    GEO_ERR_DEVICE_ASSERT = 5,  /* a kernel reported a failed internal check        */
+    GEO_ERR_UNSUPPORTED = 6     /* valid request this build does not implement      */
+} geo_status;
+
+typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2 } geo_kind;
+
+/* GEO_FP64: every operation in FP64.
+ * GEO_FP32_REFINE: a conservative FP32 pass bounds every candidate from below;
+ * only candidates that can still win are recomputed with the same FP64
+ * routines as GEO_FP64, so both modes return the same answers. */
+typedef enum { GEO_FP64 = 0, GEO_FP32_REFINE = 1 } geo_mode;
+
+/* One placed solid.  kind: geo_kind.  p: shape parameters (see above).
+ * rot: row-major 3x3 rotation local -> mother, orthonormal with det +1 within
+ * 1e-12.  trans: translation (mm). */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;   /* must be 0 */
+    double p[5];
+    double rot[9];
+    double trans[3];
+} geo_placed_shape;
+
+/* Build options.  voxelize != 0 builds a uniform-grid candidate list over the
+ * mother's bounding box (grid[i] cells per axis; 0 = chosen from the daughter
+ * count).  Daughter lists per voxel are used by geo_dist_to_boundary. */
+typedef struct {
+    int32_t voxelize;
+    int32_t grid[3];
+} geo_build_opts;
+
+typedef struct geo_volume_s* geo_volume;
+
+/* Builds the device tables of one logical volume (Fig. 1: a mother and its
+ * daughter volumes).  `mother` and `daughters[0..n_daughters)` are host
+ * structs, copied; the caller may free them on return.  n_daughters may be 0.
+ * Validation: kinds, finiteness, dz > 0, 0 <= rmin <= rmax (rmin1<=rmax1,
+ * rmin2<=rmax2, rmax1+rmax2 > 0 for cones), orthonormal rotations.  Allocates
+ * device memory and copies on `stream`, then synchronises that stream.
+ * On success *out owns the tables; on failure *out is NULL. */
+geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_shape* daughters,
+                            int32_t n_daughters, const geo_build_opts* opts, void* stream,
+                            geo_volume* out);
+
+/* Frees the device tables (synchronises the device first).  NULL is a no-op. */
+geo_status geo_destroy_volume(geo_volume v);
+
+/* Number of daughters, and whether a voxel grid was built (1/0). */
+geo_status geo_volume_info(geo_volume v, int32_t* n_daughters, int32_t* voxelized, int32_t grid[3]);
+
+/* Fig. 1 navigator step for n tracks.  Inputs x,y,z (positions) and dx,dy,dz
+ * (directions): device FP64 arrays of n elements.  Outputs: step[n] (FP64,
+ * units of |d|), hit[n] (int32: -1 mother, j >= 0 daughter j, -2 outside or
+ * invalid).  bpoint: NULL, or a device FP64 array of 3n elements receiving the
+ * boundary point p + step*d as three consecutive SoA blocks (x[n], y[n], z[n]).
+ * mode: geo_mode. */
+geo_status geo_dist_to_boundary(geo_volume v, const double* x, const double* y, const double* z,
+                                const double* dx, const double* dy, const double* dz, int64_t n,
+                                double* step, int32_t* hit, double* bpoint, int32_t mode,
+                                void* stream);
+
+/* Inside/outside check of Sec. 3.1 at navigator level: where[i] = -2 outside
+ * the mother, -1 in the mother's exclusive part, j = the lowest-index daughter
+ * whose closed solid contains the point.  x,y,z device FP64[n]; where device
+ * int32[n]. */
+geo_status geo_contains(geo_volume v, const double* x, const double* y, const double* z, int64_t n,
+                        int32_t* where, void* stream);
+
+/* Safety of Sec. 3.1 at navigator level: min(mother inside-safety, min over
+ * daughters of outside-safety), exact Euclidean; 0 outside the mother or
+ * inside a daughter.  safety device FP64[n]. */
+geo_status geo_safety(geo_volume v, const double* x, const double* y, const double* z, int64_t n,
+                      double* safety, int32_t mode, void* stream);
+
+/* Same as geo_dist_to_boundary but every array is HOST memory (pageable or
+ * pinned); the library stages the basket through a device workspace in
+ * chunks of at most `chunk` tracks (0 = 1<<20), copying on `stream`, and
+ * synchronises `stream` before returning.  The workspace is allocated on the
+ * first call and kept with the volume (grown when `chunk` grows). */
+geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double* y,
+                                     const double* z, const double* dx, const double* dy,
+                                     const double* dz, int64_t n, double* step, int32_t* hit,
+                                     int32_t mode, int64_t chunk, void* stream);
+
+/* Same as geo_dist_to_boundary in GEO_FP32_REFINE mode, and also writes, per
+ * track, the number of FP64 solid evaluations the refine stage performed
+ * (mother and daughters; 1000 is added when the track fell back to the full
+ * FP64 loop) into nref (device int32[n]).  For measurement of the filter. */
+geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const double* y, const double* z,
+                                      const double* dx, const double* dy, const double* dz, int64_t n,
+                                      double* step, int32_t* hit, int32_t* nref, void* stream);
+
+/* Reads and clears the volume's device status word (errors recorded by
+ * kernels, e.g. a bulk-copy wait that ran out of polls).  Synchronises
+ * `stream`.  Returns GEO_ERR_DEVICE_ASSERT if any was recorded; *word gets
+ * the raw bits when non-NULL. */
+geo_status geo_check_device_status(geo_volume v, uint32_t* word, void* stream);
+
+/* Measurement support (not part of the navigator): issue rate in operations
+ * per second of one arithmetic operation over the whole GPU: what = 0 FP32
+ * FMA, 1 FP64 FMA, 2 FP64 divide, 3 FP64 square root, 4 FP32 divide, 5 FP32
+ * square root.  scratch: device buffer of >= 256 doubles.  Synchronises. */
+geo_status geo_probe_pipe(int32_t what, int64_t iters, int32_t blocks, void* scratch, void* stream,
+                          double* ops_per_s);
+
+const char* geo_status_string(geo_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEONAV_GEO_H */

@@ -1,0 +1,488 @@
+// geo_abi.cu -- host side of the C ABI declared in include/geo.h: argument
+// validation, the volume builder (device tables of Fig. 1's mother and
+// daughter volumes), and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "geo_internal.h"
+
+using namespace geonav;
+
+struct geo_volume_s {
+    int device = 0;
+    VolView view{};
+    ShapeRec64* d64 = nullptr;
+    ShapeRec32* d32 = nullptr;
+    int32_t* vox_off = nullptr;
+    int32_t* vox_ids = nullptr;
+    unsigned int* status = nullptr;
+    // staging workspace of geo_dist_to_boundary_host
+    void* ws = nullptr;
+    int64_t ws_tracks = 0;
+    std::mutex ws_mu;
+};
+
+namespace {
+
+constexpr double kEps32 = 5.9604644775390625e-08;  // 2^-24, unit roundoff of FP32
+
+int num_sms_of(int dev) {
+    static int cache[64] = {0};
+    if (dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+int smem_budget(int dev) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+        v = 48 * 1024;
+    return v - 1024;   // static shared memory of the kernels (mbarrier etc.)
+}
+
+bool finite_all(const double* a, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+// Shape parameter validation (readings of the ROOT conventions, see geo.h).
+geo_status check_shape(const geo_placed_shape& s, bool is_mother) {
+    if (s.kind < GEO_BOX || s.kind > GEO_CONE) return GEO_ERR_INVALID_ARG;
+    if (s.reserved != 0) return GEO_ERR_INVALID_ARG;
+    if (!finite_all(s.p, 5) || !finite_all(s.rot, 9) || !finite_all(s.trans, 3)) return GEO_ERR_SHAPE_PARAMS;
+    const double* p = s.p;
+    switch (s.kind) {
+        case GEO_BOX:
+            if (!(p[0] > 0 && p[1] > 0 && p[2] > 0)) return GEO_ERR_SHAPE_PARAMS;
+            break;
+        case GEO_TUBE:
+            if (!(p[2] > 0 && p[0] >= 0 && p[1] > 0 && p[0] <= p[1])) return GEO_ERR_SHAPE_PARAMS;
+            break;
+        default:
+            if (!(p[0] > 0 && p[1] >= 0 && p[3] >= 0 && p[1] <= p[2] && p[3] <= p[4] && p[2] + p[4] > 0))
+                return GEO_ERR_SHAPE_PARAMS;
+    }
+    // rotation: orthonormal with det +1 within 1e-12
+    const double* R = s.rot;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double d = R[3 * a] * R[3 * b] + R[3 * a + 1] * R[3 * b + 1] + R[3 * a + 2] * R[3 * b + 2];
+            if (std::fabs(d - (a == b ? 1.0 : 0.0)) > 1e-12) return GEO_ERR_SHAPE_PARAMS;
+        }
+    const double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                       R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (std::fabs(det - 1.0) > 1e-12) return GEO_ERR_SHAPE_PARAMS;
+    if (is_mother) {
+        for (int k = 0; k < 9; ++k)
+            if (R[k] != ((k % 4 == 0) ? 1.0 : 0.0)) return GEO_ERR_INVALID_ARG;
+        if (s.trans[0] != 0 || s.trans[1] != 0 || s.trans[2] != 0) return GEO_ERR_INVALID_ARG;
+    }
+    return GEO_OK;
+}
+
+double bounding_radius(const geo_placed_shape& s) {
+    const double* p = s.p;
+    if (s.kind == GEO_BOX) return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    if (s.kind == GEO_TUBE) return std::sqrt(p[1] * p[1] + p[2] * p[2]);
+    const double r = std::max(p[2], p[4]);
+    return std::sqrt(r * r + p[0] * p[0]);
+}
+
+// derived FP64 constants (layout in geo_internal.h)
+ShapeRec64 make_rec64(const geo_placed_shape& s) {
+    ShapeRec64 r;
+    std::memset(&r, 0, sizeof r);
+    std::memcpy(r.R, s.rot, sizeof r.R);
+    std::memcpy(r.t, s.trans, sizeof r.t);
+    std::memcpy(r.p, s.p, sizeof r.p);
+    r.kind = s.kind;
+    const double* p = s.p;
+    if (s.kind == GEO_BOX) {
+        r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
+    } else if (s.kind == GEO_TUBE) {
+        r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
+        r.d[3] = p[0] * p[0]; r.d[4] = p[1] * p[1];
+    } else {
+        const double dz = p[0];
+        r.d[0] = dz;
+        r.d[1] = 0.5 * (p[2] + p[4]);
+        r.d[2] = (p[4] - p[2]) / (2.0 * dz);
+        r.d[3] = 0.5 * (p[1] + p[3]);
+        r.d[4] = (p[3] - p[1]) / (2.0 * dz);
+        r.d[5] = p[1] * p[1]; r.d[6] = p[2] * p[2]; r.d[7] = p[3] * p[3]; r.d[8] = p[4] * p[4];
+        r.d[9] = 1.0 / std::sqrt(1.0 + r.d[2] * r.d[2]);
+        r.d[10] = 1.0 / std::sqrt(1.0 + r.d[4] * r.d[4]);
+        r.d[11] = (p[1] > 0.0 || p[3] > 0.0) ? 1.0 : 0.0;
+    }
+    const double br = bounding_radius(s);
+    r.brad = br * (1.0 + 1e-12) + 1e-9;
+    return r;
+}
+
+// FP32 record of a solid grown (grow > 0) or shrunk (grow < 0) by |grow| mm.
+// Returns false when a shrunk solid degenerates.
+bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32& r) {
+    std::memset(&r, 0, sizeof r);
+    for (int k = 0; k < 9; ++k) r.R[k] = float(s.rot[k]);
+    for (int k = 0; k < 3; ++k) r.t[k] = float(s.trans[k]);
+    r.kind = s.kind;
+    r.delta = float(delta);
+    const double* p = s.p;
+    const double g = grow;
+    if (s.kind == GEO_BOX) {
+        for (int k = 0; k < 3; ++k) {
+            r.e[k] = float(p[k] + g);
+            if (!(p[k] + g > 0)) return false;
+        }
+    } else if (s.kind == GEO_TUBE) {
+        const double rmin = p[0] - g, rmax = p[1] + g, dz = p[2] + g;
+        if (!(rmax > 0 && dz > 0)) return false;
+        const bool hole = p[0] > 0 && rmin > 0;
+        r.e[0] = hole ? float(rmin * rmin) : 0.f;
+        r.e[1] = float(rmax * rmax);
+        r.e[2] = float(dz);
+        r.e[3] = hole ? 1.f : 0.f;
+    } else {
+        const double dz = p[0], dzg = dz + g;
+        if (!(dzg > 0)) return false;
+        const double ao = 0.5 * (p[2] + p[4]), bo = (p[4] - p[2]) / (2.0 * dz);
+        const double ai = 0.5 * (p[1] + p[3]), bi = (p[3] - p[1]) / (2.0 * dz);
+        // offset the supporting lines of the slanted edges by g along their normals
+        const double ao2 = ao + g * std::sqrt(1.0 + bo * bo);
+        const double ai2 = ai - g * std::sqrt(1.0 + bi * bi);
+        const double o_lo = ao2 - bo * dzg, o_hi = ao2 + bo * dzg;
+        const double i_lo = ai2 - bi * dzg, i_hi = ai2 + bi * dzg;
+        if (!(std::max(o_lo, o_hi) > 0)) return false;
+        const bool hole = (p[1] > 0 || p[3] > 0) && i_lo > 0 && i_hi > 0;
+        r.e[0] = float(dzg);
+        r.e[1] = float(ao2);
+        r.e[2] = float(bo);
+        r.e[3] = hole ? float(ai2) : 0.f;
+        r.e[4] = hole ? float(bi) : 0.f;
+        r.e[5] = hole ? 1.f : 0.f;
+        const double olo = std::max(o_lo, 0.0), ohi = std::max(o_hi, 0.0);
+        r.e[6] = hole ? float(i_lo * i_lo) : 0.f;
+        r.e[7] = float(olo * olo);
+        r.e[8] = hole ? float(i_hi * i_hi) : 0.f;
+        r.e[9] = float(ohi * ohi);
+    }
+    r.brad = float(bounding_radius(s) * (1.0 + 1e-6) + std::max(g, 0.0));
+    return true;
+}
+
+// Extent of the mother: an upper bound of |p| for every point inside it.
+double mother_scale(const geo_placed_shape& m) { return bounding_radius(m); }
+
+// Inflation of one solid's FP32 copy (mm).  It covers the FP32 rounding of
+//  - the inputs and the master->local transform, for positions up to the
+//    mother scale S:                               48 eps32 S
+//  - the shape arithmetic in the frame shifted to the closest approach
+//    (magnitudes up to the bounding radius brad):  16 eps32 brad
+//  - for a quadric of radius r and slope b, the rounding of its discriminant
+//    expressed as a change of radius:              16 eps32 brad^2 (1+b^2) / r
+//    with r taken no smaller than sqrt(eps32) brad / 2 (apexes, tiny holes).
+double inflation(const geo_placed_shape& s, double S) {
+    const double br = bounding_radius(s);
+    const double* p = s.p;
+    double d = kEps32 * (48.0 * S + 16.0 * br);
+    if (s.kind == GEO_BOX) return d;
+    double rsmall = DBL_MAX, slope2 = 0.0;
+    auto take = [&](double r) { rsmall = std::min(rsmall, r > 0 ? r : 0.0); };
+    if (s.kind == GEO_TUBE) {
+        take(p[1]);
+        if (p[0] > 0) take(p[0]);
+    } else {
+        take(p[2]);
+        take(p[4]);
+        if (p[1] > 0 || p[3] > 0) {
+            take(p[1]);
+            take(p[3]);
+        }
+        const double bo = (p[4] - p[2]) / (2.0 * p[0]), bi = (p[3] - p[1]) / (2.0 * p[0]);
+        slope2 = std::max(bo * bo, bi * bi);
+    }
+    const double floor_r = 0.5 * std::sqrt(kEps32) * br;
+    d += 16.0 * kEps32 * br * br * (1.0 + slope2) / std::max(rsmall, floor_r);
+    return d;
+}
+
+geo_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GEO_OK;
+    if (e == cudaErrorMemoryAllocation) return GEO_ERR_OOM;
+    return GEO_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+geo_status check_volume_device(geo_volume v) {
+    if (!v) return GEO_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
+    return dev == v->device ? GEO_OK : GEO_ERR_INVALID_ARG;
+}
+
+geo_status check_basket(const double* x, const double* y, const double* z, int64_t n) {
+    if (n < 0) return GEO_ERR_INVALID_ARG;
+    if (n == 0) return GEO_OK;
+    if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(z)) return GEO_ERR_INVALID_ARG;
+    return GEO_OK;
+}
+
+// Reads and clears the device status word of earlier kernels (asynchronous
+// copy would be ideal; a tiny synchronous read keeps the ABI simple and is
+// only done in checked mode).
+}  // namespace
+
+extern "C" {
+
+const char* geo_status_string(geo_status s) {
+    switch (s) {
+        case GEO_OK: return "ok";
+        case GEO_ERR_INVALID_ARG: return "invalid argument";
+        case GEO_ERR_SHAPE_PARAMS: return "invalid shape parameters or placement";
+        case GEO_ERR_OOM: return "device allocation failed";
+        case GEO_ERR_CUDA: return "CUDA runtime error";
+        case GEO_ERR_DEVICE_ASSERT: return "device-side check failed";
+        case GEO_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_shape* daughters, int32_t n_daughters,
+                            const geo_build_opts* opts, void* stream, geo_volume* out) {
+    if (!out) return GEO_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mother || n_daughters < 0 || (n_daughters > 0 && !daughters)) return GEO_ERR_INVALID_ARG;
+    if (n_daughters > (1 << 20)) return GEO_ERR_INVALID_ARG;
+    geo_status st = check_shape(*mother, true);
+    if (st != GEO_OK) return st;
+    for (int j = 0; j < n_daughters; ++j)
+        if ((st = check_shape(daughters[j], false)) != GEO_OK) return st;
+    if (opts && opts->voxelize) return GEO_ERR_UNSUPPORTED;   // voxel grid: see nav_voxel.cu
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
+
+    const double S = mother_scale(*mother);
+    std::vector<ShapeRec64> h64(n_daughters);
+    std::vector<ShapeRec32> h32(n_daughters);
+    for (int j = 0; j < n_daughters; ++j) {
+        h64[j] = make_rec64(daughters[j]);
+        const double dl = inflation(daughters[j], S);
+        if (!make_rec32(daughters[j], dl, dl, h32[j])) return GEO_ERR_SHAPE_PARAMS;
+    }
+
+    geo_volume v = new (std::nothrow) geo_volume_s;
+    if (!v) return GEO_ERR_OOM;
+    v->device = dev;
+    VolView& vw = v->view;
+    std::memset(&vw, 0, sizeof vw);
+    vw.m64 = make_rec64(*mother);
+    const double dm = inflation(*mother, S);
+    if (!make_rec32(*mother, -dm, dm, vw.m32) || !make_rec32(*mother, dm, dm, vw.m32u)) {
+        delete v;
+        return GEO_ERR_SHAPE_PARAMS;
+    }
+    vw.nd = n_daughters;
+
+    cudaError_t e = cudaSuccess;
+    const size_t b64 = sizeof(ShapeRec64) * size_t(std::max(n_daughters, 1));
+    const size_t b32 = sizeof(ShapeRec32) * size_t(std::max(n_daughters, 1));
+    if ((e = cudaMalloc(&v->d64, b64)) != cudaSuccess || (e = cudaMalloc(&v->d32, b32)) != cudaSuccess ||
+        (e = cudaMalloc(&v->status, sizeof(unsigned int))) != cudaSuccess) {
+        geo_destroy_volume(v);
+        return cuda_status(e);
+    }
+    if (n_daughters > 0) {
+        if ((e = cudaMemcpyAsync(v->d64, h64.data(), sizeof(ShapeRec64) * n_daughters, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(v->d32, h32.data(), sizeof(ShapeRec32) * n_daughters, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess) {
+            geo_destroy_volume(v);
+            return cuda_status(e);
+        }
+    }
+    if ((e = cudaMemsetAsync(v->status, 0, sizeof(unsigned int), s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        geo_destroy_volume(v);
+        return cuda_status(e);
+    }
+    vw.d64 = v->d64;
+    vw.d32 = v->d32;
+    vw.status = v->status;
+    vw.smem64 = (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64)) <= smem_budget(dev)) ? 1 : 0;
+    vw.smem_refine =
+        (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64) + sizeof(ShapeRec32)) <= smem_budget(dev)) ? 1 : 0;
+    *out = v;
+    return GEO_OK;
+}
+
+geo_status geo_destroy_volume(geo_volume v) {
+    if (!v) return GEO_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != v->device) cudaSetDevice(v->device);
+    cudaDeviceSynchronize();
+    cudaFree(v->d64);
+    cudaFree(v->d32);
+    cudaFree(v->vox_off);
+    cudaFree(v->vox_ids);
+    cudaFree(v->status);
+    cudaFree(v->ws);
+    if (prev >= 0 && prev != v->device) cudaSetDevice(prev);
+    delete v;
+    return GEO_OK;
+}
+
+geo_status geo_volume_info(geo_volume v, int32_t* n_daughters, int32_t* voxelized, int32_t grid[3]) {
+    if (!v) return GEO_ERR_INVALID_ARG;
+    if (n_daughters) *n_daughters = v->view.nd;
+    if (voxelized) *voxelized = v->view.voxelized;
+    if (grid)
+        for (int k = 0; k < 3; ++k) grid[k] = v->view.grid[k];
+    return GEO_OK;
+}
+
+geo_status geo_dist_to_boundary(geo_volume v, const double* x, const double* y, const double* z, const double* dx,
+                                const double* dy, const double* dz, int64_t n, double* step, int32_t* hit,
+                                double* bpoint, int32_t mode, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if (mode != GEO_FP64 && mode != GEO_FP32_REFINE) return GEO_ERR_INVALID_ARG;
+    if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
+    if (n == 0) return GEO_OK;
+    if (!is_device_ptr(dx) || !is_device_ptr(dy) || !is_device_ptr(dz) || !is_device_ptr(step) ||
+        !is_device_ptr(hit) || (bpoint && !is_device_ptr(bpoint)))
+        return GEO_ERR_INVALID_ARG;
+    const Basket b{x, y, z, dx, dy, dz, n};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int sms = num_sms_of(v->device);
+    cudaError_t e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, step, hit, bpoint, s, sms)
+                                       : launch_dist_refine(v->view, b, step, hit, bpoint, s, sms);
+    return cuda_status(e);
+}
+
+geo_status geo_contains(geo_volume v, const double* x, const double* y, const double* z, int64_t n, int32_t* where,
+                        void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
+    if (n == 0) return GEO_OK;
+    if (!is_device_ptr(where)) return GEO_ERR_INVALID_ARG;
+    const Basket b{x, y, z, nullptr, nullptr, nullptr, n};
+    return cuda_status(launch_contains(v->view, b, where, static_cast<cudaStream_t>(stream), num_sms_of(v->device)));
+}
+
+geo_status geo_safety(geo_volume v, const double* x, const double* y, const double* z, int64_t n, double* safety,
+                      int32_t mode, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if (mode != GEO_FP64 && mode != GEO_FP32_REFINE) return GEO_ERR_INVALID_ARG;
+    if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
+    if (n == 0) return GEO_OK;
+    if (!is_device_ptr(safety)) return GEO_ERR_INVALID_ARG;
+    const Basket b{x, y, z, nullptr, nullptr, nullptr, n};
+    return cuda_status(
+        launch_safety(v->view, b, safety, mode, static_cast<cudaStream_t>(stream), num_sms_of(v->device)));
+}
+
+geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double* y, const double* z, const double* dx,
+                                     const double* dy, const double* dz, int64_t n, double* step, int32_t* hit,
+                                     int32_t mode, int64_t chunk, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if (mode != GEO_FP64 && mode != GEO_FP32_REFINE) return GEO_ERR_INVALID_ARG;
+    if (n < 0 || chunk < 0) return GEO_ERR_INVALID_ARG;
+    if (n == 0) return GEO_OK;
+    if (!x || !y || !z || !dx || !dy || !dz || !step || !hit) return GEO_ERR_INVALID_ARG;
+    if (chunk == 0) chunk = int64_t(1) << 20;
+    if (chunk > n) chunk = n;
+    std::lock_guard<std::mutex> lock(v->ws_mu);
+    cudaError_t e = cudaSuccess;
+    if (v->ws_tracks < chunk) {
+        if (v->ws) {
+            cudaFree(v->ws);
+            v->ws = nullptr;
+            v->ws_tracks = 0;
+        }
+        if ((e = cudaMalloc(&v->ws, size_t(chunk) * (7 * sizeof(double) + sizeof(int32_t)))) != cudaSuccess)
+            return cuda_status(e);
+        v->ws_tracks = chunk;
+    }
+    double* w = static_cast<double*>(v->ws);
+    const int64_t cap = v->ws_tracks;
+    double* f[7] = {w, w + cap, w + 2 * cap, w + 3 * cap, w + 4 * cap, w + 5 * cap, w + 6 * cap};
+    int32_t* whit = reinterpret_cast<int32_t*>(w + 7 * cap);
+    const double* src[6] = {x, y, z, dx, dy, dz};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int sms = num_sms_of(v->device);
+    for (int64_t off = 0; off < n; off += chunk) {
+        const int64_t m = std::min(chunk, n - off);
+        for (int k = 0; k < 6; ++k)
+            if ((e = cudaMemcpyAsync(f[k], src[k] + off, size_t(m) * sizeof(double), cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess)
+                return cuda_status(e);
+        const Basket b{f[0], f[1], f[2], f[3], f[4], f[5], m};
+        e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, f[6], whit, nullptr, s, sms)
+                               : launch_dist_refine(v->view, b, f[6], whit, nullptr, s, sms);
+        if (e != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemcpyAsync(step + off, f[6], size_t(m) * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(hit + off, whit, size_t(m) * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+            return cuda_status(e);
+    }
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const double* y, const double* z,
+                                      const double* dx, const double* dy, const double* dz, int64_t n, double* step,
+                                      int32_t* hit, int32_t* nref, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
+    if (n == 0) return GEO_OK;
+    if (!is_device_ptr(dx) || !is_device_ptr(dy) || !is_device_ptr(dz) || !is_device_ptr(step) ||
+        !is_device_ptr(hit) || !is_device_ptr(nref))
+        return GEO_ERR_INVALID_ARG;
+    const Basket b{x, y, z, dx, dy, dz, n};
+    return cuda_status(launch_dist_refine_stats(v->view, b, step, hit, nullptr, nref,
+                                                static_cast<cudaStream_t>(stream), num_sms_of(v->device)));
+}
+
+geo_status geo_check_device_status(geo_volume v, uint32_t* word, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned int h = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&h, v->status, sizeof h, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v->status, 0, sizeof h, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_status(e);
+    if (word) *word = h;
+    return h ? GEO_ERR_DEVICE_ASSERT : GEO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// geo_internal.h -- device table layout and launch interfaces shared by the
+// CUDA translation units of the navigator library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/geo.h"
+
+namespace geonav {
+
+constexpr int KBOX = 0, KTUBE = 1, KCONE = 2;
+
+// FP64 record of one placed solid, 256 B, read warp-uniformly (broadcast).
+//  R: row-major local->mother rotation, t: translation.
+//  p: raw parameters.  d: derived constants per kind:
+//   box : d[0..2] = half-lengths
+//   tube: d[0] rmin, d[1] rmax, d[2] dz, d[3] rmin^2, d[4] rmax^2
+//   cone: d[0] dz, d[1] a_out, d[2] b_out, d[3] a_in, d[4] b_in,
+//         d[5] rmin1^2, d[6] rmax1^2, d[7] rmin2^2, d[8] rmax2^2,
+//         d[9] 1/sqrt(1+b_out^2), d[10] 1/sqrt(1+b_in^2), d[11] has_inner (0/1)
+//   (radius lines R(z) = a + b z, R(-dz) = r1, R(+dz) = r2)
+//  brad: bounding-sphere radius about t, enlarged by a relative 1e-12 + 1e-9 mm
+//  so that the FP64 sphere cull is conservative.
+struct __align__(16) ShapeRec64 {
+    double R[9];
+    double t[3];
+    double p[5];
+    double d[13];
+    double brad;
+    int32_t kind;
+    int32_t flags;
+};
+static_assert(sizeof(ShapeRec64) == 256, "ShapeRec64 layout");
+
+// FP32 record of one placed solid for the conservative filter, 128 B.
+//  The shape is INFLATED by `delta` (mm) so that every FP32 rounding of the
+//  transform and of the shape arithmetic is covered (see nav_refine.cu):
+//   box : e[0..2] = h + delta
+//   tube: e[0] rmin_in^2 (shrunk hole, 0 if none), e[1] rmax_out^2, e[2] dz + delta,
+//         e[3] has_hole (0/1)
+//   cone: e[0] dz + delta, e[1] a_out', e[2] b_out, e[3] a_in', e[4] b_in,
+//         e[5] has_hole, e[6..9] inflated end radii squared (rmin1,rmax1,rmin2,rmax2)
+//  brad: inflated bounding radius.
+struct __align__(16) ShapeRec32 {
+    float R[9];
+    float t[3];
+    float e[16];
+    float brad;
+    float delta;
+    int32_t kind;
+    int32_t flags;
+};
+static_assert(sizeof(ShapeRec32) == 128, "ShapeRec32 layout");
+
+// Everything a kernel needs about one volume, passed by value.
+struct VolView {
+    ShapeRec64 m64;            // mother (identity placement)
+    ShapeRec32 m32;            // mother, FP32 (deflated for lower bounds of the exit)
+    ShapeRec32 m32u;           // mother, FP32 inflated (upper bound of the exit)
+    const ShapeRec64* d64;     // [nd] device
+    const ShapeRec32* d32;     // [nd] device
+    int32_t nd;
+    int32_t smem64;            // 1 if the FP64 table fits the shared-memory budget
+    int32_t smem_refine;       // 1 if the FP32 + FP64 tables fit it together
+    // voxel grid (uniform over the mother's bounding box)
+    int32_t voxelized;
+    int32_t grid[3];
+    double lo[3];
+    double cell[3];
+    double inv_cell[3];
+    const int32_t* vox_off;    // [ncells+1] CSR offsets
+    const int32_t* vox_ids;    // daughter ids
+    unsigned int* status;      // device error word (0 = ok)
+};
+
+struct Basket {
+    const double *x, *y, *z, *dx, *dy, *dz;
+    int64_t n;
+};
+
+// device error codes written to VolView::status
+constexpr unsigned ST_TMA_TIMEOUT = 1u;
+constexpr unsigned ST_BAD_INDEX = 2u;
+
+// launchers (host), each returns cudaGetLastError() of its launch
+cudaError_t launch_dist_fp64(const VolView& v, const Basket& b, double* step, int32_t* hit,
+                             double* bpoint, cudaStream_t s, int num_sms);
+cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, int32_t* hit,
+                               double* bpoint, cudaStream_t s, int num_sms);
+cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
+                                     double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
+cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s,
+                            int num_sms);
+cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
+                          int num_sms);
+
+}  // namespace geonav

@@ -1,0 +1,222 @@
+// shapes32.cuh -- FP32 bounding routines of the filter stage.
+//
+// The filter never decides an answer; it only produces, per (track, solid),
+// a number that is provably not larger than the FP64 distance (a LOWER bound
+// L), or for the mother an upper bound U of its exit distance.  The argument:
+//
+//  * The FP32 copy of every solid is inflated by delta (mm); see make_rec32()
+//    and inflation() in geo_abi.cu.  delta exceeds the worst-case distance
+//    between the FP32 ray (rounded inputs, rounded transform) and the exact
+//    ray over the whole mother, so wherever the exact ray is inside the true
+//    solid the FP32 ray is inside the inflated one.  Hence the entry of the
+//    FP32 ray into the inflated solid is <= the true entry.
+//  * delta also exceeds, in radius terms, the rounding of each quadric's
+//    discriminant (8 eps32 brad^2 / r in the frame shifted to the closest
+//    approach), so a ray that truly meets a quadric never sees a negative
+//    discriminant for its inflated copy, and the computed entering root of the
+//    inflated quadric is <= the true root.
+//  * Acceptance tests of candidate crossings (is the z-plane crossing inside
+//    the annulus, is the cylinder crossing inside the slab) are LENIENT by
+//    delta: extra candidates can only lower the minimum, so leniency is safe.
+//  * The result is finally lowered by 16 eps32 |t| + delta/|d|, which covers
+//    the relative rounding of the crossing parameters.
+// Upper bounds of the mother's exit use the inflated mother the same way;
+// lower bounds of the exit use the mother shrunk by delta.
+#pragma once
+#include <cmath>
+#include "geo_internal.h"
+
+namespace geonav {
+
+constexpr float kEps32f = 5.9604645e-08f;
+
+__device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
+
+// ---------------------------------------------------------------- box ------
+// inf{ t >= tmin : x + t u in box(h) }, lenient by tol at the start point.
+__device__ __forceinline__ float box_enter32(const float* h, const float* x, const float* u, float tmin,
+                                             float tol) {
+    float tn = tmin, tf = f_inf();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (u[k] == 0.f) {
+            if (fabsf(x[k]) > h[k] + tol) return f_inf();
+        } else {
+            const float inv = __frcp_rn(u[k]);
+            const float a = (-h[k] - x[k]) * inv, b = (h[k] - x[k]) * inv;
+            tn = fmaxf(tn, fminf(a, b));
+            tf = fminf(tf, fmaxf(a, b));
+        }
+    }
+    return tn <= tf ? tn : f_inf();
+}
+
+// exit of the box for a start point inside it (first t >= 0 leaving the slabs)
+__device__ __forceinline__ float box_exit32(const float* h, const float* x, const float* u) {
+    float tf = f_inf();
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (u[k] != 0.f) tf = fminf(tf, (copysignf(h[k], u[k]) - x[k]) * __frcp_rn(u[k]));
+    return fmaxf(tf, 0.f);
+}
+
+// ------------------------------------------------------------- quadrics -----
+// D with a tolerance: a discriminant within rounding of zero counts as a
+// tangent (D = 0), which only adds candidates.
+__device__ __forceinline__ bool disc32(float A, float B, float C, float& sq) {
+    float D = fmaf(B, B, -A * C);
+    if (D < 0.f) {
+        if (D > -16.f * kEps32f * (B * B + fabsf(A * C))) D = 0.f;
+        else return false;
+    }
+    sq = sqrtf(D);
+    return true;
+}
+
+// falling root (F decreases through 0): (-B - sq)/A in stable form
+__device__ __forceinline__ float root_falling32(float A, float B, float C) {
+    float sq;
+    if (!disc32(A, B, C, sq)) return f_inf();
+    if (B < 0.f) return C / (sq - B);
+    if (A < 0.f) return (-B - sq) / A;
+    return f_inf();
+}
+
+__device__ __forceinline__ float root_rising32(float A, float B, float C) {
+    float sq;
+    if (!disc32(A, B, C, sq)) return f_inf();
+    if (B > 0.f) return C / (-B - sq);
+    if (A > 0.f) return (sq - B) / A;
+    return f_inf();
+}
+
+// ---------------------------------------------------------------- tube -----
+// e: [0] rmin'^2 (0 if no hole), [1] rmax'^2, [2] dz', [3] hole flag
+__device__ __forceinline__ float tube_enter32(const float* e, const float* x, const float* u, float tmin,
+                                              float tol) {
+    const float dz = e[2];
+    const float zl = dz + tol;
+    const float ro = sqrtf(e[1]) + tol;
+    const float ri = e[3] != 0.f ? sqrtf(e[0]) - tol : 0.f;
+    const float ro2 = ro * ro;
+    const float ri2 = ri > 0.f ? ri * ri : 0.f;
+    // start point
+    const float sx = fmaf(tmin, u[0], x[0]), sy = fmaf(tmin, u[1], x[1]), sz = fmaf(tmin, u[2], x[2]);
+    const float sr2 = fmaf(sx, sx, sy * sy);
+    if (fabsf(sz) <= zl && sr2 <= ro2 && sr2 >= ri2) return tmin;
+    float best = f_inf();
+    if (fabsf(sz) > dz && sz * u[2] < 0.f) {
+        const float t = (copysignf(dz, sz) - x[2]) / u[2];
+        const float xh = fmaf(t, u[0], x[0]), yh = fmaf(t, u[1], x[1]);
+        const float r2 = fmaf(xh, xh, yh * yh);
+        if (r2 <= ro2 && r2 >= ri2) best = fmaxf(t, tmin);
+    }
+    const float A = fmaf(u[0], u[0], u[1] * u[1]);
+    const float B = fmaf(x[0], u[0], x[1] * u[1]);
+    const float rho2 = fmaf(x[0], x[0], x[1] * x[1]);
+    {
+        const float s = root_falling32(A, B, rho2 - e[1]);
+        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+    }
+    if (e[3] != 0.f) {
+        const float s = root_rising32(A, B, rho2 - e[0]);
+        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+    }
+    return best;
+}
+
+// ---------------------------------------------------------------- cone -----
+// e: [0] dz', [1] a_out', [2] b_out, [3] a_in', [4] b_in, [5] hole,
+//    [6] rmin1'^2 [7] rmax1'^2 [8] rmin2'^2 [9] rmax2'^2 (at z = -dz', +dz')
+__device__ __forceinline__ float cone_enter32(const float* e, const float* x, const float* u, float tmin,
+                                              float tol) {
+    const float dz = e[0];
+    const float zl = dz + tol;
+    const bool hole = e[5] != 0.f;
+    const float sx = fmaf(tmin, u[0], x[0]), sy = fmaf(tmin, u[1], x[1]), sz = fmaf(tmin, u[2], x[2]);
+    const float sr2 = fmaf(sx, sx, sy * sy);
+    {
+        const float ro = fmaf(e[2], sz, e[1]) + tol, ri = fmaf(e[4], sz, e[3]) - tol;
+        if (fabsf(sz) <= zl && sr2 <= ro * ro && (!hole || ri <= 0.f || sr2 >= ri * ri)) return tmin;
+    }
+    float best = f_inf();
+    if (fabsf(sz) > dz && sz * u[2] < 0.f) {
+        const float t = (copysignf(dz, sz) - x[2]) / u[2];
+        const float xh = fmaf(t, u[0], x[0]), yh = fmaf(t, u[1], x[1]);
+        const float r2 = fmaf(xh, xh, yh * yh);
+        const float lo2 = sz > 0.f ? e[8] : e[6];
+        const float hi = sqrtf(sz > 0.f ? e[9] : e[7]) + tol;
+        const float lo = hole ? fmaxf(sqrtf(lo2) - tol, 0.f) : 0.f;
+        if (r2 <= hi * hi && r2 >= lo * lo) best = fmaxf(t, tmin);
+    }
+    const float A0 = fmaf(u[0], u[0], u[1] * u[1]);
+    const float B0 = fmaf(x[0], u[0], x[1] * u[1]);
+    const float rho2 = fmaf(x[0], x[0], x[1] * x[1]);
+    {
+        const float r0 = fmaf(e[2], x[2], e[1]), rs = e[2] * u[2];
+        const float s = root_falling32(fmaf(-rs, rs, A0), fmaf(-r0, rs, B0), fmaf(-r0, r0, rho2));
+        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+    }
+    if (hole) {
+        const float r0 = fmaf(e[4], x[2], e[3]), rs = e[4] * u[2];
+        const float s = root_rising32(fmaf(-rs, rs, A0), fmaf(-r0, rs, B0), fmaf(-r0, r0, rho2));
+        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+    }
+    return best;
+}
+
+// Lower bound on the entering distance in the shifted frame: x is the track's
+// point of closest approach to the solid's origin, tmin = -s0 the parameter of
+// the real start point.  Returns the entering parameter relative to x.
+__device__ __forceinline__ float enter32(const ShapeRec32& r, const float* x, const float* u, float tmin) {
+    const float tol = r.delta;
+    if (r.kind == KBOX) return box_enter32(r.e, x, u, tmin, tol);
+    if (r.kind == KTUBE) return tube_enter32(r.e, x, u, tmin, tol);
+    return cone_enter32(r.e, x, u, tmin, tol);
+}
+
+// ------------------------------------------------------- mother exit -------
+// Exit distance of a start point x inside the (shrunk or grown) mother, in the
+// mother's own frame (no shift).  Also reports whether x is inside it.
+__device__ __forceinline__ float exit32(const ShapeRec32& r, const float* x, const float* u, bool& inside) {
+    const float* e = r.e;
+    if (r.kind == KBOX) {
+        inside = fabsf(x[0]) <= e[0] && fabsf(x[1]) <= e[1] && fabsf(x[2]) <= e[2];
+        return box_exit32(e, x, u);
+    }
+    const float rho2 = fmaf(x[0], x[0], x[1] * x[1]);
+    const float A0 = fmaf(u[0], u[0], u[1] * u[1]);
+    const float B0 = fmaf(x[0], u[0], x[1] * u[1]);
+    float t, s;
+    if (r.kind == KTUBE) {
+        inside = fabsf(x[2]) <= e[2] && rho2 <= e[1] && (e[3] == 0.f || rho2 >= e[0]);
+        t = u[2] != 0.f ? (copysignf(e[2], u[2]) - x[2]) / u[2] : f_inf();
+        s = root_rising32(A0, B0, rho2 - e[1]);
+        if (s >= 0.f) t = fminf(t, s);
+        if (e[3] != 0.f) {
+            s = root_falling32(A0, B0, rho2 - e[0]);
+            if (s >= 0.f) t = fminf(t, s);
+        }
+        return fmaxf(t, 0.f);
+    }
+    const float ro0 = fmaf(e[2], x[2], e[1]);
+    const float ri0 = fmaf(e[4], x[2], e[3]);
+    // inside test on the same rounded constants as the roots below, so that a
+    // point counted inside never sees a root behind it
+    const float co = fmaf(-ro0, ro0, rho2), ci = fmaf(-ri0, ri0, rho2);
+    inside = fabsf(x[2]) <= e[0] && co <= 0.f && (e[5] == 0.f || ci >= 0.f);
+    t = u[2] != 0.f ? (copysignf(e[0], u[2]) - x[2]) / u[2] : f_inf();
+    {
+        const float rs = e[2] * u[2];
+        s = root_rising32(fmaf(-rs, rs, A0), fmaf(-ro0, rs, B0), co);
+        if (s >= 0.f) t = fminf(t, s);
+    }
+    if (e[5] != 0.f) {
+        const float rs = e[4] * u[2];
+        s = root_falling32(fmaf(-rs, rs, A0), fmaf(-ri0, rs, B0), ci);
+        if (s >= 0.f) t = fminf(t, s);
+    }
+    return fmaxf(t, 0.f);
+}
+
+}  // namespace geonav

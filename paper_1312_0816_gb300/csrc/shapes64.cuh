@@ -1,0 +1,259 @@
+// shapes64.cuh -- FP64 device routines for the shape queries of Sec. 3.1
+// (distance to enter, distance to leave, inside check, safety) of Box, Tube
+// and Cone, plus the master->local transform of Sec. 3.1.
+//
+// Formulation: "candidate surfaces".  DistFromOutside of a closed solid is the
+// smallest s >= 0 at which the ray crosses INTO the solid through one of its
+// bounding surfaces (z-planes, outer and inner quadric), each crossing being
+// accepted only if the crossing point satisfies the remaining constraints;
+// DistFromInside is the first s >= 0 at which any constraint is violated.
+// Quadric roots are taken in cancellation-free form (the product of the roots
+// of A s^2 + 2 B s + C is C/A).
+//
+// Every FP64 operation is an explicitly rounded intrinsic, so the values do
+// not depend on how the compiler contracts expressions in the kernel that
+// inlines them: the plain FP64 kernel and the refine stage of the FP32-filter
+// kernel produce bit-identical results.
+#pragma once
+#include <cmath>
+#include "geo_internal.h"
+
+namespace geonav {
+
+__device__ __forceinline__ double d_inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+__device__ __forceinline__ double d_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+__device__ __forceinline__ double MUL(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ADD(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double SUB(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double FMA(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double DIV(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double SQRT(double a) { return __dsqrt_rn(a); }
+// a*b + c*d with one rounding for c*d and a fused final step
+__device__ __forceinline__ double DOT2(double a, double b, double c, double d) { return FMA(a, b, MUL(c, d)); }
+
+// x = R^T (p - t), u = R^T d
+__device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, double py, double pz,
+                                           double qx, double qy, double qz, double* x, double* u) {
+    const double w0 = SUB(px, r.t[0]), w1 = SUB(py, r.t[1]), w2 = SUB(pz, r.t[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        x[k] = FMA(r.R[6 + k], w2, FMA(r.R[3 + k], w1, MUL(r.R[k], w0)));
+        u[k] = FMA(r.R[6 + k], qz, FMA(r.R[3 + k], qy, MUL(r.R[k], qx)));
+    }
+}
+
+// F(s) = A s^2 + 2 B s + C.  Root where F falls through zero (F' = -2 sqrt(D)),
+// s = (-B - sqrt(D)) / A; +inf when there is none.  May be negative.
+__device__ __forceinline__ double root_falling(double A, double B, double C) {
+    const double D = FMA(B, B, -MUL(A, C));
+    if (!(D >= 0.0)) return d_inf();
+    const double sq = SQRT(D);
+    if (B < 0.0) return DIV(C, SUB(sq, B));
+    if (A < 0.0) return DIV(SUB(-B, sq), A);
+    return d_inf();
+}
+
+// Root where F rises through zero (F' = +2 sqrt(D)): s = (-B + sqrt(D)) / A.
+__device__ __forceinline__ double root_rising(double A, double B, double C) {
+    const double D = FMA(B, B, -MUL(A, C));
+    if (!(D >= 0.0)) return d_inf();
+    const double sq = SQRT(D);
+    if (B > 0.0) return DIV(C, SUB(-B, sq));
+    if (A > 0.0) return DIV(SUB(sq, B), A);
+    return d_inf();
+}
+
+__device__ __forceinline__ double rho2_of(const double* x) { return DOT2(x[0], x[0], x[1], x[1]); }
+
+// ------------------------------------------------------------- contains ---
+__device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x) {
+    const double* d = r.d;
+    if (r.kind == KBOX) return fabs(x[0]) <= d[0] && fabs(x[1]) <= d[1] && fabs(x[2]) <= d[2];
+    const double rho2 = rho2_of(x);
+    if (r.kind == KTUBE) return fabs(x[2]) <= d[2] && rho2 <= d[4] && rho2 >= d[3];
+    if (!(fabs(x[2]) <= d[0])) return false;
+    const double ro = FMA(d[2], x[2], d[1]);
+    const double ri = FMA(d[4], x[2], d[3]);
+    return rho2 <= MUL(ro, ro) && (d[11] == 0.0 || rho2 >= MUL(ri, ri));
+}
+
+// ------------------------------------------------------ DistFromOutside ---
+__device__ __forceinline__ double box_out64(const double* h, const double* x, const double* u) {
+    if (fabs(x[0]) <= h[0] && fabs(x[1]) <= h[1] && fabs(x[2]) <= h[2]) return 0.0;
+    double tn = -d_inf(), tf = d_inf();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (u[k] == 0.0) {
+            if (fabs(x[k]) > h[k]) return d_inf();
+        } else {
+            const double a = DIV(SUB(-h[k], x[k]), u[k]);
+            const double b = DIV(SUB(h[k], x[k]), u[k]);
+            tn = fmax(tn, fmin(a, b));
+            tf = fmin(tf, fmax(a, b));
+        }
+    }
+    return (tn <= tf && tf >= 0.0) ? fmax(tn, 0.0) : d_inf();
+}
+
+// crossing of the z-plane the track approaches from outside |z| <= dz
+__device__ __forceinline__ double zplane_t(const double* x, const double* u, double dz) {
+    return DIV(SUB(copysign(dz, x[2]), x[2]), u[2]);
+}
+
+__device__ __forceinline__ double tube_out64(const double* d, const double* x, const double* u) {
+    const double rmin = d[0], dz = d[2], rmin2 = d[3], rmax2 = d[4];
+    const double rho2 = rho2_of(x);
+    if (fabs(x[2]) <= dz && rho2 <= rmax2 && rho2 >= rmin2) return 0.0;
+    double best = d_inf();
+    if (fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0) {
+        const double t = zplane_t(x, u, dz);
+        const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
+        const double r2 = DOT2(xh, xh, yh, yh);
+        if (r2 <= rmax2 && r2 >= rmin2) best = t;
+    }
+    const double A = DOT2(u[0], u[0], u[1], u[1]);
+    const double B = DOT2(x[0], u[0], x[1], u[1]);
+    {   // outer cylinder, crossed inwards
+        const double s = root_falling(A, B, SUB(rho2, rmax2));
+        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+    }
+    if (rmin > 0.0) {   // inner cylinder, crossed outwards (out of the hole)
+        const double s = root_rising(A, B, SUB(rho2, rmin2));
+        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+    }
+    return best;
+}
+
+__device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u) {
+    const double dz = d[0];
+    const double rho2 = rho2_of(x);
+    const double ro0 = FMA(d[2], x[2], d[1]);
+    const double ri0 = FMA(d[4], x[2], d[3]);
+    const bool hole = d[11] != 0.0;
+    if (fabs(x[2]) <= dz && rho2 <= MUL(ro0, ro0) && (!hole || rho2 >= MUL(ri0, ri0))) return 0.0;
+    double best = d_inf();
+    if (fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0) {
+        const double t = zplane_t(x, u, dz);
+        const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
+        const double r2 = DOT2(xh, xh, yh, yh);
+        const double lo2 = x[2] > 0.0 ? d[7] : d[5];
+        const double hi2 = x[2] > 0.0 ? d[8] : d[6];
+        if (r2 <= hi2 && r2 >= lo2) best = t;
+    }
+    const double A0 = DOT2(u[0], u[0], u[1], u[1]);
+    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    {   // outer cone rho^2 - (a + b z)^2, crossed inwards
+        const double rs = MUL(d[2], u[2]);
+        const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
+        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+    }
+    if (hole) {   // inner cone, crossed outwards
+        const double rs = MUL(d[4], u[2]);
+        const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
+        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+    }
+    return best;
+}
+
+__device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* x, const double* u) {
+    if (r.kind == KBOX) return box_out64(r.d, x, u);
+    if (r.kind == KTUBE) return tube_out64(r.d, x, u);
+    return cone_out64(r.d, x, u);
+}
+
+// ------------------------------------------------------- DistFromInside ---
+// First s >= 0 at which the track violates a constraint (x assumed inside).
+__device__ __forceinline__ double slab_exit(double xk, double uk, double h) {
+    return uk == 0.0 ? d_inf() : DIV(SUB(copysign(h, uk), xk), uk);
+}
+
+__device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u) {
+    const double* d = r.d;
+    double t;
+    if (r.kind == KBOX) {
+        t = fmin(slab_exit(x[0], u[0], d[0]), fmin(slab_exit(x[1], u[1], d[1]), slab_exit(x[2], u[2], d[2])));
+        return fmax(t, 0.0);
+    }
+    const double rho2 = rho2_of(x);
+    const double A0 = DOT2(u[0], u[0], u[1], u[1]);
+    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    double s;
+    if (r.kind == KTUBE) {
+        t = slab_exit(x[2], u[2], d[2]);
+        s = root_rising(A0, B0, SUB(rho2, d[4]));
+        if (s >= 0.0) t = fmin(t, s);
+        if (d[0] > 0.0) {
+            s = root_falling(A0, B0, SUB(rho2, d[3]));
+            if (s >= 0.0) t = fmin(t, s);
+        }
+        return fmax(t, 0.0);
+    }
+    t = slab_exit(x[2], u[2], d[0]);
+    {
+        const double ro0 = FMA(d[2], x[2], d[1]), rs = MUL(d[2], u[2]);
+        s = root_rising(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
+        if (s >= 0.0) t = fmin(t, s);
+    }
+    if (d[11] != 0.0) {
+        const double ri0 = FMA(d[4], x[2], d[3]), rs = MUL(d[4], u[2]);
+        s = root_falling(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
+        if (s >= 0.0) t = fmin(t, s);
+    }
+    return fmax(t, 0.0);
+}
+
+// --------------------------------------------------------------- safety ---
+// 2-D distance from (px, pz) to the segment a-b in the meridian half-plane.
+__device__ __forceinline__ double seg2(double px, double pz, double ax, double az, double bx, double bz) {
+    const double ex = SUB(bx, ax), ez = SUB(bz, az);
+    const double l2 = DOT2(ex, ex, ez, ez);
+    double f = l2 > 0.0 ? DIV(DOT2(SUB(px, ax), ex, SUB(pz, az), ez), l2) : 0.0;
+    f = fmin(fmax(f, 0.0), 1.0);
+    const double cx = SUB(FMA(f, ex, ax), px), cz = SUB(FMA(f, ez, az), pz);
+    return SQRT(DOT2(cx, cx, cz, cz));
+}
+
+// Distance to the boundary from a point inside (inside == true) or outside.
+// Returns 0 if the point is on the other side.
+__device__ __forceinline__ double safety64(const ShapeRec64& r, const double* x, bool inside) {
+    const bool in = contains64(r, x);
+    if (in != inside) return 0.0;
+    const double* d = r.d;
+    if (r.kind == KBOX) {
+        const double a = SUB(fabs(x[0]), d[0]), b = SUB(fabs(x[1]), d[1]), c = SUB(fabs(x[2]), d[2]);
+        if (in) return -fmax(a, fmax(b, c));
+        const double a0 = fmax(a, 0.0), b0 = fmax(b, 0.0), c0 = fmax(c, 0.0);
+        return SQRT(FMA(a0, a0, DOT2(b0, b0, c0, c0)));
+    }
+    const double rho = SQRT(rho2_of(x));
+    const double az = fabs(x[2]);
+    if (r.kind == KTUBE) {
+        if (in) {
+            double s = fmin(SUB(d[1], rho), SUB(d[2], az));
+            if (d[0] > 0.0) s = fmin(s, SUB(rho, d[0]));
+            return s;
+        }
+        const double dzo = fmax(SUB(az, d[2]), 0.0);
+        const double dro = fmax(fmax(SUB(d[0], rho), SUB(rho, d[1])), 0.0);
+        return SQRT(DOT2(dzo, dzo, dro, dro));
+    }
+    // cone: trapezoid (rmin1,-dz) (rmax1,-dz) (rmax2,dz) (rmin2,dz)
+    const double dz = d[0], z = x[2];
+    if (in) {
+        // inside a convex polygon the nearest boundary point lies on the
+        // nearest supporting line of an edge
+        double s = SUB(dz, az);
+        s = fmin(s, MUL(SUB(FMA(d[2], z, d[1]), rho), d[9]));
+        if (d[11] != 0.0) s = fmin(s, MUL(SUB(rho, FMA(d[4], z, d[3])), d[10]));
+        return s;
+    }
+    const double r1i = r.p[1], r1o = r.p[2], r2i = r.p[3], r2o = r.p[4];
+    double s = seg2(rho, z, r1i, -dz, r1o, -dz);
+    s = fmin(s, seg2(rho, z, r1o, -dz, r2o, dz));
+    s = fmin(s, seg2(rho, z, r2o, dz, r2i, dz));
+    s = fmin(s, seg2(rho, z, r2i, dz, r1i, -dz));
+    return s;
+}
+
+}  // namespace geonav

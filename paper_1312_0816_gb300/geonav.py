@@ -1,0 +1,282 @@
+"""Thin Python binding of the C ABI in include/geo.h (libgeonav.so).
+
+Each function carries the C name and only marshals arguments: torch CUDA
+tensors become device pointers, the current torch stream becomes the
+cudaStream_t.  All navigation work runs in the library's CUDA kernels; there
+is no CPU path.  If the library cannot be loaded the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build_lib
+
+GEO_OK = 0
+GEO_FP64 = 0
+GEO_FP32_REFINE = 1
+GEO_BOX, GEO_TUBE, GEO_CONE = 0, 1, 2
+
+_STATUS = {0: "GEO_OK", 1: "GEO_ERR_INVALID_ARG", 2: "GEO_ERR_SHAPE_PARAMS", 3: "GEO_ERR_OOM",
+           4: "GEO_ERR_CUDA", 5: "GEO_ERR_DEVICE_ASSERT", 6: "GEO_ERR_UNSUPPORTED"}
+
+
+class GeoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_STATUS.get(status, status)} ({geo_status_string(status)})")
+
+
+class geo_placed_shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("p", ctypes.c_double * 5),
+                ("rot", ctypes.c_double * 9), ("trans", ctypes.c_double * 3)]
+
+
+class geo_build_opts(ctypes.Structure):
+    _fields_ = [("voxelize", ctypes.c_int32), ("grid", ctypes.c_int32 * 3)]
+
+
+_lib = None
+EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dist_to_boundary",
+           "geo_contains", "geo_safety", "geo_dist_to_boundary_host", "geo_dist_to_boundary_stats",
+           "geo_check_device_status", "geo_probe_pipe", "geo_status_string")
+
+
+def library_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Loads libgeonav.so (compiling it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_stale and not build_lib.up_to_date():
+        build_lib.build()
+    if not os.path.exists(build_lib.LIB):
+        raise RuntimeError(f"libgeonav.so not found at {build_lib.LIB}; run __graft_entry__.build()")
+    L = ctypes.CDLL(build_lib.LIB)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    L.geo_build_volume.argtypes = [ctypes.POINTER(geo_placed_shape), ctypes.POINTER(geo_placed_shape), i32,
+                                   ctypes.POINTER(geo_build_opts), vp, ctypes.POINTER(vp)]
+    L.geo_destroy_volume.argtypes = [vp]
+    L.geo_volume_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32 * 3)]
+    L.geo_dist_to_boundary.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, dp, i32, vp]
+    L.geo_contains.argtypes = [vp, dp, dp, dp, i64, ip, vp]
+    L.geo_safety.argtypes = [vp, dp, dp, dp, i64, dp, i32, vp]
+    L.geo_dist_to_boundary_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, i32, i64, vp]
+    L.geo_dist_to_boundary_stats.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, ip, vp]
+    L.geo_check_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
+    L.geo_probe_pipe.argtypes = [i32, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    L.geo_status_string.argtypes = [ctypes.c_int]
+    L.geo_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "geo_status_string":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def geo_status_string(status: int) -> str:
+    return load().geo_status_string(int(status)).decode()
+
+
+def _check(st: int, what: str):
+    if st != GEO_OK:
+        raise GeoError(st, what)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _shape_struct(kind, params, rot=None, trans=None) -> geo_placed_shape:
+    s = geo_placed_shape()
+    s.kind = int(kind)
+    s.reserved = 0
+    p = np.zeros(5)
+    p[: len(params)] = params
+    s.p[:] = [float(v) for v in p]
+    s.rot[:] = [float(v) for v in (np.eye(3).reshape(9) if rot is None else np.asarray(rot).reshape(9))]
+    s.trans[:] = [float(v) for v in (np.zeros(3) if trans is None else np.asarray(trans).reshape(3))]
+    return s
+
+
+class Volume:
+    """Owns one geo_volume handle (device tables of a mother and its daughters)."""
+
+    def __init__(self, handle, n_daughters: int):
+        self.handle = handle
+        self.n_daughters = n_daughters
+
+    def close(self):
+        if self.handle:
+            load().geo_destroy_volume(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def geo_build_volume(scene, voxelize: bool = False, grid=(0, 0, 0), stream=None) -> Volume:
+    """Builds the device tables of `scene` (an object with mother_kind,
+    mother_params, kinds, params, rot, trans -- see scenes.Scene)."""
+    L = load()
+    mother = _shape_struct(scene.mother_kind, scene.mother_params)
+    nd = int(scene.n_daughters)
+    arr = (geo_placed_shape * max(nd, 1))()
+    for j in range(nd):
+        arr[j] = _shape_struct(scene.kinds[j], scene.params[j], scene.rot[j], scene.trans[j])
+    opts = geo_build_opts()
+    opts.voxelize = 1 if voxelize else 0
+    opts.grid[:] = [int(g) for g in grid]
+    out = ctypes.c_void_p()
+    _check(L.geo_build_volume(ctypes.byref(mother), arr, nd, ctypes.byref(opts), _stream(stream),
+                              ctypes.byref(out)), "geo_build_volume")
+    return Volume(out, nd)
+
+
+def geo_destroy_volume(vol: Volume):
+    vol.close()
+
+
+def geo_volume_info(vol: Volume):
+    nd, vx = ctypes.c_int32(), ctypes.c_int32()
+    g = (ctypes.c_int32 * 3)()
+    _check(load().geo_volume_info(vol.handle, ctypes.byref(nd), ctypes.byref(vx), ctypes.byref(g)),
+           "geo_volume_info")
+    return {"n_daughters": nd.value, "voxelized": bool(vx.value), "grid": tuple(g)}
+
+
+def _dev(t, dtype, n, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name}: expected contiguous {dtype} with {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def geo_dist_to_boundary(vol: Volume, x, y, z, dx, dy, dz, mode: int = GEO_FP32_REFINE, step=None, hit=None,
+                         bpoint=None, want_bpoint: bool = False, stream=None):
+    """Fig. 1 navigator step for a basket of CUDA float64 tensors.  Returns
+    (step, hit) or (step, hit, bpoint[3, n])."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    if step is None:
+        step = torch.empty(n, dtype=f64, device=x.device)
+    if hit is None:
+        hit = torch.empty(n, dtype=torch.int32, device=x.device)
+    if want_bpoint and bpoint is None:
+        bpoint = torch.empty((3, n), dtype=f64, device=x.device)
+    args = [_dev(a, f64, n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    bp = _dev(bpoint, f64, 3 * n, "bpoint") if bpoint is not None else ctypes.c_void_p(0)
+    _check(load().geo_dist_to_boundary(vol.handle, *args, n, _dev(step, f64, n, "step"),
+                                       _dev(hit, torch.int32, n, "hit"), bp, int(mode), _stream(stream)),
+           "geo_dist_to_boundary")
+    return (step, hit, bpoint) if bpoint is not None else (step, hit)
+
+
+def geo_contains(vol: Volume, x, y, z, where=None, stream=None):
+    import torch
+
+    n = int(x.numel())
+    if where is None:
+        where = torch.empty(n, dtype=torch.int32, device=x.device)
+    f64 = torch.float64
+    _check(load().geo_contains(vol.handle, _dev(x, f64, n, "x"), _dev(y, f64, n, "y"), _dev(z, f64, n, "z"), n,
+                               _dev(where, torch.int32, n, "where"), _stream(stream)), "geo_contains")
+    return where
+
+
+def geo_safety(vol: Volume, x, y, z, mode: int = GEO_FP64, safety=None, stream=None):
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    if safety is None:
+        safety = torch.empty(n, dtype=f64, device=x.device)
+    _check(load().geo_safety(vol.handle, _dev(x, f64, n, "x"), _dev(y, f64, n, "y"), _dev(z, f64, n, "z"), n,
+                             _dev(safety, f64, n, "safety"), int(mode), _stream(stream)), "geo_safety")
+    return safety
+
+
+def geo_dist_to_boundary_host(vol: Volume, x, y, z, dx, dy, dz, mode: int = GEO_FP32_REFINE, step=None, hit=None,
+                              chunk: int = 0, stream=None):
+    """Host-memory variant: numpy float64 arrays (or pinned CPU tensors) in,
+    numpy/pinned outputs filled; synchronises the stream."""
+    n = int(len(x))
+
+    def ptr(a):
+        if hasattr(a, "data_ptr"):
+            return ctypes.c_void_p(a.data_ptr())
+        if a.dtype not in (np.float64, np.int32) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous float64 / int32")
+        return ctypes.c_void_p(a.ctypes.data)
+
+    if step is None:
+        step = np.empty(n)
+    if hit is None:
+        hit = np.empty(n, dtype=np.int32)
+    _check(load().geo_dist_to_boundary_host(vol.handle, *(ptr(a) for a in (x, y, z, dx, dy, dz)), n, ptr(step),
+                                            ptr(hit), int(mode), int(chunk), _stream(stream)),
+           "geo_dist_to_boundary_host")
+    return step, hit
+
+
+def geo_dist_to_boundary_stats(vol: Volume, x, y, z, dx, dy, dz, stream=None):
+    """FP32+refine step that also returns the per-track count of FP64 solid
+    evaluations.  Returns (step, hit, nref)."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    step = torch.empty(n, dtype=f64, device=x.device)
+    hit = torch.empty(n, dtype=torch.int32, device=x.device)
+    nref = torch.empty(n, dtype=torch.int32, device=x.device)
+    args = [_dev(a, f64, n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    _check(load().geo_dist_to_boundary_stats(vol.handle, *args, n, _dev(step, f64, n, "step"),
+                                             _dev(hit, torch.int32, n, "hit"), _dev(nref, torch.int32, n, "nref"),
+                                             _stream(stream)), "geo_dist_to_boundary_stats")
+    return step, hit, nref
+
+
+def geo_check_device_status(vol: Volume, stream=None) -> int:
+    """Reads and clears the volume's device error word; raises GeoError if set."""
+    w = ctypes.c_uint32()
+    st = load().geo_check_device_status(vol.handle, ctypes.byref(w), _stream(stream))
+    if st not in (GEO_OK, 5):
+        _check(st, "geo_check_device_status")
+    if st == 5:
+        raise GeoError(st, f"device status word 0x{w.value:x}")
+    return w.value
+
+
+def geo_probe_pipe(what: int, iters: int = 1 << 16, blocks: int = 0, stream=None) -> float:
+    """Operations per second of one arithmetic operation (see geo.h)."""
+    import torch
+
+    if blocks <= 0:
+        blocks = torch.cuda.get_device_properties(0).multi_processor_count * 8
+    scratch = torch.empty(256, dtype=torch.float64, device="cuda")
+    r = ctypes.c_double()
+    _check(load().geo_probe_pipe(int(what), int(iters), int(blocks), ctypes.c_void_p(scratch.data_ptr()),
+                                 _stream(stream), ctypes.byref(r)), "geo_probe_pipe")
+    return r.value

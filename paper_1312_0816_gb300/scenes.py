@@ -376,90 +376,93 @@ def batched_tracks(vols, baskets, seed: int):
 # adversarial rays: grazing, edge and corner hits on a chosen daughter
 # --------------------------------------------------------------------------
 
-def _place(scene: Scene, j: int, q):
-    r = scene.rot[j].reshape(3, 3)
-    return r @ np.asarray(q) + scene.trans[j]
-
-
-def _dir_world(scene: Scene, j: int, v):
-    return scene.rot[j].reshape(3, 3) @ np.asarray(v)
-
-
-def _inside_mother_construct(scene: Scene, p) -> bool:
-    mp = scene.mother_params
-    if scene.mother_kind == BOX:
-        return bool(np.all(np.abs(p) < mp[:3] * 0.999))
-    return bool(p[0] ** 2 + p[1] ** 2 < (0.999 * mp[1]) ** 2 and abs(p[2]) < 0.999 * mp[2])
-
-
 def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) -> Tracks:
     """Rays aimed at feature points of randomly chosen daughters: tangent to
-    cylinders and cones, at box edges and corners, along faces.  The target is a
-    constructed point on the feature (plus a relative jitter of about `jitter`
-    mm), the start is backed off along the ray by a random distance and kept
-    only if it lies well inside the mother and outside every keep-out envelope."""
+    cylinders and cones, at box edges and corners, nearly parallel to faces.
+    The target is a constructed point on the feature (with a relative jitter
+    of about `jitter`), the start is backed off along the ray by 1..200 mm and
+    kept only if it lies well inside the mother and outside every keep-out
+    envelope."""
     rng = np.random.default_rng(seed)
-    xs = []
-    tries = 0
-    while len(xs) < n and tries < 50 * n:
-        tries += 1
-        j = int(rng.integers(0, scene.n_daughters))
-        k = scene.kinds[j]
-        p = scene.params[j]
-        mode = int(rng.integers(0, 3))
-        if k == BOX:
-            h = p[:3]
-            s = rng.choice([-1.0, 1.0], size=3)
-            q = s * h
-            if mode == 1:   # edge: free one coordinate
-                a = int(rng.integers(0, 3))
-                q[a] = rng.uniform(-h[a], h[a])
-            elif mode == 2:  # face: free two coordinates
-                a = int(rng.integers(0, 3))
-                for b in range(3):
-                    if b != a:
-                        q[b] = rng.uniform(-h[b], h[b])
-            v = np.array(isotropic(rng, 1)).reshape(3)
-            if mode == 2:  # nearly parallel to the face
-                a_ax = [b for b in range(3) if abs(q[b]) == h[b]]
-                for b in a_ax:
-                    v[b] *= 1e-6
+    out_p, out_v = [], []
+    have = 0
+    rounds = 0
+    while have < n and rounds < 200:
+        rounds += 1
+        m = max(4096, 2 * (n - have))
+        j = rng.integers(0, scene.n_daughters, size=m)
+        kind = scene.kinds[j]
+        prm = scene.params[j]
+        mode = rng.integers(0, 3, size=m)
+        q = np.zeros((m, 3))
+        v = np.stack(isotropic(rng, m), axis=1)
+        # boxes: corner (mode 0), edge (1), face with a nearly parallel ray (2)
+        b = kind == BOX
+        if b.any():
+            h = prm[b, :3]
+            sg = rng.choice([-1.0, 1.0], size=h.shape)
+            qb = sg * h
+            mb = mode[b]
+            free = rng.integers(0, 3, size=qb.shape[0])
+            u = rng.uniform(-1.0, 1.0, size=qb.shape)
+            rows = np.arange(qb.shape[0])
+            e = mb == 1
+            qb[rows[e], free[e]] = (u * h)[rows[e], free[e]]
+            f = mb == 2
+            for ax in range(3):
+                sel = f & (free != ax)
+                qb[sel, ax] = (u * h)[sel, ax]
+            vb = v[b]
+            vb[rows[f], free[f]] *= 1e-6
+            q[b] = qb
+            v[b] = vb
+        # tubes and cones: tangent lines (mode 0) or rim points (1, 2)
+        c = ~b
+        if c.any():
+            pc = prm[c]
+            kc = kind[c]
+            mc = mode[c]
+            hz = np.where(kc == TUBE, pc[:, 2], pc[:, 0])
+            zc = np.where(mc == 2, rng.choice([-1.0, 1.0], size=hz.shape) * hz, rng.uniform(-1, 1, size=hz.shape) * hz)
+            use_outer = rng.uniform(size=hz.shape) < 0.6
+            tube_r = np.where(use_outer | (pc[:, 0] == 0.0), pc[:, 1], pc[:, 0])
+            outer_c = use_outer | ((pc[:, 1] + pc[:, 3]) == 0.0)
+            r1 = np.where(outer_c, pc[:, 2], pc[:, 1])
+            r2 = np.where(outer_c, pc[:, 4], pc[:, 3])
+            cone_r = r1 + (r2 - r1) * (zc + hz) / (2.0 * hz)
+            slope = np.where(kc == CONE, (r2 - r1) / (2.0 * hz), 0.0)
+            r = np.where(kc == TUBE, tube_r, cone_r)
+            ph = rng.uniform(0.0, 2.0 * math.pi, size=hz.shape)
+            radial = np.stack([np.cos(ph), np.sin(ph), np.zeros_like(ph)], 1)
+            tang = np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)], 1)
+            qc = radial * r[:, None]
+            qc[:, 2] = zc
+            gen = np.stack([slope * radial[:, 0], slope * radial[:, 1], np.ones_like(ph)], 1)
+            gen /= np.linalg.norm(gen, axis=1, keepdims=True)
+            a = rng.uniform(-1.0, 1.0, size=hz.shape)
+            vt = tang * np.sqrt(np.maximum(0.0, 1.0 - a * a))[:, None] + gen * a[:, None]
+            vc = np.where((mc == 0)[:, None], vt, v[c])
+            q[c] = qc
+            v[c] = vc
+        q = q * (1.0 + jitter * rng.uniform(-1.0, 1.0, size=q.shape))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        R = scene.rot[j].reshape(m, 3, 3)
+        qw = np.einsum("nij,nj->ni", R, q) + scene.trans[j]
+        vw = np.einsum("nij,nj->ni", R, v)
+        back = rng.uniform(1.0, 200.0, size=m)
+        start = qw - back[:, None] * vw
+        mp = scene.mother_params
+        if scene.mother_kind == BOX:
+            inside = np.all(np.abs(start) < 0.999 * mp[:3], axis=1)
         else:
-            if k == TUBE:
-                rmin, rmax, hz = p[0], p[1], p[2]
-                zc = rng.uniform(-hz, hz) if mode != 2 else rng.choice([-hz, hz])
-                r = rmax if (rmin == 0.0 or rng.uniform() < 0.6) else rmin
-                slope = 0.0
-            else:
-                hz = p[0]
-                zc = rng.uniform(-hz, hz) if mode != 2 else rng.choice([-hz, hz])
-                outer = p[1] + p[3] == 0.0 or rng.uniform() < 0.6
-                r1, r2 = (p[2], p[4]) if outer else (p[1], p[3])
-                r = r1 + (r2 - r1) * (zc + hz) / (2.0 * hz)
-                slope = (r2 - r1) / (2.0 * hz)
-            ph = rng.uniform(0.0, 2.0 * math.pi)
-            radial = np.array([math.cos(ph), math.sin(ph), 0.0])
-            tang = np.array([-math.sin(ph), math.cos(ph), 0.0])
-            q = radial * r + np.array([0.0, 0.0, zc])
-            if mode == 0:   # tangent line to the surface at q (along the tangent plane)
-                gen = np.array([slope * radial[0], slope * radial[1], 1.0])
-                gen /= np.linalg.norm(gen)
-                a = rng.uniform(-1.0, 1.0)
-                v = tang * math.sqrt(max(0.0, 1.0 - a * a)) + gen * a
-            else:           # rim: any direction through the edge point
-                v = np.array(isotropic(rng, 1)).reshape(3)
-        q = np.asarray(q, dtype=np.float64) * (1.0 + jitter * rng.uniform(-1.0, 1.0, size=3))
-        v = v / np.linalg.norm(v)
-        qw = _place(scene, j, q)
-        vw = _dir_world(scene, j, v)
-        back = rng.uniform(1.0, 200.0)
-        start = qw - back * vw
-        if not _inside_mother_construct(scene, start):
-            continue
-        if keepout_mask(scene, start[0:1], start[1:2], start[2:3])[0]:
-            continue
-        xs.append((start, vw))
-    if len(xs) < n:
+            inside = (start[:, 0] ** 2 + start[:, 1] ** 2 < (0.999 * mp[1]) ** 2) & \
+                     (np.abs(start[:, 2]) < 0.999 * mp[2])
+        ok = inside & ~keepout_mask(scene, start[:, 0], start[:, 1], start[:, 2])
+        out_p.append(start[ok])
+        out_v.append(vw[ok])
+        have += int(ok.sum())
+    if have < n:
         raise RuntimeError("adversarial sampler could not place enough rays")
-    arr = np.array([np.concatenate(a) for a in xs])
-    return Tracks(*(arr[:, c].copy() for c in range(6)))
+    P = np.concatenate(out_p)[:n]
+    V = np.concatenate(out_v)[:n]
+    return Tracks(P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy(), V[:, 0].copy(), V[:, 1].copy(), V[:, 2].copy())

@@ -1,0 +1,91 @@
+"""CPU-only checks of the C ABI: the library builds, loads, exports every
+function include/geo.h declares, and rejects invalid arguments on the host
+before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1312_0816_gb300 import geonav
+from paper_1312_0816_gb300.geonav import geo_placed_shape
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "geo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(geo_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = geonav.load()
+    names = declared()
+    assert "geo_dist_to_boundary" in names and "geo_build_volume" in names
+    for name in names:
+        assert hasattr(L, name), name
+    # and the binding wraps each of them under the same name
+    for name in names:
+        assert hasattr(geonav, name), name
+
+
+def test_status_strings():
+    for s in range(7):
+        assert geonav.geo_status_string(s)
+    assert geonav.geo_status_string(99) == "unknown status"
+
+
+def _shape(kind, p, rot=None, trans=None):
+    return geonav._shape_struct(kind, p, rot, trans)
+
+
+def _build(mother, daughters):
+    L = geonav.load()
+    arr = (geo_placed_shape * max(1, len(daughters)))(*daughters)
+    out = ctypes.c_void_p(123)
+    st = L.geo_build_volume(ctypes.byref(mother), arr, len(daughters), None, None, ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("mother,daughter,status", [
+    ((0, (100, 100, 100)), (3, (1, 1, 1)), 1),                      # unknown kind
+    ((0, (100, 100, 100)), (1, (20, 10, 5)), 2),                    # rmin > rmax
+    ((0, (100, 100, 100)), (1, (0, 10, 0)), 2),                     # dz = 0
+    ((0, (100, 100, 100)), (2, (5, 3, 2, 0, 4)), 2),                # cone rmin1 > rmax1
+    ((0, (100, 100, 100)), (2, (5, 0, 0, 0, 0)), 2),                # cone without radius
+    ((0, (100, 100, 100)), (0, (1, float("nan"), 1)), 2),           # NaN parameter
+    ((0, (100, -1, 100)), (0, (1, 1, 1)), 2),                       # bad mother
+])
+def test_build_rejects_bad_shapes(mother, daughter, status):
+    st, out = _build(_shape(*mother), [_shape(*daughter)])
+    assert st == status
+    assert out.value is None
+
+
+def test_build_rejects_non_orthonormal_rotation():
+    rot = np.eye(3)
+    rot[0, 1] = 1e-9
+    st, out = _build(_shape(0, (100, 100, 100)), [_shape(0, (1, 1, 1), rot)])
+    assert st == 2
+    refl = np.diag([1.0, 1.0, -1.0])   # orthonormal but det = -1
+    st, _ = _build(_shape(0, (100, 100, 100)), [_shape(0, (1, 1, 1), refl)])
+    assert st == 2
+
+
+def test_build_rejects_placed_mother():
+    st, _ = _build(_shape(0, (100, 100, 100), None, (1.0, 0, 0)), [])
+    assert st == 1
+
+
+def test_null_arguments():
+    L = geonav.load()
+    assert L.geo_build_volume(None, None, 0, None, None, None) == 1
+    m = _shape(0, (1, 1, 1))
+    out = ctypes.c_void_p()
+    assert L.geo_build_volume(ctypes.byref(m), None, 3, None, None, ctypes.byref(out)) == 1
+    assert L.geo_dist_to_boundary(None, None, None, None, None, None, None, 0, None, None, None, 0, None) == 1
+    assert L.geo_contains(None, None, None, None, 0, None, None) == 1
+    assert L.geo_safety(None, None, None, None, 0, None, 0, None) == 1
+    assert L.geo_destroy_volume(None) == 0

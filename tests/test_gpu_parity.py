@@ -1,0 +1,242 @@
+"""Parity of the CUDA navigator (through the C ABI) with the CPU oracle.
+
+Bar (stated per test): steps within 1e-9 mm of the oracle and hit index
+bit-exact, except on tracks in the tie band (second-smallest oracle candidate
+within 1e-9 mm of the winner) or the conditioning band (the oracle's a-priori
+FP64 error bound E exceeds 1e-9 mm, i.e. near-tangent roots); those are
+counted and must be rare.  The FP32+refine mode must equal the plain FP64
+mode bit for bit on every track.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import golden, expr, scene_from_spec, tracks_from, tie_band
+from paper_1312_0816_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1312_0816_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.load()
+    return pkg
+
+
+_vols = {}
+
+
+def vol(g, sc):
+    key = (sc.name, id(sc))
+    if key not in _vols:
+        _vols[key] = (sc, g.geo_build_volume(sc))
+    return _vols[key][1]
+
+
+def dev(tr):
+    return [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in tr.fields()]
+
+
+def run_nav(g, sc, tr, mode, bpoint=False):
+    out = g.geo_dist_to_boundary(vol(g, sc), *dev(tr), mode=mode, want_bpoint=bpoint)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in out]
+
+
+def compare(ref, step, hit, max_exempt=1e-3):
+    """Returns the number of exempt tracks after asserting the bar on the rest."""
+    assert np.array_equal(np.isnan(step), np.isnan(ref["step"]))
+    exempt = tie_band(ref) | (ref["err"] > STEP_TOL)
+    ok = ~exempt & ~np.isnan(ref["step"])
+    d = np.abs(step - ref["step"])[ok]
+    assert d.size == 0 or d.max() <= STEP_TOL, d.max()
+    bad = np.nonzero(hit[ok] != ref["hit"][ok])[0]
+    assert bad.size == 0, (bad[:10], hit[ok][bad[:10]], ref["hit"][ok][bad[:10]])
+    assert exempt.mean() <= max_exempt, exempt.mean()
+    return int(exempt.sum())
+
+
+SCENES = {
+    "box4": lambda: scenes.box4(0),
+    "toy40": lambda: scenes.toy40(1),
+    "toy8": lambda: scenes.toy8(1),
+    "diff3": lambda: scenes.diff3(),
+    "grid512": lambda: scenes.grid512(5),
+}
+_scene_cache = {}
+
+
+def scene(name):
+    if name not in _scene_cache:
+        _scene_cache[name] = SCENES[name]()
+    return _scene_cache[name]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_box4_basket_1024(g, orc, mode):
+    """The 1024-track basket in a box mother with four boxes (seed 0)."""
+    sc = scene("box4")
+    tr = scenes.sample_tracks(sc, 1024, 0)
+    ref = orc.navigate(sc, tr, nthreads=8)
+    step, hit = run_nav(g, sc, tr, mode)
+    compare(ref, step, hit)
+
+
+@pytest.mark.parametrize("name,n", [("toy40", 65536 + 77), ("toy8", 30011), ("diff3", 30011),
+                                    ("grid512", 8191)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_scene_parity(g, orc, name, n, mode):
+    """Several blocks of 256 tracks and a ragged tail."""
+    sc = scene(name)
+    tr = scenes.sample_tracks(sc, n, 101)
+    ref = orc.navigate(sc, tr, nthreads=8)
+    step, hit = run_nav(g, sc, tr, mode)
+    compare(ref, step, hit)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_refine_equals_fp64_bitwise(g, name):
+    """GEO_FP32_REFINE returns exactly the plain FP64 answers (random and
+    adversarial grazing / edge / corner rays)."""
+    sc = scene(name)
+    for tr in (scenes.sample_tracks(sc, 50000, 7), scenes.adversarial_tracks(sc, 20000, 8)):
+        s0, h0, b0 = run_nav(g, sc, tr, 0, bpoint=True)
+        s1, h1, b1 = run_nav(g, sc, tr, 1, bpoint=True)
+        assert np.array_equal(h0, h1)
+        assert np.array_equal(s0.view(np.int64), s1.view(np.int64))
+        assert np.array_equal(b0.view(np.int64), b1.view(np.int64))
+
+
+@pytest.mark.parametrize("name", ["box4", "toy40", "diff3", "grid512"])
+def test_adversarial_parity(g, orc, name):
+    sc = scene(name)
+    tr = scenes.adversarial_tracks(sc, 20000, 9)
+    ref = orc.navigate(sc, tr, nthreads=8)
+    step, hit = run_nav(g, sc, tr, 1)
+    compare(ref, step, hit, max_exempt=0.1)
+
+
+@pytest.mark.parametrize("case", golden("closed_forms.json")["nav_cases"], ids=lambda c: c["why"][:40])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_golden_navigator_cases(g, case, mode):
+    sc = scene_from_spec(case["mother"], case["daughters"], name="golden" + case["why"][:20])
+    tr = tracks_from(case["p"], case["d"])
+    step, hit = run_nav(g, sc, tr, mode)
+    want = expr(case["step"])
+    if math.isnan(want):
+        assert math.isnan(step[0])
+    else:
+        assert step[0] == pytest.approx(want, rel=1e-15, abs=1e-12)
+    assert hit[0] == case["hit"]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_edge_cases(g, orc, mode):
+    sc = scene("toy40")
+    rng = np.random.default_rng(3)
+    base = scenes.sample_tracks(sc, 64, 11)
+    p = np.stack([base.x, base.y, base.z], 1)
+    d = np.stack([base.dx, base.dy, base.dz], 1)
+    p[0] = (2000.0, 0, 0)                 # outside the mother
+    p[1] = (0, 0, 1500.0)                 # on the mother's top face
+    d[2] = 0.0                            # zero direction
+    p[3, 0] = np.nan                      # non-finite
+    d[4, 1] = np.inf
+    p[5] = (0.0, 0.0, 0.0)                # on the axis (inside the innermost hole)
+    p[6] = (55.0, 0.0, 0.0)               # inside tube shell 0 (40..70)
+    d[7] *= 3.0                           # non-unit direction
+    p[8] = (40.0, 0.0, 200.0)             # on the inner wall of shell 0
+    p[9] = (750.0, 0.0, 0.0)              # centre of a box daughter
+    d[10] = (0.0, 0.0, 1.0)               # along the axis
+    p[10] = (300.0, 20.0, -1499.0)
+    tr = tracks_from(p, d)
+    ref = orc.navigate(sc, tr)
+    step, hit = run_nav(g, sc, tr, mode)
+    assert hit[0] == -2 and step[0] == 0.0
+    assert np.isnan(step[2]) and hit[2] == -2
+    assert np.isnan(step[3]) and np.isnan(step[4])
+    assert hit[6] == 0 and step[6] == 0.0
+    compare(ref, step, hit, max_exempt=0.1)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 255, 257])
+def test_small_and_empty_baskets(g, orc, n):
+    sc = scene("toy8")
+    tr = scenes.sample_tracks(sc, max(n, 1), 12).slice(0, n)
+    if n == 0:
+        step, hit = run_nav(g, sc, tr, 1)
+        assert step.size == 0 and hit.size == 0
+        return
+    ref = orc.navigate(sc, tr)
+    for mode in (0, 1):
+        step, hit = run_nav(g, sc, tr, mode)
+        compare(ref, step, hit, max_exempt=0.5)
+
+
+def test_boundary_point(g):
+    sc = scene("toy40")
+    tr = scenes.sample_tracks(sc, 10000, 13)
+    step, hit, bp = run_nav(g, sc, tr, 1, bpoint=True)
+    for k, (pc, dc) in enumerate(((tr.x, tr.dx), (tr.y, tr.dy), (tr.z, tr.dz))):
+        want = pc + step * dc
+        assert np.allclose(bp[k], want, rtol=0, atol=1e-12 * 3000)
+
+
+def test_contains_parity(g, orc):
+    for name in SCENES:
+        sc = scene(name)
+        tr = scenes.sample_tracks(sc, 20000, 14, exclusive=False)
+        want = orc.contains(sc, tr, nthreads=8)
+        x, y, z = dev(tr)[:3]
+        got = g.geo_contains(vol(g, sc), x, y, z).cpu().numpy()
+        # surface band: points whose answer changes under a 1e-9 mm move
+        band = np.zeros(tr.n, dtype=bool)
+        for k in range(3):
+            for sg in (-1e-9, 1e-9):
+                f = [tr.x.copy(), tr.y.copy(), tr.z.copy()]
+                f[k] = f[k] + sg
+                band |= orc.contains(sc, scenes.Tracks(*f, tr.dx, tr.dy, tr.dz), nthreads=8) != want
+        assert np.array_equal(got[~band], want[~band]), name
+        assert band.mean() < 1e-3
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_safety_parity(g, orc, mode):
+    for name in SCENES:
+        sc = scene(name)
+        tr = scenes.sample_tracks(sc, 20000, 15, exclusive=False)
+        want = orc.safety(sc, tr, nthreads=8)
+        x, y, z = dev(tr)[:3]
+        got = g.geo_safety(vol(g, sc), x, y, z, mode=mode).cpu().numpy()
+        assert np.max(np.abs(got - want)) <= STEP_TOL, name
+
+
+def test_host_entry_matches_device(g):
+    sc = scene("toy40")
+    tr = scenes.sample_tracks(sc, 100000, 16)
+    s0, h0 = run_nav(g, sc, tr, 1)
+    s1, h1 = g.geo_dist_to_boundary_host(vol(g, sc), *tr.fields(), mode=1, chunk=30000)
+    assert np.array_equal(s0.view(np.int64), s1.view(np.int64))
+    assert np.array_equal(h0, h1)
+
+
+def test_full_size_toy_detector_sampled(g, orc):
+    """The 2^20-track toy-detector basket in the launch configuration the
+    benchmark times; the oracle checks a random sample of 20000 tracks."""
+    sc = scene("toy40")
+    tr = scenes.sample_tracks(sc, 1 << 20, 1)
+    step, hit = run_nav(g, sc, tr, 1)
+    s64, h64 = run_nav(g, sc, tr, 0)
+    assert np.array_equal(step.view(np.int64), s64.view(np.int64)) and np.array_equal(hit, h64)
+    idx = np.sort(np.random.default_rng(17).choice(tr.n, 20000, replace=False))
+    sub = scenes.Tracks(*(f[idx] for f in tr.fields()))
+    ref = orc.navigate(sc, sub, nthreads=8)
+    compare(ref, step[idx], hit[idx])
