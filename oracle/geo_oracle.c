@@ -97,6 +97,52 @@ static void set_and(iset *a, const iset *b) {
     *a = r;
 }
 
+/* a <- a union b (both sorted, disjoint); touching pieces are merged. */
+static void set_or(iset *a, const iset *b) {
+    ivl all[2 * MAXI];
+    int n = 0, i = 0, j = 0;
+    while (i < a->n || j < b->n) {
+        if (j >= b->n || (i < a->n && a->v[i].lo <= b->v[j].lo)) all[n++] = a->v[i++];
+        else all[n++] = b->v[j++];
+    }
+    iset r; r.n = 0;
+    for (int k = 0; k < n; k++) {
+        if (r.n > 0 && all[k].lo <= r.v[r.n - 1].hi) {
+            if (all[k].hi > r.v[r.n - 1].hi) {
+                r.v[r.n - 1].hi = all[k].hi; r.v[r.n - 1].fhi = all[k].fhi; r.v[r.n - 1].chi = all[k].chi;
+            }
+        } else {
+            if (r.n >= MAXI) abort();
+            r.v[r.n++] = all[k];
+        }
+    }
+    *a = r;
+}
+
+/* Optional record of every finite crossing computed while building a line
+ * set (before intersection): used only for the error bound of the step. */
+typedef struct { int n; double t[16]; int f[16]; double c[16]; } xrec;
+static void rec_set(xrec *R, const iset *s) {
+    if (!R) return;
+    for (int i = 0; i < s->n; i++) {
+        if (isfinite(s->v[i].lo) && R->n < 16) { R->t[R->n] = s->v[i].lo; R->f[R->n] = s->v[i].flo; R->c[R->n++] = s->v[i].clo; }
+        if (isfinite(s->v[i].hi) && R->n < 16) { R->t[R->n] = s->v[i].hi; R->f[R->n] = s->v[i].fhi; R->c[R->n++] = s->v[i].chi; }
+    }
+}
+
+/* { s : c + s*w <= h } (upper = 0) or { s : c + s*w >= h } (upper = 1). */
+static void half_set(double c, double w, double h, int upper, int f, iset *s) {
+    if (w == 0.0) {
+        if (upper ? c >= h : c <= h) set_all(s); else set_empty(s);
+        return;
+    }
+    double t = (h - c) / w;
+    int below_after = (w < 0.0);           /* c + s w decreases with s */
+    int keep_after = upper ? !below_after : below_after;
+    if (keep_after) set_one(s, t, f, INFINITY, INFINITY, F_NONE, INFINITY);
+    else set_one(s, -INFINITY, F_NONE, INFINITY, t, f, INFINITY);
+}
+
 /* { s : |c + s*w| <= h } for a slab; faces fm (at -h) and fp (at +h). */
 static void slab_set(double c, double w, double h, int fm, int fp, iset *s) {
     if (w == 0.0) {
@@ -109,44 +155,95 @@ static void slab_set(double c, double w, double h, int fm, int fp, iset *s) {
     else         set_one(s, b, fp, INFINITY, a, fm, INFINITY);
 }
 
-/* Discriminant B*B - A*C with error-free products (W. Kahan, "On the Cost of
- * Floating-Point Computation Without Extra-Precise Arithmetic", 2004: the
- * rounding errors of both products are recovered with a fused multiply-add
- * and added back). */
-static double disc_kahan(double A, double B, double C) {
-    double p = B * B;
-    double dp = fma(B, B, -p);
-    double q = A * C;
-    double dq = fma(A, C, -q);
-    return (p - q) + (dp - dq);
-}
+/* ---- double-double arithmetic ----------------------------------------
+ * Quadric coefficients, discriminants and roots are carried as unevaluated
+ * sums hi + lo of two doubles (T. J. Dekker, "A floating-point technique for
+ * extending the available precision", Numer. Math. 18, 1971; D. E. Knuth,
+ * TAOCP vol. 2, the error-free sum; Y. Hida, X. S. Li, D. H. Bailey,
+ * "Algorithms for quad-double precision floating point arithmetic", 2001).
+ * With ~106 significant bits the roots are exact to FP64 rounding for the
+ * given FP64 local coordinates, even next to tangency or a cone apex. */
+typedef struct { double hi, lo; } dd;
 
-/* { s : A s^2 + 2 B s + C <= 0 }, endpoints tagged with surface f. */
-static void quad_le0(double A, double B, double C, int f, iset *s) {
-    if (A == 0.0) {
-        if (B == 0.0) {
-            if (C <= 0.0) set_all(s); else set_empty(s);
+static dd dd_of(double a) { dd r = { a, 0.0 }; return r; }
+static dd two_sum(double a, double b) {
+    double s = a + b, bb = s - a;
+    dd r = { s, (a - (s - bb)) + (b - bb) };
+    return r;
+}
+static dd fast_two_sum(double a, double b) {
+    double s = a + b;
+    dd r = { s, b - (s - a) };
+    return r;
+}
+static dd two_prod(double a, double b) {
+    double p = a * b;
+    dd r = { p, fma(a, b, -p) };
+    return r;
+}
+static dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+static dd dd_neg(dd a) { dd r = { -a.hi, -a.lo }; return r; }
+static dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+static dd dd_mul(dd a, dd b) {
+    dd p = two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return fast_two_sum(p.hi, p.lo);
+}
+static dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul(dd_of(q1), b));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul(dd_of(q2), b));
+    double q3 = r.hi / b.hi;
+    dd q = fast_two_sum(q1, q2);
+    return dd_add(q, dd_of(q3));
+}
+static dd dd_sqrt(dd a) {
+    if (a.hi <= 0.0) return dd_of(0.0);
+    double x = sqrt(a.hi);
+    /* one Newton step on x^2 = a in double-double */
+    dd e = dd_sub(a, two_prod(x, x));
+    return dd_add(dd_of(x), dd_of(e.hi / (2.0 * x)));
+}
+static int dd_sign(dd a) { return a.hi > 0.0 ? 1 : (a.hi < 0.0 ? -1 : (a.lo > 0.0 ? 1 : (a.lo < 0.0 ? -1 : 0))); }
+static double dd_val(dd a) { return a.hi + a.lo; }
+
+
+/* { s : A s^2 + 2 B s + C <= 0 }, endpoints tagged with surface f;
+ * coefficients in double-double. */
+static void quad_le0(dd A, dd B, dd C, int f, iset *s) {
+    int sa = dd_sign(A), sb = dd_sign(B);
+    if (sa == 0) {
+        if (sb == 0) {
+            if (dd_sign(C) <= 0) set_all(s); else set_empty(s);
             return;
         }
-        double r = -C / (2.0 * B);
-        if (B > 0.0) set_one(s, -INFINITY, F_NONE, INFINITY, r, f, INFINITY);
-        else         set_one(s, r, f, INFINITY, INFINITY, F_NONE, INFINITY);
+        double r = dd_val(dd_div(dd_neg(C), dd_add(B, B)));
+        if (sb > 0) set_one(s, -INFINITY, F_NONE, INFINITY, r, f, INFINITY);
+        else        set_one(s, r, f, INFINITY, INFINITY, F_NONE, INFINITY);
         return;
     }
-    double D = disc_kahan(A, B, C);
-    if (D < 0.0) {
-        if (A > 0.0) set_empty(s); else set_all(s);
+    dd D = dd_sub(dd_mul(B, B), dd_mul(A, C));
+    if (dd_sign(D) < 0) {
+        if (sa > 0) set_empty(s); else set_all(s);
         return;
     }
-    double sq = sqrt(D);
-    double half = sq / fabs(A);
-    double q = -(B + copysign(sq, B));
+    dd sq = dd_sqrt(D);
+    double half = dd_val(sq) / fabs(dd_val(A));
+    /* q = -(B + sign(B) sqrt(D)): no cancellation; roots q/A and C/q */
+    dd q = dd_neg(sb >= 0 ? dd_add(B, sq) : dd_sub(B, sq));
     double r1, r2;
-    if (q == 0.0) { r1 = 0.0; r2 = 0.0; }
-    else { r1 = q / A; r2 = C / q; }
+    if (dd_sign(q) == 0) { r1 = 0.0; r2 = 0.0; }
+    else { r1 = dd_val(dd_div(q, A)); r2 = dd_val(dd_div(C, q)); }
     double lo = r1 < r2 ? r1 : r2;
     double hi = r1 < r2 ? r2 : r1;
-    if (A > 0.0) {
+    if (sa > 0) {
         set_one(s, lo, f, half, hi, f, half);
     } else if (!(lo < hi)) {
         set_all(s);          /* double root of a downward parabola: <= 0 everywhere */
@@ -160,48 +257,66 @@ static void quad_le0(double A, double B, double C, int f, iset *s) {
 }
 
 /* Cone radius line R(z) = a + b z through (r1 at -dz) and (r2 at +dz). */
-static void cone_line(double dz, double r1, double r2, double *a, double *b) {
-    *a = 0.5 * (r1 + r2);
-    *b = (r2 - r1) / (2.0 * dz);
+static void cone_line(double dz, double r1, double r2, dd *a, dd *b) {
+    dd sum = two_sum(r1, r2);
+    a->hi = 0.5 * sum.hi; a->lo = 0.5 * sum.lo;
+    *b = dd_div(two_sum(r2, -r1), dd_of(2.0 * dz));
 }
 
 /* The exact line set S for a solid in its local frame. */
-static void line_set(int kind, const double *p, const double *x, const double *u, iset *S) {
+static void line_set_rec(int kind, const double *p, const double *x, const double *u, iset *S, xrec *R) {
     iset t;
     if (kind == K_BOX) {
-        slab_set(x[0], u[0], p[0], 0, 1, S);
-        slab_set(x[1], u[1], p[1], 2, 3, &t); set_and(S, &t);
-        slab_set(x[2], u[2], p[2], 4, 5, &t); set_and(S, &t);
+        slab_set(x[0], u[0], p[0], 0, 1, S); rec_set(R, S);
+        slab_set(x[1], u[1], p[1], 2, 3, &t); rec_set(R, &t); set_and(S, &t);
+        slab_set(x[2], u[2], p[2], 4, 5, &t); rec_set(R, &t); set_and(S, &t);
         return;
     }
-    double A = u[0] * u[0] + u[1] * u[1];
-    double B = x[0] * u[0] + x[1] * u[1];
-    double C = x[0] * x[0] + x[1] * x[1];
+    /* rho^2(s) = A s^2 + 2 B s + C, exactly in double-double */
+    dd A = dd_add(two_prod(u[0], u[0]), two_prod(u[1], u[1]));
+    dd B = dd_add(two_prod(x[0], u[0]), two_prod(x[1], u[1]));
+    dd C = dd_add(two_prod(x[0], x[0]), two_prod(x[1], x[1]));
     if (kind == K_TUBE) {
         double rmin = p[0], rmax = p[1], dz = p[2];
-        slab_set(x[2], u[2], dz, F_ZM, F_ZP, S);
-        quad_le0(A, B, C - rmax * rmax, F_OUT, &t); set_and(S, &t);
+        slab_set(x[2], u[2], dz, F_ZM, F_ZP, S); rec_set(R, S);
+        quad_le0(A, B, dd_sub(C, two_prod(rmax, rmax)), F_OUT, &t); rec_set(R, &t); set_and(S, &t);
         if (rmin > 0.0) {
             /* rho^2 >= rmin^2  <=>  -(rho^2 - rmin^2) <= 0 */
-            quad_le0(-A, -B, -(C - rmin * rmin), F_IN, &t); set_and(S, &t);
+            dd Ci = dd_sub(C, two_prod(rmin, rmin));
+            quad_le0(dd_neg(A), dd_neg(B), dd_neg(Ci), F_IN, &t); rec_set(R, &t); set_and(S, &t);
         }
         return;
     }
     /* cone: rho <= Rmax(z) and rho >= Rmin(z) inside |z| <= dz; both radius
      * lines are non-negative on the slab, so squaring is exact as a set
      * statement there. */
-    double dz = p[0], a, b;
-    slab_set(x[2], u[2], dz, F_ZM, F_ZP, S);
+    double dz = p[0];
+    dd a, b;
+    slab_set(x[2], u[2], dz, F_ZM, F_ZP, S); rec_set(R, S);
     cone_line(dz, p[2], p[4], &a, &b);
     {
-        double R0 = a + b * x[2], Rs = b * u[2];
-        quad_le0(A - Rs * Rs, B - R0 * Rs, C - R0 * R0, F_OUT, &t); set_and(S, &t);
+        dd R0 = dd_add(a, dd_mul(b, dd_of(x[2]))), Rs = dd_mul(b, dd_of(u[2]));
+        quad_le0(dd_sub(A, dd_mul(Rs, Rs)), dd_sub(B, dd_mul(R0, Rs)), dd_sub(C, dd_mul(R0, R0)), F_OUT, &t);
+        rec_set(R, &t); set_and(S, &t);
     }
     if (p[1] > 0.0 || p[3] > 0.0) {
+        /* rho >= Rmin(z).  Squared, this is exact on the slab (Rmin >= 0
+         * there); where an inner radius is 0 the condition also holds on the
+         * whole end plane through that apex, which is added explicitly: the
+         * squared form alone is degenerate at the apex. */
         cone_line(dz, p[1], p[3], &a, &b);
-        double R0 = a + b * x[2], Rs = b * u[2];
-        quad_le0(-(A - Rs * Rs), -(B - R0 * Rs), -(C - R0 * R0), F_IN, &t); set_and(S, &t);
+        dd R0 = dd_add(a, dd_mul(b, dd_of(x[2]))), Rs = dd_mul(b, dd_of(u[2]));
+        dd Ai = dd_sub(A, dd_mul(Rs, Rs)), Bi = dd_sub(B, dd_mul(R0, Rs)), Ci = dd_sub(C, dd_mul(R0, R0));
+        quad_le0(dd_neg(Ai), dd_neg(Bi), dd_neg(Ci), F_IN, &t); rec_set(R, &t);
+        iset hs;
+        if (p[1] == 0.0) { half_set(x[2], u[2], -dz, 0, F_ZM, &hs); set_or(&t, &hs); }
+        if (p[3] == 0.0) { half_set(x[2], u[2], dz, 1, F_ZP, &hs); set_or(&t, &hs); }
+        set_and(S, &t);
     }
+}
+
+static void line_set(int kind, const double *p, const double *x, const double *u, iset *S) {
+    line_set_rec(kind, p, x, u, S, NULL);
 }
 
 typedef struct { double s; int face; double chord; } hitinfo;
@@ -307,6 +422,47 @@ double orc_safety(int kind, const double *p, const double *x, int inside) {
     return d;
 }
 
+/* Gradient g = grad_x F of the winning surface F(x; theta) = 0 at the local
+ * point xs (F > 0 outside the solid) and dF/dtheta for the five shape
+ * parameters.  Faces as tagged by line_set. */
+static void surface_grad(int kind, const double *p, int f, const double *xs, double *g, double *dF) {
+    for (int k = 0; k < 3; k++) g[k] = 0.0;
+    for (int k = 0; k < 5; k++) dF[k] = 0.0;
+    if (kind == K_BOX) {
+        int ax = f / 2; double sg = (f % 2) ? 1.0 : -1.0;
+        g[ax] = sg;                  /* F = sg*x_ax - h_ax */
+        dF[ax] = -1.0;
+        return;
+    }
+    double dz = (kind == K_TUBE) ? p[2] : p[0];
+    int dzi = (kind == K_TUBE) ? 2 : 0;
+    if (f == F_ZM || f == F_ZP) {
+        double sg = (f == F_ZP) ? 1.0 : -1.0;
+        g[2] = sg; dF[dzi] = -1.0;   /* F = sg*z - dz */
+    } else if (kind == K_TUBE) {
+        double r = (f == F_OUT) ? p[1] : p[0];
+        double sg = (f == F_OUT) ? 1.0 : -1.0;   /* outside of the solid is F > 0 */
+        g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
+        dF[(f == F_OUT) ? 1 : 0] = sg * (-2.0 * r);
+    } else {
+        int outer = (f == F_OUT);
+        double r1 = outer ? p[2] : p[1], r2 = outer ? p[4] : p[3];
+        double sg = outer ? 1.0 : -1.0;
+        double w2 = (xs[2] + dz) / (2.0 * dz);    /* weight of r2 */
+        double Rz = r1 + (r2 - r1) * w2;
+        double dRdz = (r2 - r1) / (2.0 * dz);
+        /* F = sg (x^2 + y^2 - R(z)^2) */
+        g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
+        g[2] = sg * (-2.0 * Rz * dRdz);
+        double dRdr1 = 1.0 - w2, dRdr2 = w2;
+        /* dR/d(dz) at fixed z: w2 = (z+dz)/(2dz) -> dw2/ddz = -z/(2 dz^2) */
+        double dRddz = (r2 - r1) * (-xs[2] / (2.0 * dz * dz));
+        dF[outer ? 2 : 1] = sg * (-2.0 * Rz * dRdr1);
+        dF[outer ? 4 : 3] = sg * (-2.0 * Rz * dRdr2);
+        dF[0] = sg * (-2.0 * Rz * dRddz);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* the navigator (Fig. 1)                                               */
 /* ------------------------------------------------------------------ */
@@ -371,10 +527,48 @@ static navres navigate_one(const orc_scene *sc, const double *pw, const double *
     }
     r.step = best; r.hit = hit; r.second = second; r.face = face;
     {
-        /* E = 8 eps (|p| + |t_j| + s) (1 + L / l), eps = 2^-53 (c12 reading) */
+        /* A-priori FP64 error bound of the step:
+         *   E = 8 eps (|p| + |t_j| + s|d|) * cond,  eps = 2^-53,
+         *   cond = max(1 + L/l, 1 + |g||d| / |g.d|)
+         * with L the solid's largest dimension, l the half-chord of a winning
+         * quadric root, and g the winning surface's gradient at the hit point:
+         * |g||d|/|g.d| is the sensitivity of the hit parameter to a move of
+         * the start point (grazing incidence, on planes as on quadrics). */
         double pn = sqrt(pw[0] * pw[0] + pw[1] * pw[1] + pw[2] * pw[2]);
         double dn = sqrt(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
         double cond = isinf(chord) ? 1.0 : 1.0 + scale / (chord * dn);
+        if (isfinite(best)) {
+            /* every surface crossing of the winning solid that coincides with
+             * the step within 1e-6 (1 + s) (edges, rims, apexes: whichever
+             * surface is crossed first is decided by rounding there) */
+            double x[3], u[3], g[3], dF[5];
+            int kind; const double *prm;
+            if (hit == -1) {
+                kind = sc->mkind; prm = sc->mparams;
+                for (int k = 0; k < 3; k++) { x[k] = pw[k]; u[k] = dw[k]; }
+            } else {
+                kind = sc->kinds[hit]; prm = sc->params + 5 * hit;
+                to_local(sc, hit, pw, dw, x, u);
+            }
+            xrec R; R.n = 0;
+            iset S;
+            line_set_rec(kind, prm, x, u, &S, &R);
+            double sh = shape_scale(kind, prm);
+            for (int e = 0; e < R.n; e++) {
+                if (!(fabs(R.t[e] - best) <= 1e-6 * (1.0 + best)) || R.f[e] == F_NONE) continue;
+                double te = R.t[e];
+                double xs[3] = { x[0] + te * u[0], x[1] + te * u[1], x[2] + te * u[2] };
+                surface_grad(kind, prm, R.f[e], xs, g, dF);
+                double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                double gd = fabs(g[0] * u[0] + g[1] * u[1] + g[2] * u[2]);
+                double c2 = gd > 0.0 ? 1.0 + gn * dn / gd : INFINITY;
+                if (c2 > cond) cond = c2;
+                if (!isinf(R.c[e])) {
+                    double c1 = 1.0 + sh / (R.c[e] * dn);
+                    if (c1 > cond) cond = c1;
+                }
+            }
+        }
         r.err = 8.0 * ldexp(1.0, -53) * (pn + tnorm + best * dn) * cond;
     }
     return r;
@@ -429,41 +623,8 @@ static int adjoint_one(const orc_scene *sc, const double *pw, const double *dw,
     }
     double s = nr.step;
     double xs[3] = { x[0] + s * u[0], x[1] + s * u[1], x[2] + s * u[2] };
-    double g[3] = { 0, 0, 0 }, dF[5] = { 0, 0, 0, 0, 0 };
-    int f = nr.face;
-    if (kind == K_BOX) {
-        int ax = f / 2; double sg = (f % 2) ? 1.0 : -1.0;
-        g[ax] = sg;                  /* F = sg*x_ax - h_ax */
-        dF[ax] = -1.0;
-    } else {
-        double dz = (kind == K_TUBE) ? p[2] : p[0];
-        int dzi = (kind == K_TUBE) ? 2 : 0;
-        if (f == F_ZM || f == F_ZP) {
-            double sg = (f == F_ZP) ? 1.0 : -1.0;
-            g[2] = sg; dF[dzi] = -1.0;  /* F = sg*z - dz */
-        } else if (kind == K_TUBE) {
-            double r = (f == F_OUT) ? p[1] : p[0];
-            double sg = (f == F_OUT) ? 1.0 : -1.0;   /* outside of the solid is F > 0 */
-            g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
-            dF[(f == F_OUT) ? 1 : 0] = sg * (-2.0 * r);
-        } else {
-            int outer = (f == F_OUT);
-            double r1 = outer ? p[2] : p[1], r2 = outer ? p[4] : p[3];
-            double sg = outer ? 1.0 : -1.0;
-            double w2 = (xs[2] + dz) / (2.0 * dz);    /* weight of r2 */
-            double Rz = r1 + (r2 - r1) * w2;
-            double dRdz = (r2 - r1) / (2.0 * dz);
-            /* F = sg (x^2 + y^2 - R(z)^2) */
-            g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
-            g[2] = sg * (-2.0 * Rz * dRdz);
-            double dRdr1 = 1.0 - w2, dRdr2 = w2;
-            /* dR/d(dz) at fixed z: w2 = (z+dz)/(2dz) -> dw2/ddz = -z/(2 dz^2) */
-            double dRddz = (r2 - r1) * (-xs[2] / (2.0 * dz * dz));
-            dF[outer ? 2 : 1] = sg * (-2.0 * Rz * dRdr1);
-            dF[outer ? 4 : 3] = sg * (-2.0 * Rz * dRdr2);
-            dF[0] = sg * (-2.0 * Rz * dRddz);
-        }
-    }
+    double g[3], dF[5];
+    surface_grad(kind, p, nr.face, xs, g, dF);
     double den = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
     if (den == 0.0 || !isfinite(den)) return 0;
     double Rg[3];

@@ -210,3 +210,29 @@ def test_tracks_are_in_exclusive_region(orc):
         sc = _scene(name, seed)
         tr = scenes.sample_tracks(sc, 5000, 25)
         assert np.all(orc.contains(sc, tr) == -1)
+
+
+def test_cone_hole_apex_on_end_face(orc):
+    """A cone whose inner radius is 0 at z=-dz: its end face there is the full
+    closed disk rho <= rmax1, so every line crossing that disk enters the solid
+    at the plane, t = (-dz - z0)/uz, even when it then runs straight into the
+    hole next to the apex (reading: closed solids; rho >= Rmin(z) holds where
+    Rmin(z) = 0)."""
+    rng = np.random.default_rng(12)
+    p = (20.0, 0.0, 15.0, 5.0, 25.0)        # dz, rmin1=0, rmax1, rmin2, rmax2
+    n = 20000
+    rc = 10.0 ** rng.uniform(-12, -3, n)     # crossing radius: next to the apex
+    ph = rng.uniform(0, 2 * math.pi, n)
+    # steeper than the hole's slope 0.125, so the line enters the hole
+    tilt = rng.uniform(0, 0.1, n)
+    pa = rng.uniform(0, 2 * math.pi, n)
+    u = np.stack([tilt * np.cos(pa), tilt * np.sin(pa), np.ones(n)], 1)
+    cross = np.stack([rc * np.cos(ph), rc * np.sin(ph), np.full(n, -20.0)], 1)
+    back = rng.uniform(1.0, 50.0, n)
+    x = cross - back[:, None] * u
+    want = (-20.0 - x[:, 2]) / u[:, 2]
+    got, face = orc.shape(2, p, x, u, "dist_out")
+    assert np.allclose(got, want, rtol=1e-14, atol=1e-12)
+    # the on-axis line in closed form
+    g, _ = orc.shape(2, p, [[0.0, 0.0, -100.0]], [[0.0, 0.0, 1.0]], "dist_out")
+    assert g[0] == 80.0
