@@ -73,20 +73,23 @@ __device__ __forceinline__ bool disc32(float A, float B, float C, float& sq) {
     return true;
 }
 
+// Roots are parameters relative to the (shifted) origin of the frame and may
+// be negative: the caller compares them with its own tmin.
 // falling root (F decreases through 0): (-B - sq)/A in stable form
 __device__ __forceinline__ float root_falling32(float A, float B, float C) {
     float sq;
     if (!disc32(A, B, C, sq)) return f_inf();
     if (B < 0.f) return C / (sq - B);
-    if (A < 0.f) return (-B - sq) / A;
+    if (A != 0.f) return (-B - sq) / A;
     return f_inf();
 }
 
+// rising root (F increases through 0): (-B + sq)/A in stable form
 __device__ __forceinline__ float root_rising32(float A, float B, float C) {
     float sq;
     if (!disc32(A, B, C, sq)) return f_inf();
     if (B > 0.f) return C / (-B - sq);
-    if (A > 0.f) return (sq - B) / A;
+    if (A != 0.f) return (sq - B) / A;
     return f_inf();
 }
 
