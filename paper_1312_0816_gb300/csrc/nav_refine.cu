@@ -23,12 +23,26 @@
 
 namespace geonav {
 
+// Tracks are processed in tiles of one block (256).  After the FP32 pass each
+// track names the first solid it must evaluate in FP64; these tasks are
+// binned by solid kind (mother, box, tube, cone) in shared memory so that the
+// FP64 evaluations run with whole warps on one code path: on this part the
+// FP64 pipe issues one warp instruction per ~19 cycles per SM whether 1 or 32
+// lanes are active, so divergent refinement would multiply its cost.  The
+// remaining refinement (rare: a second candidate within the bounds) runs per
+// thread.
+constexpr int kTile = 256;
+
 template <bool SMEM>
-__global__ void __launch_bounds__(256) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
-                                                     int32_t* __restrict__ hit, double* __restrict__ bpoint,
-                                                     int32_t* __restrict__ nref) {
+__global__ void __launch_bounds__(kTile, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
+                                                       int32_t* __restrict__ hit, double* __restrict__ bpoint,
+                                                       int32_t* __restrict__ nref) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    __shared__ double s_pd[6][kTile];
+    __shared__ double s_res[kTile];
+    __shared__ int s_task[kTile];
+    __shared__ int s_bins[4];
     const ShapeRec32* tab32 = v.d32;
     const ShapeRec64* tab64 = v.d64;
     if (SMEM) {
@@ -39,15 +53,55 @@ __global__ void __launch_bounds__(256) k_dist_refine(VolView v, Basket b, double
         tab32 = reinterpret_cast<const ShapeRec32*>(smem_raw);
         tab64 = reinterpret_cast<const ShapeRec64*>(smem_raw + b32);
     }
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < b.n; i += stride) {
-        const double px = b.x[i], py = b.y[i], pz = b.z[i];
-        const double qx = b.dx[i], qy = b.dy[i], qz = b.dz[i];
-        double best;
-        int h, nev;
-        refine_track(v, tab32, tab64, px, py, pz, qx, qy, qz, best, h, nev);
-        store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
-        if (nref) nref[i] = nev;
+    const int t = threadIdx.x;
+    for (int64_t base = int64_t(blockIdx.x) * kTile; base < b.n; base += int64_t(gridDim.x) * kTile) {
+        const int64_t i = base + t;
+        const bool live = i < b.n;
+        double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
+        if (live) {
+            px = b.x[i]; py = b.y[i]; pz = b.z[i];
+            qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
+        }
+        s_pd[0][t] = px; s_pd[1][t] = py; s_pd[2][t] = pz;
+        s_pd[3][t] = qx; s_pd[4][t] = qy; s_pd[5][t] = qz;
+        RefineState st;
+        double best = 0.0;
+        int h = -2, nev = 0;
+        st.status = 1;
+        if (live) refine_pass1(v, tab32, tab64, px, py, pz, qx, qy, qz, st, best, h, nev);
+        // ---- bin the first FP64 task of every track by solid kind ----
+        int task = 0, bin = -1;
+        if (st.status == 0) {
+            task = first_task(st);
+            bin = task < 0 ? 0 : 1 + tab64[task].kind;
+        }
+        if (t < 4) s_bins[t] = 0;
+        __syncthreads();
+        const int slot = bin >= 0 ? atomicAdd(&s_bins[bin], 1) : 0;
+        __syncthreads();
+        int start = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = s_bins[k];
+            if (k < bin) start += c;
+            total += c;
+        }
+        if (bin >= 0) s_task[start + slot] = t | ((task + 1) << 8);
+        __syncthreads();
+        // ---- one kind-uniform FP64 evaluation per thread ----
+        if (t < total) {
+            const int e = s_task[t];
+            const int owner = e & (kTile - 1), j = (e >> 8) - 1;
+            s_res[owner] = eval64(v, tab64, j, s_pd[0][owner], s_pd[1][owner], s_pd[2][owner], s_pd[3][owner],
+                                  s_pd[4][owner], s_pd[5][owner]);
+        }
+        __syncthreads();
+        if (st.status == 0) refine_rest(v, tab64, st, s_res[t], px, py, pz, qx, qy, qz, best, h, nev);
+        if (live) {
+            store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
+            if (nref) nref[i] = nev;
+        }
+        __syncthreads();   // s_pd / s_res are reused by the next tile
     }
 }
 
@@ -57,11 +111,11 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
     if (v.smem_refine) {
         cudaError_t e = prep(k_dist_refine<true>, smem);
         if (e != cudaSuccess) return e;
-        k_dist_refine<true><<<blocks_for(k_dist_refine<true>, b.n, smem, num_sms), 256, smem, s>>>(
+        k_dist_refine<true><<<blocks_for(k_dist_refine<true>, b.n, smem, num_sms), kTile, smem, s>>>(
             v, b, step, hit, bpoint, nref);
     } else {
-        k_dist_refine<false><<<blocks_for(k_dist_refine<false>, b.n, 0, num_sms), 256, 0, s>>>(v, b, step, hit,
-                                                                                                 bpoint, nref);
+        k_dist_refine<false><<<blocks_for(k_dist_refine<false>, b.n, 0, num_sms), kTile, 0, s>>>(
+            v, b, step, hit, bpoint, nref);
     }
     return cudaGetLastError();
 }

@@ -47,14 +47,29 @@ __device__ __forceinline__ float lower_bound(float t, float delta, float inv_dn)
     return t - (16.f * kEps32f * fabsf(t) + delta * inv_dn);
 }
 
-// One track: returns the FP64 step and hit (identical to nav_all64 with the
-// mother prologue), and the number of FP64 solid evaluations in `nev`
-// (+1000 when the track fell back to the full FP64 loop).
-__device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32* __restrict__ tab32,
+// State of one track between the FP32 pass and the FP64 refinement.
+struct RefineState {
+    Cands c;
+    float Lm;       // lower bound of the mother's exit
+    int status;     // 0: refine, 1: result already final (invalid / outside / fallback)
+};
+
+// FP32 pass: bounds of the mother and of every daughter.  When status == 1
+// on return, best/h already hold the final answer.
+__device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32* __restrict__ tab32,
                                              const ShapeRec64* __restrict__ tab64, double px, double py,
-                                             double pz, double qx, double qy, double qz, double& best, int& h,
-                                             int& nev) {
+                                             double pz, double qx, double qy, double qz, RefineState& st,
+                                             double& best, int& h, int& nev) {
     nev = 0;
+    st.status = 1;
+    st.c.n = 0;
+    st.c.dropped = f_inf();
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) {
+        st.c.L[k] = f_inf();
+        st.c.j[k] = 0;
+    }
+    st.Lm = 0.f;
     if (!valid_track(px, py, pz, qx, qy, qz)) {
         best = d_nan();
         h = -2;
@@ -73,8 +88,8 @@ __device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32*
     }
     const float inv_dd = __frcp_rn(dd);
     const float inv_dn = rsqrtf(dd) * (1.f + 4.f * kEps32f);
-    // mother: the shrunk copy gives "surely inside" and a lower bound of
-    // the exit, the grown copy an upper bound
+    // mother: the shrunk copy gives "surely inside" and a lower bound of the
+    // exit, the grown copy an upper bound
     bool in_shrunk;
     const float e_lo = exit32(v.m32, p32, d32, in_shrunk);
     bool inside = in_shrunk;
@@ -87,20 +102,10 @@ __device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32*
         h = -2;
         return;
     }
-    const float Lm = in_shrunk ? fmaxf(lower_bound(e_lo, v.m32.delta, inv_dn), 0.f) : 0.f;
+    st.Lm = in_shrunk ? fmaxf(lower_bound(e_lo, v.m32.delta, inv_dn), 0.f) : 0.f;
     bool dummy;
     const float e_hi = exit32(v.m32u, p32, d32, dummy);
     const float Um = e_hi + 16.f * kEps32f * e_hi + v.m32u.delta * inv_dn;
-
-    // ---------------- pass 1: FP32 lower bounds of every daughter -------
-    Cands c;
-    c.n = 0;
-    c.dropped = f_inf();
-#pragma unroll
-    for (int k = 0; k < kCand; ++k) {
-        c.L[k] = f_inf();
-        c.j[k] = 0;
-    }
     for (int j = 0; j < v.nd; ++j) {
         const ShapeRec32& r = tab32[j];
         const float w0 = p32[0] - r.t[0], w1 = p32[1] - r.t[1], w2 = p32[2] - r.t[2];
@@ -120,20 +125,61 @@ __device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32*
         if (!(tp < f_inf())) continue;
         const float L = lower_bound(s0 + tp, r.delta, inv_dn);
         if (L > Um) continue;
-        cand_insert(c, L, j);
+        cand_insert(st.c, L, j);
     }
+    st.status = 0;
+}
 
-    // ---------------- pass 2: FP64 refinement in ascending bound order --
-    const double p[3] = {px, py, pz}, q[3] = {qx, qy, qz};
+// The first solid to refine: the mother (-1) when its bound comes first or
+// there is no candidate, else candidate 0.
+__device__ __forceinline__ int first_task(const RefineState& st) {
+    return (st.c.n == 0 || st.Lm <= st.c.L[0]) ? -1 : st.c.j[0];
+}
+
+// FP64 evaluation of one solid for one track (the mother's DistFromInside or
+// a daughter's transform + DistFromOutside).
+__device__ __forceinline__ double eval64(const VolView& v, const ShapeRec64* __restrict__ tab64, int j, double px,
+                                         double py, double pz, double qx, double qy, double qz) {
+    if (j < 0) {
+        const double p[3] = {px, py, pz}, q[3] = {qx, qy, qz};
+        return dist_in64(v.m64, p, q);
+    }
+    const ShapeRec64& r = tab64[j];
+    double x[3], u[3];
+    to_local64(r, px, py, pz, qx, qy, qz, x, u);
+    return dist_out64(r, x, u);
+}
+
+// FP64 refinement in ascending bound order, given the value s_first of the
+// first task (first_task()).  Ties resolve as in Fig. 1a: mother, then the
+// lowest index.
+__device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __restrict__ tab64,
+                                            const RefineState& st, double s_first, double px, double py,
+                                            double pz, double qx, double qy, double qz, double& best, int& h,
+                                            int& nev) {
     best = d_inf();
     h = -1;
-    bool mdone = false;
+    nev = 1;
+    bool mdone;
+    int k0;
+    if (first_task(st) < 0) {
+        mdone = true;
+        best = s_first;   // the mother always beats +inf
+        k0 = 0;
+    } else {
+        mdone = false;
+        if (s_first < best) {
+            best = s_first;
+            h = st.c.j[0];
+        }
+        k0 = 1;
+    }
 #pragma unroll
     for (int k = 0; k < kCand; ++k) {
-        if (k < c.n) {
-            const double L = double(c.L[k]);
-            if (!mdone && double(Lm) <= L) {
-                const double sm = dist_in64(v.m64, p, q);
+        if (k >= k0 && k < st.c.n) {
+            const double L = double(st.c.L[k]);
+            if (!mdone && double(st.Lm) <= L) {
+                const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
                 ++nev;
                 mdone = true;
                 if (sm <= best) {
@@ -142,11 +188,8 @@ __device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32*
                 }
             }
             if (L <= best) {
-                const int j = c.j[k];
-                const ShapeRec64& r = tab64[j];
-                double x[3], u[3];
-                to_local64(r, px, py, pz, qx, qy, qz, x, u);
-                const double s = dist_out64(r, x, u);
+                const int j = st.c.j[k];
+                const double s = eval64(v, tab64, j, px, py, pz, qx, qy, qz);
                 ++nev;
                 if (s < best || (s == best && h >= 0 && j < h)) {
                     best = s;
@@ -155,18 +198,31 @@ __device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32*
             }
         }
     }
-    if (!mdone && double(Lm) <= best) {
-        const double sm = dist_in64(v.m64, p, q);
+    if (!mdone && double(st.Lm) <= best) {
+        const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
         ++nev;
         if (sm <= best) {
             best = sm;
             h = -1;
         }
     }
-    if (double(c.dropped) <= best) {
+    if (double(st.c.dropped) <= best) {
         nav_all64(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
         nev += 1000;   // marks a fallback in the statistics
     }
+}
+
+// One track, all in this thread (used where no block-level compaction is
+// available).  Same answers as nav_all64 with the mother prologue.
+__device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32* __restrict__ tab32,
+                                             const ShapeRec64* __restrict__ tab64, double px, double py,
+                                             double pz, double qx, double qy, double qz, double& best, int& h,
+                                             int& nev) {
+    RefineState st;
+    refine_pass1(v, tab32, tab64, px, py, pz, qx, qy, qz, st, best, h, nev);
+    if (st.status) return;
+    const double s1 = eval64(v, tab64, first_task(st), px, py, pz, qx, qy, qz);
+    refine_rest(v, tab64, st, s1, px, py, pz, qx, qy, qz, best, h, nev);
 }
 
 }  // namespace geonav
