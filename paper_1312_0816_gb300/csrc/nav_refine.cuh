@@ -75,8 +75,8 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
         h = -2;
         return;
     }
-    const float p32[3] = {float(px), float(py), float(pz)};
-    const float d32[3] = {float(qx), float(qy), float(qz)};
+    const float p32[3] = {f64_to_f32_trunc(px), f64_to_f32_trunc(py), f64_to_f32_trunc(pz)};
+    const float d32[3] = {f64_to_f32_trunc(qx), f64_to_f32_trunc(qy), f64_to_f32_trunc(qz)};
     const float dd = fmaf(d32[0], d32[0], fmaf(d32[1], d32[1], d32[2] * d32[2]));
     if (!(dd > 1e-30f && dd < 1e30f)) {
         // direction magnitude outside the range the FP32 bounds assume
@@ -152,11 +152,12 @@ __device__ __forceinline__ double eval64(const VolView& v, const ShapeRec64* __r
 
 // FP64 refinement in ascending bound order, given the value s_first of the
 // first task (first_task()).  Ties resolve as in Fig. 1a: mother, then the
-// lowest index.
+// lowest index.  The bounds are compared in FP32 against best_up >= best, so
+// at least every solid that could tie or win is refined (a solid refined in
+// excess cannot change the answer).
 __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __restrict__ tab64,
-                                            const RefineState& st, double s_first, double px, double py,
-                                            double pz, double qx, double qy, double qz, double& best, int& h,
-                                            int& nev) {
+                                         const RefineState& st, double s_first, double px, double py, double pz,
+                                         double qx, double qy, double qz, double& best, int& h, int& nev) {
     best = d_inf();
     h = -1;
     nev = 1;
@@ -174,39 +175,43 @@ __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __r
         }
         k0 = 1;
     }
+    float best_up = f64_to_f32_up(best);
 #pragma unroll
     for (int k = 0; k < kCand; ++k) {
         if (k >= k0 && k < st.c.n) {
-            const double L = double(st.c.L[k]);
-            if (!mdone && double(st.Lm) <= L) {
+            const float L = st.c.L[k];
+            if (!mdone && st.Lm <= L) {
                 const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
                 ++nev;
                 mdone = true;
                 if (sm <= best) {
                     best = sm;
                     h = -1;
+                    best_up = f64_to_f32_up(best);
                 }
             }
-            if (L <= best) {
+            if (L <= best_up) {
                 const int j = st.c.j[k];
                 const double s = eval64(v, tab64, j, px, py, pz, qx, qy, qz);
                 ++nev;
                 if (s < best || (s == best && h >= 0 && j < h)) {
                     best = s;
                     h = j;
+                    best_up = f64_to_f32_up(best);
                 }
             }
         }
     }
-    if (!mdone && double(st.Lm) <= best) {
+    if (!mdone && st.Lm <= best_up) {
         const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
         ++nev;
         if (sm <= best) {
             best = sm;
             h = -1;
+            best_up = f64_to_f32_up(best);
         }
     }
-    if (double(st.c.dropped) <= best) {
+    if (st.c.dropped <= best_up) {
         nav_all64(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
         nev += 1000;   // marks a fallback in the statistics
     }

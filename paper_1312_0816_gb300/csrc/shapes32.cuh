@@ -32,6 +32,31 @@ constexpr float kEps32f = 5.9604645e-08f;
 
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7f800000); }
 
+// Approximate division and square root (a few ulp): the filter's margins
+// (16 eps32 |t| relative, plus the inflation delta) absorb them.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+
+// FP64 -> FP32 by truncating the significand (integer operations only, so the
+// FP64 pipe stays free).  Relative error below 2^-23, which the inflation
+// covers.  Magnitudes outside the normal FP32 range take the ordinary
+// conversion.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const unsigned hi = unsigned(__double2hiint(x)), lo = unsigned(__double2loint(x));
+    const int e = int((hi >> 20) & 0x7ffu) - 1023;
+    if (e < -126 || e > 127) return float(x);
+    const unsigned bits = (hi & 0x80000000u) | (unsigned(e + 127) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(bits);
+}
+
+// An FP32 value >= x for x >= 0 (x itself when exactly representable or one
+// ulp above the truncation), integer operations only.
+__device__ __forceinline__ float f64_to_f32_up(double x) {
+    if (!(x < 3.0e38)) return f_inf();
+    const float t = f64_to_f32_trunc(x);
+    return __uint_as_float(__float_as_uint(t) + 1u);
+}
+
 // ---------------------------------------------------------------- box ------
 // inf{ t >= tmin : x + t u in box(h) }, lenient by tol at the start point.
 __device__ __forceinline__ float box_enter32(const float* h, const float* x, const float* u, float tmin,
@@ -42,7 +67,7 @@ __device__ __forceinline__ float box_enter32(const float* h, const float* x, con
         if (u[k] == 0.f) {
             if (fabsf(x[k]) > h[k] + tol) return f_inf();
         } else {
-            const float inv = __frcp_rn(u[k]);
+            const float inv = __fdividef(1.f, u[k]);
             const float a = (-h[k] - x[k]) * inv, b = (h[k] - x[k]) * inv;
             tn = fmaxf(tn, fminf(a, b));
             tf = fminf(tf, fmaxf(a, b));
@@ -56,7 +81,7 @@ __device__ __forceinline__ float box_exit32(const float* h, const float* x, cons
     float tf = f_inf();
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-        if (u[k] != 0.f) tf = fminf(tf, (copysignf(h[k], u[k]) - x[k]) * __frcp_rn(u[k]));
+        if (u[k] != 0.f) tf = fminf(tf, fdiv(copysignf(h[k], u[k]) - x[k], u[k]));
     return fmaxf(tf, 0.f);
 }
 
@@ -69,7 +94,7 @@ __device__ __forceinline__ bool disc32(float A, float B, float C, float& sq) {
         if (D > -16.f * kEps32f * (B * B + fabsf(A * C))) D = 0.f;
         else return false;
     }
-    sq = sqrtf(D);
+    sq = fsqrt(D);
     return true;
 }
 
@@ -79,8 +104,8 @@ __device__ __forceinline__ bool disc32(float A, float B, float C, float& sq) {
 __device__ __forceinline__ float root_falling32(float A, float B, float C) {
     float sq;
     if (!disc32(A, B, C, sq)) return f_inf();
-    if (B < 0.f) return C / (sq - B);
-    if (A != 0.f) return (-B - sq) / A;
+    if (B < 0.f) return fdiv(C, sq - B);
+    if (A != 0.f) return fdiv(-B - sq, A);
     return f_inf();
 }
 
@@ -88,8 +113,8 @@ __device__ __forceinline__ float root_falling32(float A, float B, float C) {
 __device__ __forceinline__ float root_rising32(float A, float B, float C) {
     float sq;
     if (!disc32(A, B, C, sq)) return f_inf();
-    if (B > 0.f) return C / (-B - sq);
-    if (A != 0.f) return (sq - B) / A;
+    if (B > 0.f) return fdiv(C, -B - sq);
+    if (A != 0.f) return fdiv(sq - B, A);
     return f_inf();
 }
 
@@ -99,8 +124,8 @@ __device__ __forceinline__ float tube_enter32(const float* e, const float* x, co
                                               float tol) {
     const float dz = e[2];
     const float zl = dz + tol;
-    const float ro = sqrtf(e[1]) + tol;
-    const float ri = e[3] != 0.f ? sqrtf(e[0]) - tol : 0.f;
+    const float ro = fsqrt(e[1]) + tol;
+    const float ri = e[3] != 0.f ? fsqrt(e[0]) - tol : 0.f;
     const float ro2 = ro * ro;
     const float ri2 = ri > 0.f ? ri * ri : 0.f;
     // start point
@@ -109,7 +134,7 @@ __device__ __forceinline__ float tube_enter32(const float* e, const float* x, co
     if (fabsf(sz) <= zl && sr2 <= ro2 && sr2 >= ri2) return tmin;
     float best = f_inf();
     if (fabsf(sz) > dz && sz * u[2] < 0.f) {
-        const float t = (copysignf(dz, sz) - x[2]) / u[2];
+        const float t = fdiv(copysignf(dz, sz) - x[2], u[2]);
         const float xh = fmaf(t, u[0], x[0]), yh = fmaf(t, u[1], x[1]);
         const float r2 = fmaf(xh, xh, yh * yh);
         if (r2 <= ro2 && r2 >= ri2) best = fmaxf(t, tmin);
@@ -144,12 +169,12 @@ __device__ __forceinline__ float cone_enter32(const float* e, const float* x, co
     }
     float best = f_inf();
     if (fabsf(sz) > dz && sz * u[2] < 0.f) {
-        const float t = (copysignf(dz, sz) - x[2]) / u[2];
+        const float t = fdiv(copysignf(dz, sz) - x[2], u[2]);
         const float xh = fmaf(t, u[0], x[0]), yh = fmaf(t, u[1], x[1]);
         const float r2 = fmaf(xh, xh, yh * yh);
         const float lo2 = sz > 0.f ? e[8] : e[6];
-        const float hi = sqrtf(sz > 0.f ? e[9] : e[7]) + tol;
-        const float lo = hole ? fmaxf(sqrtf(lo2) - tol, 0.f) : 0.f;
+        const float hi = fsqrt(sz > 0.f ? e[9] : e[7]) + tol;
+        const float lo = hole ? fmaxf(fsqrt(lo2) - tol, 0.f) : 0.f;
         if (r2 <= hi * hi && r2 >= lo * lo) best = fmaxf(t, tmin);
     }
     const float A0 = fmaf(u[0], u[0], u[1] * u[1]);
@@ -193,7 +218,7 @@ __device__ __forceinline__ float exit32(const ShapeRec32& r, const float* x, con
     float t, s;
     if (r.kind == KTUBE) {
         inside = fabsf(x[2]) <= e[2] && rho2 <= e[1] && (e[3] == 0.f || rho2 >= e[0]);
-        t = u[2] != 0.f ? (copysignf(e[2], u[2]) - x[2]) / u[2] : f_inf();
+        t = u[2] != 0.f ? fdiv(copysignf(e[2], u[2]) - x[2], u[2]) : f_inf();
         s = root_rising32(A0, B0, rho2 - e[1]);
         if (s >= 0.f) t = fminf(t, s);
         if (e[3] != 0.f) {
@@ -208,7 +233,7 @@ __device__ __forceinline__ float exit32(const ShapeRec32& r, const float* x, con
     // point counted inside never sees a root behind it
     const float co = fmaf(-ro0, ro0, rho2), ci = fmaf(-ri0, ri0, rho2);
     inside = fabsf(x[2]) <= e[0] && co <= 0.f && (e[5] == 0.f || ci >= 0.f);
-    t = u[2] != 0.f ? (copysignf(e[0], u[2]) - x[2]) / u[2] : f_inf();
+    t = u[2] != 0.f ? fdiv(copysignf(e[0], u[2]) - x[2], u[2]) : f_inf();
     {
         const float rs = e[2] * u[2];
         s = root_rising32(fmaf(-rs, rs, A0), fmaf(-ro0, rs, B0), co);

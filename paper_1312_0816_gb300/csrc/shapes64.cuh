@@ -79,21 +79,30 @@ __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x)
 }
 
 // ------------------------------------------------------ DistFromOutside ---
+// Slab method with one division: the entry parameter of axis k is
+// N_k / a_k with a_k = |u_k| > 0 and N_k = -h_k - sign(u_k) x_k, its exit
+// F_k / a_k with F_k = h_k - sign(u_k) x_k; the largest entry and smallest
+// exit are chosen by comparing cross products, and only the entry is divided.
 __device__ __forceinline__ double box_out64(const double* h, const double* x, const double* u) {
     if (fabs(x[0]) <= h[0] && fabs(x[1]) <= h[1] && fabs(x[2]) <= h[2]) return 0.0;
-    double tn = -d_inf(), tf = d_inf();
+    double Nn = -1.0, An = 0.0;   // entry numerator / denominator so far (-inf)
+    double Nf = 1.0, Af = 0.0;    // exit numerator / denominator so far (+inf)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (u[k] == 0.0) {
             if (fabs(x[k]) > h[k]) return d_inf();
-        } else {
-            const double a = DIV(SUB(-h[k], x[k]), u[k]);
-            const double b = DIV(SUB(h[k], x[k]), u[k]);
-            tn = fmax(tn, fmin(a, b));
-            tf = fmin(tf, fmax(a, b));
+            continue;
         }
+        const double a = fabs(u[k]);
+        const double xs = u[k] > 0.0 ? x[k] : -x[k];     // sign(u_k) x_k
+        const double N = SUB(-h[k], xs), F = SUB(h[k], xs);
+        // N/a > Nn/An  <=>  N An > Nn a   (a, An >= 0; An == 0 encodes -inf)
+        if (An == 0.0 || MUL(N, An) > MUL(Nn, a)) { Nn = N; An = a; }
+        if (Af == 0.0 || MUL(F, Af) < MUL(Nf, a)) { Nf = F; Af = a; }
     }
-    return (tn <= tf && tf >= 0.0) ? fmax(tn, 0.0) : d_inf();
+    // hit iff entry <= exit and exit >= 0
+    if (!(Af == 0.0 || (MUL(Nn, Af) <= MUL(Nf, An) && Nf >= 0.0))) return d_inf();
+    return Nn <= 0.0 ? 0.0 : DIV(Nn, An);
 }
 
 // crossing of the z-plane the track approaches from outside |z| <= dz
