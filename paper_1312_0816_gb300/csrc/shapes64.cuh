@@ -45,23 +45,31 @@ __device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, doubl
 
 // F(s) = A s^2 + 2 B s + C.  Root where F falls through zero (F' = -2 sqrt(D)),
 // s = (-B - sqrt(D)) / A; +inf when there is none.  May be negative.
+// Both cancellation-free forms are selected operand-wise so that every lane
+// of a warp runs the same single square root and division.
 __device__ __forceinline__ double root_falling(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
-    if (!(D >= 0.0)) return d_inf();
-    const double sq = SQRT(D);
-    if (B < 0.0) return DIV(C, SUB(sq, B));
-    if (A < 0.0) return DIV(SUB(-B, sq), A);
-    return d_inf();
+    const bool real = D >= 0.0;
+    const double sq = SQRT(real ? D : 0.0);
+    const bool bneg = B < 0.0;
+    const double num = bneg ? C : SUB(-B, sq);
+    const double den = bneg ? SUB(sq, B) : A;
+    const bool ok = real && (bneg || A < 0.0);
+    const double s = DIV(num, ok ? den : 1.0);
+    return ok ? s : d_inf();
 }
 
 // Root where F rises through zero (F' = +2 sqrt(D)): s = (-B + sqrt(D)) / A.
 __device__ __forceinline__ double root_rising(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
-    if (!(D >= 0.0)) return d_inf();
-    const double sq = SQRT(D);
-    if (B > 0.0) return DIV(C, SUB(-B, sq));
-    if (A > 0.0) return DIV(SUB(sq, B), A);
-    return d_inf();
+    const bool real = D >= 0.0;
+    const double sq = SQRT(real ? D : 0.0);
+    const bool bpos = B > 0.0;
+    const double num = bpos ? C : SUB(sq, B);
+    const double den = bpos ? SUB(-B, sq) : A;
+    const bool ok = real && (bpos || A > 0.0);
+    const double s = DIV(num, ok ? den : 1.0);
+    return ok ? s : d_inf();
 }
 
 __device__ __forceinline__ double rho2_of(const double* x) { return DOT2(x[0], x[0], x[1], x[1]); }
@@ -105,21 +113,18 @@ __device__ __forceinline__ double box_out64(const double* h, const double* x, co
     return Nn <= 0.0 ? 0.0 : DIV(Nn, An);
 }
 
-// crossing of the z-plane the track approaches from outside |z| <= dz
-__device__ __forceinline__ double zplane_t(const double* x, const double* u, double dz) {
-    return DIV(SUB(copysign(dz, x[2]), x[2]), u[2]);
-}
 
 __device__ __forceinline__ double tube_out64(const double* d, const double* x, const double* u) {
     const double rmin = d[0], dz = d[2], rmin2 = d[3], rmax2 = d[4];
     const double rho2 = rho2_of(x);
     if (fabs(x[2]) <= dz && rho2 <= rmax2 && rho2 >= rmin2) return 0.0;
     double best = d_inf();
-    if (fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0) {
-        const double t = zplane_t(x, u, dz);
+    {   // the z-plane the track approaches from outside the slab
+        const bool zc = fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0;
+        const double t = DIV(SUB(copysign(dz, x[2]), x[2]), zc ? u[2] : 1.0);
         const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
         const double r2 = DOT2(xh, xh, yh, yh);
-        if (r2 <= rmax2 && r2 >= rmin2) best = t;
+        if (zc && r2 <= rmax2 && r2 >= rmin2) best = t;
     }
     const double A = DOT2(u[0], u[0], u[1], u[1]);
     const double B = DOT2(x[0], u[0], x[1], u[1]);
@@ -142,13 +147,14 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     const bool hole = d[11] != 0.0;
     if (fabs(x[2]) <= dz && rho2 <= MUL(ro0, ro0) && (!hole || rho2 >= MUL(ri0, ri0))) return 0.0;
     double best = d_inf();
-    if (fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0) {
-        const double t = zplane_t(x, u, dz);
+    {   // the z-plane the track approaches from outside the slab
+        const bool zc = fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0;
+        const double t = DIV(SUB(copysign(dz, x[2]), x[2]), zc ? u[2] : 1.0);
         const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
         const double r2 = DOT2(xh, xh, yh, yh);
         const double lo2 = x[2] > 0.0 ? d[7] : d[5];
         const double hi2 = x[2] > 0.0 ? d[8] : d[6];
-        if (r2 <= hi2 && r2 >= lo2) best = t;
+        if (zc && r2 <= hi2 && r2 >= lo2) best = t;
     }
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
@@ -174,7 +180,8 @@ __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* 
 // ------------------------------------------------------- DistFromInside ---
 // First s >= 0 at which the track violates a constraint (x assumed inside).
 __device__ __forceinline__ double slab_exit(double xk, double uk, double h) {
-    return uk == 0.0 ? d_inf() : DIV(SUB(copysign(h, uk), xk), uk);
+    const double t = DIV(SUB(copysign(h, uk), xk), uk == 0.0 ? 1.0 : uk);
+    return uk == 0.0 ? d_inf() : t;
 }
 
 __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u) {
