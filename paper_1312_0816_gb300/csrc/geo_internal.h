@@ -80,6 +80,7 @@ struct Basket {
 // device error codes written to VolView::status
 constexpr unsigned ST_TMA_TIMEOUT = 1u;
 constexpr unsigned ST_BAD_INDEX = 2u;
+constexpr unsigned ST_SYNC_TIMEOUT = 4u;
 
 // launchers (host), each returns cudaGetLastError() of its launch
 cudaError_t launch_dist_fp64(const VolView& v, const Basket& b, double* step, int32_t* hit,

@@ -23,26 +23,61 @@
 
 namespace geonav {
 
-// Tracks are processed in tiles of one block (256).  After the FP32 pass each
-// track names the first solid it must evaluate in FP64; these tasks are
-// binned by solid kind (mother, box, tube, cone) in shared memory so that the
-// FP64 evaluations run with whole warps on one code path: on this part the
-// FP64 pipe issues one warp instruction per ~19 cycles per SM whether 1 or 32
-// lanes are active, so divergent refinement would multiply its cost.  The
-// remaining refinement (rare: a second candidate within the bounds) runs per
-// thread.
-constexpr int kTile = 256;
+// Warp-specialised persistent kernel.  A block holds 8 producer warps (one
+// track per thread per tile of 256) and 4 consumer warps (one per SM
+// sub-partition: the FP64 units are per sub-partition, and the microbenchmark
+// shows one warp with a dependent FP64 chain keeps one busy).
+//  producers: FP32 pass of tile k, then bin each track's first FP64 task by
+//             solid kind (mother, box, tube, cone) into stage k%2, arrive on
+//             full[k%2]; then wait done[(k-1)%2] and finish tile k-1 (rare
+//             extra refinements, stores).
+//  consumers: wait full[k%2], evaluate the binned tasks of tile k in FP64 (a
+//             warp takes 32 consecutive tasks, so nearly always one kind),
+//             arrive on done[k%2].
+// The FP64 pipe therefore works on tile k while the FP32 pass of tile k+1 runs.
+// Every wait is bounded; a wait that runs out records ST_SYNC_TIMEOUT.
+constexpr int kProd = 256;
+constexpr int kCons = 128;
+constexpr int kThreads = kProd + kCons;
+
+struct Stage {
+    double res[kProd];          // FP64 value of each track's first task
+    float L[kCand][kProd];      // stashed FP32 state for the producers' second half
+    int j[kCand][kProd];
+    float Lm[kProd];
+    float dropped[kProd];
+    int n[kProd];               // candidate count, -1: answer already final
+    int task[kProd];            // binned tasks: owner | (solid + 1) << 8
+    int cnt[4];
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait; after one timeout the caller stops waiting altogether (its
+// results are then unreliable and the status word says so).
+constexpr uint32_t kSyncPolls = 1u << 20;
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned int* status,
+                                                  bool& healthy) {
+    if (!healthy) return;
+    for (uint32_t it = 0; it < kSyncPolls; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+    atomicOr(status, ST_SYNC_TIMEOUT);
+    healthy = false;
+}
+
+__device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(kTile, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
-                                                       int32_t* __restrict__ hit, double* __restrict__ bpoint,
-                                                       int32_t* __restrict__ nref) {
+__global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
+                                                             int32_t* __restrict__ hit,
+                                                             double* __restrict__ bpoint,
+                                                             int32_t* __restrict__ nref) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
-    __shared__ double s_pd[6][kTile];
-    __shared__ double s_res[kTile];
-    __shared__ int s_task[kTile];
-    __shared__ int s_bins[4];
+    __shared__ uint64_t full[2], done[2];
+    __shared__ Stage S[2];
     const ShapeRec32* tab32 = v.d32;
     const ShapeRec64* tab64 = v.d64;
     if (SMEM) {
@@ -54,55 +89,125 @@ __global__ void __launch_bounds__(kTile, 2) k_dist_refine(VolView v, Basket b, d
         tab64 = reinterpret_cast<const ShapeRec64*>(smem_raw + b32);
     }
     const int t = threadIdx.x;
-    for (int64_t base = int64_t(blockIdx.x) * kTile; base < b.n; base += int64_t(gridDim.x) * kTile) {
-        const int64_t i = base + t;
-        const bool live = i < b.n;
-        double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
-        if (live) {
-            px = b.x[i]; py = b.y[i]; pz = b.z[i];
-            qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
-        }
-        s_pd[0][t] = px; s_pd[1][t] = py; s_pd[2][t] = pz;
-        s_pd[3][t] = qx; s_pd[4][t] = qy; s_pd[5][t] = qz;
-        RefineState st;
-        double best = 0.0;
-        int h = -2, nev = 0;
-        st.status = 1;
-        if (live) refine_pass1(v, tab32, tab64, px, py, pz, qx, qy, qz, st, best, h, nev);
-        // ---- bin the first FP64 task of every track by solid kind ----
-        int task = 0, bin = -1;
-        if (st.status == 0) {
-            task = first_task(st);
-            bin = task < 0 ? 0 : 1 + tab64[task].kind;
-        }
-        if (t < 4) s_bins[t] = 0;
-        __syncthreads();
-        const int slot = bin >= 0 ? atomicAdd(&s_bins[bin], 1) : 0;
-        __syncthreads();
-        int start = 0, total = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = s_bins[k];
-            if (k < bin) start += c;
-            total += c;
-        }
-        if (bin >= 0) s_task[start + slot] = t | ((task + 1) << 8);
-        __syncthreads();
-        // ---- one kind-uniform FP64 evaluation per thread ----
-        if (t < total) {
-            const int e = s_task[t];
-            const int owner = e & (kTile - 1), j = (e >> 8) - 1;
-            s_res[owner] = eval64(v, tab64, j, s_pd[0][owner], s_pd[1][owner], s_pd[2][owner], s_pd[3][owner],
-                                  s_pd[4][owner], s_pd[5][owner]);
-        }
-        __syncthreads();
-        if (st.status == 0) refine_rest(v, tab64, st, s_res[t], px, py, pz, qx, qy, qz, best, h, nev);
-        if (live) {
-            store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
-            if (nref) nref[i] = nev;
-        }
-        __syncthreads();   // s_pd / s_res are reused by the next tile
+    if (t == 0) {
+        mbar_init(&full[0], kProd / 32);
+        mbar_init(&full[1], kProd / 32);
+        mbar_init(&done[0], kCons / 32);
+        mbar_init(&done[1], kCons / 32);
     }
+    __syncthreads();
+    const int64_t ntiles = (b.n + kProd - 1) / kProd;
+    const int K = int((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);   // tiles of this block
+    const int lane = t & 31;
+    bool healthy = true;
+
+    if (t < kProd) {
+        // ------------------------------------------------------ producers --
+        for (int k = 0; k <= K; ++k) {
+            if (k < K) {
+                Stage& st_ = S[k & 1];
+                const int64_t i = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * kProd + t;
+                const bool live = i < b.n;
+                double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
+                if (live) {
+                    px = b.x[i]; py = b.y[i]; pz = b.z[i];
+                    qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
+                }
+                RefineState rs;
+                double best = 0.0;
+                int h = -2, nev = 0;
+                rs.status = 1;
+                if (live) refine_pass1(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+                int task = 0, bin = -1;
+                if (rs.status == 0) {
+                    task = first_task(rs);
+                    bin = task < 0 ? 0 : 1 + tab64[task].kind;
+                }
+                if (t < 4) st_.cnt[t] = 0;
+                producer_barrier();
+                const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
+                producer_barrier();
+                int start = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < bin) start += st_.cnt[q];
+                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << 8);
+                // stash the FP32 state; final answers are stored right away
+                if (rs.status == 0) {
+#pragma unroll
+                    for (int q = 0; q < kCand; ++q) {
+                        st_.L[q][t] = rs.c.L[q];
+                        st_.j[q][t] = rs.c.j[q];
+                    }
+                    st_.Lm[t] = rs.Lm;
+                    st_.dropped[t] = rs.c.dropped;
+                    st_.n[t] = rs.c.n;
+                } else {
+                    st_.n[t] = -1;
+                    if (live) {
+                        store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
+                        if (nref) nref[i] = nev;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[k & 1]);
+            }
+            if (k >= 1) {
+                const int kp = k - 1;
+                Stage& sp = S[kp & 1];
+                mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), v.status, healthy);
+                const int64_t i = (int64_t(blockIdx.x) + int64_t(kp) * gridDim.x) * kProd + t;
+                if (i < b.n && sp.n[t] >= 0) {
+                    RefineState rs;
+                    rs.status = 0;
+                    rs.c.n = sp.n[t];
+#pragma unroll
+                    for (int q = 0; q < kCand; ++q) {
+                        rs.c.L[q] = sp.L[q][t];
+                        rs.c.j[q] = sp.j[q][t];
+                    }
+                    rs.c.dropped = sp.dropped[t];
+                    rs.Lm = sp.Lm[t];
+                    const double px = b.x[i], py = b.y[i], pz = b.z[i];
+                    const double qx = b.dx[i], qy = b.dy[i], qz = b.dz[i];
+                    double best;
+                    int h, nev;
+                    refine_rest(v, tab64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
+                    store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
+                    if (nref) nref[i] = nev;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------ consumers --
+        const int c = t - kProd;
+        for (int k = 0; k < K; ++k) {
+            Stage& st_ = S[k & 1];
+            mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), v.status, healthy);
+            const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
+            const int64_t base = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * kProd;
+            for (int q = c; q < total; q += kCons) {
+                const int e = st_.task[q];
+                const int owner = e & (kProd - 1), jj = (e >> 8) - 1;
+                const int64_t i = base + owner;
+                st_.res[owner] = eval64(v, tab64, jj, b.x[i], b.y[i], b.z[i], b.dx[i], b.dy[i], b.dz[i]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&done[k & 1]);
+        }
+    }
+}
+
+template <typename K>
+static int grid_refine(K kernel, int64_t n, int smem, int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t need = (n + kProd - 1) / kProd;
+    const int64_t cap = int64_t(per_sm) * num_sms;
+    return int(need < cap ? need : cap);
 }
 
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
@@ -111,10 +216,10 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
     if (v.smem_refine) {
         cudaError_t e = prep(k_dist_refine<true>, smem);
         if (e != cudaSuccess) return e;
-        k_dist_refine<true><<<blocks_for(k_dist_refine<true>, b.n, smem, num_sms), kTile, smem, s>>>(
+        k_dist_refine<true><<<grid_refine(k_dist_refine<true>, b.n, smem, num_sms), kThreads, smem, s>>>(
             v, b, step, hit, bpoint, nref);
     } else {
-        k_dist_refine<false><<<blocks_for(k_dist_refine<false>, b.n, 0, num_sms), kTile, 0, s>>>(
+        k_dist_refine<false><<<grid_refine(k_dist_refine<false>, b.n, 0, num_sms), kThreads, 0, s>>>(
             v, b, step, hit, bpoint, nref);
     }
     return cudaGetLastError();
