@@ -8,10 +8,12 @@
 namespace geonav {
 
 // Invalid input (non-finite or zero direction): NaN, -2.  Returns false.
+// (exponent bits checked with integer operations)
+__device__ __forceinline__ bool finite64(double a) { return (BITS(a) & kAbsMask) < 0x7ff0000000000000LL; }
 __device__ __forceinline__ bool valid_track(double px, double py, double pz, double qx, double qy, double qz) {
-    const bool finite = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(qx) && isfinite(qy) &&
-                        isfinite(qz);
-    return finite && !(qx == 0.0 && qy == 0.0 && qz == 0.0);
+    const bool finite = finite64(px) && finite64(py) && finite64(pz) && finite64(qx) && finite64(qy) &&
+                        finite64(qz);
+    return finite && !(IS_ZERO(qx) && IS_ZERO(qy) && IS_ZERO(qz));
 }
 
 // Mother DistFromInside, then for every daughter: bounding-sphere test against
@@ -40,7 +42,7 @@ __device__ __forceinline__ void nav_all64(const ShapeRec64& m, const ShapeRec64*
         double x[3], u[3];
         to_local64(r, px, py, pz, qx, qy, qz, x, u);
         const double s = dist_out64(r, x, u);
-        if (s < best) {
+        if (LT(s, best)) {
             best = s;
             h = j;
         }

@@ -169,7 +169,7 @@ __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __r
         k0 = 0;
     } else {
         mdone = false;
-        if (s_first < best) {
+        if (LT(s_first, best)) {
             best = s_first;
             h = st.c.j[0];
         }
@@ -184,7 +184,7 @@ __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __r
                 const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
                 ++nev;
                 mdone = true;
-                if (sm <= best) {
+                if (LE(sm, best)) {
                     best = sm;
                     h = -1;
                     best_up = f64_to_f32_up(best);
@@ -194,7 +194,9 @@ __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __r
                 const int j = st.c.j[k];
                 const double s = eval64(v, tab64, j, px, py, pz, qx, qy, qz);
                 ++nev;
-                if (s < best || (s == best && h >= 0 && j < h)) {
+                // same order as the sequential loop: bit-pattern order of
+                // non-negative steps, ties to the mother, then the lowest index
+                if (LT(s, best) || (BITS(s) == BITS(best) && h >= 0 && j < h)) {
                     best = s;
                     h = j;
                     best_up = f64_to_f32_up(best);
@@ -205,7 +207,7 @@ __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __r
     if (!mdone && st.Lm <= best_up) {
         const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
         ++nev;
-        if (sm <= best) {
+        if (LE(sm, best)) {
             best = sm;
             h = -1;
             best_up = f64_to_f32_up(best);

@@ -52,7 +52,8 @@ __device__ __forceinline__ float f64_to_f32_trunc(double x) {
 // An FP32 value >= x for x >= 0 (x itself when exactly representable or one
 // ulp above the truncation), integer operations only.
 __device__ __forceinline__ float f64_to_f32_up(double x) {
-    if (!(x < 3.0e38)) return f_inf();
+    // x >= 0 here; compared on the bit pattern (3.0e38 as a double)
+    if (!(__double_as_longlong(x) < 0x47EC363CBF21F28ALL)) return f_inf();
     const float t = f64_to_f32_trunc(x);
     return __uint_as_float(__float_as_uint(t) + 1u);
 }

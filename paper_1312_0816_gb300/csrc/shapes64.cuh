@@ -32,6 +32,28 @@ __device__ __forceinline__ double SQRT(double a) { return __dsqrt_rn(a); }
 // a*b + c*d with one rounding for c*d and a fused final step
 __device__ __forceinline__ double DOT2(double a, double b, double c, double d) { return FMA(a, b, MUL(c, d)); }
 
+// Comparisons on the bit patterns (integer ALU instead of the FP64 pipe).
+// For non-negative doubles (and +inf) the IEEE order is the integer order of
+// the bits; a NaN compares as larger than +inf, so "<=" and "<" against a
+// finite or infinite bound are false for it, as in floating point.
+__device__ __forceinline__ long long BITS(double a) { return __double_as_longlong(a); }
+constexpr long long kAbsMask = 0x7fffffffffffffffLL;
+__device__ __forceinline__ bool LE(double a, double b) { return BITS(a) <= BITS(b); }    // a, b >= 0
+__device__ __forceinline__ bool LT(double a, double b) { return BITS(a) < BITS(b); }     // a, b >= 0
+__device__ __forceinline__ bool ABS_LE(double x, double h) { return (BITS(x) & kAbsMask) <= BITS(h); }  // h >= 0
+__device__ __forceinline__ bool ABS_GT(double x, double h) { return (BITS(x) & kAbsMask) > BITS(h); }   // h >= 0
+__device__ __forceinline__ bool IS_ZERO(double a) { return (BITS(a) & kAbsMask) == 0; }
+__device__ __forceinline__ bool IS_NEG(double a) { return BITS(a) < 0 && !IS_ZERO(a); }     // a < 0
+__device__ __forceinline__ bool IS_POS(double a) { return BITS(a) > 0; }                    // a > 0
+__device__ __forceinline__ bool NONNEG(double a) { return BITS(a) >= 0 || IS_ZERO(a); }     // a >= 0
+// a * b < 0 without the product
+__device__ __forceinline__ bool OPPOSITE(double a, double b) {
+    return ((BITS(a) ^ BITS(b)) < 0) && !IS_ZERO(a) && !IS_ZERO(b);
+}
+// min / max of two values >= 0
+__device__ __forceinline__ double MINP(double a, double b) { return LT(b, a) ? b : a; }
+__device__ __forceinline__ double MAXP(double a, double b) { return LT(a, b) ? b : a; }
+
 // x = R^T (p - t), u = R^T d
 __device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, double py, double pz,
                                            double qx, double qy, double qz, double* x, double* u) {
@@ -49,12 +71,12 @@ __device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, doubl
 // of a warp runs the same single square root and division.
 __device__ __forceinline__ double root_falling(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
-    const bool real = D >= 0.0;
+    const bool real = NONNEG(D);
     const double sq = SQRT(real ? D : 0.0);
-    const bool bneg = B < 0.0;
+    const bool bneg = IS_NEG(B);
     const double num = bneg ? C : SUB(-B, sq);
     const double den = bneg ? SUB(sq, B) : A;
-    const bool ok = real && (bneg || A < 0.0);
+    const bool ok = real && (bneg || IS_NEG(A));
     const double s = DIV(num, ok ? den : 1.0);
     return ok ? s : d_inf();
 }
@@ -62,12 +84,12 @@ __device__ __forceinline__ double root_falling(double A, double B, double C) {
 // Root where F rises through zero (F' = +2 sqrt(D)): s = (-B + sqrt(D)) / A.
 __device__ __forceinline__ double root_rising(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
-    const bool real = D >= 0.0;
+    const bool real = NONNEG(D);
     const double sq = SQRT(real ? D : 0.0);
-    const bool bpos = B > 0.0;
+    const bool bpos = IS_POS(B);
     const double num = bpos ? C : SUB(sq, B);
     const double den = bpos ? SUB(-B, sq) : A;
-    const bool ok = real && (bpos || A > 0.0);
+    const bool ok = real && (bpos || IS_POS(A));
     const double s = DIV(num, ok ? den : 1.0);
     return ok ? s : d_inf();
 }
@@ -77,13 +99,13 @@ __device__ __forceinline__ double rho2_of(const double* x) { return DOT2(x[0], x
 // ------------------------------------------------------------- contains ---
 __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x) {
     const double* d = r.d;
-    if (r.kind == KBOX) return fabs(x[0]) <= d[0] && fabs(x[1]) <= d[1] && fabs(x[2]) <= d[2];
+    if (r.kind == KBOX) return ABS_LE(x[0], d[0]) && ABS_LE(x[1], d[1]) && ABS_LE(x[2], d[2]);
     const double rho2 = rho2_of(x);
-    if (r.kind == KTUBE) return fabs(x[2]) <= d[2] && rho2 <= d[4] && rho2 >= d[3];
-    if (!(fabs(x[2]) <= d[0])) return false;
+    if (r.kind == KTUBE) return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2);
+    if (!ABS_LE(x[2], d[0])) return false;
     const double ro = FMA(d[2], x[2], d[1]);
     const double ri = FMA(d[4], x[2], d[3]);
-    return rho2 <= MUL(ro, ro) && (d[11] == 0.0 || rho2 >= MUL(ri, ri));
+    return LE(rho2, MUL(ro, ro)) && (d[11] == 0.0 || LE(MUL(ri, ri), rho2));
 }
 
 // ------------------------------------------------------ DistFromOutside ---
@@ -92,49 +114,49 @@ __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x)
 // F_k / a_k with F_k = h_k - sign(u_k) x_k; the largest entry and smallest
 // exit are chosen by comparing cross products, and only the entry is divided.
 __device__ __forceinline__ double box_out64(const double* h, const double* x, const double* u) {
-    if (fabs(x[0]) <= h[0] && fabs(x[1]) <= h[1] && fabs(x[2]) <= h[2]) return 0.0;
+    if (ABS_LE(x[0], h[0]) && ABS_LE(x[1], h[1]) && ABS_LE(x[2], h[2])) return 0.0;
     double Nn = -1.0, An = 0.0;   // entry numerator / denominator so far (-inf)
     double Nf = 1.0, Af = 0.0;    // exit numerator / denominator so far (+inf)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        if (u[k] == 0.0) {
-            if (fabs(x[k]) > h[k]) return d_inf();
+        if (IS_ZERO(u[k])) {
+            if (ABS_GT(x[k], h[k])) return d_inf();
             continue;
         }
         const double a = fabs(u[k]);
-        const double xs = u[k] > 0.0 ? x[k] : -x[k];     // sign(u_k) x_k
+        const double xs = IS_POS(u[k]) ? x[k] : -x[k];   // sign(u_k) x_k
         const double N = SUB(-h[k], xs), F = SUB(h[k], xs);
         // N/a > Nn/An  <=>  N An > Nn a   (a, An >= 0; An == 0 encodes -inf)
         if (An == 0.0 || MUL(N, An) > MUL(Nn, a)) { Nn = N; An = a; }
         if (Af == 0.0 || MUL(F, Af) < MUL(Nf, a)) { Nf = F; Af = a; }
     }
     // hit iff entry <= exit and exit >= 0
-    if (!(Af == 0.0 || (MUL(Nn, Af) <= MUL(Nf, An) && Nf >= 0.0))) return d_inf();
-    return Nn <= 0.0 ? 0.0 : DIV(Nn, An);
+    if (!(Af == 0.0 || (MUL(Nn, Af) <= MUL(Nf, An) && NONNEG(Nf)))) return d_inf();
+    return IS_POS(Nn) ? DIV(Nn, An) : 0.0;
 }
 
 
 __device__ __forceinline__ double tube_out64(const double* d, const double* x, const double* u) {
     const double rmin = d[0], dz = d[2], rmin2 = d[3], rmax2 = d[4];
     const double rho2 = rho2_of(x);
-    if (fabs(x[2]) <= dz && rho2 <= rmax2 && rho2 >= rmin2) return 0.0;
+    if (ABS_LE(x[2], dz) && LE(rho2, rmax2) && LE(rmin2, rho2)) return 0.0;
     double best = d_inf();
     {   // the z-plane the track approaches from outside the slab
-        const bool zc = fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0;
+        const bool zc = ABS_GT(x[2], dz) && OPPOSITE(x[2], u[2]);
         const double t = DIV(SUB(copysign(dz, x[2]), x[2]), zc ? u[2] : 1.0);
         const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
         const double r2 = DOT2(xh, xh, yh, yh);
-        if (zc && r2 <= rmax2 && r2 >= rmin2) best = t;
+        if (zc && LE(r2, rmax2) && LE(rmin2, r2)) best = t;
     }
     const double A = DOT2(u[0], u[0], u[1], u[1]);
     const double B = DOT2(x[0], u[0], x[1], u[1]);
     {   // outer cylinder, crossed inwards
         const double s = root_falling(A, B, SUB(rho2, rmax2));
-        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
     }
     if (rmin > 0.0) {   // inner cylinder, crossed outwards (out of the hole)
         const double s = root_rising(A, B, SUB(rho2, rmin2));
-        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
     }
     return best;
 }
@@ -145,28 +167,28 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     const double ro0 = FMA(d[2], x[2], d[1]);
     const double ri0 = FMA(d[4], x[2], d[3]);
     const bool hole = d[11] != 0.0;
-    if (fabs(x[2]) <= dz && rho2 <= MUL(ro0, ro0) && (!hole || rho2 >= MUL(ri0, ri0))) return 0.0;
+    if (ABS_LE(x[2], dz) && LE(rho2, MUL(ro0, ro0)) && (!hole || LE(MUL(ri0, ri0), rho2))) return 0.0;
     double best = d_inf();
     {   // the z-plane the track approaches from outside the slab
-        const bool zc = fabs(x[2]) > dz && MUL(x[2], u[2]) < 0.0;
+        const bool zc = ABS_GT(x[2], dz) && OPPOSITE(x[2], u[2]);
         const double t = DIV(SUB(copysign(dz, x[2]), x[2]), zc ? u[2] : 1.0);
         const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
         const double r2 = DOT2(xh, xh, yh, yh);
-        const double lo2 = x[2] > 0.0 ? d[7] : d[5];
-        const double hi2 = x[2] > 0.0 ? d[8] : d[6];
-        if (zc && r2 <= hi2 && r2 >= lo2) best = t;
+        const double lo2 = IS_POS(x[2]) ? d[7] : d[5];
+        const double hi2 = IS_POS(x[2]) ? d[8] : d[6];
+        if (zc && LE(r2, hi2) && LE(lo2, r2)) best = t;
     }
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
     {   // outer cone rho^2 - (a + b z)^2, crossed inwards
         const double rs = MUL(d[2], u[2]);
         const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
     }
     if (hole) {   // inner cone, crossed outwards
         const double rs = MUL(d[4], u[2]);
         const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-        if (s >= 0.0 && s < best && fabs(FMA(s, u[2], x[2])) <= dz) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
     }
     return best;
 }
@@ -180,43 +202,49 @@ __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* 
 // ------------------------------------------------------- DistFromInside ---
 // First s >= 0 at which the track violates a constraint (x assumed inside).
 __device__ __forceinline__ double slab_exit(double xk, double uk, double h) {
-    const double t = DIV(SUB(copysign(h, uk), xk), uk == 0.0 ? 1.0 : uk);
-    return uk == 0.0 ? d_inf() : t;
+    const bool z = IS_ZERO(uk);
+    const double t = DIV(SUB(copysign(h, uk), xk), z ? 1.0 : uk);
+    return z ? d_inf() : t;
 }
+
+// Exit parameters of a point inside are >= 0 up to the sign of a zero; the
+// minimum is taken on the bit patterns and the result clamped at +0.
+__device__ __forceinline__ double clamp0(double t) { return NONNEG(t) && !IS_ZERO(t) ? t : 0.0; }
 
 __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u) {
     const double* d = r.d;
     double t;
     if (r.kind == KBOX) {
-        t = fmin(slab_exit(x[0], u[0], d[0]), fmin(slab_exit(x[1], u[1], d[1]), slab_exit(x[2], u[2], d[2])));
-        return fmax(t, 0.0);
+        t = MINP(clamp0(slab_exit(x[0], u[0], d[0])),
+                 MINP(clamp0(slab_exit(x[1], u[1], d[1])), clamp0(slab_exit(x[2], u[2], d[2]))));
+        return t;
     }
     const double rho2 = rho2_of(x);
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
     double s;
     if (r.kind == KTUBE) {
-        t = slab_exit(x[2], u[2], d[2]);
+        t = clamp0(slab_exit(x[2], u[2], d[2]));
         s = root_rising(A0, B0, SUB(rho2, d[4]));
-        if (s >= 0.0) t = fmin(t, s);
+        if (NONNEG(s)) t = MINP(t, clamp0(s));
         if (d[0] > 0.0) {
             s = root_falling(A0, B0, SUB(rho2, d[3]));
-            if (s >= 0.0) t = fmin(t, s);
+            if (NONNEG(s)) t = MINP(t, clamp0(s));
         }
-        return fmax(t, 0.0);
+        return t;
     }
-    t = slab_exit(x[2], u[2], d[0]);
+    t = clamp0(slab_exit(x[2], u[2], d[0]));
     {
         const double ro0 = FMA(d[2], x[2], d[1]), rs = MUL(d[2], u[2]);
         s = root_rising(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-        if (s >= 0.0) t = fmin(t, s);
+        if (NONNEG(s)) t = MINP(t, clamp0(s));
     }
     if (d[11] != 0.0) {
         const double ri0 = FMA(d[4], x[2], d[3]), rs = MUL(d[4], u[2]);
         s = root_falling(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-        if (s >= 0.0) t = fmin(t, s);
+        if (NONNEG(s)) t = MINP(t, clamp0(s));
     }
-    return fmax(t, 0.0);
+    return t;
 }
 
 // --------------------------------------------------------------- safety ---
