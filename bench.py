@@ -34,20 +34,30 @@ METRIC = "tracks/s dist-to-boundary, FP32+FP64-refine vs plain FP64 on GPU; % ro
 WORKLOAD = "toy detector: tube mother r0-1000 half-z 1500 mm, 40 daughters (8 tube shells, 24 rotated boxes, " \
            "8 cones), 2^20 tracks uniform in the mother's exclusive part, isotropic, seed 1"
 
-# Nominal peaks derived from unit counts and clocks (GB300: 152 SMs, 2070 MHz
-# max SM clock): FP32 = 152 x 128 lanes x 2 flop x 2.07 GHz; FP64 = the
-# nominal 1.25 TFLOP/s of the part.  Flops count an FMA as 2.
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-PEAK_FP64_TFLOPS = 1.25
+# Nominal peaks derived from unit counts and clocks (GB300: 152 SMs at a
+# 2070 MHz maximum SM clock): FP32 = 128 FMA lanes per SM; FP64 = 2 DFMA
+# lanes per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak
+# sustained = 2 per cycle per SM).  Flops count an FMA as 2.
+SM_COUNT, SM_HZ = 152, 2.07e9
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_HZ / 1e12
+PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_HZ / 1e12
 
-# FP64 pipe instructions of one evaluation of each routine (counted from
-# shapes64.cuh): (plain FP64 instructions, square roots, divisions).
+# FP64-pipe instructions of one evaluation of each routine in shapes64.cuh
+# (comparisons run on the integer ALU and are not counted):
+# (plain FP64 instructions, square roots, divisions).
 FP64_OPS = {
-    ("out", 0): (18, 0, 6), ("out", 1): (31, 2, 3), ("out", 2): (40, 2, 3),
-    ("in", 0): (9, 0, 3), ("in", 1): (12, 1, 2), ("in", 2): (20, 2, 3),
+    ("out", 0): (30, 0, 1), ("out", 1): (23, 2, 3), ("out", 2): (33, 2, 3),
+    ("in", 0): (3, 0, 3), ("in", 1): (12, 1, 2), ("in", 2): (17, 1, 2),
 }
 FP64_TRANSFORM = 21
 FP64_BPOINT = 3
+# FP32 instructions of the filter per daughter: bounding-sphere test,
+# transform, and the bound of each kind (MUFU reciprocal / square root
+# counted as 4)
+FP32_SPHERE, FP32_TRANSFORM = 16, 18
+FP32_SHAPE = {0: 45, 1: 90, 2: 110}
+KERNEL_SOURCES = ("nav_refine.cu", "nav_refine.cuh", "shapes32.cuh", "shapes64.cuh", "nav_common.cuh",
+                  "stage.cuh", "geo_internal.h")
 
 
 def log(*a):
@@ -82,6 +92,14 @@ class Clocks:
         except Exception:
             self.proc = None
 
+    def mark(self):
+        """Samples before this point (idle pre-roll) are not counted."""
+        try:
+            self.fh.flush()
+            self.skip = sum(1 for _ in open(self.path))
+        except Exception:
+            self.skip = 0
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -92,9 +110,9 @@ class Clocks:
             self.proc.kill()
         self.fh.close()
         rows = []
-        for line in open(self.path):
+        for k, line in enumerate(open(self.path)):
             f = [c.strip() for c in line.split(",")]
-            if len(f) >= 9:
+            if len(f) >= 9 and k >= getattr(self, "skip", 0):
                 rows.append(f)
         os.unlink(self.path)
         if not rows:
@@ -131,29 +149,43 @@ def algorithmic_ops(sc, hit):
 
 
 def fp64_ops_per_track(sc, frac_mother, frac_kind, q_sqrt, q_div):
+    """Algorithmic FP64 work of the filter+refine step per track, in DFMA
+    equivalents: the mother's DistFromInside (always), the transform and
+    DistFromOutside of the winning daughter, and the boundary point."""
     def cost(key):
         a, s, d = FP64_OPS[key]
         return a + s * q_sqrt + d * q_div
 
-    ops = frac_mother * cost(("in", sc.mother_kind))
+    ops = cost(("in", sc.mother_kind))
     for k, f in frac_kind.items():
         ops += f * (FP64_TRANSFORM + cost(("out", k)))
     return ops + FP64_BPOINT
 
 
-def fp32_visits(sc, tr, sample=20000):
-    """Mean number of daughters whose bounding sphere meets the track's line
-    ahead of it (the filter's algorithmic work), on a sample."""
-    rng = np.random.default_rng(0)
-    idx = rng.choice(tr.n, min(sample, tr.n), replace=False)
-    p = np.stack([tr.x[idx], tr.y[idx], tr.z[idx]], 1)
-    d = np.stack([tr.dx[idx], tr.dy[idx], tr.dz[idx]], 1)
-    rad = sc.bounding_radius()
-    w = sc.trans[None, :, :] - p[:, None, :]
-    proj = np.einsum("nkc,nc->nk", w, d)
-    perp2 = np.einsum("nkc,nkc->nk", w, w) - proj ** 2
-    hitsph = (perp2 <= rad[None, :] ** 2) & (proj + rad[None, :] >= 0)
-    return float(hitsph.sum(1).mean())
+def fp32_ops_per_track(sc):
+    """Algorithmic FP32 work: every daughter bounded in FP32."""
+    return float(sum(FP32_SPHERE + FP32_TRANSFORM + FP32_SHAPE[int(k)] for k in sc.kinds))
+
+
+def sources_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1312_0816_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic():
+    """DRAM bytes per launch of the refine kernel from the committed ncu
+    summary, only if the kernel sources are those that were captured."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_dist_refine_toy40_2p20.json")))
+    except Exception:
+        return None, None
+    if rec.get("sources_sha") != sources_sha():
+        return None, rec.get("sources_sha")
+    return rec.get("dram_bytes_per_launch"), rec.get("sources_sha")
 
 
 def run_reference(args):
@@ -206,7 +238,7 @@ def cpu_baseline(sc, tr):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_TRACKS)
@@ -267,7 +299,8 @@ def main():
         torch.cuda.synchronize()
         if clocks:
             clocks.start()
-            time.sleep(0.3)
+            time.sleep(0.5)
+            clocks.mark()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -290,7 +323,7 @@ def main():
 
     clocks = Clocks(local)
     ms_ref, clk = timed(1, args.steps, args.warmup, clocks)
-    ms_f64, _ = timed(0, max(3, args.steps // 5), 3)
+    ms_f64, _ = timed(0, max(3, args.steps // 20), 3)
     pkg.geo_check_device_status(vol)
 
     # statistics of the refine stage
@@ -310,9 +343,8 @@ def main():
 
     hit0 = np.asarray(hit)
     fm, fk = algorithmic_ops(sc, hit0)
-    ops64 = fp64_ops_per_track(sc, fm, fk, q_sqrt, q_div)        # FP64 instructions per track
-    visits = fp32_visits(sc, tr)
-    ops32 = 16 * sc.n_daughters + visits * 70                     # FP32 instructions per track
+    ops64 = fp64_ops_per_track(sc, fm, fk, q_sqrt, q_div)        # DFMA equivalents per track
+    ops32 = fp32_ops_per_track(sc)                                # FP32 instructions per track
     hbm_bytes = 60.0
     peak_hbm = 6760.9
     try:
@@ -325,12 +357,15 @@ def main():
     t_roof = max(t_hbm, t_f64, t_f32)
     launch_s = ms_ref * 1e-3
     achieved64 = n * ops64 * 2 / launch_s / 1e12
+    traffic, sha = captured_traffic()
     roof = {"bound": "alu", "achieved": achieved64, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved64 / PEAK_FP64_TFLOPS, "traffic": None,
-            "pipe": "fp64", "peak_source": "nominal 1.25 TFLOP/s FP64 (unit counts x clock), not measured",
-            "algorithmic_per_track": {"hbm_bytes": hbm_bytes, "fp64_instr": ops64, "fp32_instr": ops32},
+            "frac": achieved64 / PEAK_FP64_TFLOPS, "traffic": traffic,
+            "pipe": "fp64",
+            "peak_source": "nominal: 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz (unit counts and clock); "
+                           "the probe measured %.3f TFLOP/s" % (2 * r_f64 / 1e12),
+            "kernel": "k_dist_refine (one launch per step)", "kernel_sources_sha": sources_sha(),
+            "algorithmic_per_track": {"hbm_bytes": hbm_bytes, "fp64_dfma_equiv": ops64, "fp32_instr": ops32},
             "t_roof_us": {"hbm": t_hbm * 1e6, "fp64": t_f64 * 1e6, "fp32": t_f32 * 1e6},
-            "roof_frac_of_time": t_roof / launch_s,
             "measured_rates": {"fp32_fma_tflops": 2 * r_f32 / 1e12, "fp64_fma_tflops": 2 * r_f64 / 1e12,
                                "fp64_div_per_s": r_div, "fp64_sqrt_per_s": r_sqrt,
                                "div_in_dfma": q_div, "sqrt_in_dfma": q_sqrt}}
@@ -341,7 +376,7 @@ def main():
     hh = torch.empty(n, dtype=torch.int32).pin_memory()
     for _ in range(2):
         pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=n)
-    k_e2e = max(3, args.steps // 5)
+    k_e2e = max(3, args.steps // 40)
     barrier()
     t0 = time.perf_counter()
     for _ in range(k_e2e):

@@ -332,11 +332,11 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
     vw.d32 = v->d32;
     vw.status = v->status;
     vw.smem64 = (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64)) <= smem_budget(dev)) ? 1 : 0;
-    // the refine kernel keeps ~29 KB of stage buffers and wants two blocks per
-    // SM, so its staged tables are capped at 80 KB; larger tables are read
+    // the refine kernel keeps ~53 KB of stage buffers and wants two blocks per
+    // SM, so its staged tables are capped at 56 KB; larger tables are read
     // through L1 from global memory
     vw.smem_refine = (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64) + sizeof(ShapeRec32)) <=
-                      std::min(smem_budget(dev) - 32 * 1024, 80 * 1024))
+                      std::min(smem_budget(dev) - 56 * 1024, 56 * 1024))
                          ? 1
                          : 0;
     *out = v;

@@ -41,6 +41,7 @@ constexpr int kCons = 128;
 constexpr int kThreads = kProd + kCons;
 
 struct Stage {
+    double pd[6][kProd];        // the tile's positions and directions (FP64)
     double res[kProd];          // FP64 value of each track's first task
     float L[kCand][kProd];      // stashed FP32 state for the producers' second half
     int j[kCand][kProd];
@@ -74,19 +75,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                                                              int32_t* __restrict__ hit,
                                                              double* __restrict__ bpoint,
                                                              int32_t* __restrict__ nref) {
+    // dynamic shared memory: the two stages, then (SMEM) the solid tables
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
     __shared__ uint64_t full[2], done[2];
-    __shared__ Stage S[2];
+    Stage* S = reinterpret_cast<Stage*>(smem_raw);
+    unsigned char* tables = smem_raw + 2 * sizeof(Stage);
     const ShapeRec32* tab32 = v.d32;
     const ShapeRec64* tab64 = v.d64;
     if (SMEM) {
         const uint32_t b32 = uint32_t(v.nd) * sizeof(ShapeRec32);
-        if (!stage_tables(smem_raw, v.d32, b32, smem_raw + b32, v.d64, uint32_t(v.nd) * sizeof(ShapeRec64), &bar,
+        if (!stage_tables(tables, v.d32, b32, tables + b32, v.d64, uint32_t(v.nd) * sizeof(ShapeRec64), &bar,
                           v.status))
             return;
-        tab32 = reinterpret_cast<const ShapeRec32*>(smem_raw);
-        tab64 = reinterpret_cast<const ShapeRec64*>(smem_raw + b32);
+        tab32 = reinterpret_cast<const ShapeRec32*>(tables);
+        tab64 = reinterpret_cast<const ShapeRec64*>(tables + b32);
     }
     const int t = threadIdx.x;
     if (t == 0) {
@@ -113,6 +116,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                     px = b.x[i]; py = b.y[i]; pz = b.z[i];
                     qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
                 }
+                st_.pd[0][t] = px; st_.pd[1][t] = py; st_.pd[2][t] = pz;
+                st_.pd[3][t] = qx; st_.pd[4][t] = qy; st_.pd[5][t] = qz;
                 RefineState rs;
                 double best = 0.0;
                 int h = -2, nev = 0;
@@ -168,8 +173,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                     }
                     rs.c.dropped = sp.dropped[t];
                     rs.Lm = sp.Lm[t];
-                    const double px = b.x[i], py = b.y[i], pz = b.z[i];
-                    const double qx = b.dx[i], qy = b.dy[i], qz = b.dz[i];
+                    const double px = sp.pd[0][t], py = sp.pd[1][t], pz = sp.pd[2][t];
+                    const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
                     double best;
                     int h, nev;
                     refine_rest(v, tab64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
@@ -185,12 +190,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
             Stage& st_ = S[k & 1];
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), v.status, healthy);
             const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
-            const int64_t base = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * kProd;
             for (int q = c; q < total; q += kCons) {
                 const int e = st_.task[q];
-                const int owner = e & (kProd - 1), jj = (e >> 8) - 1;
-                const int64_t i = base + owner;
-                st_.res[owner] = eval64(v, tab64, jj, b.x[i], b.y[i], b.z[i], b.dx[i], b.dy[i], b.dz[i]);
+                const int o = e & (kProd - 1), jj = (e >> 8) - 1;
+                st_.res[o] = eval64(v, tab64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
+                                    st_.pd[4][o], st_.pd[5][o]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);
@@ -212,14 +216,18 @@ static int grid_refine(K kernel, int64_t n, int smem, int num_sms) {
 
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms) {
-    const int smem = v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0;
+    static_assert(sizeof(Stage) % 16 == 0, "stage size keeps the tables 16-byte aligned");
+    const int stages = 2 * int(sizeof(Stage));
+    const int smem = stages + (v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0);
     if (v.smem_refine) {
         cudaError_t e = prep(k_dist_refine<true>, smem);
         if (e != cudaSuccess) return e;
         k_dist_refine<true><<<grid_refine(k_dist_refine<true>, b.n, smem, num_sms), kThreads, smem, s>>>(
             v, b, step, hit, bpoint, nref);
     } else {
-        k_dist_refine<false><<<grid_refine(k_dist_refine<false>, b.n, 0, num_sms), kThreads, 0, s>>>(
+        cudaError_t e = prep(k_dist_refine<false>, smem);
+        if (e != cudaSuccess) return e;
+        k_dist_refine<false><<<grid_refine(k_dist_refine<false>, b.n, smem, num_sms), kThreads, smem, s>>>(
             v, b, step, hit, bpoint, nref);
     }
     return cudaGetLastError();
