@@ -143,6 +143,51 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
                                      const double* dz, int64_t n, double* step, int32_t* hit,
                                      int32_t mode, int64_t chunk, void* stream);
 
+/* ---- many logical volumes in one launch -------------------------------
+ * Tracks grouped by logical volume (the "basket" of Sec. 2: particles in the
+ * same logical volume).  A batch is a list of baskets; basket k holds the
+ * tracks [offset, offset + count) of shared SoA arrays, all inside volume
+ * vols[volume]. */
+typedef struct {
+    int32_t volume;     /* index into the vols array of geo_build_batch      */
+    int32_t reserved;   /* must be 0                                          */
+    int64_t offset;     /* first track of the basket in the SoA arrays        */
+    int64_t count;      /* number of tracks (>= 0)                            */
+} geo_basket;
+
+/* tile_order: 0 = largest estimated cost first (tracks x daughters), 1 = in
+ * basket order.  blocks_per_sm: resident blocks of the persistent launch
+ * (0 = as many as fit).  Values other than these give GEO_ERR_INVALID_ARG. */
+typedef struct {
+    int32_t tile_order;
+    int32_t blocks_per_sm;
+} geo_batch_opts;
+
+typedef struct geo_batch_s* geo_batch;
+
+/* Builds a batch: copies the baskets, splits them into tiles of at most 256
+ * tracks, orders the tiles, and uploads the per-volume views, the tile list
+ * and a tile counter to the device (the batch owns them).  The volumes must
+ * stay alive while the batch is used.  All volumes must live on the current
+ * device.  Synchronises `stream`. */
+geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_basket* baskets,
+                           int32_t n_baskets, const geo_batch_opts* opts, void* stream,
+                           geo_batch* out);
+geo_status geo_destroy_batch(geo_batch b);
+
+/* Navigator step for every basket of the batch in ONE persistent launch
+ * (GEO_FP32_REFINE; answers identical to geo_dist_to_boundary per basket).
+ * x..dz: device FP64 SoA arrays of n_total tracks; step (FP64) and hit (int32)
+ * device arrays of n_total, written for the tracks of the baskets only.
+ * n_total must cover every basket (offset + count <= n_total).  Blocks claim
+ * tiles from the batch's device counter, which the call resets with an
+ * asynchronous memset on `stream` first; the call allocates nothing and does
+ * not synchronise, so it can be captured in a CUDA graph.  Calls on the same
+ * batch must not overlap on the GPU (they share the counter). */
+geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const double* y, const double* z,
+                                        const double* dx, const double* dy, const double* dz,
+                                        int64_t n_total, double* step, int32_t* hit, void* stream);
+
 /* Same as geo_dist_to_boundary in GEO_FP32_REFINE mode, and also writes, per
  * track, the number of FP64 solid evaluations the refine stage performed
  * (mother and daughters; 1000 is added when the track fell back to the full

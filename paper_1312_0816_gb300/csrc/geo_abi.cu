@@ -29,6 +29,17 @@ struct geo_volume_s {
     std::mutex ws_mu;
 };
 
+struct geo_batch_s {
+    int device = 0;
+    int32_t n_vols = 0;
+    int blocks_per_sm = 0;
+    int64_t ntiles = 0;
+    int64_t max_end = 0;
+    VolView* d_vols = nullptr;
+    BatchTile* d_tiles = nullptr;
+    unsigned int* d_words = nullptr;   // [0] tile counter, [1] status
+};
+
 namespace {
 
 constexpr double kEps32 = 5.9604644775390625e-08;  // 2^-24, unit roundoff of FP32
@@ -459,6 +470,108 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
             return cuda_status(e);
     }
     return cuda_status(cudaStreamSynchronize(s));
+}
+
+geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_basket* baskets, int32_t n_baskets,
+                           const geo_batch_opts* opts, void* stream, geo_batch* out) {
+    if (!out) return GEO_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!vols || n_vols <= 0 || n_baskets < 0 || (n_baskets > 0 && !baskets)) return GEO_ERR_INVALID_ARG;
+    const int order = opts ? opts->tile_order : 0;
+    const int bps = opts ? opts->blocks_per_sm : 0;
+    if ((order != 0 && order != 1) || bps < 0) return GEO_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
+    for (int i = 0; i < n_vols; ++i)
+        if (!vols[i] || vols[i]->device != dev) return GEO_ERR_INVALID_ARG;
+    std::vector<BatchTile> tiles;
+    std::vector<int64_t> cost;
+    int64_t max_end = 0;
+    for (int k = 0; k < n_baskets; ++k) {
+        const geo_basket& bk = baskets[k];
+        if (bk.reserved != 0 || bk.volume < 0 || bk.volume >= n_vols || bk.offset < 0 || bk.count < 0)
+            return GEO_ERR_INVALID_ARG;
+        max_end = std::max(max_end, bk.offset + bk.count);
+        for (int64_t off = 0; off < bk.count; off += 256) {
+            BatchTile t;
+            t.vol = bk.volume;
+            t.count = int32_t(std::min<int64_t>(256, bk.count - off));
+            t.base = bk.offset + off;
+            tiles.push_back(t);
+            cost.push_back(int64_t(t.count) * (vols[bk.volume]->view.nd + 1));
+        }
+    }
+    if (order == 0) {
+        std::vector<size_t> idx(tiles.size());
+        for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+        std::vector<BatchTile> sorted(tiles.size());
+        for (size_t i = 0; i < idx.size(); ++i) sorted[i] = tiles[idx[i]];
+        tiles.swap(sorted);
+    }
+    std::vector<VolView> views(n_vols);
+    for (int i = 0; i < n_vols; ++i) views[i] = vols[i]->view;
+    geo_batch b = new (std::nothrow) geo_batch_s;
+    if (!b) return GEO_ERR_OOM;
+    b->device = dev;
+    b->n_vols = n_vols;
+    b->blocks_per_sm = bps;
+    b->ntiles = int64_t(tiles.size());
+    b->max_end = max_end;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_vols, sizeof(VolView) * n_vols)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_words, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_vols, views.data(), sizeof(VolView) * n_vols, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (!tiles.empty() && (e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(),
+                                                cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+        (e = cudaMemsetAsync(b->d_words, 0, 2 * sizeof(unsigned int), s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        geo_destroy_batch(b);
+        return cuda_status(e);
+    }
+    *out = b;
+    return GEO_OK;
+}
+
+geo_status geo_destroy_batch(geo_batch b) {
+    if (!b) return GEO_OK;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    cudaFree(b->d_vols);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_words);
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    delete b;
+    return GEO_OK;
+}
+
+geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const double* y, const double* z,
+                                        const double* dx, const double* dy, const double* dz, int64_t n_total,
+                                        double* step, int32_t* hit, void* stream) {
+    if (!b) return GEO_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
+    if (dev != b->device || n_total < b->max_end) return GEO_ERR_INVALID_ARG;
+    if (b->ntiles == 0) return GEO_OK;
+    if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(z) || !is_device_ptr(dx) || !is_device_ptr(dy) ||
+        !is_device_ptr(dz) || !is_device_ptr(step) || !is_device_ptr(hit))
+        return GEO_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(b->d_words, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    BatchView bv;
+    bv.vols = b->d_vols;
+    bv.tiles = b->d_tiles;
+    bv.ntiles = b->ntiles;
+    bv.counter = b->d_words;
+    bv.status = b->d_words + 1;
+    const Basket bk{x, y, z, dx, dy, dz, n_total};
+    return cuda_status(launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, s, num_sms_of(b->device)));
 }
 
 geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const double* y, const double* z,

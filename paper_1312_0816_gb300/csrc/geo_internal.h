@@ -51,8 +51,9 @@ struct __align__(16) ShapeRec32 {
 };
 static_assert(sizeof(ShapeRec32) == 128, "ShapeRec32 layout");
 
-// Everything a kernel needs about one volume, passed by value.
-struct VolView {
+// Everything a kernel needs about one volume, passed by value (or copied
+// from a device array of views by the batched kernel).
+struct __align__(16) VolView {
     ShapeRec64 m64;            // mother (identity placement)
     ShapeRec32 m32;            // mother, FP32 (deflated for lower bounds of the exit)
     ShapeRec32 m32u;           // mother, FP32 inflated (upper bound of the exit)
@@ -77,6 +78,22 @@ struct Basket {
     int64_t n;
 };
 
+// One tile of the batched launch: up to 256 consecutive tracks of one basket.
+struct BatchTile {
+    int32_t vol;
+    int32_t count;
+    int64_t base;
+};
+static_assert(sizeof(BatchTile) == 16, "BatchTile layout");
+
+struct BatchView {
+    const VolView* vols;      // device array of per-volume views
+    const BatchTile* tiles;   // device array, in claim order
+    int64_t ntiles;
+    unsigned int* counter;    // next tile to claim (reset before every launch)
+    unsigned int* status;     // device error word of the batch
+};
+
 // device error codes written to VolView::status
 constexpr unsigned ST_TMA_TIMEOUT = 1u;
 constexpr unsigned ST_BAD_INDEX = 2u;
@@ -89,6 +106,9 @@ cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, 
                                double* bpoint, cudaStream_t s, int num_sms);
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
+cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit,
+                                int blocks_per_sm, cudaStream_t s, int num_sms);
+int batched_max_blocks_per_sm();
 cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s,
                             int num_sms);
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,

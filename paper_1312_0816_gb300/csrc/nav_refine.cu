@@ -202,6 +202,189 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched persistent launch: tiles of many logical volumes, claimed in order
+// from a device counter (largest estimated cost first when the host sorted
+// them so), with the same producer / consumer pipeline.  The tile header of a
+// stage carries a copy of the tile's volume view; the solid tables are read
+// from global memory through L1 (a table change per tile would otherwise
+// need a restage while the other stage still uses the previous one).
+struct __align__(16) TileHdr {
+    VolView vol;
+    int64_t base;
+    int count;
+    int tile;   // -1: the queue is empty
+    int vol_index;
+    int pad[3];
+};
+
+__global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
+                                                              int32_t* __restrict__ hit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t full[2], done[2];
+    Stage* S = reinterpret_cast<Stage*>(smem_raw);
+    TileHdr* H = reinterpret_cast<TileHdr*>(smem_raw + 2 * sizeof(Stage));
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    bool healthy = true;
+    if (t == 0) {
+        mbar_init(&full[0], kProd / 32);
+        mbar_init(&full[1], kProd / 32);
+        mbar_init(&done[0], kCons / 32);
+        mbar_init(&done[1], kCons / 32);
+    }
+    __syncthreads();
+    constexpr int kWords = int(sizeof(VolView) / sizeof(int4));
+
+    if (t < kProd) {
+        // ------------------------------------------------------ producers --
+        int64_t prev_base = 0;
+        int prev_count = 0;
+        for (int k = 0;; ++k) {
+            Stage& st_ = S[k & 1];
+            TileHdr& hd = H[k & 1];
+            if (t == 0) {
+                const unsigned q = atomicAdd(bv.counter, 1u);
+                if (int64_t(q) < bv.ntiles) {
+                    const BatchTile tl = bv.tiles[q];
+                    hd.tile = int(q);
+                    hd.base = tl.base;
+                    hd.count = tl.count;
+                    hd.vol_index = tl.vol;
+                } else {
+                    hd.tile = -1;
+                }
+                st_.cnt[0] = st_.cnt[1] = st_.cnt[2] = st_.cnt[3] = 0;
+            }
+            producer_barrier();
+            const int tile = hd.tile;
+            if (tile >= 0) {
+                if (t < kWords)
+                    reinterpret_cast<int4*>(&hd.vol)[t] = reinterpret_cast<const int4*>(bv.vols + hd.vol_index)[t];
+                const int64_t base = hd.base;
+                const int count = hd.count;
+                producer_barrier();
+                const VolView& v = hd.vol;
+                const bool live = t < count;
+                const int64_t i = base + t;
+                double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
+                if (live) {
+                    px = b.x[i]; py = b.y[i]; pz = b.z[i];
+                    qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
+                }
+                st_.pd[0][t] = px; st_.pd[1][t] = py; st_.pd[2][t] = pz;
+                st_.pd[3][t] = qx; st_.pd[4][t] = qy; st_.pd[5][t] = qz;
+                RefineState rs;
+                double best = 0.0;
+                int h = -2, nev = 0;
+                rs.status = 1;
+                if (live) refine_pass1(v, v.d32, v.d64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+                int task = 0, bin = -1;
+                if (rs.status == 0) {
+                    task = first_task(rs);
+                    bin = task < 0 ? 0 : 1 + v.d64[task].kind;
+                }
+                const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
+                producer_barrier();
+                int start = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < bin) start += st_.cnt[q];
+                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << 8);
+                if (rs.status == 0) {
+#pragma unroll
+                    for (int q = 0; q < kCand; ++q) {
+                        st_.L[q][t] = rs.c.L[q];
+                        st_.j[q][t] = rs.c.j[q];
+                    }
+                    st_.Lm[t] = rs.Lm;
+                    st_.dropped[t] = rs.c.dropped;
+                    st_.n[t] = rs.c.n;
+                } else {
+                    st_.n[t] = -1;
+                    if (live) store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[k & 1]);
+            if (k >= 1) {
+                const int kp = k - 1;
+                Stage& sp = S[kp & 1];
+                const VolView& vp = H[kp & 1].vol;
+                mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), bv.status, healthy);
+                if (t < prev_count && sp.n[t] >= 0) {
+                    RefineState rs;
+                    rs.status = 0;
+                    rs.c.n = sp.n[t];
+#pragma unroll
+                    for (int q = 0; q < kCand; ++q) {
+                        rs.c.L[q] = sp.L[q][t];
+                        rs.c.j[q] = sp.j[q][t];
+                    }
+                    rs.c.dropped = sp.dropped[t];
+                    rs.Lm = sp.Lm[t];
+                    const double px = sp.pd[0][t], py = sp.pd[1][t], pz = sp.pd[2][t];
+                    const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
+                    double best;
+                    int h, nev;
+                    refine_rest(vp, vp.d64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
+                    store_result(prev_base + t, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
+                }
+            }
+            if (tile < 0) break;
+            prev_base = hd.base;
+            prev_count = hd.count;
+        }
+    } else {
+        // ------------------------------------------------------ consumers --
+        const int c = t - kProd;
+        for (int k = 0;; ++k) {
+            Stage& st_ = S[k & 1];
+            TileHdr& hd = H[k & 1];
+            mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), bv.status, healthy);
+            if (!healthy || hd.tile < 0) break;
+            const VolView& v = hd.vol;
+            const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
+            for (int q = c; q < total; q += kCons) {
+                const int e = st_.task[q];
+                const int o = e & (kProd - 1), jj = (e >> 8) - 1;
+                st_.res[o] = eval64(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
+                                    st_.pd[4][o], st_.pd[5][o]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&done[k & 1]);
+        }
+    }
+}
+
+int batched_max_blocks_per_sm() {
+    static int cached = 0;
+    if (cached == 0) {
+        const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(k_dist_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched, kThreads, smem) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        cached = per_sm;
+    }
+    return cached;
+}
+
+cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
+                                cudaStream_t s, int num_sms) {
+    static_assert(sizeof(TileHdr) % 16 == 0 && sizeof(VolView) % 16 == 0, "16-byte copies");
+    const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
+    const int maxb = batched_max_blocks_per_sm();
+    const int per_sm = (blocks_per_sm <= 0 || blocks_per_sm > maxb) ? maxb : blocks_per_sm;
+    cudaError_t e = cudaFuncSetAttribute(k_dist_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_dist_batched<<<per_sm * num_sms, kThreads, smem, s>>>(bv, b, step, hit);
+    return cudaGetLastError();
+}
+
 template <typename K>
 static int grid_refine(K kernel, int64_t n, int smem, int num_sms) {
     int per_sm = 0;

@@ -38,10 +38,20 @@ class geo_build_opts(ctypes.Structure):
     _fields_ = [("voxelize", ctypes.c_int32), ("grid", ctypes.c_int32 * 3)]
 
 
+class geo_basket(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_int32), ("reserved", ctypes.c_int32), ("offset", ctypes.c_int64),
+                ("count", ctypes.c_int64)]
+
+
+class geo_batch_opts(ctypes.Structure):
+    _fields_ = [("tile_order", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 _lib = None
 EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dist_to_boundary",
            "geo_contains", "geo_safety", "geo_dist_to_boundary_host", "geo_dist_to_boundary_stats",
-           "geo_check_device_status", "geo_probe_pipe", "geo_status_string")
+           "geo_check_device_status", "geo_probe_pipe", "geo_build_batch", "geo_destroy_batch",
+           "geo_dist_to_boundary_batched", "geo_status_string")
 
 
 def library_path() -> str:
@@ -71,6 +81,10 @@ def load(build_if_stale: bool = True):
     L.geo_dist_to_boundary_stats.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, ip, vp]
     L.geo_check_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
     L.geo_probe_pipe.argtypes = [i32, i64, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    L.geo_build_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(geo_basket), i32,
+                                  ctypes.POINTER(geo_batch_opts), vp, ctypes.POINTER(vp)]
+    L.geo_destroy_batch.argtypes = [vp]
+    L.geo_dist_to_boundary_batched.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
     L.geo_status_string.argtypes = [ctypes.c_int]
     L.geo_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -280,3 +294,62 @@ def geo_probe_pipe(what: int, iters: int = 1 << 16, blocks: int = 0, stream=None
     _check(load().geo_probe_pipe(int(what), int(iters), int(blocks), ctypes.c_void_p(scratch.data_ptr()),
                                  _stream(stream), ctypes.byref(r)), "geo_probe_pipe")
     return r.value
+
+
+class Batch:
+    """Owns one geo_batch handle; keeps its volumes alive."""
+
+    def __init__(self, handle, volumes, ntracks_needed):
+        self.handle = handle
+        self.volumes = list(volumes)
+        self.ntracks_needed = ntracks_needed
+
+    def close(self):
+        if self.handle:
+            load().geo_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def geo_build_batch(volumes, baskets, tile_order: int = 0, blocks_per_sm: int = 0, stream=None) -> Batch:
+    """volumes: list of Volume; baskets: (volume index, offset, count) rows."""
+    L = load()
+    nv = len(volumes)
+    handles = (ctypes.c_void_p * max(nv, 1))(*[v.handle for v in volumes])
+    rows = np.asarray(baskets, dtype=np.int64).reshape(-1, 3)
+    arr = (geo_basket * max(len(rows), 1))()
+    for k, (v, off, cnt) in enumerate(rows):
+        arr[k].volume, arr[k].reserved, arr[k].offset, arr[k].count = int(v), 0, int(off), int(cnt)
+    opts = geo_batch_opts()
+    opts.tile_order, opts.blocks_per_sm = int(tile_order), int(blocks_per_sm)
+    out = ctypes.c_void_p()
+    _check(L.geo_build_batch(handles, nv, arr, len(rows), ctypes.byref(opts), _stream(stream), ctypes.byref(out)),
+           "geo_build_batch")
+    need = int((rows[:, 1] + rows[:, 2]).max()) if len(rows) else 0
+    return Batch(out, volumes, need)
+
+
+def geo_destroy_batch(batch: Batch):
+    batch.close()
+
+
+def geo_dist_to_boundary_batched(batch: Batch, x, y, z, dx, dy, dz, step=None, hit=None, stream=None):
+    """One persistent launch over every basket of the batch (FP32+refine)."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    if step is None:
+        step = torch.empty(n, dtype=f64, device=x.device)
+    if hit is None:
+        hit = torch.empty(n, dtype=torch.int32, device=x.device)
+    args = [_dev(a, f64, n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    _check(load().geo_dist_to_boundary_batched(batch.handle, *args, n, _dev(step, f64, n, "step"),
+                                               _dev(hit, torch.int32, n, "hit"), _stream(stream)),
+           "geo_dist_to_boundary_batched")
+    return step, hit

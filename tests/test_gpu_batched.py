@@ -1,0 +1,128 @@
+"""The batched persistent launch (many logical volumes, uneven baskets, one
+launch): answers identical to one geo_dist_to_boundary call per basket and to
+the oracle; capturable in a CUDA graph."""
+import numpy as np
+import pytest
+
+from helpers import tie_band
+from paper_1312_0816_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1312_0816_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.load()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    vols, baskets = scenes.batched64(seed=3, n_volumes=12, total=60000)
+    tr, rows = scenes.batched_tracks(vols, baskets, 3)
+    return vols, tr, rows
+
+
+def dev(tr):
+    return [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in tr.fields()]
+
+
+def per_basket(g, vols, volh, tr, rows, mode):
+    step = np.empty(tr.n)
+    hit = np.empty(tr.n, dtype=np.int32)
+    for v, off, cnt in rows:
+        sub = tr.slice(int(off), int(off + cnt))
+        s, h = g.geo_dist_to_boundary(volh[int(v)], *dev(sub), mode=mode)
+        step[off:off + cnt] = s.cpu().numpy()
+        hit[off:off + cnt] = h.cpu().numpy()
+    return step, hit
+
+
+@pytest.mark.parametrize("order,bps", [(0, 0), (1, 0), (0, 1)])
+def test_batched_equals_per_basket(g, small_batch, order, bps):
+    vols, tr, rows = small_batch
+    volh = [g.geo_build_volume(v) for v in vols]
+    batch = g.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps)
+    s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
+    torch.cuda.synchronize()
+    s, h = s.cpu().numpy(), h.cpu().numpy()
+    s64, h64 = per_basket(g, vols, volh, tr, rows, 0)
+    assert np.array_equal(h, h64)
+    assert np.array_equal(s.view(np.int64), s64.view(np.int64))
+
+
+def test_batched_oracle_parity(g, orc, small_batch):
+    vols, tr, rows = small_batch
+    volh = [g.geo_build_volume(v) for v in vols]
+    batch = g.geo_build_batch(volh, rows)
+    s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
+    torch.cuda.synchronize()
+    s, h = s.cpu().numpy(), h.cpu().numpy()
+    for v, off, cnt in rows:
+        sub = tr.slice(int(off), int(off + cnt))
+        ref = orc.navigate(vols[int(v)], sub, nthreads=8)
+        ex = tie_band(ref) | (ref["err"] > 1e-9)
+        assert np.max(np.abs(s[off:off + cnt] - ref["step"])[~ex], initial=0.0) <= 1e-9
+        assert np.array_equal(h[off:off + cnt][~ex], ref["hit"][~ex])
+
+
+def test_batched_graph_replay(g, small_batch):
+    vols, tr, rows = small_batch
+    volh = [g.geo_build_volume(v) for v in vols]
+    batch = g.geo_build_batch(volh, rows)
+    x = dev(tr)
+    step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
+    hit = torch.empty(tr.n, dtype=torch.int32, device="cuda")
+    g.geo_dist_to_boundary_batched(batch, *x, step=step, hit=hit)   # warm-up outside capture
+    torch.cuda.synchronize()
+    ref_s, ref_h = step.clone(), hit.clone()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            g.geo_dist_to_boundary_batched(batch, *x, step=step, hit=hit)
+    for _ in range(3):
+        step.fill_(-1.0)
+        hit.fill_(99)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(step, ref_s) and torch.equal(hit, ref_h)
+
+
+def test_batched_rejects_short_arrays(g, small_batch):
+    vols, tr, rows = small_batch
+    volh = [g.geo_build_volume(v) for v in vols]
+    batch = g.geo_build_batch(volh, rows)
+    short = [f[:-1] for f in dev(tr)]
+    with pytest.raises(g.GeoError):
+        g.geo_dist_to_boundary_batched(batch, *short)
+
+
+def test_full_batched_workload_sampled(g, orc):
+    """64 volumes, ~530 baskets of 16..65536 tracks, 2^22 tracks: one launch,
+    bitwise equal to the per-basket FP64 calls on sampled baskets, oracle on a
+    sample of tracks."""
+    vols, baskets = scenes.batched64(seed=3)
+    tr, rows = scenes.batched_tracks(vols, baskets, 3)
+    volh = [g.geo_build_volume(v) for v in vols]
+    batch = g.geo_build_batch(volh, rows)
+    s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
+    torch.cuda.synchronize()
+    s, h = s.cpu().numpy(), h.cpu().numpy()
+    rng = np.random.default_rng(1)
+    pick = rng.choice(len(rows), 40, replace=False)
+    for k in pick:
+        v, off, cnt = rows[k]
+        sub = tr.slice(int(off), int(off + cnt))
+        s64, h64 = g.geo_dist_to_boundary(volh[int(v)], *dev(sub), mode=0)
+        assert np.array_equal(h[off:off + cnt], h64.cpu().numpy())
+        assert np.array_equal(s[off:off + cnt].view(np.int64), s64.cpu().numpy().view(np.int64))
+        n = min(int(cnt), 500)
+        ref = orc.navigate(vols[int(v)], sub.slice(0, n), nthreads=8)
+        ex = tie_band(ref) | (ref["err"] > 1e-9)
+        assert np.max(np.abs(s[off:off + n] - ref["step"])[~ex], initial=0.0) <= 1e-9
