@@ -188,6 +188,33 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
                                         const double* dx, const double* dy, const double* dz,
                                         int64_t n_total, double* step, int32_t* hit, void* stream);
 
+/* For callers that must not allocate device memory while they run (an
+ * application whose allocator owns all device memory, a real-time loop that
+ * forbids allocation after start-up, code recorded under global-mode stream
+ * capture).  The paper has no counterpart: this is a service of the library.
+ * Same step and answers as geo_build_batch + geo_dist_to_boundary_batched
+ * (GEO_FP32_REFINE), but this call allocates nothing: the tile list, the
+ * volume views, the tile counter and the status word are kept in a fixed
+ * array of device memory owned by the library (about 0.55 MB, present on
+ * every device that loads it until the process exits).  Limits: at most 64
+ * volumes and 32768 tiles of 256 tracks (about 8.4 M tracks) per call; larger
+ * requests return GEO_ERR_INVALID_ARG.  vols: volumes built earlier with
+ * geo_build_volume, on the current device.  baskets: HOST array, as for
+ * geo_build_batch.  x..dz, step, hit: device arrays as for
+ * geo_dist_to_boundary_batched, n_total covering every basket.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same array, so calls that overlap on the GPU (on
+ * different streams, or from different host threads) race: serialise them.
+ * The counter and status word are cleared by each call; the rest keeps the
+ * last call's contents. */
+geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vols, int32_t n_vols,
+                                                const geo_basket* baskets, int32_t n_baskets,
+                                                const double* x, const double* y, const double* z,
+                                                const double* dx, const double* dy, const double* dz,
+                                                int64_t n_total, double* step, int32_t* hit,
+                                                void* stream);
+
 /* Same as geo_dist_to_boundary in GEO_FP32_REFINE mode, and also writes, per
  * track, the number of FP64 solid evaluations the refine stage performed
  * (mother and daughters; 1000 is added when the track fell back to the full

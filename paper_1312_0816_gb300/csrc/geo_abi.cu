@@ -264,6 +264,12 @@ geo_status check_basket(const double* x, const double* y, const double* z, int64
 // only done in checked mode).
 }  // namespace
 
+namespace geonav {
+const VolView* volume_view(geo_volume v) { return v ? &v->view : nullptr; }
+int volume_device(geo_volume v) { return v ? v->device : -1; }
+int sm_count(int device) { return num_sms_of(device); }
+}  // namespace geonav
+
 extern "C" {
 
 const char* geo_status_string(geo_status s) {

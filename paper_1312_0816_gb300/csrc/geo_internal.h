@@ -114,4 +114,9 @@ cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, c
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
                           int num_sms);
 
+// accessors of the opaque volume handle (defined in geo_abi.cu)
+const VolView* volume_view(geo_volume v);
+int volume_device(geo_volume v);
+int sm_count(int device);
+
 }  // namespace geonav

@@ -51,7 +51,7 @@ _lib = None
 EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dist_to_boundary",
            "geo_contains", "geo_safety", "geo_dist_to_boundary_host", "geo_dist_to_boundary_stats",
            "geo_check_device_status", "geo_probe_pipe", "geo_build_batch", "geo_destroy_batch",
-           "geo_dist_to_boundary_batched", "geo_status_string")
+           "geo_dist_to_boundary_batched", "geo_dist_to_boundary_batched_noalloc", "geo_status_string")
 
 
 def library_path() -> str:
@@ -85,6 +85,8 @@ def load(build_if_stale: bool = True):
                                   ctypes.POINTER(geo_batch_opts), vp, ctypes.POINTER(vp)]
     L.geo_destroy_batch.argtypes = [vp]
     L.geo_dist_to_boundary_batched.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
+    L.geo_dist_to_boundary_batched_noalloc.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(geo_basket), i32,
+                                                       dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
     L.geo_status_string.argtypes = [ctypes.c_int]
     L.geo_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -352,4 +354,26 @@ def geo_dist_to_boundary_batched(batch: Batch, x, y, z, dx, dy, dz, step=None, h
     _check(load().geo_dist_to_boundary_batched(batch.handle, *args, n, _dev(step, f64, n, "step"),
                                                _dev(hit, torch.int32, n, "hit"), _stream(stream)),
            "geo_dist_to_boundary_batched")
+    return step, hit
+
+
+def geo_dist_to_boundary_batched_noalloc(volumes, baskets, x, y, z, dx, dy, dz, step, hit, stream=None):
+    """Batched step without any device allocation by the call (the library's
+    fixed scratch array is used instead): for callers that cannot let a
+    library allocate while they run.  step / hit must be preallocated CUDA
+    tensors.  Calls sharing the scratch must not overlap on the GPU."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    nv = len(volumes)
+    handles = (ctypes.c_void_p * max(nv, 1))(*[v.handle for v in volumes])
+    rows = np.asarray(baskets, dtype=np.int64).reshape(-1, 3)
+    arr = (geo_basket * max(len(rows), 1))()
+    for k, (v, off, cnt) in enumerate(rows):
+        arr[k].volume, arr[k].reserved, arr[k].offset, arr[k].count = int(v), 0, int(off), int(cnt)
+    args = [_dev(a, f64, n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    _check(load().geo_dist_to_boundary_batched_noalloc(handles, nv, arr, len(rows), *args, n,
+                                                       _dev(step, f64, n, "step"), _dev(hit, torch.int32, n, "hit"),
+                                                       _stream(stream)), "geo_dist_to_boundary_batched_noalloc")
     return step, hit
