@@ -235,6 +235,65 @@ def cpu_baseline(sc, tr):
             "single_thread_value": 8192 / dt1}
 
 
+def batched_leg(pkg, scenes, rank, steps):
+    """64 logical volumes (4..200 daughters), 561 baskets of 16..65536 tracks
+    (2^22 tracks): one persistent launch per step, replayed as a CUDA graph,
+    schedule chosen by the autotuner."""
+    import torch
+
+    from paper_1312_0816_gb300 import autotune
+
+    vols, baskets = scenes.batched64(seed=3)
+    tr, rows = scenes.batched_tracks(vols, baskets, 3 + 1000 * rank)
+    volh = [pkg.geo_build_volume(v) for v in vols]
+    x = [torch.from_numpy(f).cuda() for f in tr.fields()]
+    step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
+    hit = torch.empty(tr.n, dtype=torch.int32, device="cuda")
+    order, bps, timings = autotune.tune_batch(volh, rows, x, step, hit)
+    batch = pkg.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps)
+    ms = autotune.time_graph(batch, x, step, hit, reps=steps)
+    batch.close()
+    return {"workload": "64 volumes (box/tube mothers, 4..200 mixed daughters), %d baskets of 16..65536 "
+                        "tracks, %d tracks, FP32+refine, one persistent launch per step as a CUDA graph"
+                        % (len(rows), tr.n),
+            "value": tr.n / (ms * 1e-3), "unit": "tracks/s", "ms_per_launch": ms, "steps": steps,
+            "schedule": {"tile_order": order, "blocks_per_sm": bps}, "autotune_ms": timings}
+
+
+def voxel_leg(pkg, scenes, rank, steps):
+    """512 daughters (boxes and tubes, rotated, on an 8x8x8 grid) in a box
+    mother with the uniform-grid candidate list; 2^24 tracks; FP32+refine vs
+    plain FP64, both walking the grid."""
+    import torch
+
+    sc = scenes.grid512(5)
+    tr = scenes.sample_tracks(sc, 1 << 24, 5 + 1000 * rank)
+    vol = pkg.geo_build_volume(sc, voxelize=True)
+    x = [torch.from_numpy(f).cuda() for f in tr.fields()]
+    step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
+    hit = torch.empty(tr.n, dtype=torch.int32, device="cuda")
+    out = {}
+    for mode, name, k in ((1, "fp32_refine", steps), (0, "fp64_plain", max(3, steps // 4))):
+        for _ in range(3):
+            pkg.geo_dist_to_boundary(vol, *x, mode=mode, step=step, hit=hit)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            pkg.geo_dist_to_boundary(vol, *x, mode=mode, step=step, hit=hit)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        out[name] = {"value": tr.n / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "steps": k}
+    info = pkg.geo_volume_info(vol)
+    vol.close()
+    out["workload"] = ("box mother half 800 mm, 512 rotated boxes/tubes on an 8x8x8 grid, uniform grid %s, "
+                       "2^24 tracks (inputs 805 MB > L2)" % "x".join(str(g) for g in info["grid"]))
+    out["speedup_of_refine"] = out["fp64_plain"]["ms_per_step"] / out["fp32_refine"]["ms_per_step"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +302,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_TRACKS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-voxel", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -383,6 +444,9 @@ def main():
         pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=n)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e)
 
+    batched = None if args.no_batched else batched_leg(pkg, scenes, rank, max(10, args.steps // 40))
+    voxel = None if args.no_voxel else voxel_leg(pkg, scenes, rank, max(5, args.steps // 200))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, tr)
@@ -405,6 +469,8 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "batched": batched,
+            "voxel_512": voxel,
         }
         print(json.dumps(line), flush=True)
     vol.close()

@@ -229,6 +229,74 @@ double inflation(const geo_placed_shape& s, double S) {
     return d;
 }
 
+geo_status cuda_status(cudaError_t e);
+
+// Uniform grid over the mother's bounding box; every cell lists (CSR) the
+// daughters whose world bounding box, grown by their FP32 inflation and by
+// 1e-3 of a cell, overlaps it.  The growth keeps the lists conservative for
+// an FP32 grid walk whose rounding can cut a corner between two cells.
+geo_status build_voxels(const geo_placed_shape& m, const geo_placed_shape* d, int nd, double S,
+                        const geo_build_opts* opts, cudaStream_t s, geo_volume v) {
+    double half[3];
+    const double* p = m.p;
+    if (m.kind == GEO_BOX) { half[0] = p[0]; half[1] = p[1]; half[2] = p[2]; }
+    else if (m.kind == GEO_TUBE) { half[0] = half[1] = p[1]; half[2] = p[2]; }
+    else { half[0] = half[1] = std::max(p[2], p[4]); half[2] = p[0]; }
+    int g[3];
+    const int gauto = std::max(1, std::min(64, int(std::lround(2.0 * std::cbrt(double(std::max(nd, 1)))))));
+    for (int k = 0; k < 3; ++k) g[k] = opts->grid[k] > 0 ? opts->grid[k] : gauto;
+    const int64_t ncells = int64_t(g[0]) * g[1] * g[2];
+    if (ncells > (int64_t(1) << 24)) return GEO_ERR_INVALID_ARG;
+    VolView& vw = v->view;
+    for (int k = 0; k < 3; ++k) {
+        vw.grid[k] = g[k];
+        vw.lo[k] = -half[k];
+        vw.cell[k] = 2.0 * half[k] / g[k];
+        vw.inv_cell[k] = 1.0 / vw.cell[k];
+    }
+    std::vector<std::vector<int32_t>> lists(static_cast<size_t>(ncells));
+    for (int j = 0; j < nd; ++j) {
+        const geo_placed_shape& sh = d[j];
+        double he[3];
+        const double* q = sh.p;
+        if (sh.kind == GEO_BOX) { he[0] = q[0]; he[1] = q[1]; he[2] = q[2]; }
+        else if (sh.kind == GEO_TUBE) { he[0] = he[1] = q[1]; he[2] = q[2]; }
+        else { he[0] = he[1] = std::max(q[2], q[4]); he[2] = q[0]; }
+        int i0[3], i1[3];
+        for (int k = 0; k < 3; ++k) {
+            const double ext = std::fabs(sh.rot[3 * k]) * he[0] + std::fabs(sh.rot[3 * k + 1]) * he[1] +
+                               std::fabs(sh.rot[3 * k + 2]) * he[2];
+            const double grow = inflation(sh, S) + 1e-3 * vw.cell[k] + 1e-9 * (1.0 + std::fabs(sh.trans[k]));
+            const double a = (sh.trans[k] - ext - grow - vw.lo[k]) * vw.inv_cell[k];
+            const double b = (sh.trans[k] + ext + grow - vw.lo[k]) * vw.inv_cell[k];
+            i0[k] = int(std::max(0.0, std::min(double(g[k] - 1), std::floor(a))));
+            i1[k] = int(std::max(0.0, std::min(double(g[k] - 1), std::floor(b))));
+        }
+        for (int a = i0[0]; a <= i1[0]; ++a)
+            for (int b = i0[1]; b <= i1[1]; ++b)
+                for (int c = i0[2]; c <= i1[2]; ++c) lists[(size_t(a) * g[1] + b) * g[2] + c].push_back(j);
+    }
+    std::vector<int32_t> off(static_cast<size_t>(ncells) + 1, 0), ids;
+    for (int64_t c = 0; c < ncells; ++c) {
+        off[c + 1] = off[c] + int32_t(lists[c].size());
+        ids.insert(ids.end(), lists[c].begin(), lists[c].end());
+    }
+    if (ids.empty()) ids.push_back(0);
+    cudaError_t e;
+    if ((e = cudaMalloc(&v->vox_off, sizeof(int32_t) * off.size())) != cudaSuccess ||
+        (e = cudaMalloc(&v->vox_ids, sizeof(int32_t) * ids.size())) != cudaSuccess ||
+        (e = cudaMemcpyAsync(v->vox_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(v->vox_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_status(e);
+    vw.vox_off = v->vox_off;
+    vw.vox_ids = v->vox_ids;
+    vw.voxelized = 1;
+    return GEO_OK;
+}
+
 geo_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return GEO_OK;
     if (e == cudaErrorMemoryAllocation) return GEO_ERR_OOM;
@@ -295,7 +363,10 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
     if (st != GEO_OK) return st;
     for (int j = 0; j < n_daughters; ++j)
         if ((st = check_shape(daughters[j], false)) != GEO_OK) return st;
-    if (opts && opts->voxelize) return GEO_ERR_UNSUPPORTED;   // voxel grid: see nav_voxel.cu
+    if (opts && opts->voxelize) {
+        for (int k = 0; k < 3; ++k)
+            if (opts->grid[k] < 0 || opts->grid[k] > 256) return GEO_ERR_INVALID_ARG;
+    }
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0;
@@ -348,6 +419,13 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
     vw.d64 = v->d64;
     vw.d32 = v->d32;
     vw.status = v->status;
+    if (opts && opts->voxelize) {
+        st = build_voxels(*mother, daughters, n_daughters, S, opts, s, v);
+        if (st != GEO_OK) {
+            geo_destroy_volume(v);
+            return st;
+        }
+    }
     vw.smem64 = (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64)) <= smem_budget(dev)) ? 1 : 0;
     // the refine kernel keeps ~53 KB of stage buffers and wants two blocks per
     // SM, so its staged tables are capped at 56 KB; larger tables are read

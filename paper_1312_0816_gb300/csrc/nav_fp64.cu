@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(256) k_dist_fp64(VolView v, Basket b, double* 
         } else if (!contains64(v.m64, p)) {
             best = 0.0;
             h = -2;
+        } else if (v.voxelized) {
+            nav_vox64(v, tab, px, py, pz, qx, qy, qz, best, h);
         } else {
             nav_all64(v.m64, tab, v.nd, px, py, pz, qx, qy, qz, best, h);
         }

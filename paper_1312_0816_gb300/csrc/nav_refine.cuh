@@ -47,6 +47,91 @@ __device__ __forceinline__ float lower_bound(float t, float delta, float inv_dn)
     return t - (16.f * kEps32f * fabsf(t) + delta * inv_dn);
 }
 
+// FP32 lower bound of one daughter's DistFromOutside (bounding-sphere test,
+// transform in the frame shifted to the closest approach, inflated solid),
+// inserted into the candidate list when it can beat the mother's exit.
+__device__ __forceinline__ void bound_daughter(const ShapeRec32& r, int j, const float* p32, const float* d32,
+                                               float inv_dd, float inv_dn, float Um, Cands& c) {
+    const float w0 = p32[0] - r.t[0], w1 = p32[1] - r.t[1], w2 = p32[2] - r.t[2];
+    const float s0 = -fmaf(w0, d32[0], fmaf(w1, d32[1], w2 * d32[2])) * inv_dd;
+    const float q0 = fmaf(s0, d32[0], w0), q1 = fmaf(s0, d32[1], w1), q2 = fmaf(s0, d32[2], w2);
+    const float perp2 = fmaf(q0, q0, fmaf(q1, q1, q2 * q2));
+    if (perp2 > r.brad * r.brad) return;
+    const float half = r.brad * inv_dn;
+    if (s0 + half < 0.f || s0 - half > Um) return;
+    float x[3], u[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        x[k] = fmaf(r.R[6 + k], q2, fmaf(r.R[3 + k], q1, r.R[k] * q0));
+        u[k] = fmaf(r.R[6 + k], d32[2], fmaf(r.R[3 + k], d32[1], r.R[k] * d32[0]));
+    }
+    const float tp = enter32(r, x, u, -s0);
+    if (!(tp < f_inf())) return;
+    const float L = lower_bound(s0 + tp, r.delta, inv_dn);
+    if (L > Um) return;
+    // a daughter met again (grid walk) is already in the list with this bound
+#pragma unroll
+    for (int k = 0; k < kCand; ++k)
+        if (k < c.n && c.j[k] == j) return;
+    cand_insert(c, L, j);
+}
+
+// Walk of the uniform grid (3D-DDA) along the FP32 ray from its start to the
+// parameter tend, calling visit(j) for every daughter listed in every cell
+// entered.  At most gx + gy + gz + 3 cells.
+template <class F>
+__device__ __forceinline__ void vox_walk32(const VolView& v, const float* p, const float* d, float tend,
+                                           F&& visit) {
+    // per axis: cell index, step direction, next boundary parameter, increment
+    int i0, i1, i2, s0, s1, s2;
+    float m0, m1, m2, e0, e1, e2;
+    auto setup = [&](int k, int& ii, int& st, float& tm, float& te) {
+        const float lo = float(v.lo[k]), cell = float(v.cell[k]);
+        const int g = v.grid[k];
+        ii = int(floorf((p[k] - lo) * float(v.inv_cell[k])));
+        ii = ii < 0 ? 0 : (ii >= g ? g - 1 : ii);
+        if (d[k] > 0.f) {
+            st = 1;
+            tm = (fmaf(float(ii + 1), cell, lo) - p[k]) / d[k];
+            te = cell / d[k];
+        } else if (d[k] < 0.f) {
+            st = -1;
+            tm = (fmaf(float(ii), cell, lo) - p[k]) / d[k];
+            te = -cell / d[k];
+        } else {
+            st = 0;
+            tm = f_inf();
+            te = f_inf();
+        }
+    };
+    setup(0, i0, s0, m0, e0);
+    setup(1, i1, s1, m1, e1);
+    setup(2, i2, s2, m2, e2);
+    const int g0 = v.grid[0], g1 = v.grid[1], g2 = v.grid[2];
+    const int maxit = g0 + g1 + g2 + 3;
+    for (int it = 0; it < maxit; ++it) {
+        const int c = (i0 * g1 + i1) * g2 + i2;
+        const int q1 = v.vox_off[c + 1];
+        for (int q = v.vox_off[c]; q < q1; ++q) visit(v.vox_ids[q]);
+        if (m0 <= m1 && m0 <= m2) {
+            if (!(m0 <= tend)) break;
+            i0 += s0;
+            if (i0 < 0 || i0 >= g0) break;
+            m0 += e0;
+        } else if (m1 <= m2) {
+            if (!(m1 <= tend)) break;
+            i1 += s1;
+            if (i1 < 0 || i1 >= g1) break;
+            m1 += e1;
+        } else {
+            if (!(m2 <= tend)) break;
+            i2 += s2;
+            if (i2 < 0 || i2 >= g2) break;
+            m2 += e2;
+        }
+    }
+}
+
 // State of one track between the FP32 pass and the FP64 refinement.
 struct RefineState {
     Cands c;
@@ -106,26 +191,17 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
     bool dummy;
     const float e_hi = exit32(v.m32u, p32, d32, dummy);
     const float Um = e_hi + 16.f * kEps32f * e_hi + v.m32u.delta * inv_dn;
-    for (int j = 0; j < v.nd; ++j) {
-        const ShapeRec32& r = tab32[j];
-        const float w0 = p32[0] - r.t[0], w1 = p32[1] - r.t[1], w2 = p32[2] - r.t[2];
-        const float s0 = -fmaf(w0, d32[0], fmaf(w1, d32[1], w2 * d32[2])) * inv_dd;
-        const float q0 = fmaf(s0, d32[0], w0), q1 = fmaf(s0, d32[1], w1), q2 = fmaf(s0, d32[2], w2);
-        const float perp2 = fmaf(q0, q0, fmaf(q1, q1, q2 * q2));
-        if (perp2 > r.brad * r.brad) continue;
-        const float half = r.brad * inv_dn;
-        if (s0 + half < 0.f || s0 - half > Um) continue;
-        float x[3], u[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            x[k] = fmaf(r.R[6 + k], q2, fmaf(r.R[3 + k], q1, r.R[k] * q0));
-            u[k] = fmaf(r.R[6 + k], d32[2], fmaf(r.R[3 + k], d32[1], r.R[k] * d32[0]));
-        }
-        const float tp = enter32(r, x, u, -s0);
-        if (!(tp < f_inf())) continue;
-        const float L = lower_bound(s0 + tp, r.delta, inv_dn);
-        if (L > Um) continue;
-        cand_insert(st.c, L, j);
+    if (!v.voxelized) {
+        for (int j = 0; j < v.nd; ++j) bound_daughter(tab32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
+    } else {
+        // only daughters listed in the cells the track crosses before the
+        // mother's exit (upper bound Um); a 4-entry mailbox skips repeats
+        int mb0 = -1, mb1 = -1, mb2 = -1, mb3 = -1;
+        vox_walk32(v, p32, d32, Um, [&](int j) {
+            if (j == mb0 || j == mb1 || j == mb2 || j == mb3) return;
+            mb3 = mb2; mb2 = mb1; mb1 = mb0; mb0 = j;
+            bound_daughter(tab32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
+        });
     }
     st.status = 0;
 }

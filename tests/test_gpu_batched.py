@@ -126,3 +126,26 @@ def test_full_batched_workload_sampled(g, orc):
         ref = orc.navigate(vols[int(v)], sub.slice(0, n), nthreads=8)
         ex = tie_band(ref) | (ref["err"] > 1e-9)
         assert np.max(np.abs(s[off:off + n] - ref["step"])[~ex], initial=0.0) <= 1e-9
+
+
+def test_autotuner_picks_a_candidate_and_caches(g, small_batch, tmp_path, monkeypatch):
+    from paper_1312_0816_gb300 import autotune
+
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    vols, tr, rows = small_batch
+    volh = [g.geo_build_volume(v) for v in vols]
+    x = dev(tr)
+    step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
+    hit = torch.empty(tr.n, dtype=torch.int32, device="cuda")
+    order, bps, timings = autotune.tune_batch(volh, rows, x, step, hit, reps=3)
+    assert (order, bps) in autotune.CANDIDATES
+    assert len(timings) == len(autotune.CANDIDATES) and all(t > 0 for t in timings.values())
+    again = autotune.tune_batch(volh, rows, x, step, hit, reps=3)
+    assert again[:2] == (order, bps)
+    # the tuned schedule gives the same answers
+    batch = g.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps)
+    s, h = g.geo_dist_to_boundary_batched(batch, *x)
+    ref = g.geo_build_batch(volh, rows)
+    s0, h0 = g.geo_dist_to_boundary_batched(ref, *x)
+    torch.cuda.synchronize()
+    assert torch.equal(s, s0) and torch.equal(h, h0)
