@@ -65,10 +65,9 @@ def log(*a):
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1312_0816_gb300 import replicas
+
+    return replicas.env()
 
 
 class Clocks:
@@ -316,21 +315,15 @@ def main():
     import paper_1312_0816_gb300 as pkg
     from paper_1312_0816_gb300 import scenes
 
+    from paper_1312_0816_gb300 import replicas
+
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    if ws > 1:
-        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if ws > 1:
-            tdist.barrier()
+    replicas.init("nccl", device=torch.device("cuda", local))
+    barrier = replicas.barrier
 
     def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, device="cuda")
 
     sc = scenes.toy40(1)
     n = args.n

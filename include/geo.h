@@ -215,6 +215,29 @@ geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vols, int32_t 
                                                 int64_t n_total, double* step, int32_t* hit,
                                                 void* stream);
 
+/* ---- gradients of the step (the paper has no gradients; this supports a
+ * differentiable use of the navigator) ----------------------------------
+ * For loss L with dL/dstep = grad_step (device FP64[n]) and the forward
+ * answers hit (device int32[n], from geo_dist_to_boundary on the same
+ * inputs, either mode), writes
+ *   grad_p (device FP64[3n], SoA x|y|z blocks)  dL/dposition per track,
+ *   grad_d (device FP64[3n], SoA)               dL/ddirection per track,
+ *   grad_trans (device FP64[3*nd] or NULL)      dL/dt_j summed over tracks,
+ *   grad_params (device FP64[5*(nd+1)] or NULL) dL/dp_j[0..4] summed over
+ *       tracks, daughters first then the mother's parameters at 5*nd,
+ * by the implicit-function rule on the surface the winning solid's FP64
+ * routine crossed.  Tracks without a defined surface (inside a daughter,
+ * outside the mother, invalid) get 0; so does a hit index >= nd, which also
+ * sets the volume's device status word (geo_check_device_status).  The sums over tracks are deterministic
+ * (fixed-order two-pass reduction) and need a caller-provided device
+ * workspace of geo_adjoint_workspace_size() bytes. */
+geo_status geo_adjoint_workspace_size(geo_volume v, int64_t n, uint64_t* bytes);
+geo_status geo_dist_to_boundary_adjoint(geo_volume v, const double* x, const double* y, const double* z,
+                                        const double* dx, const double* dy, const double* dz, int64_t n,
+                                        const int32_t* hit, const double* grad_step, double* grad_p,
+                                        double* grad_d, double* grad_trans, double* grad_params,
+                                        void* workspace, uint64_t workspace_bytes, void* stream);
+
 /* Same as geo_dist_to_boundary in GEO_FP32_REFINE mode, and also writes, per
  * track, the number of FP64 solid evaluations the refine stage performed
  * (mother and daughters; 1000 is added when the track fell back to the full

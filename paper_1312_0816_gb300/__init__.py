@@ -7,4 +7,5 @@ from .geonav import (GEO_BOX, GEO_CONE, GEO_FP32_REFINE, GEO_FP64, GEO_TUBE, Geo
                      geo_build_volume, geo_contains, geo_destroy_volume, geo_dist_to_boundary,
                      geo_dist_to_boundary_host, geo_dist_to_boundary_stats, geo_check_device_status, geo_probe_pipe,
                      geo_safety, geo_status_string, geo_volume_info, load, Batch, geo_build_batch,
-                     geo_destroy_batch, geo_dist_to_boundary_batched, geo_dist_to_boundary_batched_noalloc)
+                     geo_destroy_batch, geo_dist_to_boundary_batched, geo_dist_to_boundary_batched_noalloc,
+                     geo_adjoint_workspace_size, geo_dist_to_boundary_adjoint)

@@ -1,0 +1,200 @@
+// adjoint.cu -- gradients of the navigator step (not in the paper: the
+// differentiable use of the step).
+//
+// For a track whose step s ends on the surface F(x; theta) = 0 of the winning
+// solid (F > 0 outside the solid), with local point x* = x + s u, local
+// gradient g = grad_x F(x*) and den = g . u, the implicit-function rule gives
+//     ds/dp = -R g / den,  ds/dd = -s R g / den,  ds/dt = +R g / den,
+//     ds/dtheta = -(dF/dtheta)(x*) / den
+// (R the solid's rotation, t its translation, theta its shape parameters; the
+// mother has R = 1 and no translation).  The surface is the one the FP64
+// routine of the forward step crossed (same arithmetic, so the same step).
+// Where the surface is undefined (start inside a daughter, outside the mother,
+// invalid input) or den = 0, the gradients are 0; a hit index >= nd (not one
+// the forward step of this volume writes) also gives 0 and sets ST_BAD_INDEX
+// in the volume's device status word.
+//
+// Geometry gradients are sums over tracks; they are reduced deterministically:
+// every block owns a fixed set of tiles and adds its tracks in index order into
+// per-block partials (workspace), then one pass adds the partials in block
+// order.
+#include <cuda_runtime.h>
+
+#include "geo_internal.h"
+#include "launch.cuh"
+#include "nav_common.cuh"
+#include "shapes64.cuh"
+
+namespace geonav {
+
+constexpr int kAdjTile = 256;
+constexpr int kGeo = 8;   // per owner: 3 translation + 5 shape-parameter components
+
+// g = grad F at local x* on surface `face` of solid r, and dF/dtheta[5].
+__device__ __forceinline__ void surface_grad64(const ShapeRec64& r, int face, const double* xs, double* g,
+                                               double* dF) {
+    for (int k = 0; k < 3; ++k) g[k] = 0.0;
+    for (int k = 0; k < 5; ++k) dF[k] = 0.0;
+    const double* p = r.p;
+    if (r.kind == KBOX) {
+        const int ax = face >> 1;
+        const double sg = (face & 1) ? 1.0 : -1.0;   // F = sg x_ax - h_ax
+        g[ax] = sg;
+        dF[ax] = -1.0;
+        return;
+    }
+    const bool tube = r.kind == KTUBE;
+    const double dz = tube ? p[2] : p[0];
+    const int idz = tube ? 2 : 0;
+    if (face == 4 || face == 5) {                    // F = +-z - dz
+        g[2] = face == 5 ? 1.0 : -1.0;
+        dF[idz] = -1.0;
+        return;
+    }
+    const bool outer = face == 6;
+    const double sg = outer ? 1.0 : -1.0;            // outer: rho^2 - R^2, inner: R^2 - rho^2
+    g[0] = sg * 2.0 * xs[0];
+    g[1] = sg * 2.0 * xs[1];
+    if (tube) {
+        const double rr = outer ? p[1] : p[0];
+        dF[outer ? 1 : 0] = -sg * 2.0 * rr;
+        return;
+    }
+    const double r1 = outer ? p[2] : p[1], r2 = outer ? p[4] : p[3];
+    const double w = (xs[2] + dz) / (2.0 * dz);      // weight of the radius at +dz
+    const double R = r1 + (r2 - r1) * w;
+    const double dRdz = (r2 - r1) / (2.0 * dz);
+    g[2] = -sg * 2.0 * R * dRdz;
+    dF[outer ? 2 : 1] = -sg * 2.0 * R * (1.0 - w);
+    dF[outer ? 4 : 3] = -sg * 2.0 * R * w;
+    dF[0] = -sg * 2.0 * R * (r2 - r1) * (-xs[2] / (2.0 * dz * dz));   // dR/d(dz) at fixed z
+}
+
+__global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const int32_t* __restrict__ hit,
+                                                     const double* __restrict__ gstep, double* __restrict__ gp,
+                                                     double* __restrict__ gd, double* __restrict__ partials) {
+    extern __shared__ __align__(16) double smem_adj[];
+    const int nown = v.nd + 1;                       // daughters, then the mother
+    double* acc = smem_adj;                          // [nown * kGeo]
+    double* val = acc + size_t(nown) * kGeo;         // [kGeo][kAdjTile]
+    int* own = reinterpret_cast<int*>(val + kGeo * kAdjTile);
+    const int t = threadIdx.x;
+    for (int q = t; q < nown * kGeo; q += kAdjTile) acc[q] = 0.0;
+    __syncthreads();
+    const int64_t ntiles = (b.n + kAdjTile - 1) / kAdjTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * kAdjTile + t;
+        int o = -1;
+        double c[kGeo] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (i < b.n) {
+            const double px = b.x[i], py = b.y[i], pz = b.z[i];
+            const double qx = b.dx[i], qy = b.dy[i], qz = b.dz[i];
+            const int h = hit[i];
+            const double ws = gstep[i];
+            double op[3] = {0, 0, 0}, od[3] = {0, 0, 0};
+            if (h >= v.nd) atomicOr(v.status, ST_BAD_INDEX);   // not a hit of this volume: gradients 0
+            if (h >= -1 && h < v.nd && valid_track(px, py, pz, qx, qy, qz)) {
+                double x[3], u[3];
+                int face = -1;
+                double s;
+                const ShapeRec64* r;
+                if (h < 0) {
+                    r = &v.m64;
+                    x[0] = px; x[1] = py; x[2] = pz;
+                    u[0] = qx; u[1] = qy; u[2] = qz;
+                    s = dist_in64<true>(*r, x, u, &face);
+                } else {
+                    r = &v.d64[h];
+                    to_local64(*r, px, py, pz, qx, qy, qz, x, u);
+                    s = dist_out64<true>(*r, x, u, &face);
+                }
+                if (face >= 0 && isfinite(s)) {
+                    const double xs[3] = {FMA(s, u[0], x[0]), FMA(s, u[1], x[1]), FMA(s, u[2], x[2])};
+                    double g[3], dF[5];
+                    surface_grad64(*r, face, xs, g, dF);
+                    const double den = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+                    if (den != 0.0) {
+                        double Rg[3];
+                        if (h < 0) {
+                            Rg[0] = g[0]; Rg[1] = g[1]; Rg[2] = g[2];
+                        } else {
+                            for (int k = 0; k < 3; ++k)
+                                Rg[k] = r->R[3 * k] * g[0] + r->R[3 * k + 1] * g[1] + r->R[3 * k + 2] * g[2];
+                        }
+                        const double f = ws / den;
+                        for (int k = 0; k < 3; ++k) {
+                            op[k] = -f * Rg[k];
+                            od[k] = -f * s * Rg[k];
+                            if (h >= 0) c[k] = f * Rg[k];
+                        }
+                        for (int k = 0; k < 5; ++k) c[3 + k] = -f * dF[k];
+                        o = h < 0 ? v.nd : h;
+                    }
+                }
+            }
+            for (int k = 0; k < 3; ++k) {
+                gp[k * b.n + i] = op[k];
+                gd[k * b.n + i] = od[k];
+            }
+        }
+        own[t] = o;
+        for (int k = 0; k < kGeo; ++k) val[k * kAdjTile + t] = c[k];
+        __syncthreads();
+        // fixed-order accumulation: owner q is handled by thread q % 256 and
+        // takes the tile's tracks in index order
+        for (int q = t; q < nown; q += kAdjTile) {
+            for (int e = 0; e < kAdjTile; ++e) {
+                if (own[e] != q) continue;
+                for (int k = 0; k < kGeo; ++k) acc[q * kGeo + k] += val[k * kAdjTile + e];
+            }
+        }
+        __syncthreads();
+    }
+    for (int q = t; q < nown * kGeo; q += kAdjTile) partials[size_t(blockIdx.x) * nown * kGeo + q] = acc[q];
+}
+
+// Sum of the block partials in block order.
+__global__ void k_adjoint_reduce(int nblocks, int nd, const double* __restrict__ partials,
+                                 double* __restrict__ gtrans, double* __restrict__ gparams) {
+    const int nown = nd + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nown * kGeo) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[size_t(b) * nown * kGeo + q];
+    const int o = q / kGeo, k = q % kGeo;
+    if (k < 3) {
+        if (o < nd && gtrans) gtrans[3 * o + k] = s;
+    } else if (gparams) {
+        gparams[5 * o + (k - 3)] = s;
+    }
+}
+
+int adjoint_blocks(int64_t n, int num_sms) {
+    const int64_t need = (n + kAdjTile - 1) / kAdjTile;
+    const int64_t cap = int64_t(2) * num_sms;
+    return int(need < 1 ? 1 : (need < cap ? need : cap));
+}
+
+size_t adjoint_workspace_bytes(int nd, int64_t n, int num_sms) {
+    return size_t(adjoint_blocks(n, num_sms)) * size_t(nd + 1) * kGeo * sizeof(double);
+}
+
+cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit, const double* gstep, double* gp,
+                           double* gd, double* gtrans, double* gparams, double* workspace, cudaStream_t s,
+                           int num_sms) {
+    const int nb = adjoint_blocks(b.n, num_sms);
+    const int smem = int((size_t(v.nd + 1) * kGeo + size_t(kGeo) * kAdjTile) * sizeof(double) +
+                         kAdjTile * sizeof(int));
+    cudaError_t e = prep(k_adjoint, smem);
+    if (e != cudaSuccess) return e;
+    k_adjoint<<<nb, kAdjTile, smem, s>>>(v, b, hit, gstep, gp, gd, workspace);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (gtrans || gparams) {
+        const int tot = (v.nd + 1) * kGeo;
+        k_adjoint_reduce<<<(tot + 255) / 256, 256, 0, s>>>(nb, v.nd, workspace, gtrans, gparams);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace geonav

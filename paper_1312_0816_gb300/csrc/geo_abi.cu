@@ -658,6 +658,35 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
     return cuda_status(launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, s, num_sms_of(b->device)));
 }
 
+geo_status geo_adjoint_workspace_size(geo_volume v, int64_t n, uint64_t* bytes) {
+    if (!v || !bytes || n < 0) return GEO_ERR_INVALID_ARG;
+    *bytes = uint64_t(adjoint_workspace_bytes(v->view.nd, n, num_sms_of(v->device)));
+    return GEO_OK;
+}
+
+geo_status geo_dist_to_boundary_adjoint(geo_volume v, const double* x, const double* y, const double* z,
+                                        const double* dx, const double* dy, const double* dz, int64_t n,
+                                        const int32_t* hit, const double* grad_step, double* grad_p, double* grad_d,
+                                        double* grad_trans, double* grad_params, void* workspace,
+                                        uint64_t workspace_bytes, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
+    if (n == 0) return GEO_OK;
+    if (!is_device_ptr(dx) || !is_device_ptr(dy) || !is_device_ptr(dz) || !is_device_ptr(hit) ||
+        !is_device_ptr(grad_step) || !is_device_ptr(grad_p) || !is_device_ptr(grad_d) ||
+        (grad_trans && !is_device_ptr(grad_trans)) || (grad_params && !is_device_ptr(grad_params)) ||
+        !is_device_ptr(workspace))
+        return GEO_ERR_INVALID_ARG;
+    const int sms = num_sms_of(v->device);
+    if (workspace_bytes < adjoint_workspace_bytes(v->view.nd, n, sms)) return GEO_ERR_INVALID_ARG;
+    const size_t smem = (size_t(v->view.nd + 1) * 8 + 8 * 256) * sizeof(double) + 256 * sizeof(int);
+    if (int64_t(smem) > smem_budget(v->device)) return GEO_ERR_UNSUPPORTED;
+    const Basket b{x, y, z, dx, dy, dz, n};
+    return cuda_status(launch_adjoint(v->view, b, hit, grad_step, grad_p, grad_d, grad_trans, grad_params,
+                                      static_cast<double*>(workspace), static_cast<cudaStream_t>(stream), sms));
+}
+
 geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const double* y, const double* z,
                                       const double* dx, const double* dy, const double* dz, int64_t n, double* step,
                                       int32_t* hit, int32_t* nref, void* stream) {

@@ -114,6 +114,11 @@ cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, c
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
                           int num_sms);
 
+size_t adjoint_workspace_bytes(int nd, int64_t n, int num_sms);
+cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit, const double* gstep, double* gp,
+                           double* gd, double* gtrans, double* gparams, double* workspace, cudaStream_t s,
+                           int num_sms);
+
 // accessors of the opaque volume handle (defined in geo_abi.cu)
 const VolView* volume_view(geo_volume v);
 int volume_device(geo_volume v);

@@ -70,7 +70,7 @@ __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
 
-template <bool SMEM>
+template <bool SMEM, int TRAV>
 __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
                                                              int32_t* __restrict__ hit,
                                                              double* __restrict__ bpoint,
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                 double best = 0.0;
                 int h = -2, nev = 0;
                 rs.status = 1;
-                if (live) refine_pass1(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+                if (live) refine_pass1<TRAV>(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
                 int task = 0, bin = -1;
                 if (rs.status == 0) {
                     task = first_task(rs);
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 double best = 0.0;
                 int h = -2, nev = 0;
                 rs.status = 1;
-                if (live) refine_pass1(v, v.d32, v.d64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+                if (live) refine_pass1<2>(v, v.d32, v.d64, px, py, pz, qx, qy, qz, rs, best, h, nev);
                 int task = 0, bin = -1;
                 if (rs.status == 0) {
                     task = first_task(rs);
@@ -402,15 +402,20 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
     static_assert(sizeof(Stage) % 16 == 0, "stage size keeps the tables 16-byte aligned");
     const int stages = 2 * int(sizeof(Stage));
     const int smem = stages + (v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0);
-    if (v.smem_refine) {
-        cudaError_t e = prep(k_dist_refine<true>, smem);
+    if (v.voxelized) {
+        cudaError_t e = prep(k_dist_refine<false, 1>, smem);
         if (e != cudaSuccess) return e;
-        k_dist_refine<true><<<grid_refine(k_dist_refine<true>, b.n, smem, num_sms), kThreads, smem, s>>>(
+        k_dist_refine<false, 1><<<grid_refine(k_dist_refine<false, 1>, b.n, smem, num_sms), kThreads, smem, s>>>(
+            v, b, step, hit, bpoint, nref);
+    } else if (v.smem_refine) {
+        cudaError_t e = prep(k_dist_refine<true, 0>, smem);
+        if (e != cudaSuccess) return e;
+        k_dist_refine<true, 0><<<grid_refine(k_dist_refine<true, 0>, b.n, smem, num_sms), kThreads, smem, s>>>(
             v, b, step, hit, bpoint, nref);
     } else {
-        cudaError_t e = prep(k_dist_refine<false>, smem);
+        cudaError_t e = prep(k_dist_refine<false, 0>, smem);
         if (e != cudaSuccess) return e;
-        k_dist_refine<false><<<grid_refine(k_dist_refine<false>, b.n, smem, num_sms), kThreads, smem, s>>>(
+        k_dist_refine<false, 0><<<grid_refine(k_dist_refine<false, 0>, b.n, smem, num_sms), kThreads, smem, s>>>(
             v, b, step, hit, bpoint, nref);
     }
     return cudaGetLastError();

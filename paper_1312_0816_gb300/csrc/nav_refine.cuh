@@ -69,10 +69,6 @@ __device__ __forceinline__ void bound_daughter(const ShapeRec32& r, int j, const
     if (!(tp < f_inf())) return;
     const float L = lower_bound(s0 + tp, r.delta, inv_dn);
     if (L > Um) return;
-    // a daughter met again (grid walk) is already in the list with this bound
-#pragma unroll
-    for (int k = 0; k < kCand; ++k)
-        if (k < c.n && c.j[k] == j) return;
     cand_insert(c, L, j);
 }
 
@@ -140,7 +136,9 @@ struct RefineState {
 };
 
 // FP32 pass: bounds of the mother and of every daughter.  When status == 1
-// on return, best/h already hold the final answer.
+// on return, best/h already hold the final answer.  TRAVERSAL: 0 = every
+// daughter, 1 = the uniform grid, 2 = chosen per volume at run time.
+template <int TRAVERSAL>
 __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32* __restrict__ tab32,
                                              const ShapeRec64* __restrict__ tab64, double px, double py,
                                              double pz, double qx, double qy, double qz, RefineState& st,
@@ -191,15 +189,20 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
     bool dummy;
     const float e_hi = exit32(v.m32u, p32, d32, dummy);
     const float Um = e_hi + 16.f * kEps32f * e_hi + v.m32u.delta * inv_dn;
-    if (!v.voxelized) {
+    const bool grid = TRAVERSAL == 1 || (TRAVERSAL == 2 && v.voxelized);
+    if (!grid) {
         for (int j = 0; j < v.nd; ++j) bound_daughter(tab32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
     } else {
         // only daughters listed in the cells the track crosses before the
-        // mother's exit (upper bound Um); a 4-entry mailbox skips repeats
+        // mother's exit (upper bound Um); a daughter met again is skipped
+        // (4-entry mailbox, then the candidate list)
         int mb0 = -1, mb1 = -1, mb2 = -1, mb3 = -1;
         vox_walk32(v, p32, d32, Um, [&](int j) {
             if (j == mb0 || j == mb1 || j == mb2 || j == mb3) return;
             mb3 = mb2; mb2 = mb1; mb1 = mb0; mb0 = j;
+#pragma unroll
+            for (int k = 0; k < kCand; ++k)
+                if (k < st.c.n && st.c.j[k] == j) return;
             bound_daughter(tab32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
         });
     }
@@ -302,7 +305,7 @@ __device__ __forceinline__ void refine_track(const VolView& v, const ShapeRec32*
                                              double pz, double qx, double qy, double qz, double& best, int& h,
                                              int& nev) {
     RefineState st;
-    refine_pass1(v, tab32, tab64, px, py, pz, qx, qy, qz, st, best, h, nev);
+    refine_pass1<2>(v, tab32, tab64, px, py, pz, qx, qy, qz, st, best, h, nev);
     if (st.status) return;
     const double s1 = eval64(v, tab64, first_task(st), px, py, pz, qx, qy, qz);
     refine_rest(v, tab64, st, s1, px, py, pz, qx, qy, qz, best, h, nev);

@@ -113,10 +113,16 @@ __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x)
 // N_k / a_k with a_k = |u_k| > 0 and N_k = -h_k - sign(u_k) x_k, its exit
 // F_k / a_k with F_k = h_k - sign(u_k) x_k; the largest entry and smallest
 // exit are chosen by comparing cross products, and only the entry is divided.
-__device__ __forceinline__ double box_out64(const double* h, const double* x, const double* u) {
+// Surface tags (FACE output of the routines below, used by the adjoint):
+// box 0..5 = -x,+x,-y,+y,-z,+z; tube and cone 4/5 = -z/+z planes, 6 outer,
+// 7 inner quadric; -1 = none (start point inside, or no crossing).
+template <bool FACE = false>
+__device__ __forceinline__ double box_out64(const double* h, const double* x, const double* u, int* face = nullptr) {
+    if (FACE) *face = -1;
     if (ABS_LE(x[0], h[0]) && ABS_LE(x[1], h[1]) && ABS_LE(x[2], h[2])) return 0.0;
     double Nn = -1.0, An = 0.0;   // entry numerator / denominator so far (-inf)
     double Nf = 1.0, Af = 0.0;    // exit numerator / denominator so far (+inf)
+    int fn = -1;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (IS_ZERO(u[k])) {
@@ -127,16 +133,23 @@ __device__ __forceinline__ double box_out64(const double* h, const double* x, co
         const double xs = IS_POS(u[k]) ? x[k] : -x[k];   // sign(u_k) x_k
         const double N = SUB(-h[k], xs), F = SUB(h[k], xs);
         // N/a > Nn/An  <=>  N An > Nn a   (a, An >= 0; An == 0 encodes -inf)
-        if (An == 0.0 || MUL(N, An) > MUL(Nn, a)) { Nn = N; An = a; }
+        if (An == 0.0 || MUL(N, An) > MUL(Nn, a)) {
+            Nn = N;
+            An = a;
+            if (FACE) fn = 2 * k + (IS_POS(u[k]) ? 0 : 1);   // entered through -h (u>0) or +h
+        }
         if (Af == 0.0 || MUL(F, Af) < MUL(Nf, a)) { Nf = F; Af = a; }
     }
     // hit iff entry <= exit and exit >= 0
     if (!(Af == 0.0 || (MUL(Nn, Af) <= MUL(Nf, An) && NONNEG(Nf)))) return d_inf();
+    if (FACE && IS_POS(Nn)) *face = fn;
     return IS_POS(Nn) ? DIV(Nn, An) : 0.0;
 }
 
 
-__device__ __forceinline__ double tube_out64(const double* d, const double* x, const double* u) {
+template <bool FACE = false>
+__device__ __forceinline__ double tube_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
+    if (FACE) *face = -1;
     const double rmin = d[0], dz = d[2], rmin2 = d[3], rmax2 = d[4];
     const double rho2 = rho2_of(x);
     if (ABS_LE(x[2], dz) && LE(rho2, rmax2) && LE(rmin2, rho2)) return 0.0;
@@ -146,22 +159,33 @@ __device__ __forceinline__ double tube_out64(const double* d, const double* x, c
         const double t = DIV(SUB(copysign(dz, x[2]), x[2]), zc ? u[2] : 1.0);
         const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
         const double r2 = DOT2(xh, xh, yh, yh);
-        if (zc && LE(r2, rmax2) && LE(rmin2, r2)) best = t;
+        if (zc && LE(r2, rmax2) && LE(rmin2, r2)) {
+            best = t;
+            if (FACE) *face = IS_POS(x[2]) ? 5 : 4;
+        }
     }
     const double A = DOT2(u[0], u[0], u[1], u[1]);
     const double B = DOT2(x[0], u[0], x[1], u[1]);
     {   // outer cylinder, crossed inwards
         const double s = root_falling(A, B, SUB(rho2, rmax2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+            best = s;
+            if (FACE) *face = 6;
+        }
     }
     if (rmin > 0.0) {   // inner cylinder, crossed outwards (out of the hole)
         const double s = root_rising(A, B, SUB(rho2, rmin2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+            best = s;
+            if (FACE) *face = 7;
+        }
     }
     return best;
 }
 
-__device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u) {
+template <bool FACE = false>
+__device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
+    if (FACE) *face = -1;
     const double dz = d[0];
     const double rho2 = rho2_of(x);
     const double ro0 = FMA(d[2], x[2], d[1]);
@@ -176,27 +200,38 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
         const double r2 = DOT2(xh, xh, yh, yh);
         const double lo2 = IS_POS(x[2]) ? d[7] : d[5];
         const double hi2 = IS_POS(x[2]) ? d[8] : d[6];
-        if (zc && LE(r2, hi2) && LE(lo2, r2)) best = t;
+        if (zc && LE(r2, hi2) && LE(lo2, r2)) {
+            best = t;
+            if (FACE) *face = IS_POS(x[2]) ? 5 : 4;
+        }
     }
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
     {   // outer cone rho^2 - (a + b z)^2, crossed inwards
         const double rs = MUL(d[2], u[2]);
         const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+            best = s;
+            if (FACE) *face = 6;
+        }
     }
     if (hole) {   // inner cone, crossed outwards
         const double rs = MUL(d[4], u[2]);
         const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) best = s;
+        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+            best = s;
+            if (FACE) *face = 7;
+        }
     }
     return best;
 }
 
-__device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* x, const double* u) {
-    if (r.kind == KBOX) return box_out64(r.d, x, u);
-    if (r.kind == KTUBE) return tube_out64(r.d, x, u);
-    return cone_out64(r.d, x, u);
+template <bool FACE = false>
+__device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* x, const double* u,
+                                             int* face = nullptr) {
+    if (r.kind == KBOX) return box_out64<FACE>(r.d, x, u, face);
+    if (r.kind == KTUBE) return tube_out64<FACE>(r.d, x, u, face);
+    return cone_out64<FACE>(r.d, x, u, face);
 }
 
 // ------------------------------------------------------- DistFromInside ---
@@ -211,12 +246,25 @@ __device__ __forceinline__ double slab_exit(double xk, double uk, double h) {
 // minimum is taken on the bit patterns and the result clamped at +0.
 __device__ __forceinline__ double clamp0(double t) { return NONNEG(t) && !IS_ZERO(t) ? t : 0.0; }
 
-__device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u) {
+template <bool FACE = false>
+__device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u,
+                                            int* face = nullptr) {
+    // the exit is the least of the constraints' exit parameters (minimum on
+    // the bit patterns of values >= 0; equal values are equal bit patterns)
     const double* d = r.d;
     double t;
+    int f = -1;
+    auto take = [&](double c, int fc) {
+        if (LT(c, t)) {
+            t = c;
+            if (FACE) f = fc;
+        }
+    };
     if (r.kind == KBOX) {
-        t = MINP(clamp0(slab_exit(x[0], u[0], d[0])),
-                 MINP(clamp0(slab_exit(x[1], u[1], d[1])), clamp0(slab_exit(x[2], u[2], d[2]))));
+        t = d_inf();
+#pragma unroll
+        for (int k = 0; k < 3; ++k) take(clamp0(slab_exit(x[k], u[k], d[k])), 2 * k + (IS_POS(u[k]) ? 1 : 0));
+        if (FACE) *face = f;
         return t;
     }
     const double rho2 = rho2_of(x);
@@ -224,26 +272,30 @@ __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
     double s;
     if (r.kind == KTUBE) {
-        t = clamp0(slab_exit(x[2], u[2], d[2]));
+        t = d_inf();
+        take(clamp0(slab_exit(x[2], u[2], d[2])), IS_POS(u[2]) ? 5 : 4);
         s = root_rising(A0, B0, SUB(rho2, d[4]));
-        if (NONNEG(s)) t = MINP(t, clamp0(s));
+        if (NONNEG(s)) take(clamp0(s), 6);
         if (d[0] > 0.0) {
             s = root_falling(A0, B0, SUB(rho2, d[3]));
-            if (NONNEG(s)) t = MINP(t, clamp0(s));
+            if (NONNEG(s)) take(clamp0(s), 7);
         }
+        if (FACE) *face = f;
         return t;
     }
-    t = clamp0(slab_exit(x[2], u[2], d[0]));
+    t = d_inf();
+    take(clamp0(slab_exit(x[2], u[2], d[0])), IS_POS(u[2]) ? 5 : 4);
     {
         const double ro0 = FMA(d[2], x[2], d[1]), rs = MUL(d[2], u[2]);
         s = root_rising(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-        if (NONNEG(s)) t = MINP(t, clamp0(s));
+        if (NONNEG(s)) take(clamp0(s), 6);
     }
     if (d[11] != 0.0) {
         const double ri0 = FMA(d[4], x[2], d[3]), rs = MUL(d[4], u[2]);
         s = root_falling(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-        if (NONNEG(s)) t = MINP(t, clamp0(s));
+        if (NONNEG(s)) take(clamp0(s), 7);
     }
+    if (FACE) *face = f;
     return t;
 }
 

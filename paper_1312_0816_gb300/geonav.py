@@ -51,7 +51,8 @@ _lib = None
 EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dist_to_boundary",
            "geo_contains", "geo_safety", "geo_dist_to_boundary_host", "geo_dist_to_boundary_stats",
            "geo_check_device_status", "geo_probe_pipe", "geo_build_batch", "geo_destroy_batch",
-           "geo_dist_to_boundary_batched", "geo_dist_to_boundary_batched_noalloc", "geo_status_string")
+           "geo_dist_to_boundary_batched", "geo_dist_to_boundary_batched_noalloc", "geo_adjoint_workspace_size",
+           "geo_dist_to_boundary_adjoint", "geo_status_string")
 
 
 def library_path() -> str:
@@ -87,6 +88,9 @@ def load(build_if_stale: bool = True):
     L.geo_dist_to_boundary_batched.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
     L.geo_dist_to_boundary_batched_noalloc.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(geo_basket), i32,
                                                        dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
+    L.geo_adjoint_workspace_size.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_uint64)]
+    L.geo_dist_to_boundary_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, ip, dp, dp, dp, dp, dp, vp,
+                                               ctypes.c_uint64, vp]
     L.geo_status_string.argtypes = [ctypes.c_int]
     L.geo_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -377,3 +381,37 @@ def geo_dist_to_boundary_batched_noalloc(volumes, baskets, x, y, z, dx, dy, dz, 
                                                        _dev(step, f64, n, "step"), _dev(hit, torch.int32, n, "hit"),
                                                        _stream(stream)), "geo_dist_to_boundary_batched_noalloc")
     return step, hit
+
+
+def geo_adjoint_workspace_size(vol: Volume, n: int) -> int:
+    b = ctypes.c_uint64()
+    _check(load().geo_adjoint_workspace_size(vol.handle, int(n), ctypes.byref(b)), "geo_adjoint_workspace_size")
+    return int(b.value)
+
+
+def geo_dist_to_boundary_adjoint(vol: Volume, x, y, z, dx, dy, dz, hit, grad_step, want_geometry: bool = True,
+                                 stream=None):
+    """Gradients of sum(grad_step * step): returns grad_p (3, n), grad_d (3, n)
+    and, when want_geometry, grad_trans (nd, 3) and grad_params (nd + 1, 5)
+    (the mother's parameters last)."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    nd = vol.n_daughters
+    gp = torch.empty((3, n), dtype=f64, device=x.device)
+    gd = torch.empty((3, n), dtype=f64, device=x.device)
+    gt = torch.zeros((max(nd, 1), 3), dtype=f64, device=x.device) if want_geometry else None
+    gprm = torch.zeros((nd + 1, 5), dtype=f64, device=x.device) if want_geometry else None
+    ws = torch.empty(max(geo_adjoint_workspace_size(vol, n), 8) // 8 + 1, dtype=f64, device=x.device)
+    args = [_dev(a, f64, n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    _check(load().geo_dist_to_boundary_adjoint(
+        vol.handle, *args, n, _dev(hit, torch.int32, n, "hit"), _dev(grad_step, f64, n, "grad_step"),
+        _dev(gp, f64, 3 * n, "grad_p"), _dev(gd, f64, 3 * n, "grad_d"),
+        ctypes.c_void_p(gt.data_ptr()) if gt is not None else ctypes.c_void_p(0),
+        ctypes.c_void_p(gprm.data_ptr()) if gprm is not None else ctypes.c_void_p(0),
+        ctypes.c_void_p(ws.data_ptr()), ctypes.c_uint64(ws.numel() * 8), _stream(stream)),
+        "geo_dist_to_boundary_adjoint")
+    if not want_geometry:
+        return gp, gd
+    return gp, gd, gt[:nd], gprm
