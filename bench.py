@@ -293,6 +293,91 @@ def voxel_leg(pkg, scenes, rank, steps):
     return out
 
 
+def _event_time(fn, k):
+    import torch
+
+    for _ in range(3):
+        fn(0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for it in range(k):
+        fn(it)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def adjoint_leg(pkg, scenes, rank, steps):
+    """Gradients of the summed step: box mother with four boxes and the
+    box/tube/cone scene, 2^18 tracks; the adjoint alone (per-track gradients
+    plus the deterministic geometry reduction) and forward + adjoint.  Eight
+    rotating basket copies keep the inputs out of L2."""
+    import torch
+
+    out = {}
+    n = 1 << 18
+    for name, sc in (("box4", scenes.box4(0)), ("diff3", scenes.diff3())):
+        tr = scenes.sample_tracks(sc, n, 4 + 1000 * rank)
+        vol = pkg.geo_build_volume(sc)
+        base = [torch.from_numpy(f).cuda() for f in tr.fields()]
+        g = torch.Generator(device="cuda")
+        g.manual_seed(77 + rank)
+        copies = [base] + [[f[p].contiguous() for f in base]
+                           for p in (torch.randperm(n, device="cuda", generator=g) for _ in range(7))]
+        hits = [pkg.geo_dist_to_boundary(vol, *c, mode=0)[1] for c in copies]
+        w = torch.ones(n, dtype=torch.float64, device="cuda")
+        ms_adj = _event_time(lambda it: pkg.geo_dist_to_boundary_adjoint(vol, *copies[it % 8], hits[it % 8], w),
+                             steps)
+
+        def fwd_bwd(it):
+            c = copies[it % 8]
+            _, h = pkg.geo_dist_to_boundary(vol, *c, mode=1)
+            pkg.geo_dist_to_boundary_adjoint(vol, *c, h, w)
+
+        ms_fb = _event_time(fwd_bwd, steps)
+        vol.close()
+        # algorithmic bytes of the adjoint: p, d, hit, dL/dstep in; dL/dp, dL/dd out
+        gbs = 108.0 * n / (ms_adj * 1e-3) / 1e9
+        out[name] = {"adjoint": {"value": n / (ms_adj * 1e-3), "unit": "tracks/s", "ms_per_step": ms_adj,
+                                 "algorithmic_gb_s": gbs},
+                     "forward_plus_adjoint": {"value": n / (ms_fb * 1e-3), "unit": "tracks/s",
+                                              "ms_per_step": ms_fb}}
+    out["workload"] = ("2^18 tracks; box mother half 100 mm with 4 boxes, and box mother with one rotated box, "
+                       "tube and cone; dL/dstep = 1; 8 rotating copies (226 MB > L2); steps %d" % steps)
+    out["bytes_per_track"] = 108
+    return out
+
+
+def queries_leg(pkg, scenes, rank, steps, sc):
+    """Contains and Safety over the toy detector, 2^22 points (inputs 100 MB,
+    4 rotating copies > L2)."""
+    import torch
+
+    n = 1 << 22
+    tr = scenes.sample_tracks(sc, n, 9 + 1000 * rank, exclusive=False)
+    vol = pkg.geo_build_volume(sc)
+    base = [torch.from_numpy(f).cuda() for f in tr.fields()[:3]]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(99 + rank)
+    copies = [base] + [[f[p].contiguous() for f in base]
+                       for p in (torch.randperm(n, device="cuda", generator=g) for _ in range(3))]
+    where = torch.empty(n, dtype=torch.int32, device="cuda")
+    saf = torch.empty(n, dtype=torch.float64, device="cuda")
+    out = {"workload": "toy detector (40 daughters), 2^22 points uniform in the mother (daughters included), "
+                       "4 rotating copies; steps %d" % steps}
+    ms = _event_time(lambda it: pkg.geo_contains(vol, *copies[it % 4], where=where), steps)
+    out["contains"] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+                       "algorithmic_gb_s": 28.0 * n / (ms * 1e-3) / 1e9}
+    for mode, key in ((0, "safety_fp64"), (1, "safety_fp32_refine")):
+        ms = _event_time(lambda it: pkg.geo_safety(vol, *copies[it % 4], mode=mode, safety=saf), steps)
+        out[key] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+                    "algorithmic_gb_s": 32.0 * n / (ms * 1e-3) / 1e9}
+    vol.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +388,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-voxel", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-queries", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -439,6 +526,8 @@ def main():
 
     batched = None if args.no_batched else batched_leg(pkg, scenes, rank, max(10, args.steps // 40))
     voxel = None if args.no_voxel else voxel_leg(pkg, scenes, rank, max(5, args.steps // 200))
+    adjoint = None if args.no_adjoint else adjoint_leg(pkg, scenes, rank, max(10, args.steps // 40))
+    queries = None if args.no_queries else queries_leg(pkg, scenes, rank, max(10, args.steps // 100), sc)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -464,6 +553,8 @@ def main():
             "cpu_baseline": cpu,
             "batched": batched,
             "voxel_512": voxel,
+            "adjoint": adjoint,
+            "contains_safety": queries,
         }
         print(json.dumps(line), flush=True)
     vol.close()

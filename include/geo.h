@@ -123,13 +123,21 @@ geo_status geo_dist_to_boundary(geo_volume v, const double* x, const double* y, 
 /* Inside/outside check of Sec. 3.1 at navigator level: where[i] = -2 outside
  * the mother, -1 in the mother's exclusive part, j = the lowest-index daughter
  * whose closed solid contains the point.  x,y,z device FP64[n]; where device
- * int32[n]. */
+ * int32[n].  mode GEO_FP64 tests every daughter's bounding sphere and solid
+ * in FP64; GEO_FP32_REFINE decides in FP32 on inflated (or, for the mother,
+ * deflated) copies and tests in FP64 only the daughters the FP32 test cannot
+ * exclude.  Both modes give the same answer for every point.  Other modes:
+ * GEO_ERR_INVALID_ARG. */
 geo_status geo_contains(geo_volume v, const double* x, const double* y, const double* z, int64_t n,
-                        int32_t* where, void* stream);
+                        int32_t* where, int32_t mode, void* stream);
 
 /* Safety of Sec. 3.1 at navigator level: min(mother inside-safety, min over
  * daughters of outside-safety), exact Euclidean; 0 outside the mother or
- * inside a daughter.  safety device FP64[n]. */
+ * inside a daughter.  safety device FP64[n].  mode GEO_FP64 evaluates every
+ * candidate not culled by its FP64 bounding sphere; GEO_FP32_REFINE bounds
+ * every candidate from below in FP32 and evaluates in FP64 only those whose
+ * bound does not exceed the smallest FP64 value found (usually one); both
+ * modes return the same FP64 minimum. */
 geo_status geo_safety(geo_volume v, const double* x, const double* y, const double* z, int64_t n,
                       double* safety, int32_t mode, void* stream);
 

@@ -484,14 +484,16 @@ geo_status geo_dist_to_boundary(geo_volume v, const double* x, const double* y, 
 }
 
 geo_status geo_contains(geo_volume v, const double* x, const double* y, const double* z, int64_t n, int32_t* where,
-                        void* stream) {
+                        int32_t mode, void* stream) {
     geo_status st = check_volume_device(v);
     if (st != GEO_OK) return st;
+    if (mode != GEO_FP64 && mode != GEO_FP32_REFINE) return GEO_ERR_INVALID_ARG;
     if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
     if (n == 0) return GEO_OK;
     if (!is_device_ptr(where)) return GEO_ERR_INVALID_ARG;
     const Basket b{x, y, z, nullptr, nullptr, nullptr, n};
-    return cuda_status(launch_contains(v->view, b, where, static_cast<cudaStream_t>(stream), num_sms_of(v->device)));
+    return cuda_status(launch_contains(v->view, b, where, mode, static_cast<cudaStream_t>(stream),
+                                       num_sms_of(v->device)));
 }
 
 geo_status geo_safety(geo_volume v, const double* x, const double* y, const double* z, int64_t n, double* safety,

@@ -109,10 +109,14 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit,
                                 int blocks_per_sm, cudaStream_t s, int num_sms);
 int batched_max_blocks_per_sm();
-cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s,
+cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, int mode, cudaStream_t s,
                             int num_sms);
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
                           int num_sms);
+// FP32-filtered Contains and Safety (queries.cu); same answers as the FP64 ones
+cudaError_t launch_contains_filter(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s,
+                                   int num_sms);
+cudaError_t launch_safety_filter(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms);
 
 size_t adjoint_workspace_bytes(int nd, int64_t n, int num_sms);
 cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit, const double* gstep, double* gp,

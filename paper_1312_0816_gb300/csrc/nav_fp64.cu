@@ -130,13 +130,15 @@ cudaError_t launch_dist_fp64(const VolView& v, const Basket& b, double* step, in
     GEO_LAUNCH(k_dist_fp64, v, b, step, hit, bpoint);
 }
 
-cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s, int num_sms) {
+cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, int mode, cudaStream_t s,
+                            int num_sms) {
+    if (mode == GEO_FP32_REFINE) return launch_contains_filter(v, b, where, s, num_sms);
     GEO_LAUNCH(k_contains, v, b, where);
 }
 
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
                           int num_sms) {
-    (void)mode;
+    if (mode == GEO_FP32_REFINE) return launch_safety_filter(v, b, saf, s, num_sms);
     GEO_LAUNCH(k_safety_fp64, v, b, saf);
 }
 

@@ -248,4 +248,87 @@ __device__ __forceinline__ float exit32(const ShapeRec32& r, const float* x, con
     return fmaxf(t, 0.f);
 }
 
+// ------------------------------------------------------- point queries ---
+// Containment of a point on an FP32 copy.  On an inflated copy (daughters,
+// the mother's m32u) a point that is exactly inside the true solid is inside
+// the copy; on the deflated mother (m32) a point inside the copy is exactly
+// inside the true mother, with a margin larger than the FP64 rounding.  The
+// argument is the one above with the ray replaced by a point: delta exceeds
+// the distance between the FP32 local point and the exact one plus the
+// rounding of the radius arithmetic.
+__device__ __forceinline__ bool contains32(const ShapeRec32& r, const float* x) {
+    const float* e = r.e;
+    if (r.kind == KBOX) return fabsf(x[0]) <= e[0] && fabsf(x[1]) <= e[1] && fabsf(x[2]) <= e[2];
+    const float rho2 = fmaf(x[0], x[0], x[1] * x[1]);
+    if (r.kind == KTUBE) return fabsf(x[2]) <= e[2] && rho2 <= e[1] && (e[3] == 0.f || rho2 >= e[0]);
+    if (!(fabsf(x[2]) <= e[0])) return false;
+    const float ro = fmaf(e[2], x[2], e[1]), ri = fmaf(e[4], x[2], e[3]);
+    return fmaf(-ro, ro, rho2) <= 0.f && (e[5] == 0.f || fmaf(-ri, ri, rho2) >= 0.f);
+}
+
+// Relative margin of the safety bounds below: covers the rounding of the
+// FP32 distance arithmetic relative to the distance itself (the absolute
+// part, proportional to the solid's size, is inside delta).
+constexpr float kSafMargin = 3.8146973e-06f;   // 2^-18
+
+// Lower bound of the outside-safety of an INFLATED copy (distance from x to
+// the solid).  Box and tube: the exact Euclidean distance to the copy (the
+// tube in the meridian half-plane, to the rectangle [rmin, rmax] x [-dz, dz]).
+// Cone: the largest distance to a supporting half-plane of its trapezoid
+// (z-slab, outer and inner radius lines), which cannot exceed the distance to
+// a convex section.  The copy contains the true solid grown by delta, so the
+// distance to it is at most the true distance minus delta, and delta covers
+// the FP32 position and radius errors; the result is lowered by kSafMargin.
+__device__ __forceinline__ float safety_out_lb32(const ShapeRec32& r, const float* x) {
+    const float* e = r.e;
+    float s;
+    if (r.kind == KBOX) {
+        const float a = fmaxf(fabsf(x[0]) - e[0], 0.f), b = fmaxf(fabsf(x[1]) - e[1], 0.f),
+                    c = fmaxf(fabsf(x[2]) - e[2], 0.f);
+        s = fsqrt(fmaf(a, a, fmaf(b, b, c * c)));
+    } else {
+        const float rho = fsqrt(fmaf(x[0], x[0], x[1] * x[1]));
+        const float az = fabsf(x[2]);
+        if (r.kind == KTUBE) {
+            float dr = rho - fsqrt(e[1]);
+            if (e[3] != 0.f) dr = fmaxf(dr, fsqrt(e[0]) - rho);
+            dr = fmaxf(dr, 0.f);
+            const float dz = fmaxf(az - e[2], 0.f);
+            s = fsqrt(fmaf(dr, dr, dz * dz));
+        } else {
+            s = az - e[0];
+            s = fmaxf(s, (rho - fmaf(e[2], x[2], e[1])) * rsqrtf(fmaf(e[2], e[2], 1.f)));
+            if (e[5] != 0.f) s = fmaxf(s, (fmaf(e[4], x[2], e[3]) - rho) * rsqrtf(fmaf(e[4], e[4], 1.f)));
+            s = fmaxf(s, 0.f);
+        }
+    }
+    return s * (1.f - kSafMargin);
+}
+
+// Lower bound of the inside-safety on the DEFLATED mother copy: for a point
+// inside a solid whose meridian section is convex, the distance to the
+// boundary is the smallest distance to a supporting line of the section
+// (box: faces; tube: rmax, rmin, z planes; cone: z planes and radius lines).
+// The copy lies delta inside the true solid, so its inside-distance is at most
+// the true one minus delta; negative (the point is outside the copy) gives 0.
+__device__ __forceinline__ float safety_in_lb32(const ShapeRec32& r, const float* x) {
+    const float* e = r.e;
+    float s;
+    if (r.kind == KBOX) {
+        s = fminf(e[0] - fabsf(x[0]), fminf(e[1] - fabsf(x[1]), e[2] - fabsf(x[2])));
+    } else {
+        const float rho = fsqrt(fmaf(x[0], x[0], x[1] * x[1]));
+        const float az = fabsf(x[2]);
+        if (r.kind == KTUBE) {
+            s = fminf(fsqrt(e[1]) - rho, e[2] - az);
+            if (e[3] != 0.f) s = fminf(s, rho - fsqrt(e[0]));
+        } else {
+            s = e[0] - az;
+            s = fminf(s, (fmaf(e[2], x[2], e[1]) - rho) * rsqrtf(fmaf(e[2], e[2], 1.f)));
+            if (e[5] != 0.f) s = fminf(s, (rho - fmaf(e[4], x[2], e[3])) * rsqrtf(fmaf(e[4], e[4], 1.f)));
+        }
+    }
+    return fmaxf(s, 0.f) * (1.f - kSafMargin);
+}
+
 }  // namespace geonav

@@ -65,6 +65,13 @@ __device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, doubl
     }
 }
 
+// x = R^T (p - t) alone (the same operations as to_local64, so the same bits)
+__device__ __forceinline__ void point_to_local64(const ShapeRec64& r, double px, double py, double pz, double* x) {
+    const double w0 = SUB(px, r.t[0]), w1 = SUB(py, r.t[1]), w2 = SUB(pz, r.t[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = FMA(r.R[6 + k], w2, FMA(r.R[3 + k], w1, MUL(r.R[k], w0)));
+}
+
 // F(s) = A s^2 + 2 B s + C.  Root where F falls through zero (F' = -2 sqrt(D)),
 // s = (-B - sqrt(D)) / A; +inf when there is none.  May be negative.
 // Both cancellation-free forms are selected operand-wise so that every lane

@@ -76,7 +76,7 @@ def load(build_if_stale: bool = True):
     L.geo_destroy_volume.argtypes = [vp]
     L.geo_volume_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32 * 3)]
     L.geo_dist_to_boundary.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, dp, i32, vp]
-    L.geo_contains.argtypes = [vp, dp, dp, dp, i64, ip, vp]
+    L.geo_contains.argtypes = [vp, dp, dp, dp, i64, ip, i32, vp]
     L.geo_safety.argtypes = [vp, dp, dp, dp, i64, dp, i32, vp]
     L.geo_dist_to_boundary_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, i32, i64, vp]
     L.geo_dist_to_boundary_stats.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, ip, vp]
@@ -214,7 +214,10 @@ def geo_dist_to_boundary(vol: Volume, x, y, z, dx, dy, dz, mode: int = GEO_FP32_
     return (step, hit, bpoint) if bpoint is not None else (step, hit)
 
 
-def geo_contains(vol: Volume, x, y, z, where=None, stream=None):
+def geo_contains(vol: Volume, x, y, z, mode: int = GEO_FP32_REFINE, where=None, stream=None):
+    """Navigator-level Contains: -2 outside the mother, -1 mother only, else
+    the lowest-index daughter containing the point (same answer in both
+    modes)."""
     import torch
 
     n = int(x.numel())
@@ -222,11 +225,13 @@ def geo_contains(vol: Volume, x, y, z, where=None, stream=None):
         where = torch.empty(n, dtype=torch.int32, device=x.device)
     f64 = torch.float64
     _check(load().geo_contains(vol.handle, _dev(x, f64, n, "x"), _dev(y, f64, n, "y"), _dev(z, f64, n, "z"), n,
-                               _dev(where, torch.int32, n, "where"), _stream(stream)), "geo_contains")
+                               _dev(where, torch.int32, n, "where"), int(mode), _stream(stream)), "geo_contains")
     return where
 
 
-def geo_safety(vol: Volume, x, y, z, mode: int = GEO_FP64, safety=None, stream=None):
+def geo_safety(vol: Volume, x, y, z, mode: int = GEO_FP32_REFINE, safety=None, stream=None):
+    """Navigator-level Safety (exact Euclidean; same FP64 value in both
+    modes)."""
     import torch
 
     n = int(x.numel())

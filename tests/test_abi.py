@@ -86,6 +86,6 @@ def test_null_arguments():
     out = ctypes.c_void_p()
     assert L.geo_build_volume(ctypes.byref(m), None, 3, None, None, ctypes.byref(out)) == 1
     assert L.geo_dist_to_boundary(None, None, None, None, None, None, None, 0, None, None, None, 0, None) == 1
-    assert L.geo_contains(None, None, None, None, 0, None, None) == 1
+    assert L.geo_contains(None, None, None, None, 0, None, 0, None) == 1
     assert L.geo_safety(None, None, None, None, 0, None, 0, None) == 1
     assert L.geo_destroy_volume(None) == 0

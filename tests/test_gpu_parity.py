@@ -192,13 +192,14 @@ def test_boundary_point(g):
         assert np.allclose(bp[k], want, rtol=0, atol=1e-12 * 3000)
 
 
-def test_contains_parity(g, orc):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_contains_parity(g, orc, mode):
     for name in SCENES:
         sc = scene(name)
         tr = scenes.sample_tracks(sc, 20000, 14, exclusive=False)
         want = orc.contains(sc, tr, nthreads=8)
         x, y, z = dev(tr)[:3]
-        got = g.geo_contains(vol(g, sc), x, y, z).cpu().numpy()
+        got = g.geo_contains(vol(g, sc), x, y, z, mode=mode).cpu().numpy()
         # surface band: points whose answer changes under a 1e-9 mm move
         band = np.zeros(tr.n, dtype=bool)
         for k in range(3):

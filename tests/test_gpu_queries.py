@@ -1,0 +1,111 @@
+"""Contains and Safety (Sec. 3.1) on the GPU: the FP32-filtered mode against
+the plain FP64 mode (same answers, bit for bit, on every point) and both
+against the oracle.
+
+Points: uniform in the mother (daughters included), points on the surfaces
+(oracle boundary points p + s d of random tracks: every kind of face, the
+mother's included) and those points moved by +-1e-7 mm and +-1e-12 mm along
+the track, points in the band between the mother's deflated and inflated FP32
+copies, and non-finite points.  Scenes cover the staged FP32 table (up to 768
+daughters) and the global-memory one (1000 daughters).
+"""
+import numpy as np
+import pytest
+
+from paper_1312_0816_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1312_0816_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.load()
+    return pkg
+
+
+def scene_list():
+    return [scenes.toy40(1), scenes.toy8(1), scenes.box4(0), scenes.diff3(), scenes.grid512(5),
+            scenes.cell_volume(11, 200, False), scenes.cell_volume(12, 1000, True)]
+
+
+def hard_points(orc, sc, n, seed):
+    rng = np.random.default_rng(seed)
+    tr = scenes.sample_tracks(sc, n, seed)
+    ref = orc.navigate(sc, tr, nthreads=8)
+    s = ref["step"]
+    pts = [np.stack([tr.x, tr.y, tr.z], 1)]
+    d = np.stack([tr.dx, tr.dy, tr.dz], 1)
+    on = pts[0] + s[:, None] * d
+    pts.append(on)
+    for eps in (1e-7, -1e-7, 1e-12, -1e-12):
+        pts.append(on + eps * d)
+    # points just inside the mother's boundary (the FP32 band of the mother)
+    m = ref["hit"] == -1
+    for eps in (1e-4, 1e-6, 1e-9):
+        pts.append(on[m] - eps * d[m])
+    p = np.concatenate(pts)
+    p = p[rng.permutation(p.shape[0])]
+    bad = np.array([[np.nan, 0, 0], [0, np.inf, 0], [0, 0, -np.inf], [1e300, 0, 0]])
+    p = np.concatenate([p, bad])
+    z = np.zeros(p.shape[0])
+    return scenes.Tracks(p[:, 0].copy(), p[:, 1].copy(), p[:, 2].copy(), z + 1.0, z, z)
+
+
+def dev3(tr):
+    return [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in (tr.x, tr.y, tr.z)]
+
+
+@pytest.mark.parametrize("idx", range(7))
+def test_modes_agree_and_match_oracle(g, orc, idx):
+    sc = scene_list()[idx]
+    vol = g.geo_build_volume(sc)
+    for tr in (scenes.sample_tracks(sc, 50000, 20 + idx, exclusive=False), hard_points(orc, sc, 20000, 30 + idx)):
+        x = dev3(tr)
+        w = [g.geo_contains(vol, *x, mode=m).cpu().numpy() for m in (0, 1)]
+        s = [g.geo_safety(vol, *x, mode=m).cpu().numpy() for m in (0, 1)]
+        assert np.array_equal(w[0], w[1]), sc.name
+        assert np.array_equal(s[0], s[1], equal_nan=True), sc.name
+        want_w = orc.contains(sc, tr, nthreads=8)
+        want_s = orc.safety(sc, tr, nthreads=8)
+        finite = np.isfinite(tr.x) & np.isfinite(tr.y) & np.isfinite(tr.z)
+        assert np.all(w[1][~finite] == -2) and np.all(s[1][~finite] == 0.0)
+        # Contains is exact away from surfaces: points whose oracle safety is
+        # below 1e-9 mm may differ (surface band)
+        band = (want_s < STEP_TOL) | ~finite
+        assert np.array_equal(w[1][~band], want_w[~band]), sc.name
+        assert np.max(np.abs(s[1] - want_s)[finite]) <= STEP_TOL, sc.name
+    assert g.geo_check_device_status(vol) == 0
+    vol.close()
+
+
+def test_empty_and_single(g):
+    sc = scenes.toy40(1)
+    vol = g.geo_build_volume(sc)
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert g.geo_contains(vol, e, e, e, mode=1).numel() == 0
+    assert g.geo_safety(vol, e, e, e, mode=1).numel() == 0
+    one = torch.tensor([0.0], dtype=torch.float64, device="cuda")
+    # on the axis at the centre: inside the innermost shell's hole, mother only
+    assert int(g.geo_contains(vol, one, one, one, mode=1).item()) == -1
+    assert float(g.geo_safety(vol, one, one, one, mode=1).item()) == 40.0
+    vol.close()
+
+
+def test_mother_only_volume(g, orc):
+    sc = scenes.Scene("empty", scenes.TUBE, np.array([10.0, 100.0, 50.0, 0, 0]), np.zeros(0, np.int32),
+                      np.zeros((0, 5)), np.zeros((0, 9)), np.zeros((0, 3)))
+    vol = g.geo_build_volume(sc)
+    tr = scenes.sample_tracks(sc, 10000, 5)
+    x = dev3(tr)
+    for m in (0, 1):
+        assert np.array_equal(g.geo_contains(vol, *x, mode=m).cpu().numpy(), orc.contains(sc, tr))
+        got = g.geo_safety(vol, *x, mode=m).cpu().numpy()
+        assert np.max(np.abs(got - orc.safety(sc, tr))) <= STEP_TOL
+    vol.close()
