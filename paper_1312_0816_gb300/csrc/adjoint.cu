@@ -14,10 +14,14 @@
 // the forward step of this volume writes) also gives 0 and sets ST_BAD_INDEX
 // in the volume's device status word.
 //
-// Geometry gradients are sums over tracks; they are reduced deterministically:
-// every block owns a fixed set of tiles and adds its tracks in index order into
-// per-block partials (workspace), then one pass adds the partials in block
-// order.
+// Geometry gradients are sums over tracks; they are reduced deterministically.
+// Every block owns a fixed set of tiles of 256 tracks.  Within a tile each warp
+// groups its lanes by owner (the winning daughter, or the mother's parameters)
+// and sums every group with a fixed butterfly of shuffles; the warps then add
+// their group sums into the block's shared accumulators one warp after the
+// other (a warp's groups have distinct owners).  Block partials go to a
+// caller-provided workspace and a second kernel adds them in block order.  No
+// step depends on timing, so repeated calls give the same bits.
 #include <cuda_runtime.h>
 
 #include "geo_internal.h"
@@ -31,24 +35,30 @@ constexpr int kAdjTile = 256;
 constexpr int kGeo = 8;   // per owner: 3 translation + 5 shape-parameter components
 
 // g = grad F at local x* on surface `face` of solid r, and dF/dtheta[5].
+// (Every element is written by a select, so the arrays stay in registers.)
 __device__ __forceinline__ void surface_grad64(const ShapeRec64& r, int face, const double* xs, double* g,
                                                double* dF) {
-    for (int k = 0; k < 3; ++k) g[k] = 0.0;
-    for (int k = 0; k < 5; ++k) dF[k] = 0.0;
     const double* p = r.p;
     if (r.kind == KBOX) {
         const int ax = face >> 1;
         const double sg = (face & 1) ? 1.0 : -1.0;   // F = sg x_ax - h_ax
-        g[ax] = sg;
-        dF[ax] = -1.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            g[k] = ax == k ? sg : 0.0;
+            dF[k] = ax == k ? -1.0 : 0.0;
+        }
+        dF[3] = dF[4] = 0.0;
         return;
     }
     const bool tube = r.kind == KTUBE;
     const double dz = tube ? p[2] : p[0];
-    const int idz = tube ? 2 : 0;
     if (face == 4 || face == 5) {                    // F = +-z - dz
+        g[0] = g[1] = 0.0;
         g[2] = face == 5 ? 1.0 : -1.0;
-        dF[idz] = -1.0;
+        dF[0] = tube ? 0.0 : -1.0;
+        dF[1] = 0.0;
+        dF[2] = tube ? -1.0 : 0.0;
+        dF[3] = dF[4] = 0.0;
         return;
     }
     const bool outer = face == 6;
@@ -56,19 +66,26 @@ __device__ __forceinline__ void surface_grad64(const ShapeRec64& r, int face, co
     g[0] = sg * 2.0 * xs[0];
     g[1] = sg * 2.0 * xs[1];
     if (tube) {
-        const double rr = outer ? p[1] : p[0];
-        dF[outer ? 1 : 0] = -sg * 2.0 * rr;
+        g[2] = 0.0;
+        dF[0] = outer ? 0.0 : -sg * 2.0 * p[0];
+        dF[1] = outer ? -sg * 2.0 * p[1] : 0.0;
+        dF[2] = dF[3] = dF[4] = 0.0;
         return;
     }
     const double r1 = outer ? p[2] : p[1], r2 = outer ? p[4] : p[3];
     const double w = (xs[2] + dz) / (2.0 * dz);      // weight of the radius at +dz
     const double R = r1 + (r2 - r1) * w;
     const double dRdz = (r2 - r1) / (2.0 * dz);
+    const double a1 = -sg * 2.0 * R * (1.0 - w), a2 = -sg * 2.0 * R * w;
     g[2] = -sg * 2.0 * R * dRdz;
-    dF[outer ? 2 : 1] = -sg * 2.0 * R * (1.0 - w);
-    dF[outer ? 4 : 3] = -sg * 2.0 * R * w;
     dF[0] = -sg * 2.0 * R * (r2 - r1) * (-xs[2] / (2.0 * dz * dz));   // dR/d(dz) at fixed z
+    dF[1] = outer ? 0.0 : a1;
+    dF[2] = outer ? a1 : 0.0;
+    dF[3] = outer ? 0.0 : a2;
+    dF[4] = outer ? a2 : 0.0;
 }
+
+constexpr int kAdjWarps = kAdjTile / 32;
 
 __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const int32_t* __restrict__ hit,
                                                      const double* __restrict__ gstep, double* __restrict__ gp,
@@ -76,9 +93,9 @@ __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const
     extern __shared__ __align__(16) double smem_adj[];
     const int nown = v.nd + 1;                       // daughters, then the mother
     double* acc = smem_adj;                          // [nown * kGeo]
-    double* val = acc + size_t(nown) * kGeo;         // [kGeo][kAdjTile]
-    int* own = reinterpret_cast<int*>(val + kGeo * kAdjTile);
-    const int t = threadIdx.x;
+    double* gsum = acc + size_t(nown) * kGeo;        // [kAdjWarps][32][kGeo] group sums
+    int* gown = reinterpret_cast<int*>(gsum + kAdjWarps * 32 * kGeo);   // [kAdjWarps][32] group owners
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int q = t; q < nown * kGeo; q += kAdjTile) acc[q] = 0.0;
     __syncthreads();
     const int64_t ntiles = (b.n + kAdjTile - 1) / kAdjTile;
@@ -137,15 +154,38 @@ __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const
                 gd[k * b.n + i] = od[k];
             }
         }
-        own[t] = o;
-        for (int k = 0; k < kGeo; ++k) val[k * kAdjTile + t] = c[k];
-        __syncthreads();
-        // fixed-order accumulation: owner q is handled by thread q % 256 and
-        // takes the tile's tracks in index order
-        for (int q = t; q < nown; q += kAdjTile) {
-            for (int e = 0; e < kAdjTile; ++e) {
-                if (own[e] != q) continue;
-                for (int k = 0; k < kGeo; ++k) acc[q * kGeo + k] += val[k * kAdjTile + e];
+        // group the warp's lanes by owner; each group is summed by the same
+        // butterfly (non-members contribute 0) and its lowest lane keeps it
+        int ngroups = 0;
+        unsigned pending = __ballot_sync(0xffffffffu, o >= 0);
+        while (pending) {
+            const int leader = __ffs(pending) - 1;
+            const int q = __shfl_sync(0xffffffffu, o, leader);
+            const bool mine = o == q;
+            double sum[kGeo];
+#pragma unroll
+            for (int k = 0; k < kGeo; ++k) sum[k] = mine ? c[k] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                for (int k = 0; k < kGeo; ++k) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], off);
+            }
+            if (lane == leader) {
+                gown[warp * 32 + ngroups] = q;
+#pragma unroll
+                for (int k = 0; k < kGeo; ++k) gsum[(warp * 32 + ngroups) * kGeo + k] = sum[k];
+            }
+            ++ngroups;
+            pending &= ~__ballot_sync(0xffffffffu, mine);
+        }
+        // the warps add their groups one after the other (fixed order); the
+        // groups of one warp have distinct owners
+        for (int w = 0; w < kAdjWarps; ++w) {
+            __syncthreads();
+            if (warp == w && lane < ngroups) {
+                const int q = gown[w * 32 + lane];
+#pragma unroll
+                for (int k = 0; k < kGeo; ++k) acc[q * kGeo + k] += gsum[(w * 32 + lane) * kGeo + k];
             }
         }
         __syncthreads();
@@ -153,14 +193,24 @@ __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const
     for (int q = t; q < nown * kGeo; q += kAdjTile) partials[size_t(blockIdx.x) * nown * kGeo + q] = acc[q];
 }
 
-// Sum of the block partials in block order.
-__global__ void k_adjoint_reduce(int nblocks, int nd, const double* __restrict__ partials,
-                                 double* __restrict__ gtrans, double* __restrict__ gparams) {
+// Sum of the block partials: one block per (owner, component) column; thread
+// t adds the partials t, t + 256, ... in order, then a fixed shared-memory
+// tree adds the 256 thread sums.  The order depends only on the block count.
+__global__ void __launch_bounds__(256) k_adjoint_reduce(int nblocks, int nd, const double* __restrict__ partials,
+                                                        double* __restrict__ gtrans, double* __restrict__ gparams) {
+    __shared__ double red[256];
     const int nown = nd + 1;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nown * kGeo) return;
+    const int q = blockIdx.x;                        // column: owner q / kGeo, component q % kGeo
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[size_t(b) * nown * kGeo + q];
+    for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[size_t(b) * nown * kGeo + q];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    s = red[0];
     const int o = q / kGeo, k = q % kGeo;
     if (k < 3) {
         if (o < nd && gtrans) gtrans[3 * o + k] = s;
@@ -169,9 +219,14 @@ __global__ void k_adjoint_reduce(int nblocks, int nd, const double* __restrict__
     }
 }
 
+size_t adjoint_smem_bytes(int nd) {
+    return (size_t(nd + 1) * kGeo + size_t(kAdjWarps) * 32 * kGeo) * sizeof(double) +
+           size_t(kAdjWarps) * 32 * sizeof(int);
+}
+
 int adjoint_blocks(int64_t n, int num_sms) {
     const int64_t need = (n + kAdjTile - 1) / kAdjTile;
-    const int64_t cap = int64_t(2) * num_sms;
+    const int64_t cap = int64_t(2) * num_sms;   // two resident blocks per SM (96 registers a thread)
     return int(need < 1 ? 1 : (need < cap ? need : cap));
 }
 
@@ -183,15 +238,13 @@ cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit
                            double* gd, double* gtrans, double* gparams, double* workspace, cudaStream_t s,
                            int num_sms) {
     const int nb = adjoint_blocks(b.n, num_sms);
-    const int smem = int((size_t(v.nd + 1) * kGeo + size_t(kGeo) * kAdjTile) * sizeof(double) +
-                         kAdjTile * sizeof(int));
+    const int smem = int(adjoint_smem_bytes(v.nd));
     cudaError_t e = prep(k_adjoint, smem);
     if (e != cudaSuccess) return e;
     k_adjoint<<<nb, kAdjTile, smem, s>>>(v, b, hit, gstep, gp, gd, workspace);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (gtrans || gparams) {
-        const int tot = (v.nd + 1) * kGeo;
-        k_adjoint_reduce<<<(tot + 255) / 256, 256, 0, s>>>(nb, v.nd, workspace, gtrans, gparams);
+        k_adjoint_reduce<<<(v.nd + 1) * kGeo, 256, 0, s>>>(nb, v.nd, workspace, gtrans, gparams);
         e = cudaGetLastError();
     }
     return e;

@@ -682,8 +682,7 @@ geo_status geo_dist_to_boundary_adjoint(geo_volume v, const double* x, const dou
         return GEO_ERR_INVALID_ARG;
     const int sms = num_sms_of(v->device);
     if (workspace_bytes < adjoint_workspace_bytes(v->view.nd, n, sms)) return GEO_ERR_INVALID_ARG;
-    const size_t smem = (size_t(v->view.nd + 1) * 8 + 8 * 256) * sizeof(double) + 256 * sizeof(int);
-    if (int64_t(smem) > smem_budget(v->device)) return GEO_ERR_UNSUPPORTED;
+    if (int64_t(adjoint_smem_bytes(v->view.nd)) > smem_budget(v->device)) return GEO_ERR_UNSUPPORTED;
     const Basket b{x, y, z, dx, dy, dz, n};
     return cuda_status(launch_adjoint(v->view, b, hit, grad_step, grad_p, grad_d, grad_trans, grad_params,
                                       static_cast<double*>(workspace), static_cast<cudaStream_t>(stream), sms));

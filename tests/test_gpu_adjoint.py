@@ -58,12 +58,22 @@ def forward(g, vol, tr, mode=0):
     return s, h
 
 
-def close(got, want, err, rel=1e-6):
+def close(got, want, err, trunc, rel=1e-6):
     """Central difference vs the adjoint: each forward step is within about
     twice the oracle's a-priori bound `err` of the exact one, so the
-    difference quotient carries up to 2 err / H of rounding."""
-    tol = rel * np.maximum(1.0, np.abs(want)) + 2.0 * err / H
+    difference quotient carries up to 2 err / H of rounding; `trunc` is the
+    difference quotient's own truncation error, estimated from a second
+    quotient at H/2 (large only next to tangency, where the step's higher
+    derivatives blow up)."""
+    tol = rel * np.maximum(1.0, np.abs(want)) + 2.0 * err / H + trunc
     return np.abs(got - want) <= tol
+
+
+def central(fstep, base, k, h):
+    a, b = base.copy(), base.copy()
+    a[:, k] += h
+    b[:, k] -= h
+    return (fstep(a) - fstep(b)) / (2 * h)
 
 
 @pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("toy8", 1 << 16)])
@@ -89,15 +99,21 @@ def test_track_gradients(g, orc, name, n):
     p, d = points(tr), dirs(tr)
     for k in range(3):
         for which, base in (("p", p), ("d", d)):
-            a, b = base.copy(), base.copy()
-            a[:, k] += H
-            b[:, k] -= H
-            ta = tracks_from(a, d) if which == "p" else tracks_from(p, a)
-            tb = tracks_from(b, d) if which == "p" else tracks_from(p, b)
-            fd = (forward(g, vol, ta)[0].cpu().numpy() - forward(g, vol, tb)[0].cpu().numpy()) / (2 * H)
+            def fstep(q):
+                t = tracks_from(q, d) if which == "p" else tracks_from(p, q)
+                return forward(g, vol, t)[0].cpu().numpy()
+
+            fd = central(fstep, base, k, H)
+            fd2 = central(fstep, base, k, H / 2)
+            # truncation of the H quotient ~ 4/3 of its difference to the H/2
+            # one, plus the rounding the H/2 quotient adds to that difference
+            trunc = 4.0 / 3.0 * np.abs(fd - fd2) + 4.0 * err / H
             got = (gp if which == "p" else gd)[k]
-            bad = ~close(got[ok], fd[ok], err[ok])
+            bad = ~close(got[ok], fd[ok], err[ok], trunc[ok])
             assert not bad.any(), (which, k, int(bad.sum()))
+            # truncation above the rounding noise is rare (next to tangency)
+            big = 4.0 / 3.0 * np.abs(fd - fd2) > 1e-6 * np.maximum(1.0, np.abs(fd)) + 8.0 * err / H
+            assert np.mean(big[ok]) < 0.01
 
 
 def _scene_with(sc, trans=None, params=None, mparams=None):
