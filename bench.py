@@ -367,14 +367,56 @@ def queries_leg(pkg, scenes, rank, steps, sc):
     saf = torch.empty(n, dtype=torch.float64, device="cuda")
     out = {"workload": "toy detector (40 daughters), 2^22 points uniform in the mother (daughters included), "
                        "4 rotating copies; steps %d" % steps}
-    ms = _event_time(lambda it: pkg.geo_contains(vol, *copies[it % 4], where=where), steps)
-    out["contains"] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
-                       "algorithmic_gb_s": 28.0 * n / (ms * 1e-3) / 1e9}
+    for mode, key in ((0, "contains_fp64"), (1, "contains_fp32_refine")):
+        ms = _event_time(lambda it: pkg.geo_contains(vol, *copies[it % 4], mode=mode, where=where), steps)
+        out[key] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
+                    "algorithmic_gb_s": 28.0 * n / (ms * 1e-3) / 1e9}
     for mode, key in ((0, "safety_fp64"), (1, "safety_fp32_refine")):
         ms = _event_time(lambda it: pkg.geo_safety(vol, *copies[it % 4], mode=mode, safety=saf), steps)
         out[key] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
                     "algorithmic_gb_s": 32.0 * n / (ms * 1e-3) / 1e9}
     vol.close()
+    return out
+
+
+def shapes_leg(pkg, steps, q_sqrt, q_div):
+    """Each solid's queries on their own (the per-shape algorithms of Sec. 3.1
+    that Fig. 2 times per shape): DistFromOutside and DistFromInside of a box,
+    a tube shell and a hollow cone, for baskets of 1024 tracks (launch-bound:
+    microseconds per call) and 2^20 tracks (8 rotating copies, 403 MB > L2);
+    FP64 work per track from the routines' instruction mix (placement
+    transform included), as a fraction of the FP64 peak."""
+    import torch
+
+    solids = {"box": (0, (10.0, 20.0, 30.0)), "tube": (1, (5.0, 20.0, 30.0)),
+              "cone": (2, (30.0, 5.0, 10.0, 8.0, 20.0))}
+    out = {"workload": "points uniform in 1.5x the solid's extent (inside and outside), isotropic directions; "
+                       "identity placement; steps %d" % steps}
+    rng = np.random.default_rng(5)
+    for name, (kind, prm) in solids.items():
+        ext = np.array(prm[:3]) if kind == 0 else (np.array([prm[1], prm[1], prm[2]]) if kind == 1
+                                                   else np.array([max(prm[2], prm[4])] * 2 + [prm[0]]))
+        row = {}
+        for n in (1024, 1 << 20):
+            x = rng.uniform(-1.5, 1.5, size=(n, 3)) * ext
+            v = rng.normal(size=(n, 3))
+            v /= np.linalg.norm(v, axis=1, keepdims=True)
+            base = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (*x.T, *v.T)]
+            ncp = 8 if n > 1024 else 1
+            g = torch.Generator(device="cuda")
+            g.manual_seed(11)
+            copies = [base] + [[f[p].contiguous() for f in base]
+                               for p in (torch.randperm(n, device="cuda", generator=g) for _ in range(ncp - 1))]
+            res = torch.empty(n, dtype=torch.float64, device="cuda")
+            for what, key in ((pkg.GEO_Q_DIST_OUT, "out"), (pkg.GEO_Q_DIST_IN, "in")):
+                ms = _event_time(lambda it: pkg.geo_shape_query(kind, prm, what, *copies[it % ncp], out=res), steps)
+                a, sq, dv = FP64_OPS[(key, kind)]
+                ops = FP64_TRANSFORM + a + sq * q_sqrt + dv * q_div
+                achieved = n * ops * 2 / (ms * 1e-3) / 1e12
+                row[f"dist_{key}_{n}"] = {"value": n / (ms * 1e-3), "unit": "tracks/s", "us_per_call": ms * 1e3,
+                                          "fp64_dfma_equiv_per_track": ops,
+                                          "fp64_frac": achieved / PEAK_FP64_TFLOPS}
+        out[name] = row
     return out
 
 
@@ -390,6 +432,7 @@ def main():
     ap.add_argument("--no-voxel", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-queries", action="store_true")
+    ap.add_argument("--no-shapes", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -528,6 +571,7 @@ def main():
     voxel = None if args.no_voxel else voxel_leg(pkg, scenes, rank, max(5, args.steps // 200))
     adjoint = None if args.no_adjoint else adjoint_leg(pkg, scenes, rank, max(10, args.steps // 40))
     queries = None if args.no_queries else queries_leg(pkg, scenes, rank, max(10, args.steps // 100), sc)
+    shapes = None if args.no_shapes else shapes_leg(pkg, max(10, args.steps // 100), q_sqrt, q_div)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -555,6 +599,7 @@ def main():
             "voxel_512": voxel,
             "adjoint": adjoint,
             "contains_safety": queries,
+            "shapes": shapes,
         }
         print(json.dumps(line), flush=True)
     vol.close()

@@ -92,6 +92,31 @@ typedef struct {
 
 typedef struct geo_volume_s* geo_volume;
 
+/* ---- one solid on its own (Sec. 3.1's per-shape algorithms, as measured
+ * per shape in Fig. 2) ------------------------------------------------------ */
+typedef enum {
+    GEO_Q_DIST_OUT = 0,    /* DistFromOutside: inf{s >= 0 : x + s u in solid}; 0 inside; +inf miss */
+    GEO_Q_DIST_IN = 1,     /* DistFromInside: end of the component of s = 0; 0 for x outside       */
+    GEO_Q_SAFETY_OUT = 2,  /* distance from a point outside to the solid; 0 inside                 */
+    GEO_Q_SAFETY_IN = 3,   /* distance from a point inside to the boundary; 0 outside              */
+    GEO_Q_CONTAINS = 4     /* 1.0 if the closed solid contains the point, else 0.0                 */
+} geo_shape_query_kind;
+
+/* Evaluates one query of one placed solid for n tracks: positions x,y,z and
+ * (for the two distances) directions dx,dy,dz are device FP64[n] in the frame
+ * the solid is placed in (the placement's master->local transform is applied
+ * per track; an identity placement queries the solid in its own frame).
+ * Writes out[n] (device FP64) and, if face is not NULL, face[n] (device
+ * int32): the surface crossed by a distance (box 0..5 = -x,+x,-y,+y,-z,+z;
+ * tube and cone 4/5 = -z/+z planes, 6 outer, 7 inner; -1 none), -1 for the
+ * other queries.  dx,dy,dz may be NULL for the safeties and Contains.
+ * Non-finite input, or a zero direction for a distance: NaN.  The values are
+ * those of the navigator's FP64 routines.  Errors: bad kind or parameters of
+ * the solid (as geo_build_volume), bad query, host pointers. */
+geo_status geo_shape_query(const geo_placed_shape* shape, int32_t what, const double* x, const double* y,
+                           const double* z, const double* dx, const double* dy, const double* dz, int64_t n,
+                           double* out, int32_t* face, void* stream);
+
 /* Builds the device tables of one logical volume (Fig. 1: a mother and its
  * daughter volumes).  `mother` and `daughters[0..n_daughters)` are host
  * structs, copied; the caller may free them on return.  n_daughters may be 0.

@@ -8,4 +8,6 @@ from .geonav import (GEO_BOX, GEO_CONE, GEO_FP32_REFINE, GEO_FP64, GEO_TUBE, Geo
                      geo_dist_to_boundary_host, geo_dist_to_boundary_stats, geo_check_device_status, geo_probe_pipe,
                      geo_safety, geo_status_string, geo_volume_info, load, Batch, geo_build_batch,
                      geo_destroy_batch, geo_dist_to_boundary_batched, geo_dist_to_boundary_batched_noalloc,
-                     geo_adjoint_workspace_size, geo_dist_to_boundary_adjoint)
+                     geo_adjoint_workspace_size, geo_dist_to_boundary_adjoint,
+                     geo_shape_query, GEO_Q_DIST_OUT, GEO_Q_DIST_IN, GEO_Q_SAFETY_OUT, GEO_Q_SAFETY_IN,
+                     GEO_Q_CONTAINS)

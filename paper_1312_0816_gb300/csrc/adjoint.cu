@@ -86,6 +86,7 @@ __device__ __forceinline__ void surface_grad64(const ShapeRec64& r, int face, co
 }
 
 constexpr int kAdjWarps = kAdjTile / 32;
+constexpr int kTval = kAdjTile + 1;   // odd row length: the 8 components of one entry fall in different banks
 
 __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const int32_t* __restrict__ hit,
                                                      const double* __restrict__ gstep, double* __restrict__ gp,
@@ -94,7 +95,9 @@ __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const
     const int nown = v.nd + 1;                       // daughters, then the mother
     double* acc = smem_adj;                          // [nown * kGeo]
     double* gsum = acc + size_t(nown) * kGeo;        // [kAdjWarps][32][kGeo] group sums
-    int* gown = reinterpret_cast<int*>(gsum + kAdjWarps * 32 * kGeo);   // [kAdjWarps][32] group owners
+    double* tval = gsum + kAdjWarps * 32 * kGeo;     // [kGeo][kTval] per-track contributions
+    int* gown = reinterpret_cast<int*>(tval + kGeo * kTval);   // [kAdjWarps][32] group owners
+    int* town = gown + kAdjWarps * 32;                // [kAdjTile] per-track owners
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int q = t; q < nown * kGeo; q += kAdjTile) acc[q] = 0.0;
     __syncthreads();
@@ -154,29 +157,34 @@ __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const
                 gd[k * b.n + i] = od[k];
             }
         }
-        // group the warp's lanes by owner; each group is summed by the same
-        // butterfly (non-members contribute 0) and its lowest lane keeps it
-        int ngroups = 0;
+        // group the warp's lanes by owner (in order of first appearance); then
+        // lane l sums component l % 8 of group l / 8 (and of group l / 8 + 4,
+        // ... when there are more than four) over the warp's 32 entries in
+        // lane order.  One FP64 add per entry serves four groups at once.
+        double* wv = tval + warp * 32;                 // tval[k * kTval + warp * 32 + e]
+        int* wo = town + warp * 32;
+        wo[lane] = o;
+#pragma unroll
+        for (int k = 0; k < kGeo; ++k) wv[k * kTval + lane] = c[k];
+        int ngroups = 0, myq = -1;
         unsigned pending = __ballot_sync(0xffffffffu, o >= 0);
         while (pending) {
             const int leader = __ffs(pending) - 1;
             const int q = __shfl_sync(0xffffffffu, o, leader);
-            const bool mine = o == q;
-            double sum[kGeo];
-#pragma unroll
-            for (int k = 0; k < kGeo; ++k) sum[k] = mine ? c[k] : 0.0;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                for (int k = 0; k < kGeo; ++k) sum[k] += __shfl_xor_sync(0xffffffffu, sum[k], off);
-            }
-            if (lane == leader) {
-                gown[warp * 32 + ngroups] = q;
-#pragma unroll
-                for (int k = 0; k < kGeo; ++k) gsum[(warp * 32 + ngroups) * kGeo + k] = sum[k];
-            }
+            if (lane == ngroups) myq = q;
             ++ngroups;
-            pending &= ~__ballot_sync(0xffffffffu, mine);
+            pending &= ~__ballot_sync(0xffffffffu, o == q);
+        }
+        __syncwarp();
+        for (int base = 0; base < ngroups; base += 4) {
+            const int g = base + (lane >> 3), k = lane & 7;
+            const int q = __shfl_sync(0xffffffffu, myq, g & 31);
+            double sum = 0.0;
+            for (int e = 0; e < 32; ++e) sum += wo[e] == q ? wv[k * kTval + e] : 0.0;
+            if (g < ngroups) {
+                gsum[(warp * 32 + g) * kGeo + k] = sum;
+                if (k == 0) gown[warp * 32 + g] = q;
+            }
         }
         // the warps add their groups one after the other (fixed order); the
         // groups of one warp have distinct owners
@@ -220,8 +228,8 @@ __global__ void __launch_bounds__(256) k_adjoint_reduce(int nblocks, int nd, con
 }
 
 size_t adjoint_smem_bytes(int nd) {
-    return (size_t(nd + 1) * kGeo + size_t(kAdjWarps) * 32 * kGeo) * sizeof(double) +
-           size_t(kAdjWarps) * 32 * sizeof(int);
+    return (size_t(nd + 1) * kGeo + size_t(kAdjWarps) * 32 * kGeo + size_t(kGeo) * kTval) * sizeof(double) +
+           (size_t(kAdjWarps) * 32 + kAdjTile) * sizeof(int);
 }
 
 int adjoint_blocks(int64_t n, int num_sms) {

@@ -688,6 +688,26 @@ geo_status geo_dist_to_boundary_adjoint(geo_volume v, const double* x, const dou
                                       static_cast<double*>(workspace), static_cast<cudaStream_t>(stream), sms));
 }
 
+geo_status geo_shape_query(const geo_placed_shape* shape, int32_t what, const double* x, const double* y,
+                           const double* z, const double* dx, const double* dy, const double* dz, int64_t n,
+                           double* out, int32_t* face, void* stream) {
+    if (!shape) return GEO_ERR_INVALID_ARG;
+    geo_status st = check_shape(*shape, false);
+    if (st != GEO_OK) return st;
+    if (what < GEO_Q_DIST_OUT || what > GEO_Q_CONTAINS) return GEO_ERR_INVALID_ARG;
+    if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
+    if (n == 0) return GEO_OK;
+    const bool dist = what == GEO_Q_DIST_OUT || what == GEO_Q_DIST_IN;
+    if (dist && (!is_device_ptr(dx) || !is_device_ptr(dy) || !is_device_ptr(dz))) return GEO_ERR_INVALID_ARG;
+    if (!is_device_ptr(out) || (face && !is_device_ptr(face))) return GEO_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
+    const ShapeRec64 r = make_rec64(*shape);
+    const Basket b{x, y, z, dist ? dx : nullptr, dist ? dy : nullptr, dist ? dz : nullptr, n};
+    return cuda_status(launch_shape_query(r, what, b, out, face, static_cast<cudaStream_t>(stream),
+                                          num_sms_of(dev)));
+}
+
 geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const double* y, const double* z,
                                       const double* dx, const double* dy, const double* dz, int64_t n, double* step,
                                       int32_t* hit, int32_t* nref, void* stream) {

@@ -118,6 +118,8 @@ cudaError_t launch_contains_filter(const VolView& v, const Basket& b, int32_t* w
                                    int num_sms);
 cudaError_t launch_safety_filter(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms);
 
+cudaError_t launch_shape_query(const ShapeRec64& r, int what, const Basket& b, double* out, int32_t* face,
+                               cudaStream_t s, int num_sms);
 size_t adjoint_smem_bytes(int nd);
 size_t adjoint_workspace_bytes(int nd, int64_t n, int num_sms);
 cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit, const double* gstep, double* gp,

@@ -104,10 +104,17 @@ __device__ __forceinline__ bool beyond(const ShapeRec32& r, float c2, float L) {
     return c2 > lim * lim * (1.f + kSafMargin);
 }
 
-// Safety of one point; *nev counts the FP64 evaluations.
-__device__ __forceinline__ double safety_filter(const VolView& v, const ShapeRec32* __restrict__ t32,
-                                                const double* p, const float* p32, float tau, int* nev) {
-    if (!mother_contains(v, p, p32)) return 0.0;
+// FP32 pass of the safety of one point: the two smallest lower bounds (L1 of
+// candidate j1, L2) and the mother's bound Lm.  Returns false when the point
+// is outside the mother (safety 0, no FP64 work).
+struct SafetyState {
+    float Lm, L2;
+    int j1;
+};
+
+__device__ __forceinline__ bool safety_pass1(const VolView& v, const ShapeRec32* __restrict__ t32, const double* p,
+                                             const float* p32, SafetyState& st) {
+    if (!mother_contains(v, p, p32)) return false;
     const float Lm = safety_in_lb32(v.m32, p32);
     float L1 = Lm, L2 = f_inf();
     int j1 = -1;
@@ -126,18 +133,29 @@ __device__ __forceinline__ double safety_filter(const VolView& v, const ShapeRec
             L2 = l;
         }
     }
-    double s = safety_of(v, j1, p);
+    st.Lm = Lm;
+    st.L2 = L2;
+    st.j1 = j1;
+    return true;
+}
+
+// Given s = the FP64 safety of candidate j1: done if the second bound
+// exceeds s; otherwise every other candidate whose bound does not exceed the
+// running minimum is evaluated in FP64.  *nev counts the evaluations.
+__device__ __forceinline__ double safety_finish(const VolView& v, const ShapeRec32* __restrict__ t32,
+                                                const double* p, const float* p32, const SafetyState& st,
+                                                double s, float tau, int* nev) {
     int ne = 1;
     float th = above(s, tau);
-    if (!(L2 > th)) {
+    if (!(st.L2 > th)) {
         // another candidate may still be below s: visit them all
-        if (j1 >= 0 && !(Lm > th)) {
+        if (st.j1 >= 0 && !(st.Lm > th)) {
             s = fmin(s, safety_of(v, -1, p));
             ++ne;
             th = above(s, tau);
         }
         for (int j = 0; j < v.nd; ++j) {
-            if (j == j1) continue;
+            if (j == st.j1) continue;
             const ShapeRec32& r = t32[j];
             float o[3], x[3];
             const float c2 = offset32(r, p32, o);
@@ -151,6 +169,17 @@ __device__ __forceinline__ double safety_filter(const VolView& v, const ShapeRec
     }
     *nev = ne;
     return s;
+}
+
+// Safety of one point (the two phases back to back).
+__device__ __forceinline__ double safety_filter(const VolView& v, const ShapeRec32* __restrict__ t32,
+                                                const double* p, const float* p32, float tau, int* nev) {
+    SafetyState st;
+    if (!safety_pass1(v, t32, p, p32, st)) {
+        *nev = 0;
+        return 0.0;
+    }
+    return safety_finish(v, t32, p, p32, st, safety_of(v, st.j1, p), tau, nev);
 }
 
 // 2^-36 of the mother's extent: far above the FP64 rounding of any safety

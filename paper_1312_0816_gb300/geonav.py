@@ -52,7 +52,7 @@ EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dis
            "geo_contains", "geo_safety", "geo_dist_to_boundary_host", "geo_dist_to_boundary_stats",
            "geo_check_device_status", "geo_probe_pipe", "geo_build_batch", "geo_destroy_batch",
            "geo_dist_to_boundary_batched", "geo_dist_to_boundary_batched_noalloc", "geo_adjoint_workspace_size",
-           "geo_dist_to_boundary_adjoint", "geo_status_string")
+           "geo_dist_to_boundary_adjoint", "geo_shape_query", "geo_status_string")
 
 
 def library_path() -> str:
@@ -78,6 +78,7 @@ def load(build_if_stale: bool = True):
     L.geo_dist_to_boundary.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, dp, i32, vp]
     L.geo_contains.argtypes = [vp, dp, dp, dp, i64, ip, i32, vp]
     L.geo_safety.argtypes = [vp, dp, dp, dp, i64, dp, i32, vp]
+    L.geo_shape_query.argtypes = [ctypes.POINTER(geo_placed_shape), i32, dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
     L.geo_dist_to_boundary_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, i32, i64, vp]
     L.geo_dist_to_boundary_stats.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, ip, vp]
     L.geo_check_device_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
@@ -241,6 +242,32 @@ def geo_safety(vol: Volume, x, y, z, mode: int = GEO_FP32_REFINE, safety=None, s
     _check(load().geo_safety(vol.handle, _dev(x, f64, n, "x"), _dev(y, f64, n, "y"), _dev(z, f64, n, "z"), n,
                              _dev(safety, f64, n, "safety"), int(mode), _stream(stream)), "geo_safety")
     return safety
+
+
+GEO_Q_DIST_OUT, GEO_Q_DIST_IN, GEO_Q_SAFETY_OUT, GEO_Q_SAFETY_IN, GEO_Q_CONTAINS = range(5)
+
+
+def geo_shape_query(kind, params, what, x, y, z, dx=None, dy=None, dz=None, rot=None, trans=None, out=None,
+                    face=None, want_face=False, stream=None):
+    """One solid's DistFromOutside / DistFromInside / safeties / Contains for a
+    basket of CUDA float64 tensors (positions in the frame the solid is placed
+    in).  Returns out, or (out, face) with want_face."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    if out is None:
+        out = torch.empty(n, dtype=f64, device=x.device)
+    if want_face and face is None:
+        face = torch.empty(n, dtype=torch.int32, device=x.device)
+    shape = _shape_struct(kind, params, rot, trans)
+    dist = what in (GEO_Q_DIST_OUT, GEO_Q_DIST_IN)
+    dirs = [_dev(a, f64, n, nm) if dist else ctypes.c_void_p(0) for a, nm in ((dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    _check(load().geo_shape_query(ctypes.byref(shape), int(what), _dev(x, f64, n, "x"), _dev(y, f64, n, "y"),
+                                  _dev(z, f64, n, "z"), *dirs, n, _dev(out, f64, n, "out"),
+                                  _dev(face, torch.int32, n, "face") if face is not None else ctypes.c_void_p(0),
+                                  _stream(stream)), "geo_shape_query")
+    return (out, face) if want_face else out
 
 
 def geo_dist_to_boundary_host(vol: Volume, x, y, z, dx, dy, dz, mode: int = GEO_FP32_REFINE, step=None, hit=None,

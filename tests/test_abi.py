@@ -89,3 +89,19 @@ def test_null_arguments():
     assert L.geo_contains(None, None, None, None, 0, None, 0, None) == 1
     assert L.geo_safety(None, None, None, None, 0, None, 0, None) == 1
     assert L.geo_destroy_volume(None) == 0
+
+
+def test_shape_query_validation():
+    """Rejected before any device work: null shape, bad kind or parameters,
+    unknown query, negative n; n == 0 with a valid solid is a no-op."""
+    L = geonav.load()
+    assert L.geo_shape_query(None, 0, None, None, None, None, None, None, 0, None, None, None) == 1
+    good = _shape(1, (5, 10, 20))
+    assert L.geo_shape_query(ctypes.byref(good), 0, None, None, None, None, None, None, 0, None, None, None) == 0
+    assert L.geo_shape_query(ctypes.byref(good), 5, None, None, None, None, None, None, 0, None, None, None) == 1
+    assert L.geo_shape_query(ctypes.byref(good), -1, None, None, None, None, None, None, 0, None, None, None) == 1
+    assert L.geo_shape_query(ctypes.byref(good), 0, None, None, None, None, None, None, -1, None, None, None) == 1
+    bad = _shape(1, (10, 5, 20))   # rmin > rmax
+    assert L.geo_shape_query(ctypes.byref(bad), 0, None, None, None, None, None, None, 0, None, None, None) == 2
+    kind = _shape(7, (1, 1, 1))
+    assert L.geo_shape_query(ctypes.byref(kind), 0, None, None, None, None, None, None, 0, None, None, None) == 1

@@ -1,0 +1,141 @@
+"""Per-shape queries (Sec. 3.1, measured per shape in Fig. 2) on the GPU
+against the oracle's shape routines: DistFromOutside, DistFromInside, the two
+safeties and Contains of one Box, Tube or Cone, in its own frame and placed.
+
+Bars: distances within 1e-9 mm (relative to max(1, s)) and the crossed face
+equal, except on a small fraction of rays that graze a surface or cross at an
+edge (both answers are then correct to rounding); safeties within 1e-9 mm;
+Contains exact outside the 1e-9 mm surface band.
+"""
+import numpy as np
+import pytest
+
+from paper_1312_0816_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+SOLIDS = [
+    (0, (10.0, 20.0, 30.0)),
+    (1, (0.0, 20.0, 30.0)),
+    (1, (5.0, 20.0, 30.0)),
+    (2, (30.0, 0.0, 10.0, 0.0, 20.0)),
+    (2, (30.0, 5.0, 10.0, 8.0, 20.0)),
+    (2, (30.0, 0.0, 10.0, 5.0, 20.0)),
+    (2, (30.0, 0.0, 0.0, 0.0, 20.0)),
+]
+WHAT = {"dist_out": 0, "dist_in": 1, "safety_out": 2, "safety_in": 3, "contains": 4}
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1312_0816_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.load()
+    return pkg
+
+
+def extent(kind, p):
+    if kind == 0:
+        return np.array(p[:3])
+    if kind == 1:
+        return np.array([p[1], p[1], p[2]])
+    r = max(p[2], p[4])
+    return np.array([r, r, p[0]])
+
+
+def sample(kind, p, n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1.5, 1.5, size=(n, 3)) * extent(kind, p)
+    u = np.stack(scenes.isotropic(rng, n), axis=1)
+    return x, u
+
+
+def on_surface(orc, kind, p, x, u):
+    """Points on the surface: the oracle's DistFromOutside hits, moved by
+    0, +-1e-12 and +-1e-7 mm along the ray."""
+    s, _ = orc.shape(kind, p, x, u, "dist_out")
+    m = np.isfinite(s) & (s > 0)
+    hit = x[m] + s[m, None] * u[m]
+    pts = [hit + e * u[m] for e in (0.0, 1e-12, -1e-12, 1e-7, -1e-7)]
+    dirs = [u[m]] * 5
+    return np.concatenate(pts), np.concatenate(dirs)
+
+
+def gpu(g, kind, p, what, x, u, rot=None, trans=None):
+    t = [torch.from_numpy(np.ascontiguousarray(x[:, k])).cuda() for k in range(3)]
+    d = [torch.from_numpy(np.ascontiguousarray(u[:, k])).cuda() for k in range(3)]
+    out, face = g.geo_shape_query(kind, p, WHAT[what], *t, *d, rot=rot, trans=trans, want_face=True)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), face.cpu().numpy()
+
+
+def check_distance(got, gface, want, wface, max_bad):
+    """Values within TOL; the crossed face must agree where the crossing is
+    more than TOL away (a point on the surface has none that is unique)."""
+    both_inf = np.isinf(got) & np.isinf(want)
+    with np.errstate(invalid="ignore"):
+        close = both_inf | (np.abs(got - want) <= TOL * np.maximum(1.0, np.abs(want)))
+    same_face = (gface == wface) | (want <= TOL)
+    bad = ~(close & same_face)
+    assert bad.mean() <= max_bad, (bad.sum(), got[bad][:5], want[bad][:5], gface[bad][:5], wface[bad][:5])
+
+
+@pytest.mark.parametrize("idx", range(len(SOLIDS)))
+def test_shape_queries_match_oracle(g, orc, idx):
+    kind, p = SOLIDS[idx]
+    x, u = sample(kind, p, 200000, 100 + idx)
+    xs, us = on_surface(orc, kind, p, x[:20000], u[:20000])
+    for pts, dirs, max_bad in ((x, u, 1e-5), (xs, us, 2e-3)):
+        # within 1e-9 mm of the surface, inside/outside (and so both
+        # distances) is decided by rounding: that band is exempt
+        band = orc.shape(kind, p, pts, None, "safety_out") + orc.shape(kind, p, pts, None, "safety_in") < TOL
+        for what in ("dist_out", "dist_in"):
+            got, gface = gpu(g, kind, p, what, pts, dirs)
+            want, wface = orc.shape(kind, p, pts, dirs, what)
+            check_distance(got[~band], gface[~band], want[~band], wface[~band], max_bad)
+        for what in ("safety_out", "safety_in"):
+            got, gface = gpu(g, kind, p, what, pts, dirs)
+            want = orc.shape(kind, p, pts, None, what)
+            assert np.max(np.abs(got - want)) <= TOL, what
+            assert np.all(gface == -1)
+        got, _ = gpu(g, kind, p, "contains", pts, dirs)
+        want = orc.shape(kind, p, pts, None, "contains")
+        assert np.array_equal(got[~band], want[~band])
+
+
+@pytest.mark.parametrize("idx", [0, 2, 4])
+def test_placed_solid(g, orc, idx):
+    """Placement applied in the kernel: compare with the oracle on points
+    transformed on the host (the transforms round differently, so distances
+    get a 1e-9 relative tolerance and Contains the surface band)."""
+    kind, p = SOLIDS[idx]
+    rng = np.random.default_rng(7 + idx)
+    R = np.asarray(scenes.haar_rotation(rng)).reshape(3, 3)
+    t = np.array([120.0, -40.0, 75.0])
+    xl, ul = sample(kind, p, 50000, 200 + idx)
+    xw = xl @ R.T + t
+    uw = ul @ R.T
+    x_back = (xw - t) @ R
+    u_back = uw @ R
+    for what in ("dist_out", "dist_in"):
+        got, gface = gpu(g, kind, p, what, xw, uw, rot=R, trans=t)
+        want, wface = orc.shape(kind, p, x_back, u_back, what)
+        check_distance(got, gface, want, wface, 1e-4)
+    got, _ = gpu(g, kind, p, "safety_out", xw, uw, rot=R, trans=t)
+    want = orc.shape(kind, p, x_back, None, "safety_out")
+    assert np.max(np.abs(got - want)) <= 1e-9 * 300
+
+
+def test_invalid_inputs(g):
+    x = np.array([[np.nan, 0, 0], [0, np.inf, 0], [1.0, 2.0, 3.0]])
+    u = np.array([[1.0, 0, 0], [1.0, 0, 0], [0.0, 0.0, 0.0]])
+    for what in ("dist_out", "dist_in"):
+        got, face = gpu(g, 1, (5.0, 20.0, 30.0), what, x, u)
+        assert np.all(np.isnan(got)) and np.all(face == -1)
+    got, _ = gpu(g, 1, (5.0, 20.0, 30.0), "safety_out", x[:2], u[:2])
+    assert np.all(np.isnan(got))
