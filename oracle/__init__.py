@@ -52,6 +52,13 @@ def lib():
         L.orc_adjoint.restype = None
         L.orc_shape_batch.argtypes = [ctypes.c_int, dp, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ip]
         L.orc_shape_batch.restype = None
+        world = [ctypes.c_int, ip, dp, ip, ip, ip, dp, dp, dp, ip, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip]
+        L.orc_world_nodes.argtypes = world
+        L.orc_world_nodes.restype = ctypes.c_int
+        L.orc_world_locate.argtypes = world + [ctypes.c_int64, dp, dp, dp, ip]
+        L.orc_world_locate.restype = ctypes.c_int
+        L.orc_world_step.argtypes = world + [ctypes.c_int64] + [dp] * 6 + [ip, ip, dp, ip, ip]
+        L.orc_world_step.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -156,3 +163,55 @@ def shape(kind: int, params, x, u=None, what: str = "dist_out"):
     if what in ("dist_out", "dist_in"):
         return out, face
     return out
+
+
+MAX_NODES = 1 << 20
+
+
+def _world_args(world, max_nodes=MAX_NODES):
+    f = world.flat()
+    keep, args = [], []
+    nlv = len(world.volumes)
+    for key, conv in (("mkind", _i), ("mparams", _d), ("nd", _i), ("doff", _i), ("kinds", _i), ("params", _d),
+                      ("rot", _d), ("trans", _d), ("child", _i)):
+        a, ptr = conv(np.asarray(f[key]).reshape(-1))
+        keep.append(a)
+        args.append(ptr)
+    table = [np.zeros(max_nodes, dtype=np.int32) for _ in range(4)]
+    keep += table
+    return keep, table, [nlv] + args + [f["root"], max_nodes] + [_i(t)[1] for t in table]
+
+
+def world_nodes(world):
+    """Breadth-first node table: dict of lv, parent, slot, first (child)."""
+    keep, table, args = _world_args(world)
+    nn = lib().orc_world_nodes(*args)
+    assert nn > 0
+    return {k: t[:nn].copy() for k, t in zip(("lv", "parent", "slot", "first"), table)}
+
+
+def world_locate(world, tracks):
+    """Node of every point (-1 outside the root, -2 non-finite)."""
+    keep, table, args = _world_args(world)
+    kt, targs = _track_args(tracks, 3)
+    node = np.empty(tracks.n, dtype=np.int32)
+    assert lib().orc_world_locate(*args, tracks.n, *targs, _i(node)[1]) > 0
+    return node
+
+
+def world_step(world, tracks, node_in, blocked_in=None):
+    """The step of Fig. 1 in each track's node (the daughter slot blocked_in
+    just left taken by its re-entry distance), then the track's node after
+    the step (-1 left the root, -2 not inside its node or invalid) and its
+    blocked slot.  Returns step, node, blocked."""
+    keep, table, args = _world_args(world)
+    kt, targs = _track_args(tracks)
+    nin, nptr = _i(node_in)
+    if blocked_in is None:
+        blocked_in = np.full(tracks.n, -1, dtype=np.int32)
+    bin_, bptr = _i(blocked_in)
+    step = np.empty(tracks.n)
+    node = np.empty(tracks.n, dtype=np.int32)
+    blk = np.empty(tracks.n, dtype=np.int32)
+    assert lib().orc_world_step(*args, tracks.n, *targs, nptr, bptr, _d(step)[1], _i(node)[1], _i(blk)[1]) > 0
+    return step, node, blk

@@ -334,6 +334,18 @@ static hitinfo dist_out_info(int kind, const double *p, const double *x, const d
     return h;
 }
 
+/* Re-entry into a solid the track has just left (its start point is on the
+ * solid's surface): the first component of S that begins after s = 0; the
+ * component holding (or ending at) the start point is the one just left. */
+static hitinfo dist_reentry_info(int kind, const double *p, const double *x, const double *u) {
+    iset S; line_set(kind, p, x, u, &S);
+    hitinfo h = { INFINITY, F_NONE, INFINITY };
+    for (int i = 0; i < S.n; i++) {
+        if (S.v[i].lo > 0.0) { h.s = S.v[i].lo; h.face = S.v[i].flo; h.chord = S.v[i].clo; return h; }
+    }
+    return h;
+}
+
 static hitinfo dist_in_info(int kind, const double *p, const double *x, const double *u) {
     iset S; line_set(kind, p, x, u, &S);
     hitinfo h = { 0.0, F_NONE, INFINITY };
@@ -502,7 +514,9 @@ typedef struct {
     double err;    /* a-priori FP64 error bound of the step                      */
 } navres;
 
-static navres navigate_one(const orc_scene *sc, const double *pw, const double *dw) {
+/* blocked >= 0: that daughter was just left through its surface; it enters
+ * the minimum with its re-entry distance instead of DistFromOutside (0). */
+static navres navigate_one_b(const orc_scene *sc, const double *pw, const double *dw, int blocked) {
     navres r;
     r.second = INFINITY; r.face = F_NONE; r.err = 0.0;
     if (bad_input(pw, dw)) { r.step = NAN; r.hit = -2; return r; }
@@ -514,7 +528,8 @@ static navres navigate_one(const orc_scene *sc, const double *pw, const double *
     for (int j = 0; j < sc->nd; j++) {
         double x[3], u[3];
         to_local(sc, j, pw, dw, x, u);
-        hitinfo h = dist_out_info(sc->kinds[j], sc->params + 5 * j, x, u);
+        hitinfo h = j == blocked ? dist_reentry_info(sc->kinds[j], sc->params + 5 * j, x, u)
+                                 : dist_out_info(sc->kinds[j], sc->params + 5 * j, x, u);
         if (h.s < best) {
             second = best;
             best = h.s; hit = j; face = h.face; chord = h.chord;
@@ -572,6 +587,10 @@ static navres navigate_one(const orc_scene *sc, const double *pw, const double *
         r.err = 8.0 * ldexp(1.0, -53) * (pn + tnorm + best * dn) * cond;
     }
     return r;
+}
+
+static navres navigate_one(const orc_scene *sc, const double *pw, const double *dw) {
+    return navigate_one_b(sc, pw, dw, -1);
 }
 
 static int contains_nav(const orc_scene *sc, const double *pw) {
@@ -759,4 +778,206 @@ void orc_shape_batch(int kind, const double *p, int64_t n, const double *x, cons
         else if (what == 3) out[i] = orc_safety(kind, p, xi, 0);
         else out[i] = orc_safety(kind, p, xi, 1);
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* geometry tree: a step followed by final localisation                 */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper's navigator stops at "the next boundary and the volume hit" and
+ * leaves the location of the track after the step out.  These functions
+ * write out that last part for a tree of logical volumes.  Readings:
+ *   - Logical volume v has a mother solid and daughters; daughter j of v is
+ *     an instance of logical volume child[doff[v] + j] (whose mother solid is
+ *     that daughter's solid), placed by the daughter's R, t.
+ *   - A node is one placed instance (a path from the root).  Nodes are
+ *     numbered breadth first: the root is 0; the children of a node get
+ *     consecutive numbers in daughter order, nodes being expanded in the
+ *     order they were numbered.
+ *   - Locate(x in node N): the lowest-index daughter of N whose closed solid
+ *     contains x becomes the new node, repeatedly; N itself when none does.
+ *   - After the step of Fig. 1 in node N (boundary point b, in N's frame):
+ *       hit j >= 0: the track is in child j; locate from there.
+ *       hit -1: it leaves N.  Climbing: in the parent P the lowest-index
+ *       daughter other than the one just left that contains b is entered
+ *       (then located); else P itself if its solid contains b; else the
+ *       track leaves P too and the climb goes on.  Leaving the root: -1.
+ *       hit -2 (track not inside N's solid, or invalid input): node -2.
+ *   - A track that has just left daughter j of its node (climbing) starts
+ *     on j's surface, inside j's closed solid, so DistFromOutside(j) = 0
+ *     would send it straight back.  Its next step takes for j the distance
+ *     to RE-ENTER j instead: the start of the first component of
+ *     { s : x + s u in j } that begins after s = 0 (+inf for a convex j;
+ *     across the hole for a shell).  The state of a track is therefore
+ *     (node, blocked slot), the slot being -1 after Locate or after
+ *     entering a daughter.
+ *   - The local point of a node is obtained by applying the placements of
+ *     its path one level after the other, from the root's frame (the frame
+ *     of the tracks).
+ */
+typedef struct {
+    int nlv;
+    const int32_t *mkind; const double *mparams;                 /* per lv: kind, 5 params        */
+    const int32_t *nd, *doff;                                    /* per lv: daughters, offset     */
+    const int32_t *kinds; const double *params, *rot, *trans;    /* daughters, concatenated       */
+    const int32_t *child;                                        /* per daughter: lv placed there */
+    int root;
+    /* node table */
+    int nnodes;
+    int32_t *lv, *parent, *slot, *first;
+} orc_world;
+
+static orc_scene world_scene(const orc_world *W, int v) {
+    orc_scene s;
+    const int o = W->doff[v];
+    s.mkind = W->mkind[v]; s.mparams = W->mparams + 5 * v;
+    s.nd = W->nd[v]; s.kinds = W->kinds + o; s.params = W->params + 5 * o;
+    s.rot = W->rot + 9 * o; s.trans = W->trans + 3 * o;
+    return s;
+}
+
+/* breadth-first node table; returns the node count or -1 past max_nodes */
+static int world_nodes(orc_world *W, int max_nodes) {
+    int n = 1, head = 0;
+    W->lv[0] = W->root; W->parent[0] = -1; W->slot[0] = -1;
+    while (head < n) {
+        const int v = W->lv[head];
+        W->first[head] = n;
+        for (int j = 0; j < W->nd[v]; j++) {
+            if (n >= max_nodes) return -1;
+            W->lv[n] = W->child[W->doff[v] + j]; W->parent[n] = head; W->slot[n] = j;
+            n++;
+        }
+        head++;
+    }
+    W->nnodes = n;
+    return n;
+}
+
+/* x in the frame of child j of logical volume v: R^T (x - t) */
+static void into_child(const orc_world *W, int v, int j, const double *x, double *xl, const double *u, double *ul) {
+    orc_scene s = world_scene(W, v);
+    double d0[3] = { 0, 0, 0 }, dd[3];
+    to_local(&s, j, x, u ? u : d0, xl, dd);
+    if (ul) { ul[0] = dd[0]; ul[1] = dd[1]; ul[2] = dd[2]; }
+}
+
+/* x in the frame of the parent: R x + t (placement of daughter j of v) */
+static void into_parent(const orc_world *W, int v, int j, const double *x, double *xp) {
+    const int o = W->doff[v] + j;
+    const double *R = W->rot + 9 * o, *t = W->trans + 3 * o;
+    for (int k = 0; k < 3; k++) xp[k] = R[3 * k] * x[0] + R[3 * k + 1] * x[1] + R[3 * k + 2] * x[2] + t[k];
+}
+
+static int descend(const orc_world *W, int node, const double *x0) {
+    double x[3] = { x0[0], x0[1], x0[2] };
+    for (;;) {
+        const int v = W->lv[node];
+        int next = -1;
+        double xn[3];
+        for (int j = 0; j < W->nd[v] && next < 0; j++) {
+            double xl[3];
+            into_child(W, v, j, x, xl, NULL, NULL);
+            if (orc_contains(W->kinds[W->doff[v] + j], W->params + 5 * (W->doff[v] + j), xl)) {
+                next = W->first[node] + j;
+                xn[0] = xl[0]; xn[1] = xl[1]; xn[2] = xl[2];
+            }
+        }
+        if (next < 0) return node;
+        node = next;
+        x[0] = xn[0]; x[1] = xn[1]; x[2] = xn[2];
+    }
+}
+
+/* world point and direction in the frame of node */
+static void node_frame(const orc_world *W, int node, const double *pw, const double *dw, double *x, double *u) {
+    int path[64], depth = 0;
+    for (int m = node; m > 0 && depth < 64; m = W->parent[m]) path[depth++] = m;
+    x[0] = pw[0]; x[1] = pw[1]; x[2] = pw[2];
+    u[0] = dw[0]; u[1] = dw[1]; u[2] = dw[2];
+    for (int l = depth - 1; l >= 0; l--) {
+        const int m = path[l];
+        double xl[3], ul[3];
+        into_child(W, W->lv[W->parent[m]], W->slot[m], x, xl, u, ul);
+        for (int k = 0; k < 3; k++) { x[k] = xl[k]; u[k] = ul[k]; }
+    }
+}
+
+static int world_locate_one(const orc_world *W, const double *pw) {
+    for (int k = 0; k < 3; k++)
+        if (!isfinite(pw[k])) return -2;
+    if (!orc_contains(W->mkind[W->root], W->mparams + 5 * W->root, pw)) return -1;
+    return descend(W, 0, pw);
+}
+
+static int world_step_one(const orc_world *W, int node, int blocked, const double *pw, const double *dw,
+                          double *step, int *blocked_out) {
+    *blocked_out = -1;
+    if (node < 0 || node >= W->nnodes) { *step = NAN; return -2; }
+    double x[3], u[3];
+    node_frame(W, node, pw, dw, x, u);
+    orc_scene s = world_scene(W, W->lv[node]);
+    navres r = navigate_one_b(&s, x, u, blocked >= 0 && blocked < s.nd ? blocked : -1);
+    *step = r.step;
+    if (r.hit == -2) return -2;
+    const double b[3] = { x[0] + r.step * u[0], x[1] + r.step * u[1], x[2] + r.step * u[2] };
+    if (r.hit >= 0) {
+        double xl[3];
+        into_child(W, W->lv[node], r.hit, b, xl, NULL, NULL);
+        return descend(W, W->first[node] + r.hit, xl);
+    }
+    double xb[3] = { b[0], b[1], b[2] };
+    for (int m = node; m != 0; m = W->parent[m]) {
+        const int P = W->parent[m], v = W->lv[P], left = W->slot[m];
+        double xp[3];
+        into_parent(W, v, left, xb, xp);
+        for (int j = 0; j < W->nd[v]; j++) {
+            if (j == left) continue;
+            double xl[3];
+            into_child(W, v, j, xp, xl, NULL, NULL);
+            if (orc_contains(W->kinds[W->doff[v] + j], W->params + 5 * (W->doff[v] + j), xl))
+                return descend(W, W->first[P] + j, xl);
+        }
+        if (orc_contains(W->mkind[v], W->mparams + 5 * v, xp)) { *blocked_out = left; return P; }
+        xb[0] = xp[0]; xb[1] = xp[1]; xb[2] = xp[2];
+    }
+    return -1;   /* left the root */
+}
+
+#define WORLD_ARGS int nlv, const int32_t *mkind, const double *mparams, const int32_t *nd, \
+                   const int32_t *doff, const int32_t *kinds, const double *params, const double *rot, \
+                   const double *trans, const int32_t *child, int root, int max_nodes, int32_t *t_lv, \
+                   int32_t *t_parent, int32_t *t_slot, int32_t *t_first
+#define MAKE_WORLD orc_world W = { nlv, mkind, mparams, nd, doff, kinds, params, rot, trans, child, root, \
+                                   0, t_lv, t_parent, t_slot, t_first }
+
+/* Node table only; returns the node count (-1 past max_nodes). */
+int orc_world_nodes(WORLD_ARGS) {
+    MAKE_WORLD;
+    return world_nodes(&W, max_nodes);
+}
+
+int orc_world_locate(WORLD_ARGS, int64_t n, const double *px, const double *py, const double *pz,
+                     int32_t *node) {
+    MAKE_WORLD;
+    if (world_nodes(&W, max_nodes) < 0) return -1;
+    for (int64_t i = 0; i < n; i++) {
+        const double pw[3] = { px[i], py[i], pz[i] };
+        node[i] = world_locate_one(&W, pw);
+    }
+    return W.nnodes;
+}
+
+int orc_world_step(WORLD_ARGS, int64_t n, const double *px, const double *py, const double *pz,
+                   const double *dx, const double *dy, const double *dz, const int32_t *node_in,
+                   const int32_t *blocked_in, double *step, int32_t *node_out, int32_t *blocked_out) {
+    MAKE_WORLD;
+    if (world_nodes(&W, max_nodes) < 0) return -1;
+    for (int64_t i = 0; i < n; i++) {
+        const double pw[3] = { px[i], py[i], pz[i] }, dw[3] = { dx[i], dy[i], dz[i] };
+        int b;
+        node_out[i] = world_step_one(&W, node_in[i], blocked_in ? blocked_in[i] : -1, pw, dw, &step[i], &b);
+        if (blocked_out) blocked_out[i] = b;
+    }
+    return W.nnodes;
 }

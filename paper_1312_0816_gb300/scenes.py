@@ -466,3 +466,115 @@ def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) ->
     P = np.concatenate(out_p)[:n]
     V = np.concatenate(out_v)[:n]
     return Tracks(P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy(), V[:, 0].copy(), V[:, 1].copy(), V[:, 2].copy())
+
+
+# --------------------------------------------------------------------------
+# a tree of logical volumes (final localisation after a step)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class World:
+    """A tree of logical volumes.  Volume v's daughter j is an instance of
+    volume child[v][j], whose mother solid equals that daughter's solid; the
+    frame of the root volume is the frame of the tracks."""
+
+    volumes: list          # Scene per logical volume
+    child: list            # per volume: child volume index per daughter
+    root: int = 0
+
+    def flat(self) -> dict:
+        nd = np.array([v.n_daughters for v in self.volumes], dtype=np.int32)
+        doff = np.concatenate([[0], np.cumsum(nd)[:-1]]).astype(np.int32)
+        cat = lambda f, w: (np.concatenate([f(v) for v in self.volumes]) if nd.sum() else np.zeros((0, w)))
+        return {
+            "mkind": np.array([v.mother_kind for v in self.volumes], dtype=np.int32),
+            "mparams": np.stack([v.mother_params for v in self.volumes]).astype(np.float64),
+            "nd": nd, "doff": doff,
+            "kinds": np.concatenate([v.kinds for v in self.volumes]).astype(np.int32),
+            "params": cat(lambda v: v.params, 5).reshape(-1, 5).astype(np.float64),
+            "rot": cat(lambda v: v.rot, 9).reshape(-1, 9).astype(np.float64),
+            "trans": cat(lambda v: v.trans, 3).reshape(-1, 3).astype(np.float64),
+            "child": np.concatenate([np.asarray(c, dtype=np.int32) for c in self.child]).astype(np.int32),
+            "root": int(self.root),
+        }
+
+    def check(self):
+        for v, vol in enumerate(self.volumes):
+            assert len(self.child[v]) == vol.n_daughters
+            for j, c in enumerate(self.child[v]):
+                cv = self.volumes[c]
+                assert cv.mother_kind == vol.kinds[j] and np.array_equal(cv.mother_params, vol.params[j]), (v, j)
+
+
+def leaf(kind, params, name="leaf") -> Scene:
+    p = np.zeros(5)
+    p[: len(params)] = params
+    return Scene(name, int(kind), p, np.zeros(0, np.int32), np.zeros((0, 5)), np.zeros((0, 9)), np.zeros((0, 3)))
+
+
+def _rot_z(phi):
+    c, s = math.cos(phi), math.sin(phi)
+    return np.array([c, -s, 0.0, s, c, 0.0, 0.0, 0.0, 1.0])
+
+
+def world_toy(seed: int = 1) -> World:
+    """Three levels below a hall: the toy detector of Sec. 3.2 (40 daughters)
+    placed in a box hall (half 1600 x 1600 x 2000 mm) beside 4 racks (boxes
+    holding a tube); every tube shell of the detector holds 8 sensor boxes,
+    every rotated box holds two sub-boxes; cones and the rest are leaves.
+    162 placed volumes, non-overlapping by construction."""
+    toy = toy40(seed)
+    vols, child = [], []
+
+    def add(scene, kids):
+        vols.append(scene)
+        child.append(list(kids))
+        return len(vols) - 1
+
+    sensor = add(leaf(BOX, (8.0, 8.0, 100.0), "sensor"), [])
+    cone = add(leaf(CONE, toy.params[32], "endcap"), [])
+    rack_tube = add(leaf(TUBE, (0.0, 50.0, 300.0), "rack_tube"), [])
+    rack = add(_scene("rack", BOX, (100.0, 100.0, 400.0), [(TUBE, (0.0, 50.0, 300.0), _EYE, (0.0, 0.0, 0.0))]),
+               [rack_tube])
+    det_kids = []
+    for j in range(toy.n_daughters):
+        k, p = int(toy.kinds[j]), toy.params[j]
+        if k == TUBE:
+            mid = 0.5 * (p[0] + p[1])
+            rows = []
+            for m in range(8):
+                ph = math.radians(45.0 * m)
+                rows.append((BOX, (8.0, 8.0, 100.0), _rot_z(ph),
+                             (mid * math.cos(ph), mid * math.sin(ph), 400.0 * (-1) ** m)))
+            sh = _scene(f"shell{j}", TUBE, p[:3], rows)
+            det_kids.append(add(sh, [sensor] * 8))
+        elif k == BOX:
+            h = p[:3]
+            sub = add(leaf(BOX, (h[0] / 4, h[1] / 2, h[2] / 2), f"sub{j}"), [])
+            rows = [(BOX, (h[0] / 4, h[1] / 2, h[2] / 2), _EYE, (s * h[0] / 2, 0.0, 0.0)) for s in (-1.0, 1.0)]
+            det_kids.append(add(_scene(f"box{j}", BOX, h, rows), [sub, sub]))
+        else:
+            det_kids.append(cone)
+    det = add(Scene("detector", toy.mother_kind, toy.mother_params, toy.kinds, toy.params, toy.rot, toy.trans),
+              det_kids)
+    rows = [(TUBE, toy.mother_params[:3], _EYE, (0.0, 0.0, 0.0))]
+    for cx, cy in ((1350.0, 0.0), (-1350.0, 0.0), (0.0, 1350.0), (0.0, -1350.0)):
+        rows.append((BOX, (100.0, 100.0, 400.0), _EYE, (cx, cy, 0.0)))
+    hall = add(_scene("hall", BOX, (1600.0, 1600.0, 2000.0), rows), [det, rack, rack, rack, rack])
+    w = World(vols, child, root=hall)
+    w.check()
+    return w
+
+
+def world_points(world: World, n: int, seed: int) -> Tracks:
+    """n points uniform in the root volume's bounding box (the root is a box
+    here), isotropic unit directions."""
+    rng = np.random.default_rng(seed)
+    r = world.volumes[world.root]
+    assert r.mother_kind == BOX
+    h = r.mother_params[:3]
+    x = rng.uniform(-h[0], h[0], n)
+    y = rng.uniform(-h[1], h[1], n)
+    z = rng.uniform(-h[2], h[2], n)
+    dx, dy, dz = isotropic(rng, n)
+    return Tracks(x, y, z, dx, dy, dz)
