@@ -200,10 +200,12 @@ def world_locate(world, tracks):
 
 
 def world_step(world, tracks, node_in, blocked_in=None):
-    """The step of Fig. 1 in each track's node (the daughter slot blocked_in
-    just left taken by its re-entry distance), then the track's node after
+    """The step of Fig. 1 in each track's node, then the track's node after
     the step (-1 left the root, -2 not inside its node or invalid) and its
-    blocked slot.  Returns step, node, blocked."""
+    flag: j >= 0 = daughter j of the node was just left (its re-entry
+    distance replaces DistFromOutside), -2 = the node was just entered
+    through its surface, -1 = none (after Locate).  Returns step, node,
+    flag."""
     keep, table, args = _world_args(world)
     kt, targs = _track_args(tracks)
     nin, nptr = _i(node_in)

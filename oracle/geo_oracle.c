@@ -346,6 +346,18 @@ static hitinfo dist_reentry_info(int kind, const double *p, const double *x, con
     return h;
 }
 
+/* Exit from a solid the track has just entered through its surface (its
+ * start point lies on that surface, inside or a rounding outside): the end
+ * of the first component of S that ends after s = 0; 0 if there is none. */
+static hitinfo dist_in_entered_info(int kind, const double *p, const double *x, const double *u) {
+    iset S; line_set(kind, p, x, u, &S);
+    hitinfo h = { 0.0, F_NONE, INFINITY };
+    for (int i = 0; i < S.n; i++) {
+        if (S.v[i].hi > 0.0) { h.s = S.v[i].hi; h.face = S.v[i].fhi; h.chord = S.v[i].chi; return h; }
+    }
+    return h;
+}
+
 static hitinfo dist_in_info(int kind, const double *p, const double *x, const double *u) {
     iset S; line_set(kind, p, x, u, &S);
     hitinfo h = { 0.0, F_NONE, INFINITY };
@@ -515,13 +527,18 @@ typedef struct {
 } navres;
 
 /* blocked >= 0: that daughter was just left through its surface; it enters
- * the minimum with its re-entry distance instead of DistFromOutside (0). */
+ * the minimum with its re-entry distance instead of DistFromOutside (0).
+ * blocked == -2: the track has just entered the mother through its surface;
+ * the mother's exit is that of the component being entered, and a start
+ * point a rounding outside the mother is not "outside". */
 static navres navigate_one_b(const orc_scene *sc, const double *pw, const double *dw, int blocked) {
     navres r;
     r.second = INFINITY; r.face = F_NONE; r.err = 0.0;
+    const int entered = blocked == -2;
     if (bad_input(pw, dw)) { r.step = NAN; r.hit = -2; return r; }
-    if (!orc_contains(sc->mkind, sc->mparams, pw)) { r.step = 0.0; r.hit = -2; return r; }
-    hitinfo m = dist_in_info(sc->mkind, sc->mparams, pw, dw);
+    if (!entered && !orc_contains(sc->mkind, sc->mparams, pw)) { r.step = 0.0; r.hit = -2; return r; }
+    hitinfo m = entered ? dist_in_entered_info(sc->mkind, sc->mparams, pw, dw)
+                        : dist_in_info(sc->mkind, sc->mparams, pw, dw);
     double best = m.s, chord = m.chord, tnorm = 0.0, scale = shape_scale(sc->mkind, sc->mparams);
     int hit = -1, face = m.face;
     double second = INFINITY;
@@ -809,8 +826,11 @@ void orc_shape_batch(int kind, const double *p, int64_t n, const double *x, cons
  *     to RE-ENTER j instead: the start of the first component of
  *     { s : x + s u in j } that begins after s = 0 (+inf for a convex j;
  *     across the hole for a shell).  The state of a track is therefore
- *     (node, blocked slot), the slot being -1 after Locate or after
- *     entering a daughter.
+ *     (node, flag): flag j >= 0 after leaving daughter j into this node;
+ *     -2 after entering this node through its surface, where the mother's
+ *     exit is that of the component being entered (the end of the first
+ *     component of S ending after s = 0), since the boundary point may lie
+ *     a rounding outside the solid; -1 after Locate.
  *   - The local point of a node is obtained by applying the placements of
  *     its path one level after the other, from the root's frame (the frame
  *     of the tracks).
@@ -917,13 +937,14 @@ static int world_step_one(const orc_world *W, int node, int blocked, const doubl
     double x[3], u[3];
     node_frame(W, node, pw, dw, x, u);
     orc_scene s = world_scene(W, W->lv[node]);
-    navres r = navigate_one_b(&s, x, u, blocked >= 0 && blocked < s.nd ? blocked : -1);
+    navres r = navigate_one_b(&s, x, u, blocked == -2 || (blocked >= 0 && blocked < s.nd) ? blocked : -1);
     *step = r.step;
     if (r.hit == -2) return -2;
     const double b[3] = { x[0] + r.step * u[0], x[1] + r.step * u[1], x[2] + r.step * u[2] };
     if (r.hit >= 0) {
         double xl[3];
         into_child(W, W->lv[node], r.hit, b, xl, NULL, NULL);
+        *blocked_out = -2;
         return descend(W, W->first[node] + r.hit, xl);
     }
     double xb[3] = { b[0], b[1], b[2] };
@@ -935,8 +956,10 @@ static int world_step_one(const orc_world *W, int node, int blocked, const doubl
             if (j == left) continue;
             double xl[3];
             into_child(W, v, j, xp, xl, NULL, NULL);
-            if (orc_contains(W->kinds[W->doff[v] + j], W->params + 5 * (W->doff[v] + j), xl))
+            if (orc_contains(W->kinds[W->doff[v] + j], W->params + 5 * (W->doff[v] + j), xl)) {
+                *blocked_out = -2;
                 return descend(W, W->first[P] + j, xl);
+            }
         }
         if (orc_contains(W->mkind[v], W->mparams + 5 * v, xp)) { *blocked_out = left; return P; }
         xb[0] = xp[0]; xb[1] = xp[1]; xb[2] = xp[2];

@@ -170,3 +170,36 @@ def test_toy_world_invariants(orc):
         node = np.where(ok, nn, -1).astype(np.int32)
     assert total > 2000 and 0 < down < total
     assert agree / total > 0.995
+
+
+def test_transport_makes_progress(orc):
+    """Transporting tracks step after step through the toy world: no track
+    ping-pongs across a surface (never more than two zero steps in a row),
+    every track eventually leaves the root, and the path length of a track
+    equals the distance from its start to where it left the hall."""
+    w = scenes.world_toy()
+    tr = scenes.world_points(w, 3000, 22)
+    x0 = np.stack([tr.x, tr.y, tr.z], 1)
+    node = orc.world_locate(w, tr)
+    flag = np.full(tr.n, -1, dtype=np.int32)
+    zeros = np.zeros(tr.n, dtype=int)
+    path = np.zeros(tr.n)
+    alive = node >= 0
+    for _ in range(60):
+        if not alive.any():
+            break
+        s, nn, fl = orc.world_step(w, tr, node, flag)
+        s = np.where(alive, s, 0.0)
+        assert np.all(nn[alive] != -2)
+        zeros = np.where(alive & (s == 0.0), zeros + 1, 0)
+        assert zeros.max() <= 2
+        path += s
+        tr = scenes.Tracks(tr.x + s * tr.dx, tr.y + s * tr.dy, tr.z + s * tr.dz, tr.dx, tr.dy, tr.dz)
+        node = np.where(alive, nn, -1).astype(np.int32)
+        flag = fl
+        alive = node >= 0
+    assert not alive.any()
+    x1 = np.stack([tr.x, tr.y, tr.z], 1)
+    assert np.allclose(path, np.linalg.norm(x1 - x0, axis=1), rtol=0, atol=1e-9)
+    h = w.volumes[w.root].mother_params[:3]
+    assert np.all(np.isclose(np.abs(x1), h, rtol=0, atol=1e-9).any(axis=1))
