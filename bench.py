@@ -420,6 +420,52 @@ def shapes_leg(pkg, steps, q_sqrt, q_div):
     return out
 
 
+def world_leg(pkg, scenes, rank, steps):
+    """Transport steps in a tree of logical volumes (the toy detector in a
+    hall with racks; 162 placed volumes, 3 levels): the step of Fig. 1 in
+    each track's node followed by final localisation.  2^20 tracks; the
+    states after 0..3 transport steps (flags and nodes of every kind) are
+    prepared once and the timed steps rotate over them."""
+    import torch
+
+    w = scenes.world_toy()
+    vols = [pkg.geo_build_volume(v) for v in w.volumes]
+    W = pkg.geo_build_world(vols, w.child, w.root)
+    n = 1 << 20
+    tr = scenes.world_points(w, n, 11 + 1000 * rank)
+    x = [torch.from_numpy(f).cuda() for f in tr.fields()]
+    node = pkg.geo_world_locate(W, *x[:3])
+    flag = torch.full_like(node, -1)
+    states = []
+    for _ in range(4):
+        states.append(([t.clone() for t in x], node.clone(), flag.clone()))
+        s, nn, ff = pkg.geo_world_step(W, *x, node, flag, mode=1)
+        alive = node >= 0
+        s = torch.where(alive, s, torch.zeros_like(s))
+        for k in range(3):
+            x[k] = x[k] + s * x[3 + k]
+        node = torch.where(alive, nn, torch.full_like(nn, -1))
+        flag = torch.where(alive, ff, torch.full_like(ff, -1))
+    alive_frac = [float((st[1] >= 0).float().mean()) for st in states]
+    step = torch.empty(n, dtype=torch.float64, device="cuda")
+    no = torch.empty(n, dtype=torch.int32, device="cuda")
+    fo = torch.empty(n, dtype=torch.int32, device="cuda")
+    out = {"workload": "toy world: hall > detector (40 daughters) > shells with 8 sensors / boxes with 2 sub-boxes, "
+                       "racks > tube; 162 placed volumes; 2^20 tracks uniform in the hall, states after 0..3 "
+                       "transport steps in rotation (alive fractions %s); steps %d"
+                       % ([round(a, 3) for a in alive_frac], steps)}
+    for mode, key in ((1, "fp32_refine"), (0, "fp64_plain")):
+        k = steps if mode == 1 else max(3, steps // 4)
+        ms = _event_time(lambda it: pkg.geo_world_step(W, *states[it % 4][0], states[it % 4][1], states[it % 4][2],
+                                                       mode=mode, step=step, node_out=no, flag_out=fo), k)
+        out[key] = {"value": n / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "steps": k}
+    out["speedup_of_refine"] = out["fp64_plain"]["ms_per_step"] / out["fp32_refine"]["ms_per_step"]
+    W.close()
+    for v in vols:
+        v.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,6 +479,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
+    ap.add_argument("--no-world", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -572,6 +619,7 @@ def main():
     adjoint = None if args.no_adjoint else adjoint_leg(pkg, scenes, rank, max(10, args.steps // 40))
     queries = None if args.no_queries else queries_leg(pkg, scenes, rank, max(10, args.steps // 100), sc)
     shapes = None if args.no_shapes else shapes_leg(pkg, max(10, args.steps // 100), q_sqrt, q_div)
+    world = None if args.no_world else world_leg(pkg, scenes, rank, max(10, args.steps // 100))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -600,6 +648,7 @@ def main():
             "adjoint": adjoint,
             "contains_safety": queries,
             "shapes": shapes,
+            "world": world,
         }
         print(json.dumps(line), flush=True)
     vol.close()

@@ -248,6 +248,63 @@ geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vols, int32_t 
                                                 int64_t n_total, double* step, int32_t* hit,
                                                 void* stream);
 
+/* ---- a tree of logical volumes: the step followed by final localisation -
+ * The paper's navigator ends at the distance to the next boundary and the
+ * volume hit; locating the track in the volume it then enters (or returns
+ * to) is left out there.  These calls add it for a tree of logical volumes.
+ *
+ * Tree: volumes[v] are built logical volumes (geo_build_volume); daughter j
+ * of volume v is an instance of volumes[child[o_v + j]], o_v = the number of
+ * daughters of volumes 0..v-1; that volume's mother solid must equal the
+ * daughter's solid (kind and parameters, else GEO_ERR_SHAPE_PARAMS).  The
+ * frame of volumes[root] is the frame of the tracks.  Placed volumes (nodes)
+ * are numbered breadth first from the root (node 0): the children of a node
+ * are consecutive in daughter order, nodes expanded in number order.  At
+ * most 2^24 nodes and 64 levels (else GEO_ERR_INVALID_ARG).  The world keeps
+ * pointers to the volumes' device tables: destroy the world before them.
+ *
+ * Track state: a node (-1 outside the root) and a flag: j >= 0 when the
+ * track has just left daughter j of its node (its next step takes j's
+ * re-entry distance instead of DistFromOutside, which would be 0 on j's
+ * surface), -2 when it has just entered its node through the node's surface
+ * (a start point a rounding outside the node is accepted and the mother's
+ * exit is that of the part being entered), -1 otherwise (after Locate). */
+typedef struct geo_world_s* geo_world;
+
+geo_status geo_build_world(const geo_volume* volumes, int32_t n_volumes, const int32_t* child, int32_t root,
+                           void* stream, geo_world* out);
+geo_status geo_destroy_world(geo_world w);
+/* Number of nodes and depth of the deepest node (root = 0). */
+geo_status geo_world_info(geo_world w, int32_t* n_nodes, int32_t* max_depth);
+/* Host arrays of n_nodes: logical volume, parent (-1 for the root), slot in
+ * the parent's daughters (-1), first child's node number.  Any may be NULL. */
+geo_status geo_world_nodes(geo_world w, int32_t* lv, int32_t* parent, int32_t* slot, int32_t* first_child);
+
+/* Locate: node[i] = the deepest node whose closed solid contains point i,
+ * choosing at every level the lowest-index daughter that contains it; -1
+ * outside the root's solid, -2 non-finite.  Device arrays. */
+geo_status geo_world_locate(geo_world w, const double* x, const double* y, const double* z, int64_t n,
+                            int32_t* node, void* stream);
+
+/* One step of every track: the step of Fig. 1 in the logical volume of its
+ * node (mode as in geo_dist_to_boundary; both modes give the same answers),
+ * then relocation at the boundary point:
+ *   a daughter hit: that child, then down while a daughter contains the
+ *   point (lowest index first); flag_out -2;
+ *   the node's own boundary: up to the parent, where the lowest-index
+ *   daughter other than the one left that contains the point is entered
+ *   (then down; flag -2), else the parent itself if its solid contains the
+ *   point (flag = the slot left), else up again; leaving the root: node -1.
+ * A track not inside its node's solid (flag != -2), with an invalid node or
+ * invalid input gets node -2 (step 0, or NaN for invalid input).
+ * Inputs: positions and directions in the root frame, node_in, flag_in
+ * (NULL = all -1); outputs step[n] (units of |d|), node_out[n], flag_out[n]
+ * (may be NULL).  The caller moves the track: p + step * d.  Device arrays. */
+geo_status geo_world_step(geo_world w, const double* x, const double* y, const double* z, const double* dx,
+                          const double* dy, const double* dz, int64_t n, const int32_t* node_in,
+                          const int32_t* flag_in, double* step, int32_t* node_out, int32_t* flag_out, int32_t mode,
+                          void* stream);
+
 /* ---- gradients of the step (the paper has no gradients; this supports a
  * differentiable use of the navigator) ----------------------------------
  * For loss L with dL/dstep = grad_step (device FP64[n]) and the forward

@@ -23,6 +23,7 @@ struct geo_volume_s {
     int32_t* vox_off = nullptr;
     int32_t* vox_ids = nullptr;
     unsigned int* status = nullptr;
+    std::vector<ShapeRec64> h64;      // host copy of the daughter records
     // staging workspace of geo_dist_to_boundary_host
     void* ws = nullptr;
     int64_t ws_tracks = 0;
@@ -334,6 +335,7 @@ geo_status check_basket(const double* x, const double* y, const double* z, int64
 
 namespace geonav {
 const VolView* volume_view(geo_volume v) { return v ? &v->view : nullptr; }
+const ShapeRec64* volume_host_daughters(geo_volume v) { return v ? v->h64.data() : nullptr; }
 int volume_device(geo_volume v) { return v ? v->device : -1; }
 int sm_count(int device) { return num_sms_of(device); }
 }  // namespace geonav
@@ -419,6 +421,7 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
     vw.d64 = v->d64;
     vw.d32 = v->d32;
     vw.status = v->status;
+    v->h64 = std::move(h64);
     if (opts && opts->voxelize) {
         st = build_voxels(*mother, daughters, n_daughters, S, opts, s, v);
         if (st != GEO_OK) {

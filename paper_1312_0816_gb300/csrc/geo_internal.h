@@ -128,6 +128,7 @@ cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit
 
 // accessors of the opaque volume handle (defined in geo_abi.cu)
 const VolView* volume_view(geo_volume v);
+const ShapeRec64* volume_host_daughters(geo_volume v);   // host copy, nd records
 int volume_device(geo_volume v);
 int sm_count(int device);
 

@@ -234,7 +234,7 @@ __device__ __forceinline__ double eval64(const VolView& v, const ShapeRec64* __r
 // lowest index.  The bounds are compared in FP32 against best_up >= best, so
 // at least every solid that could tie or win is refined (a solid refined in
 // excess cannot change the answer).
-__device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __restrict__ tab64,
+static __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __restrict__ tab64,
                                          const RefineState& st, double s_first, double px, double py, double pz,
                                          double qx, double qy, double qz, double& best, int& h, int& nev) {
     best = d_inf();

@@ -154,12 +154,15 @@ __device__ __forceinline__ double box_out64(const double* h, const double* x, co
 }
 
 
-template <bool FACE = false>
+// REENTRY: the start point lies on the surface of a solid it has just left;
+// the inside test is skipped and only entering crossings strictly after the
+// start count (the crossing it left through is an exiting one).
+template <bool FACE = false, bool REENTRY = false>
 __device__ __forceinline__ double tube_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
     if (FACE) *face = -1;
     const double rmin = d[0], dz = d[2], rmin2 = d[3], rmax2 = d[4];
     const double rho2 = rho2_of(x);
-    if (ABS_LE(x[2], dz) && LE(rho2, rmax2) && LE(rmin2, rho2)) return 0.0;
+    if (!REENTRY && ABS_LE(x[2], dz) && LE(rho2, rmax2) && LE(rmin2, rho2)) return 0.0;
     double best = d_inf();
     {   // the z-plane the track approaches from outside the slab
         const bool zc = ABS_GT(x[2], dz) && OPPOSITE(x[2], u[2]);
@@ -175,14 +178,14 @@ __device__ __forceinline__ double tube_out64(const double* d, const double* x, c
     const double B = DOT2(x[0], u[0], x[1], u[1]);
     {   // outer cylinder, crossed inwards
         const double s = root_falling(A, B, SUB(rho2, rmax2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
             best = s;
             if (FACE) *face = 6;
         }
     }
     if (rmin > 0.0) {   // inner cylinder, crossed outwards (out of the hole)
         const double s = root_rising(A, B, SUB(rho2, rmin2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
             best = s;
             if (FACE) *face = 7;
         }
@@ -190,7 +193,7 @@ __device__ __forceinline__ double tube_out64(const double* d, const double* x, c
     return best;
 }
 
-template <bool FACE = false>
+template <bool FACE = false, bool REENTRY = false>
 __device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
     if (FACE) *face = -1;
     const double dz = d[0];
@@ -198,7 +201,8 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     const double ro0 = FMA(d[2], x[2], d[1]);
     const double ri0 = FMA(d[4], x[2], d[3]);
     const bool hole = d[11] != 0.0;
-    if (ABS_LE(x[2], dz) && LE(rho2, MUL(ro0, ro0)) && (!hole || LE(MUL(ri0, ri0), rho2))) return 0.0;
+    if (!REENTRY && ABS_LE(x[2], dz) && LE(rho2, MUL(ro0, ro0)) && (!hole || LE(MUL(ri0, ri0), rho2)))
+        return 0.0;
     double best = d_inf();
     {   // the z-plane the track approaches from outside the slab
         const bool zc = ABS_GT(x[2], dz) && OPPOSITE(x[2], u[2]);
@@ -217,7 +221,7 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     {   // outer cone rho^2 - (a + b z)^2, crossed inwards
         const double rs = MUL(d[2], u[2]);
         const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
             best = s;
             if (FACE) *face = 6;
         }
@@ -225,7 +229,7 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     if (hole) {   // inner cone, crossed outwards
         const double rs = MUL(d[4], u[2]);
         const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-        if (NONNEG(s) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
             best = s;
             if (FACE) *face = 7;
         }
@@ -239,6 +243,23 @@ __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* 
     if (r.kind == KBOX) return box_out64<FACE>(r.d, x, u, face);
     if (r.kind == KTUBE) return tube_out64<FACE>(r.d, x, u, face);
     return cone_out64<FACE>(r.d, x, u, face);
+}
+
+// Distance to enter again a solid the track has just left (its start point
+// on the solid's surface): +inf for a convex solid, the crossing on the far
+// side of the hole for a shell left into its hole.
+template <bool FACE = false>
+__device__ __forceinline__ double reentry64(const ShapeRec64& r, const double* x, const double* u,
+                                           int* face = nullptr) {
+    if (r.kind == KBOX) {
+        if (contains64(r, x)) {
+            if (FACE) *face = -1;
+            return d_inf();
+        }
+        return box_out64<FACE>(r.d, x, u, face);
+    }
+    if (r.kind == KTUBE) return tube_out64<FACE, true>(r.d, x, u, face);
+    return cone_out64<FACE, true>(r.d, x, u, face);
 }
 
 // ------------------------------------------------------- DistFromInside ---

@@ -52,7 +52,8 @@ EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dis
            "geo_contains", "geo_safety", "geo_dist_to_boundary_host", "geo_dist_to_boundary_stats",
            "geo_check_device_status", "geo_probe_pipe", "geo_build_batch", "geo_destroy_batch",
            "geo_dist_to_boundary_batched", "geo_dist_to_boundary_batched_noalloc", "geo_adjoint_workspace_size",
-           "geo_dist_to_boundary_adjoint", "geo_shape_query", "geo_status_string")
+           "geo_dist_to_boundary_adjoint", "geo_shape_query", "geo_build_world", "geo_destroy_world",
+           "geo_world_info", "geo_world_nodes", "geo_world_locate", "geo_world_step", "geo_status_string")
 
 
 def library_path() -> str:
@@ -78,6 +79,12 @@ def load(build_if_stale: bool = True):
     L.geo_dist_to_boundary.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, dp, i32, vp]
     L.geo_contains.argtypes = [vp, dp, dp, dp, i64, ip, i32, vp]
     L.geo_safety.argtypes = [vp, dp, dp, dp, i64, dp, i32, vp]
+    L.geo_build_world.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(ctypes.c_int32), i32, vp, ctypes.POINTER(vp)]
+    L.geo_destroy_world.argtypes = [vp]
+    L.geo_world_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.geo_world_nodes.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int32)] * 4
+    L.geo_world_locate.argtypes = [vp, dp, dp, dp, i64, ip, vp]
+    L.geo_world_step.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, ip, ip, dp, ip, ip, i32, vp]
     L.geo_shape_query.argtypes = [ctypes.POINTER(geo_placed_shape), i32, dp, dp, dp, dp, dp, dp, i64, dp, ip, vp]
     L.geo_dist_to_boundary_host.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, i32, i64, vp]
     L.geo_dist_to_boundary_stats.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, dp, ip, ip, vp]
@@ -268,6 +275,100 @@ def geo_shape_query(kind, params, what, x, y, z, dx=None, dy=None, dz=None, rot=
                                   _dev(face, torch.int32, n, "face") if face is not None else ctypes.c_void_p(0),
                                   _stream(stream)), "geo_shape_query")
     return (out, face) if want_face else out
+
+
+class World:
+    """Owns one geo_world handle (a tree of logical volumes); keeps its
+    volumes alive."""
+
+    def __init__(self, handle, volumes, n_nodes: int, max_depth: int):
+        self.handle = handle
+        self.volumes = list(volumes)
+        self.n_nodes = n_nodes
+        self.max_depth = max_depth
+
+    def close(self):
+        if self.handle:
+            load().geo_destroy_world(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def geo_build_world(volumes, child, root: int = 0, stream=None) -> World:
+    """volumes: list of Volume (logical volumes); child: per volume, the
+    volume index placed as each of its daughters (list of lists, or the
+    concatenated int array); root: index of the top volume."""
+    L = load()
+    nv = len(volumes)
+    handles = (ctypes.c_void_p * max(nv, 1))(*[v.handle for v in volumes])
+    flat = np.concatenate([np.asarray(c, dtype=np.int32).reshape(-1) for c in child]) if len(child) and \
+        not np.isscalar(child[0]) else np.asarray(child, dtype=np.int32)
+    flat = np.ascontiguousarray(flat, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(L.geo_build_world(handles, nv, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(root),
+                             _stream(stream), ctypes.byref(out)), "geo_build_world")
+    nn, md = ctypes.c_int32(), ctypes.c_int32()
+    _check(L.geo_world_info(out, ctypes.byref(nn), ctypes.byref(md)), "geo_world_info")
+    return World(out, volumes, nn.value, md.value)
+
+
+def geo_destroy_world(world: World):
+    world.close()
+
+
+def geo_world_info(world: World):
+    nn, md = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().geo_world_info(world.handle, ctypes.byref(nn), ctypes.byref(md)), "geo_world_info")
+    return nn.value, md.value
+
+
+def geo_world_nodes(world: World) -> dict:
+    """Node table (host numpy int32 arrays): lv, parent, slot, first."""
+    n = world.n_nodes
+    arrs = [np.empty(n, dtype=np.int32) for _ in range(4)]
+    _check(load().geo_world_nodes(world.handle, *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) for a in arrs]),
+           "geo_world_nodes")
+    return dict(zip(("lv", "parent", "slot", "first"), arrs))
+
+
+def geo_world_locate(world: World, x, y, z, node=None, stream=None):
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    if node is None:
+        node = torch.empty(n, dtype=torch.int32, device=x.device)
+    _check(load().geo_world_locate(world.handle, _dev(x, f64, n, "x"), _dev(y, f64, n, "y"), _dev(z, f64, n, "z"), n,
+                                   _dev(node, torch.int32, n, "node"), _stream(stream)), "geo_world_locate")
+    return node
+
+
+def geo_world_step(world: World, x, y, z, dx, dy, dz, node, flag=None, mode: int = GEO_FP32_REFINE, step=None,
+                   node_out=None, flag_out=None, stream=None):
+    """One step of every track in its node, then relocation.  Returns
+    (step, node_out, flag_out)."""
+    import torch
+
+    n = int(x.numel())
+    f64 = torch.float64
+    if step is None:
+        step = torch.empty(n, dtype=f64, device=x.device)
+    if node_out is None:
+        node_out = torch.empty(n, dtype=torch.int32, device=x.device)
+    if flag_out is None:
+        flag_out = torch.empty(n, dtype=torch.int32, device=x.device)
+    args = [_dev(a, f64, n, nm) for a, nm in ((x, "x"), (y, "y"), (z, "z"), (dx, "dx"), (dy, "dy"), (dz, "dz"))]
+    _check(load().geo_world_step(world.handle, *args, n, _dev(node, torch.int32, n, "node"),
+                                 _dev(flag, torch.int32, n, "flag") if flag is not None else ctypes.c_void_p(0),
+                                 _dev(step, f64, n, "step"), _dev(node_out, torch.int32, n, "node_out"),
+                                 _dev(flag_out, torch.int32, n, "flag_out"), int(mode), _stream(stream)),
+           "geo_world_step")
+    return step, node_out, flag_out
 
 
 def geo_dist_to_boundary_host(vol: Volume, x, y, z, dx, dy, dz, mode: int = GEO_FP32_REFINE, step=None, hit=None,
