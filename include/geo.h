@@ -299,7 +299,11 @@ geo_status geo_world_locate(geo_world w, const double* x, const double* y, const
  * invalid input gets node -2 (step 0, or NaN for invalid input).
  * Inputs: positions and directions in the root frame, node_in, flag_in
  * (NULL = all -1); outputs step[n] (units of |d|), node_out[n], flag_out[n]
- * (may be NULL).  The caller moves the track: p + step * d.  Device arrays. */
+ * (may be NULL).  The caller moves the track: p + step * d.  Device arrays.
+ * The tracks are first grouped by the logical volume of their node (in a
+ * scratch array the world owns, allocated on the first call and grown when
+ * n grows: such a call synchronises `stream`); calls on one world must not
+ * overlap on the GPU. */
 geo_status geo_world_step(geo_world w, const double* x, const double* y, const double* z, const double* dx,
                           const double* dy, const double* dz, int64_t n, const int32_t* node_in,
                           const int32_t* flag_in, double* step, int32_t* node_out, int32_t* flag_out, int32_t mode,

@@ -148,6 +148,9 @@ ShapeRec64 make_rec64(const geo_placed_shape& s) {
 bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32& r) {
     std::memset(&r, 0, sizeof r);
     for (int k = 0; k < 9; ++k) r.R[k] = float(s.rot[k]);
+    bool eye = true;
+    for (int k = 0; k < 9; ++k) eye = eye && s.rot[k] == ((k % 4) == 0 ? 1.0 : 0.0);
+    r.flags = eye ? kRec32Identity : 0;
     for (int k = 0; k < 3; ++k) r.t[k] = float(s.trans[k]);
     r.kind = s.kind;
     r.delta = float(delta);

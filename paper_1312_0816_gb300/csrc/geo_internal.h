@@ -40,6 +40,9 @@ static_assert(sizeof(ShapeRec64) == 256, "ShapeRec64 layout");
 //   cone: e[0] dz + delta, e[1] a_out', e[2] b_out, e[3] a_in', e[4] b_in,
 //         e[5] has_hole, e[6..9] inflated end radii squared (rmin1,rmax1,rmin2,rmax2)
 //  brad: inflated bounding radius.
+//  flags: kRec32Identity when the rotation is exactly the identity (the
+//  filter then skips the rotation: x = R^T w is w itself).
+constexpr int32_t kRec32Identity = 1;
 struct __align__(16) ShapeRec32 {
     float R[9];
     float t[3];

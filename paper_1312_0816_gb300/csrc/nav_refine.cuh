@@ -60,10 +60,15 @@ __device__ __forceinline__ void bound_daughter(const ShapeRec32& r, int j, const
     const float half = r.brad * inv_dn;
     if (s0 + half < 0.f || s0 - half > Um) return;
     float x[3], u[3];
+    if (r.flags & kRec32Identity) {   // warp-uniform: every lane visits solid j together
+        x[0] = q0; x[1] = q1; x[2] = q2;
+        u[0] = d32[0]; u[1] = d32[1]; u[2] = d32[2];
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        x[k] = fmaf(r.R[6 + k], q2, fmaf(r.R[3 + k], q1, r.R[k] * q0));
-        u[k] = fmaf(r.R[6 + k], d32[2], fmaf(r.R[3 + k], d32[1], r.R[k] * d32[0]));
+        for (int k = 0; k < 3; ++k) {
+            x[k] = fmaf(r.R[6 + k], q2, fmaf(r.R[3 + k], q1, r.R[k] * q0));
+            u[k] = fmaf(r.R[6 + k], d32[2], fmaf(r.R[3 + k], d32[1], r.R[k] * d32[0]));
+        }
     }
     const float tp = enter32(r, x, u, -s0);
     if (!(tp < f_inf())) return;

@@ -48,9 +48,13 @@ struct WorldView {
 };
 
 cudaError_t launch_world_locate(const WorldView& w, const Basket& b, int32_t* node, cudaStream_t s, int num_sms);
-cudaError_t launch_world_step(const WorldView& w, const Basket& b, const int32_t* node_in, const int32_t* flag_in,
-                              double* step, int32_t* node_out, int32_t* flag_out, int mode, cudaStream_t s,
-                              int num_sms);
+// counting sort of the track indices by the logical volume of their node:
+// cnt holds nlv + 1 ints of scratch, perm n ints (the order)
+cudaError_t launch_world_group(const WorldView& w, int64_t n, const int32_t* node_in, int nlv, int32_t* cnt,
+                               int32_t* perm, cudaStream_t s, int num_sms);
+cudaError_t launch_world_step(const WorldView& w, const Basket& b, const int32_t* perm, const int32_t* node_in,
+                              const int32_t* flag_in, double* step, int32_t* node_out, int32_t* flag_out, int mode,
+                              cudaStream_t s, int num_sms);
 
 // x in N's frame: R^T (p - t)
 __device__ __forceinline__ void world_to_node(const double* G, double px, double py, double pz, double qx,

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -19,6 +20,12 @@ struct geo_world_s {
     int device = 0;
     int32_t nnodes = 0;
     int32_t max_depth = 0;
+    int32_t nlv = 0;
+    // grouping scratch of geo_world_step (grown on demand)
+    int32_t* d_cnt = nullptr;
+    int32_t* d_perm = nullptr;
+    int64_t perm_cap = 0;
+    std::mutex mu;
     std::vector<int32_t> h_lv, h_parent, h_slot, h_first;
     VolView* d_vols = nullptr;
     int32_t* d_node = nullptr;   // lv | parent | slot | first, nnodes each
@@ -124,6 +131,7 @@ geo_status geo_build_world(const geo_volume* volumes, int32_t n_volumes, const i
     geo_world w = new (std::nothrow) geo_world_s;
     if (!w) return GEO_ERR_OOM;
     w->device = dev;
+    w->nlv = n_volumes;
     w->nnodes = int32_t(lv.size());
     w->max_depth = maxd;
     w->h_lv = lv;
@@ -165,6 +173,8 @@ geo_status geo_destroy_world(geo_world w) {
     cudaFree(w->d_vols);
     cudaFree(w->d_node);
     cudaFree(w->d_xf);
+    cudaFree(w->d_cnt);
+    cudaFree(w->d_perm);
     if (prev >= 0 && prev != w->device) cudaSetDevice(prev);
     delete w;
     return GEO_OK;
@@ -212,8 +222,28 @@ geo_status geo_world_step(geo_world w, const double* x, const double* y, const d
         (flag_in && !device_ptr(flag_in)) || (flag_out && !device_ptr(flag_out)))
         return GEO_ERR_INVALID_ARG;
     const Basket b{x, y, z, dx, dy, dz, n};
-    return world_cuda_status(launch_world_step(world_view(w), b, node_in, flag_in, step, node_out, flag_out, mode,
-                                               static_cast<cudaStream_t>(stream), sm_count(w->device)));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int sms = sm_count(w->device);
+    std::lock_guard<std::mutex> lock(w->mu);
+    if (n > w->perm_cap) {
+        // grow the grouping scratch (the only allocation of the call)
+        cudaError_t e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return world_cuda_status(e);
+        cudaFree(w->d_perm);
+        cudaFree(w->d_cnt);
+        w->d_perm = nullptr;
+        w->d_cnt = nullptr;
+        w->perm_cap = 0;
+        if ((e = cudaMalloc(&w->d_perm, sizeof(int32_t) * size_t(n))) != cudaSuccess ||
+            (e = cudaMalloc(&w->d_cnt, sizeof(int32_t) * (size_t(w->nlv) + 1))) != cudaSuccess)
+            return world_cuda_status(e);
+        w->perm_cap = n;
+    }
+    const WorldView wv = world_view(w);
+    cudaError_t e = launch_world_group(wv, n, node_in, w->nlv, w->d_cnt, w->d_perm, s, sms);
+    if (e != cudaSuccess) return world_cuda_status(e);
+    return world_cuda_status(launch_world_step(wv, b, w->d_perm, node_in, flag_in, step, node_out, flag_out, mode, s,
+                                               sms));
 }
 
 }  // extern "C"

@@ -152,3 +152,33 @@ def test_invalid_state_and_single_volume(g, orc):
     assert np.isnan(s[1]) and n[1] == -2                 # zero direction
     assert np.isnan(s[2]) and n[2] == -2                 # no such node
     assert s[3] == 0.0 and n[3] == -2                    # not inside its node
+
+
+def test_grouping_paths_give_the_same_answers(g):
+    """The step groups tracks by logical volume with a shared-memory
+    histogram up to 8192 keys and with global atomics above; unused logical
+    volumes appended to the list only add keys, so both trees give the same
+    bits."""
+    w = scenes.world_toy()
+    W1, vols1 = build(g, w)
+    extra = [g.geo_build_volume(scenes.leaf(0, (1.0, 1.0, 1.0))) for _ in range(8200)]
+    W2 = g.geo_build_world(vols1 + extra, list(w.child) + [[]] * len(extra), w.root)
+    tr = scenes.world_points(w, 1 << 16, 9)
+    x = [dev(f) for f in tr.fields()]
+    node = g.geo_world_locate(W1, *x[:3])
+    flag = torch.full_like(node, -1)
+    for _ in range(3):
+        a = g.geo_world_step(W1, *x, node, flag, mode=1)
+        b = g.geo_world_step(W2, *x, node, flag, mode=1)
+        torch.cuda.synchronize()
+        assert torch.equal(a[0].nan_to_num(-7.0), b[0].nan_to_num(-7.0))
+        assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+        alive = node >= 0
+        s = torch.where(alive, a[0], torch.zeros_like(a[0]))
+        for k in range(3):
+            x[k] = x[k] + s * x[3 + k]
+        node = torch.where(alive, a[1], torch.full_like(a[1], -1))
+        flag = torch.where(alive, a[2], torch.full_like(a[2], -1))
+    W2.close()
+    for v in extra:
+        v.close()
