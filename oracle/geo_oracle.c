@@ -30,6 +30,11 @@
  *   Box  params (dx,dy,dz) half-lengths.
  *   Tube params (rmin,rmax,dz); solid when rmin == 0.
  *   Cone params (dz,rmin1,rmax1,rmin2,rmax2), index 1 at z=-dz, 2 at z=+dz.
+ *   Tube segment (rmin,rmax,dz,sphi,dphi): the tube cut to the closed wedge
+ *     of azimuths [sphi, sphi+dphi], 0 < dphi <= 2 pi (2 pi: the whole tube);
+ *     the wedge is the intersection (dphi <= pi) or the union (dphi > pi) of
+ *     the half-planes n1.(x,y) >= 0, n1 = (-sin sphi, cos sphi), and
+ *     n2.(x,y) >= 0, n2 = (sin(sphi+dphi), -cos(sphi+dphi)); it holds the axis.
  *   Placement p_mother = R p_local + t, R row-major.
  *   Miss = +inf.  Ties: mother first, then lowest daughter index.
  *   Track outside the mother: step 0, hit -2.  Zero/non-finite input: NaN, -2.
@@ -44,6 +49,7 @@
 #define K_BOX 0
 #define K_TUBE 1
 #define K_CONE 2
+#define K_TUBS 3   /* tube segment: (rmin, rmax, dz, sphi, dphi) */
 
 /* Surface (face) tags carried on interval endpoints.  Box faces 0..5 are
  * -x,+x,-y,+y,-z,+z; tubes and cones use 4/5 for -z/+z, 6 outer, 7 inner. */
@@ -52,6 +58,8 @@
 #define F_ZP 5
 #define F_OUT 6
 #define F_IN 7
+#define F_PHI1 8   /* tube segment: the face at sphi        */
+#define F_PHI2 9   /* tube segment: the face at sphi + dphi */
 
 typedef struct {
     double lo, hi;
@@ -263,6 +271,26 @@ static void cone_line(double dz, double r1, double r2, dd *a, dd *b) {
     *b = dd_div(two_sum(r2, -r1), dd_of(2.0 * dz));
 }
 
+/* Wedge of a tube segment: the half-plane normals, whether the wedge is the
+ * intersection of the two half-planes (dphi <= pi) and whether it is all of
+ * the plane (dphi >= 2 pi). */
+#define ORC_PI 3.14159265358979323846
+typedef struct { double n1[2], n2[2]; int convex, full; } wedge;
+static wedge wedge_of(const double *p) {
+    wedge w;
+    double f1 = p[3], f2 = p[3] + p[4];
+    w.n1[0] = -sin(f1); w.n1[1] = cos(f1);
+    w.n2[0] = sin(f2);  w.n2[1] = -cos(f2);
+    w.convex = p[4] <= ORC_PI;
+    w.full = !(p[4] < 2.0 * ORC_PI);
+    return w;
+}
+static int wedge_has(const wedge *w, double x, double y) {
+    if (w->full) return 1;
+    int a = w->n1[0] * x + w->n1[1] * y >= 0.0, b = w->n2[0] * x + w->n2[1] * y >= 0.0;
+    return w->convex ? (a && b) : (a || b);
+}
+
 /* The exact line set S for a solid in its local frame. */
 static void line_set_rec(int kind, const double *p, const double *x, const double *u, iset *S, xrec *R) {
     iset t;
@@ -276,7 +304,7 @@ static void line_set_rec(int kind, const double *p, const double *x, const doubl
     dd A = dd_add(two_prod(u[0], u[0]), two_prod(u[1], u[1]));
     dd B = dd_add(two_prod(x[0], u[0]), two_prod(x[1], u[1]));
     dd C = dd_add(two_prod(x[0], x[0]), two_prod(x[1], x[1]));
-    if (kind == K_TUBE) {
+    if (kind == K_TUBE || kind == K_TUBS) {
         double rmin = p[0], rmax = p[1], dz = p[2];
         slab_set(x[2], u[2], dz, F_ZM, F_ZP, S); rec_set(R, S);
         quad_le0(A, B, dd_sub(C, two_prod(rmax, rmax)), F_OUT, &t); rec_set(R, &t); set_and(S, &t);
@@ -284,6 +312,19 @@ static void line_set_rec(int kind, const double *p, const double *x, const doubl
             /* rho^2 >= rmin^2  <=>  -(rho^2 - rmin^2) <= 0 */
             dd Ci = dd_sub(C, two_prod(rmin, rmin));
             quad_le0(dd_neg(A), dd_neg(B), dd_neg(Ci), F_IN, &t); rec_set(R, &t); set_and(S, &t);
+        }
+        if (kind == K_TUBS) {
+            wedge w = wedge_of(p);
+            if (!w.full) {
+                /* each half-plane n.(x + s u) >= 0 is a half-line of s */
+                iset h2;
+                half_set(w.n1[0] * x[0] + w.n1[1] * x[1], w.n1[0] * u[0] + w.n1[1] * u[1], 0.0, 1, F_PHI1, &t);
+                rec_set(R, &t);
+                half_set(w.n2[0] * x[0] + w.n2[1] * x[1], w.n2[0] * u[0] + w.n2[1] * u[1], 0.0, 1, F_PHI2, &h2);
+                rec_set(R, &h2);
+                if (w.convex) set_and(&t, &h2); else set_or(&t, &h2);
+                set_and(S, &t);
+            }
         }
         return;
     }
@@ -382,9 +423,12 @@ int orc_contains(int kind, const double *p, const double *x) {
     if (kind == K_BOX)
         return fabs(x[0]) <= p[0] && fabs(x[1]) <= p[1] && fabs(x[2]) <= p[2];
     double r2 = x[0] * x[0] + x[1] * x[1];
-    if (kind == K_TUBE) {
+    if (kind == K_TUBE || kind == K_TUBS) {
         if (fabs(x[2]) > p[2]) return 0;
-        return r2 <= p[1] * p[1] && r2 >= p[0] * p[0];
+        if (!(r2 <= p[1] * p[1] && r2 >= p[0] * p[0])) return 0;
+        if (kind == K_TUBE) return 1;
+        wedge w = wedge_of(p);
+        return wedge_has(&w, x[0], x[1]);
     }
     double dz = p[0];
     if (fabs(x[2]) > dz) return 0;
@@ -429,6 +473,42 @@ double orc_safety(int kind, const double *p, const double *x, int inside) {
         if (c < 0.0) c = 0.0;
         return sqrt(a * a + b * b + c * c);
     }
+    if (kind == K_TUBS) {
+        wedge w = wedge_of(p);
+        double rmin = p[0], rmax = p[1], dz = p[2];
+        double rho = sqrt(x[0] * x[0] + x[1] * x[1]), az = fabs(x[2]);
+        /* distance to the phi face at unit direction e (the rectangle
+         * rmin <= r <= rmax, |z| <= dz of its half-plane) */
+        double e1[2] = { w.n1[1], -w.n1[0] }, e2[2] = { -w.n2[1], w.n2[0] };
+        double face[2];
+        for (int i = 0; i < 2; i++) {
+            const double *n = i ? w.n2 : w.n1, *e = i ? e2 : e1;
+            double h = n[0] * x[0] + n[1] * x[1];
+            double r = e[0] * x[0] + e[1] * x[1];
+            double rc = r < rmin ? rmin : (r > rmax ? rmax : r);
+            double zc = az > dz ? az - dz : 0.0;
+            face[i] = sqrt(h * h + (r - rc) * (r - rc) + zc * zc);
+        }
+        if (in) {
+            double d = rmax - rho;
+            if (dz - az < d) d = dz - az;
+            if (rmin > 0.0 && rho - rmin < d) d = rho - rmin;
+            if (!w.full) {
+                if (face[0] < d) d = face[0];
+                if (face[1] < d) d = face[1];
+            }
+            return d;
+        }
+        if (w.full || wedge_has(&w, x[0], x[1])) {
+            /* azimuth inside the wedge: the tube's own 2-D distance */
+            double dr = rho > rmax ? rho - rmax : (rho < rmin ? rmin - rho : 0.0);
+            double dzo = az > dz ? az - dz : 0.0;
+            return sqrt(dr * dr + dzo * dzo);
+        }
+        /* azimuth outside: for every radius and height the nearest azimuth
+         * of the wedge is one of its ends, so a phi face is nearest */
+        return face[0] < face[1] ? face[0] : face[1];
+    }
     /* Solids of revolution: the distance is the 2-D distance in the meridian
      * half-plane (rho, z) to the cross-section polygon
      * (rmin1,-dz) (rmax1,-dz) (rmax2,dz) (rmin2,dz). */
@@ -458,12 +538,26 @@ static void surface_grad(int kind, const double *p, int f, const double *xs, dou
         dF[ax] = -1.0;
         return;
     }
-    double dz = (kind == K_TUBE) ? p[2] : p[0];
-    int dzi = (kind == K_TUBE) ? 2 : 0;
+    if (f == F_PHI1 || f == F_PHI2) {
+        /* F = -n.(x, y) for the face's normal n; theta = (..., sphi, dphi) */
+        wedge w = wedge_of(p);
+        if (f == F_PHI1) {
+            g[0] = -w.n1[0]; g[1] = -w.n1[1];
+            dF[3] = w.n1[1] * xs[0] - w.n1[0] * xs[1];          /* e1 . (x, y) */
+        } else {
+            g[0] = -w.n2[0]; g[1] = -w.n2[1];
+            double de = -(-w.n2[1] * xs[0] + w.n2[0] * xs[1]);  /* -e2 . (x, y) */
+            dF[3] = de; dF[4] = de;
+        }
+        return;
+    }
+    int tubelike = kind == K_TUBE || kind == K_TUBS;
+    double dz = tubelike ? p[2] : p[0];
+    int dzi = tubelike ? 2 : 0;
     if (f == F_ZM || f == F_ZP) {
         double sg = (f == F_ZP) ? 1.0 : -1.0;
         g[2] = sg; dF[dzi] = -1.0;   /* F = sg*z - dz */
-    } else if (kind == K_TUBE) {
+    } else if (tubelike) {
         double r = (f == F_OUT) ? p[1] : p[0];
         double sg = (f == F_OUT) ? 1.0 : -1.0;   /* outside of the solid is F > 0 */
         g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1];
@@ -515,7 +609,7 @@ static int bad_input(const double *pw, const double *dw) {
 
 static double shape_scale(int kind, const double *p) {
     if (kind == K_BOX) { double m = p[0]; if (p[1] > m) m = p[1]; if (p[2] > m) m = p[2]; return m; }
-    if (kind == K_TUBE) return p[1] > p[2] ? p[1] : p[2];
+    if (kind == K_TUBE || kind == K_TUBS) return p[1] > p[2] ? p[1] : p[2];
     double m = p[0]; if (p[2] > m) m = p[2]; if (p[4] > m) m = p[4]; return m;
 }
 

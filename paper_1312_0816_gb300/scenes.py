@@ -27,8 +27,8 @@ import math
 
 import numpy as np
 
-BOX, TUBE, CONE = 0, 1, 2
-KIND_NAMES = {BOX: "box", TUBE: "tube", CONE: "cone"}
+BOX, TUBE, CONE, TUBS = 0, 1, 2, 3
+KIND_NAMES = {BOX: "box", TUBE: "tube", CONE: "cone", TUBS: "tube segment"}
 
 
 @dataclasses.dataclass
@@ -58,7 +58,7 @@ class Scene:
         for j, k in enumerate(self.kinds):
             if k == BOX:
                 r[j] = math.sqrt(p[j, 0] ** 2 + p[j, 1] ** 2 + p[j, 2] ** 2)
-            elif k == TUBE:
+            elif k in (TUBE, TUBS):
                 r[j] = math.sqrt(p[j, 1] ** 2 + p[j, 2] ** 2)
             else:
                 r[j] = math.sqrt(max(p[j, 2], p[j, 4]) ** 2 + p[j, 0] ** 2)
@@ -185,6 +185,20 @@ def diff3() -> Scene:
     return _scene("diff3", BOX, (100.0, 100.0, 100.0), rows)
 
 
+def seg4() -> Scene:
+    """Box mother (half 100 mm) with four tube segments (Sec. 3.1 lists the
+    segmented tube among the ported shapes): a solid quarter-ish wedge, a
+    half shell, a shell of 258 degrees (a non-convex wedge) and a whole turn;
+    two of them rotated."""
+    rows = [
+        (TUBS, (0.0, 30.0, 20.0, 0.3, 1.2), euler_zxz(0.4, 0.9, 1.7), (-50.0, -50.0, 0.0)),
+        (TUBS, (10.0, 25.0, 15.0, 2.0, math.pi), _EYE, (50.0, -50.0, 0.0)),
+        (TUBS, (5.0, 30.0, 20.0, -1.0, 4.5), euler_zxz(2.2, 0.5, 0.3), (-50.0, 50.0, 0.0)),
+        (TUBS, (0.0, 20.0, 25.0, 0.0, 2.0 * math.pi), _EYE, (50.0, 50.0, 0.0)),
+    ]
+    return _scene("seg4", BOX, (100.0, 100.0, 100.0), rows)
+
+
 def grid512(seed: int = 5) -> Scene:
     """Box mother (half 800 mm) with 512 daughters on an 8x8x8 grid (pitch 200 mm):
     boxes or tubes by a seeded coin, random rotations."""
@@ -252,7 +266,7 @@ def batched64(seed: int = 3, n_volumes: int = 64, total: int = 1 << 22):
     return vols, baskets
 
 
-SCENES = {"box4": box4, "toy40": toy40, "toy8": toy8, "diff3": diff3, "grid512": grid512}
+SCENES = {"box4": box4, "toy40": toy40, "toy8": toy8, "diff3": diff3, "grid512": grid512, "seg4": seg4}
 
 
 # --------------------------------------------------------------------------
@@ -302,7 +316,7 @@ def keepout_mask(scene: Scene, x, y, z, margin: float = 1e-6) -> np.ndarray:
             m = (np.abs(lx) <= p[j, 0] + margin) & (np.abs(ly) <= p[j, 1] + margin) & \
                 (np.abs(lz) <= p[j, 2] + margin)
         else:
-            if k == TUBE:
+            if k in (TUBE, TUBS):   # a segment lies inside its whole tube
                 rlo, rhi, hz = p[j, 0], p[j, 1], p[j, 2]
             else:
                 rlo, rhi, hz = min(p[j, 1], p[j, 3]), max(p[j, 2], p[j, 4]), p[j, 0]

@@ -46,6 +46,7 @@ def _march(orc, sc, tr, h, smax):
 
 
 @pytest.mark.parametrize("name,seed,n,h", [("box4", 0, 10000, 1.25), ("diff3", None, 10000, 0.6),
+                                           ("seg4", None, 6000, 0.6),
                                            ("toy8", 1, 1500, 3.5)])
 def test_ray_marching_agrees(orc, name, seed, n, h):
     sc = scenes.SCENES[name]() if seed is None else scenes.SCENES[name](seed)
@@ -72,7 +73,7 @@ def test_ray_marching_agrees(orc, name, seed, n, h):
         assert np.all(w == -1)
 
 
-@pytest.mark.parametrize("name,seed", [("box4", 0), ("diff3", None), ("toy40", 1)])
+@pytest.mark.parametrize("name,seed", [("box4", 0), ("diff3", None), ("toy40", 1), ("seg4", None)])
 def test_sphere_tracing_agrees(orc, name, seed):
     sc = scenes.SCENES[name]() if seed is None else scenes.SCENES[name](seed)
     tr = scenes.sample_tracks(sc, 3000, 32)
@@ -89,7 +90,7 @@ def test_sphere_tracing_agrees(orc, name, seed):
     assert np.max(np.abs(s - r["step"])[conv]) < 1e-9
 
 
-@pytest.mark.parametrize("name,seed", [("diff3", None), ("toy8", 1)])
+@pytest.mark.parametrize("name,seed", [("diff3", None), ("toy8", 1), ("seg4", None)])
 def test_safety_is_exact_distance(orc, name, seed):
     """min over 20000 directions of the step >= safety and within the angular
     resolution of it (an under-estimating safety would fail the upper side)."""

@@ -68,6 +68,8 @@ def _iur_chords(orc, kind, params, rb, n, seed):
     (0, (10.0, 20.0, 5.0), 4 * 10 * 20 * 5 / (10 * 20 + 20 * 5 + 5 * 10)),
     (1, (0.0, 15.0, 25.0), 4 * 15 * 25 / (2 * 25 + 15)),
     (2, (20.0, 0.0, 5.0, 0.0, 25.0), None),
+    # solid wedge of 1 rad: V = dphi r^2 dz, S = dphi r^2 (caps) + dphi r 2dz + 2 r 2dz (phi faces)
+    (3, (0.0, 10.0, 10.0, 0.0, 1.0), 4 * 1.0 * 100 * 10 / (1.0 * 100 + 1.0 * 10 * 20 + 2 * 10 * 20)),
 ])
 def test_cauchy_mean_chord(orc, kind, params, mean):
     """Cauchy: E[chord] = 4V/S for IUR lines hitting a convex body."""
@@ -84,7 +86,7 @@ def test_cauchy_mean_chord(orc, kind, params, mean):
 
 # ------------------------------------------------------------ invariants ---
 
-SCENES = [("box4", 0), ("toy40", 1), ("toy8", 1), ("diff3", None)]
+SCENES = [("box4", 0), ("toy40", 1), ("toy8", 1), ("diff3", None), ("seg4", None)]
 
 
 def _scene(name, seed):
