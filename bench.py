@@ -389,12 +389,12 @@ def shapes_leg(pkg, steps, q_sqrt, q_div):
     import torch
 
     solids = {"box": (0, (10.0, 20.0, 30.0)), "tube": (1, (5.0, 20.0, 30.0)),
-              "cone": (2, (30.0, 5.0, 10.0, 8.0, 20.0))}
+              "cone": (2, (30.0, 5.0, 10.0, 8.0, 20.0)), "tube_segment": (3, (5.0, 20.0, 30.0, 0.4, 4.0))}
     out = {"workload": "points uniform in 1.5x the solid's extent (inside and outside), isotropic directions; "
                        "identity placement; steps %d" % steps}
     rng = np.random.default_rng(5)
     for name, (kind, prm) in solids.items():
-        ext = np.array(prm[:3]) if kind == 0 else (np.array([prm[1], prm[1], prm[2]]) if kind == 1
+        ext = np.array(prm[:3]) if kind == 0 else (np.array([prm[1], prm[1], prm[2]]) if kind in (1, 3)
                                                    else np.array([max(prm[2], prm[4])] * 2 + [prm[0]]))
         row = {}
         for n in (1024, 1 << 20):
@@ -410,12 +410,13 @@ def shapes_leg(pkg, steps, q_sqrt, q_div):
             res = torch.empty(n, dtype=torch.float64, device="cuda")
             for what, key in ((pkg.GEO_Q_DIST_OUT, "out"), (pkg.GEO_Q_DIST_IN, "in")):
                 ms = _event_time(lambda it: pkg.geo_shape_query(kind, prm, what, *copies[it % ncp], out=res), steps)
-                a, sq, dv = FP64_OPS[(key, kind)]
-                ops = FP64_TRANSFORM + a + sq * q_sqrt + dv * q_div
-                achieved = n * ops * 2 / (ms * 1e-3) / 1e12
-                row[f"dist_{key}_{n}"] = {"value": n / (ms * 1e-3), "unit": "tracks/s", "us_per_call": ms * 1e3,
-                                          "fp64_dfma_equiv_per_track": ops,
-                                          "fp64_frac": achieved / PEAK_FP64_TFLOPS}
+                rec = {"value": n / (ms * 1e-3), "unit": "tracks/s", "us_per_call": ms * 1e3}
+                if (key, kind) in FP64_OPS:   # instruction mixes are counted for box, tube, cone
+                    a, sq, dv = FP64_OPS[(key, kind)]
+                    ops = FP64_TRANSFORM + a + sq * q_sqrt + dv * q_div
+                    rec["fp64_dfma_equiv_per_track"] = ops
+                    rec["fp64_frac"] = n * ops * 2 / (ms * 1e-3) / 1e12 / PEAK_FP64_TFLOPS
+                row[f"dist_{key}_{n}"] = rec
         out[name] = row
     return out
 

@@ -21,6 +21,10 @@
  *   - Box  p = (dx, dy, dz, -, -)               half-lengths
  *     Tube p = (rmin, rmax, dz, -, -)           rmin = 0 is a solid cylinder
  *     Cone p = (dz, rmin1, rmax1, rmin2, rmax2)  radii "1" at z=-dz, "2" at +dz
+ *     Tube segment (GEO_TUBS) p = (rmin, rmax, dz, sphi, dphi): the tube cut
+ *       to the closed wedge of azimuths [sphi, sphi + dphi], 0 < dphi <= 2 pi
+ *       (2 pi: the whole tube); the wedge holds the z axis.  Its surfaces are
+ *       tagged 8 (the face at sphi) and 9 (the face at sphi + dphi).
  *   - A daughter is placed by a rotation R (row-major, local -> mother) and a
  *     translation t:  p_mother = R p_local + t.  The mother's frame is the
  *     frame of the tracks (its rot must be the identity and trans zero).
@@ -63,7 +67,7 @@ typedef enum {
     GEO_ERR_UNSUPPORTED = 6     /* valid request this build does not implement      */
 } geo_status;
 
-typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2 } geo_kind;
+typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2, GEO_TUBS = 3 } geo_kind;
 
 /* GEO_FP64: every operation in FP64.
  * GEO_FP32_REFINE: a conservative FP32 pass bounds every candidate from below;

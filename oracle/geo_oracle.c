@@ -324,6 +324,17 @@ static void line_set_rec(int kind, const double *p, const double *x, const doubl
                 rec_set(R, &h2);
                 if (w.convex) set_and(&t, &h2); else set_or(&t, &h2);
                 set_and(S, &t);
+                /* dphi = pi: the two planes coincide, and a phi endpoint lies
+                 * on the face on whose side of the axis it is */
+                for (int i = 0; i < S->n && p[4] == ORC_PI; i++) {
+                    for (int e = 0; e < 2; e++) {
+                        int *f = e ? &S->v[i].fhi : &S->v[i].flo;
+                        double tt = e ? S->v[i].hi : S->v[i].lo;
+                        if ((*f != F_PHI1 && *f != F_PHI2) || !isfinite(tt)) continue;
+                        double px = x[0] + tt * u[0], py = x[1] + tt * u[1];
+                        *f = (w.n1[1] * px - w.n1[0] * py >= 0.0) ? F_PHI1 : F_PHI2;
+                    }
+                }
             }
         }
         return;

@@ -50,7 +50,21 @@ __device__ __forceinline__ void surface_grad64(const ShapeRec64& r, int face, co
         dF[3] = dF[4] = 0.0;
         return;
     }
-    const bool tube = r.kind == KTUBE;
+    if (face == 8 || face == 9) {                    // tube segment: F = -n.(x, y)
+        const double* d = r.d;
+        const double nx = face == 8 ? d[5] : d[7], ny = face == 8 ? d[6] : d[8];
+        g[0] = -nx;
+        g[1] = -ny;
+        g[2] = 0.0;
+        // d/dsphi of the face at sphi: e1.(x, y); of the face at sphi + dphi:
+        // -e2.(x, y), for sphi and dphi alike
+        const double de = face == 8 ? ny * xs[0] - nx * xs[1] : -(-ny * xs[0] + nx * xs[1]);
+        dF[0] = dF[1] = dF[2] = 0.0;
+        dF[3] = de;
+        dF[4] = face == 8 ? 0.0 : de;
+        return;
+    }
+    const bool tube = r.kind == KTUBE || r.kind == KTUBS;
     const double dz = tube ? p[2] : p[0];
     if (face == 4 || face == 5) {                    // F = +-z - dz
         g[0] = g[1] = 0.0;

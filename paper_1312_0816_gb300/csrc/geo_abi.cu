@@ -44,6 +44,7 @@ struct geo_batch_s {
 namespace {
 
 constexpr double kEps32 = 5.9604644775390625e-08;  // 2^-24, unit roundoff of FP32
+constexpr double kPi = 3.14159265358979323846;
 
 int num_sms_of(int dev) {
     static int cache[64] = {0};
@@ -71,7 +72,7 @@ bool finite_all(const double* a, int n) {
 
 // Shape parameter validation (readings of the ROOT conventions, see geo.h).
 geo_status check_shape(const geo_placed_shape& s, bool is_mother) {
-    if (s.kind < GEO_BOX || s.kind > GEO_CONE) return GEO_ERR_INVALID_ARG;
+    if (s.kind < GEO_BOX || s.kind > GEO_TUBS) return GEO_ERR_INVALID_ARG;
     if (s.reserved != 0) return GEO_ERR_INVALID_ARG;
     if (!finite_all(s.p, 5) || !finite_all(s.rot, 9) || !finite_all(s.trans, 3)) return GEO_ERR_SHAPE_PARAMS;
     const double* p = s.p;
@@ -81,6 +82,10 @@ geo_status check_shape(const geo_placed_shape& s, bool is_mother) {
             break;
         case GEO_TUBE:
             if (!(p[2] > 0 && p[0] >= 0 && p[1] > 0 && p[0] <= p[1])) return GEO_ERR_SHAPE_PARAMS;
+            break;
+        case GEO_TUBS:
+            if (!(p[2] > 0 && p[0] >= 0 && p[1] > 0 && p[0] <= p[1] && p[4] > 0 && p[4] <= 2.0 * kPi))
+                return GEO_ERR_SHAPE_PARAMS;
             break;
         default:
             if (!(p[0] > 0 && p[1] >= 0 && p[3] >= 0 && p[1] <= p[2] && p[3] <= p[4] && p[2] + p[4] > 0))
@@ -107,7 +112,7 @@ geo_status check_shape(const geo_placed_shape& s, bool is_mother) {
 double bounding_radius(const geo_placed_shape& s) {
     const double* p = s.p;
     if (s.kind == GEO_BOX) return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    if (s.kind == GEO_TUBE) return std::sqrt(p[1] * p[1] + p[2] * p[2]);
+    if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) return std::sqrt(p[1] * p[1] + p[2] * p[2]);
     const double r = std::max(p[2], p[4]);
     return std::sqrt(r * r + p[0] * p[0]);
 }
@@ -123,9 +128,17 @@ ShapeRec64 make_rec64(const geo_placed_shape& s) {
     const double* p = s.p;
     if (s.kind == GEO_BOX) {
         r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
-    } else if (s.kind == GEO_TUBE) {
+    } else if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) {
         r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
         r.d[3] = p[0] * p[0]; r.d[4] = p[1] * p[1];
+        if (s.kind == GEO_TUBS) {
+            const double f1 = p[3], f2 = p[3] + p[4];
+            r.d[5] = -std::sin(f1); r.d[6] = std::cos(f1);   // n1: wedge side of the face at sphi
+            r.d[7] = std::sin(f2);  r.d[8] = -std::cos(f2);  // n2: wedge side of the face at sphi + dphi
+            r.d[9] = p[4] <= kPi ? 1.0 : 0.0;                // the wedge is n1 >= 0 AND n2 >= 0
+            r.d[10] = p[4] < 2.0 * kPi ? 0.0 : 1.0;          // a whole turn: no wedge
+            r.d[11] = p[4] == kPi ? 1.0 : 0.0;               // a half turn: the two planes coincide
+        }
     } else {
         const double dz = p[0];
         r.d[0] = dz;
@@ -161,7 +174,14 @@ bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32
             r.e[k] = float(p[k] + g);
             if (!(p[k] + g > 0)) return false;
         }
-    } else if (s.kind == GEO_TUBE) {
+    } else if (s.kind == GEO_TUBS && g < 0) {
+        // a shrunk whole tube is no subset of a segment: an empty solid, so
+        // the filter never decides "surely inside" for a segment mother
+        r.kind = GEO_TUBE;
+        r.e[0] = 0.f; r.e[1] = -1.f; r.e[2] = -1.f; r.e[3] = 0.f;
+    } else if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) {
+        // a segment is bounded by its whole tube (superset: valid lower bounds)
+        r.kind = GEO_TUBE;
         const double rmin = p[0] - g, rmax = p[1] + g, dz = p[2] + g;
         if (!(rmax > 0 && dz > 0)) return false;
         const bool hole = p[0] > 0 && rmin > 0;
@@ -215,7 +235,7 @@ double inflation(const geo_placed_shape& s, double S) {
     if (s.kind == GEO_BOX) return d;
     double rsmall = DBL_MAX, slope2 = 0.0;
     auto take = [&](double r) { rsmall = std::min(rsmall, r > 0 ? r : 0.0); };
-    if (s.kind == GEO_TUBE) {
+    if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) {
         take(p[1]);
         if (p[0] > 0) take(p[0]);
     } else {
@@ -244,7 +264,7 @@ geo_status build_voxels(const geo_placed_shape& m, const geo_placed_shape* d, in
     double half[3];
     const double* p = m.p;
     if (m.kind == GEO_BOX) { half[0] = p[0]; half[1] = p[1]; half[2] = p[2]; }
-    else if (m.kind == GEO_TUBE) { half[0] = half[1] = p[1]; half[2] = p[2]; }
+    else if (m.kind == GEO_TUBE || m.kind == GEO_TUBS) { half[0] = half[1] = p[1]; half[2] = p[2]; }
     else { half[0] = half[1] = std::max(p[2], p[4]); half[2] = p[0]; }
     int g[3];
     const int gauto = std::max(1, std::min(64, int(std::lround(2.0 * std::cbrt(double(std::max(nd, 1)))))));
@@ -264,7 +284,7 @@ geo_status build_voxels(const geo_placed_shape& m, const geo_placed_shape* d, in
         double he[3];
         const double* q = sh.p;
         if (sh.kind == GEO_BOX) { he[0] = q[0]; he[1] = q[1]; he[2] = q[2]; }
-        else if (sh.kind == GEO_TUBE) { he[0] = he[1] = q[1]; he[2] = q[2]; }
+        else if (sh.kind == GEO_TUBE || sh.kind == GEO_TUBS) { he[0] = he[1] = q[1]; he[2] = q[2]; }
         else { he[0] = he[1] = std::max(q[2], q[4]); he[2] = q[0]; }
         int i0[3], i1[3];
         for (int k = 0; k < 3; ++k) {

@@ -7,7 +7,7 @@
 
 namespace geonav {
 
-constexpr int KBOX = 0, KTUBE = 1, KCONE = 2;
+constexpr int KBOX = 0, KTUBE = 1, KCONE = 2, KTUBS = 3;
 
 // FP64 record of one placed solid, 256 B, read warp-uniformly (broadcast).
 //  R: row-major local->mother rotation, t: translation.
@@ -17,6 +17,11 @@ constexpr int KBOX = 0, KTUBE = 1, KCONE = 2;
 //   cone: d[0] dz, d[1] a_out, d[2] b_out, d[3] a_in, d[4] b_in,
 //         d[5] rmin1^2, d[6] rmax1^2, d[7] rmin2^2, d[8] rmax2^2,
 //         d[9] 1/sqrt(1+b_out^2), d[10] 1/sqrt(1+b_in^2), d[11] has_inner (0/1)
+//   tube segment: d[0..4] as the tube, d[5], d[6] n1 = (-sin sphi, cos sphi),
+//         d[7], d[8] n2 = (sin(sphi+dphi), -cos(sphi+dphi)): the wedge is
+//         {n1.(x,y) >= 0} AND (d[9] = 1, dphi <= pi) or OR (d[9] = 0) the
+//         same for n2; d[10] = 1 for a whole turn (no wedge); d[11] = 1 for
+//         a half turn (both faces in one plane)
 //   (radius lines R(z) = a + b z, R(-dz) = r1, R(+dz) = r2)
 //  brad: bounding-sphere radius about t, enlarged by a relative 1e-12 + 1e-9 mm
 //  so that the FP64 sphere cull is conservative.

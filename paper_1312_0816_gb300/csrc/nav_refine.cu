@@ -68,6 +68,9 @@ __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity
     healthy = false;
 }
 
+// FP64 task bins: 0 the mother, then box, tube (and tube segment), cone
+__device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : 1 + kind; }
+
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
 
 template <bool SMEM, int TRAV>
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                 int task = 0, bin = -1;
                 if (rs.status == 0) {
                     task = first_task(rs);
-                    bin = task < 0 ? 0 : 1 + tab64[task].kind;
+                    bin = task < 0 ? 0 : kind_bin(tab64[task].kind);
                 }
                 if (t < 4) st_.cnt[t] = 0;
                 producer_barrier();
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 int task = 0, bin = -1;
                 if (rs.status == 0) {
                     task = first_task(rs);
-                    bin = task < 0 ? 0 : 1 + v.d64[task].kind;
+                    bin = task < 0 ? 0 : kind_bin(v.d64[task].kind);
                 }
                 const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
                 producer_barrier();

@@ -103,12 +103,22 @@ __device__ __forceinline__ double root_rising(double A, double B, double C) {
 
 __device__ __forceinline__ double rho2_of(const double* x) { return DOT2(x[0], x[0], x[1], x[1]); }
 
+// ---------------------------------------------------- tube segment wedge ---
+// (x, y) in the wedge of a tube segment (d as in geo_internal.h)
+__device__ __forceinline__ bool wedge_has64(const double* d, double x, double y) {
+    if (d[10] != 0.0) return true;
+    const bool a = NONNEG(DOT2(d[5], x, d[6], y)), b = NONNEG(DOT2(d[7], x, d[8], y));
+    return d[9] != 0.0 ? (a && b) : (a || b);
+}
+
 // ------------------------------------------------------------- contains ---
 __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x) {
     const double* d = r.d;
     if (r.kind == KBOX) return ABS_LE(x[0], d[0]) && ABS_LE(x[1], d[1]) && ABS_LE(x[2], d[2]);
     const double rho2 = rho2_of(x);
     if (r.kind == KTUBE) return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2);
+    if (r.kind == KTUBS)
+        return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2) && wedge_has64(d, x[0], x[1]);
     if (!ABS_LE(x[2], d[0])) return false;
     const double ro = FMA(d[2], x[2], d[1]);
     const double ri = FMA(d[4], x[2], d[3]);
@@ -193,6 +203,66 @@ __device__ __forceinline__ double tube_out64(const double* d, const double* x, c
     return best;
 }
 
+// Tube segment: the tube's candidates restricted to the wedge, and the two
+// phi faces (entered where the track crosses a face's plane into the wedge
+// side, at a point of the face: rmin <= r <= rmax along the face's
+// direction, |z| <= dz).
+template <bool FACE = false, bool REENTRY = false>
+__device__ __forceinline__ double tubs_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
+    if (FACE) *face = -1;
+    const double rmin = d[0], dz = d[2], rmin2 = d[3], rmax2 = d[4];
+    const double rho2 = rho2_of(x);
+    if (!REENTRY && ABS_LE(x[2], dz) && LE(rho2, rmax2) && LE(rmin2, rho2) && wedge_has64(d, x[0], x[1]))
+        return 0.0;
+    double best = d_inf();
+    {   // the z-plane the track approaches from outside the slab
+        const bool zc = ABS_GT(x[2], dz) && OPPOSITE(x[2], u[2]);
+        const double t = DIV(SUB(copysign(dz, x[2]), x[2]), zc ? u[2] : 1.0);
+        const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
+        const double r2 = DOT2(xh, xh, yh, yh);
+        if (zc && LE(r2, rmax2) && LE(rmin2, r2) && wedge_has64(d, xh, yh)) {
+            best = t;
+            if (FACE) *face = IS_POS(x[2]) ? 5 : 4;
+        }
+    }
+    const double A = DOT2(u[0], u[0], u[1], u[1]);
+    const double B = DOT2(x[0], u[0], x[1], u[1]);
+    {   // outer cylinder, crossed inwards
+        const double s = root_falling(A, B, SUB(rho2, rmax2));
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz) &&
+            wedge_has64(d, FMA(s, u[0], x[0]), FMA(s, u[1], x[1]))) {
+            best = s;
+            if (FACE) *face = 6;
+        }
+    }
+    if (rmin > 0.0) {   // inner cylinder, crossed outwards (out of the hole)
+        const double s = root_rising(A, B, SUB(rho2, rmin2));
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz) &&
+            wedge_has64(d, FMA(s, u[0], x[0]), FMA(s, u[1], x[1]))) {
+            best = s;
+            if (FACE) *face = 7;
+        }
+    }
+    if (d[10] == 0.0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double nx = d[5 + 2 * i], ny = d[6 + 2 * i];
+            const double ex = i == 0 ? ny : -ny, ey = i == 0 ? -nx : nx;   // the face's direction
+            const double wn = DOT2(nx, u[0], ny, u[1]);
+            if (!IS_POS(wn)) continue;                                       // not moving to the wedge side
+            const double s = DIV(-DOT2(nx, x[0], ny, x[1]), wn);
+            if (!(REENTRY ? IS_POS(s) : NONNEG(s)) || !LT(s, best)) continue;
+            const double xh = FMA(s, u[0], x[0]), yh = FMA(s, u[1], x[1]);
+            const double r2 = DOT2(xh, xh, yh, yh);
+            if (ABS_LE(FMA(s, u[2], x[2]), dz) && NONNEG(DOT2(ex, xh, ey, yh)) && LE(r2, rmax2) && LE(rmin2, r2)) {
+                best = s;
+                if (FACE) *face = 8 + i;
+            }
+        }
+    }
+    return best;
+}
+
 template <bool FACE = false, bool REENTRY = false>
 __device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
     if (FACE) *face = -1;
@@ -242,6 +312,7 @@ __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* 
                                              int* face = nullptr) {
     if (r.kind == KBOX) return box_out64<FACE>(r.d, x, u, face);
     if (r.kind == KTUBE) return tube_out64<FACE>(r.d, x, u, face);
+    if (r.kind == KTUBS) return tubs_out64<FACE>(r.d, x, u, face);
     return cone_out64<FACE>(r.d, x, u, face);
 }
 
@@ -259,6 +330,7 @@ __device__ __forceinline__ double reentry64(const ShapeRec64& r, const double* x
         return box_out64<FACE>(r.d, x, u, face);
     }
     if (r.kind == KTUBE) return tube_out64<FACE, true>(r.d, x, u, face);
+    if (r.kind == KTUBS) return tubs_out64<FACE, true>(r.d, x, u, face);
     return cone_out64<FACE, true>(r.d, x, u, face);
 }
 
@@ -299,7 +371,7 @@ __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
     double s;
-    if (r.kind == KTUBE) {
+    if (r.kind == KTUBE || r.kind == KTUBS) {
         t = d_inf();
         take(clamp0(slab_exit(x[2], u[2], d[2])), IS_POS(u[2]) ? 5 : 4);
         s = root_rising(A0, B0, SUB(rho2, d[4]));
@@ -307,6 +379,44 @@ __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x
         if (d[0] > 0.0) {
             s = root_falling(A0, B0, SUB(rho2, d[3]));
             if (NONNEG(s)) take(clamp0(s), 7);
+        }
+        if (r.kind == KTUBS && d[10] == 0.0) {
+            // the wedge: each half-plane holds s where c + s w >= 0
+            const double c1 = DOT2(d[5], x[0], d[6], x[1]), w1 = DOT2(d[5], u[0], d[6], u[1]);
+            const double c2 = DOT2(d[7], x[0], d[8], x[1]), w2 = DOT2(d[7], u[0], d[8], u[1]);
+            const double e1 = IS_NEG(w1) ? DIV(-c1, w1) : d_inf();   // where the track leaves half-plane 1
+            const double e2 = IS_NEG(w2) ? DIV(-c2, w2) : d_inf();
+            if (d[9] != 0.0) {
+                // intersection: leaves the wedge when it leaves either (when
+                // dphi = pi the two planes coincide, and the face is the one
+                // on whose side of the axis the track leaves)
+                if (d[11] != 0.0) {
+                    const double ec = MINP(clamp0(e1), clamp0(e2));
+                    const double xh = FMA(ec, u[0], x[0]), yh = FMA(ec, u[1], x[1]);
+                    take(ec, NONNEG(DOT2(d[6], xh, -d[5], yh)) ? 8 : 9);
+                } else {
+                    take(clamp0(e1), 8);
+                    take(clamp0(e2), 9);
+                }
+            } else {
+                // union: of the half-lines holding the start (c >= 0), a
+                // rising one (w >= 0) never ends; a falling one ends at e; a
+                // rising one that starts later (at -c/w > 0) continues the
+                // union if it starts before that end
+                const bool in1 = NONNEG(c1), in2 = NONNEG(c2);
+                const bool up1 = !IS_NEG(w1), up2 = !IS_NEG(w2);
+                if (!((in1 && up1) || (in2 && up2))) {
+                    // every half-plane holding the start ends: the later end
+                    const double x1 = in1 ? clamp0(e1) : 0.0, x2 = in2 ? clamp0(e2) : 0.0;
+                    const bool second = in2 && (!in1 || LT(x1, x2));
+                    const double E = second ? x2 : x1;
+                    // a half-plane not holding the start but entered by then
+                    // continues the union
+                    const double a1 = (!in1 && IS_POS(w1)) ? DIV(-c1, w1) : d_inf();
+                    const double a2 = (!in2 && IS_POS(w2)) ? DIV(-c2, w2) : d_inf();
+                    if (!(LE(a1, E) || LE(a2, E))) take(E, second ? 9 : 8);
+                }
+            }
         }
         if (FACE) *face = f;
         return t;
@@ -352,6 +462,36 @@ __device__ __forceinline__ double safety64(const ShapeRec64& r, const double* x,
     }
     const double rho = SQRT(rho2_of(x));
     const double az = fabs(x[2]);
+    if (r.kind == KTUBS) {
+        // phi faces: the rectangles rmin <= r <= rmax, |z| <= dz of the two
+        // half-planes (distance with the foot clamped into the rectangle)
+        double fd[2] = {d_inf(), d_inf()};
+        if (d[10] == 0.0) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const double nx = d[5 + 2 * i], ny = d[6 + 2 * i];
+                const double ex = i == 0 ? ny : -ny, ey = i == 0 ? -nx : nx;
+                const double h = DOT2(nx, x[0], ny, x[1]);
+                const double rr = DOT2(ex, x[0], ey, x[1]);
+                const double rc = fmin(fmax(rr, d[0]), d[1]);
+                const double dr = SUB(rr, rc), dzf = fmax(SUB(az, d[2]), 0.0);
+                fd[i] = SQRT(FMA(h, h, DOT2(dr, dr, dzf, dzf)));
+            }
+        }
+        if (in) {
+            double s = fmin(SUB(d[1], rho), SUB(d[2], az));
+            if (d[0] > 0.0) s = fmin(s, SUB(rho, d[0]));
+            return fmin(s, fmin(fd[0], fd[1]));
+        }
+        if (wedge_has64(d, x[0], x[1])) {
+            // azimuth in the wedge: the tube's distance in the meridian plane
+            const double dzo = fmax(SUB(az, d[2]), 0.0);
+            const double dro = fmax(fmax(SUB(d[0], rho), SUB(rho, d[1])), 0.0);
+            return SQRT(DOT2(dzo, dzo, dro, dro));
+        }
+        // azimuth outside: the nearest azimuth of the wedge is one of its ends
+        return fmin(fd[0], fd[1]);
+    }
     if (r.kind == KTUBE) {
         if (in) {
             double s = fmin(SUB(d[1], rho), SUB(d[2], az));

@@ -17,7 +17,7 @@ from . import build_lib
 GEO_OK = 0
 GEO_FP64 = 0
 GEO_FP32_REFINE = 1
-GEO_BOX, GEO_TUBE, GEO_CONE = 0, 1, 2
+GEO_BOX, GEO_TUBE, GEO_CONE, GEO_TUBS = 0, 1, 2, 3
 
 _STATUS = {0: "GEO_OK", 1: "GEO_ERR_INVALID_ARG", 2: "GEO_ERR_SHAPE_PARAMS", 3: "GEO_ERR_OOM",
            4: "GEO_ERR_CUDA", 5: "GEO_ERR_DEVICE_ASSERT", 6: "GEO_ERR_UNSUPPORTED"}

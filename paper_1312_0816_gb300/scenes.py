@@ -430,13 +430,16 @@ def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) ->
             vb[rows[f], free[f]] *= 1e-6
             q[b] = qb
             v[b] = vb
-        # tubes and cones: tangent lines (mode 0) or rim points (1, 2)
+        # tubes, tube segments and cones: tangent lines (mode 0) or rim
+        # points (1, 2); on a segment the points lie in its wedge, half of the
+        # rim points on the edges of its phi faces
         c = ~b
         if c.any():
             pc = prm[c]
             kc = kind[c]
             mc = mode[c]
-            hz = np.where(kc == TUBE, pc[:, 2], pc[:, 0])
+            tubelike = (kc == TUBE) | (kc == TUBS)
+            hz = np.where(tubelike, pc[:, 2], pc[:, 0])
             zc = np.where(mc == 2, rng.choice([-1.0, 1.0], size=hz.shape) * hz, rng.uniform(-1, 1, size=hz.shape) * hz)
             use_outer = rng.uniform(size=hz.shape) < 0.6
             tube_r = np.where(use_outer | (pc[:, 0] == 0.0), pc[:, 1], pc[:, 0])
@@ -444,9 +447,15 @@ def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) ->
             r1 = np.where(outer_c, pc[:, 2], pc[:, 1])
             r2 = np.where(outer_c, pc[:, 4], pc[:, 3])
             cone_r = r1 + (r2 - r1) * (zc + hz) / (2.0 * hz)
-            slope = np.where(kc == CONE, (r2 - r1) / (2.0 * hz), 0.0)
-            r = np.where(kc == TUBE, tube_r, cone_r)
+            slope = np.where(kc == CONE, (r2 - r1) / np.where(kc == CONE, 2.0 * hz, 1.0), 0.0)
+            r = np.where(tubelike, tube_r, cone_r)
             ph = rng.uniform(0.0, 2.0 * math.pi, size=hz.shape)
+            seg = kc == TUBS
+            if seg.any():
+                f0, dphi = pc[seg, 3], pc[seg, 4]
+                at_face = (mc[seg] != 0) & (rng.uniform(size=f0.shape) < 0.5)
+                end = np.where(rng.uniform(size=f0.shape) < 0.5, 0.0, 1.0)
+                ph[seg] = f0 + dphi * np.where(at_face, end, rng.uniform(size=f0.shape))
             radial = np.stack([np.cos(ph), np.sin(ph), np.zeros_like(ph)], 1)
             tang = np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)], 1)
             qc = radial * r[:, None]

@@ -50,7 +50,10 @@ def _build(mother, daughters):
 
 
 @pytest.mark.parametrize("mother,daughter,status", [
-    ((0, (100, 100, 100)), (3, (1, 1, 1)), 1),                      # unknown kind
+    ((0, (100, 100, 100)), (4, (1, 1, 1)), 1),                      # unknown kind
+    ((0, (100, 100, 100)), (3, (0, 10, 5, 0, 0)), 2),               # tube segment of no angle
+    ((0, (100, 100, 100)), (3, (0, 10, 5, 0, 7)), 2),               # tube segment beyond a whole turn
+    ((0, (100, 100, 100)), (3, (8, 6, 5, 0, 1)), 2),                # tube segment rmin > rmax
     ((0, (100, 100, 100)), (1, (20, 10, 5)), 2),                    # rmin > rmax
     ((0, (100, 100, 100)), (1, (0, 10, 0)), 2),                     # dz = 0
     ((0, (100, 100, 100)), (2, (5, 3, 2, 0, 4)), 2),                # cone rmin1 > rmax1

@@ -76,7 +76,7 @@ def central(fstep, base, k, h):
     return (fstep(a) - fstep(b)) / (2 * h)
 
 
-@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("toy8", 1 << 16)])
+@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("toy8", 1 << 16), ("seg4", 1 << 16)])
 def test_track_gradients(g, orc, name, n):
     sc = scenes.SCENES[name]()
     vol = g.geo_build_volume(sc)
@@ -121,7 +121,7 @@ def _scene_with(sc, trans=None, params=None, mparams=None):
                         sc.params if params is None else params, sc.rot, sc.trans if trans is None else trans)
 
 
-@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16)])
+@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("seg4", 1 << 16)])
 def test_geometry_gradients_match_fd(g, orc, name, n):
     """d(sum over smooth tracks of step)/d(translations, shape parameters)."""
     sc = scenes.SCENES[name]()
@@ -164,6 +164,8 @@ def test_geometry_gradients_match_fd(g, orc, name, n):
         for k in range(5):
             if sc.params[j, k] == 0.0:
                 continue
+            if sc.kinds[j] == scenes.TUBS and k == 4 and sc.params[j, 4] + H > 2 * np.pi:
+                continue   # a whole turn cannot grow
             pp, pm = sc.params.copy(), sc.params.copy()
             pp[j, k] += H
             pm[j, k] -= H

@@ -70,6 +70,7 @@ SCENES = {
     "toy8": lambda: scenes.toy8(1),
     "diff3": lambda: scenes.diff3(),
     "grid512": lambda: scenes.grid512(5),
+    "seg4": lambda: scenes.seg4(),
 }
 _scene_cache = {}
 

@@ -7,6 +7,8 @@ equal, except on a small fraction of rays that graze a surface or cross at an
 edge (both answers are then correct to rounding); safeties within 1e-9 mm;
 Contains exact outside the 1e-9 mm surface band.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -25,6 +27,11 @@ SOLIDS = [
     (2, (30.0, 5.0, 10.0, 8.0, 20.0)),
     (2, (30.0, 0.0, 10.0, 5.0, 20.0)),
     (2, (30.0, 0.0, 0.0, 0.0, 20.0)),
+    (3, (0.0, 10.0, 10.0, 0.0, math.pi / 2)),         # tube segments: a solid quarter,
+    (3, (4.0, 10.0, 10.0, 0.5, 1.5 * math.pi)),       # a non-convex shell wedge,
+    (3, (2.0, 10.0, 8.0, -1.0, math.pi)),             # a half shell (both faces in one plane),
+    (3, (0.0, 10.0, 8.0, 2.0, 0.2)),                  # a thin wedge,
+    (3, (3.0, 10.0, 8.0, 0.3, 2 * math.pi)),          # a whole turn
 ]
 WHAT = {"dist_out": 0, "dist_in": 1, "safety_out": 2, "safety_in": 3, "contains": 4}
 
@@ -42,7 +49,7 @@ def g():
 def extent(kind, p):
     if kind == 0:
         return np.array(p[:3])
-    if kind == 1:
+    if kind in (1, 3):
         return np.array([p[1], p[1], p[2]])
     r = max(p[2], p[4])
     return np.array([r, r, p[0]])
@@ -108,7 +115,7 @@ def test_shape_queries_match_oracle(g, orc, idx):
         assert np.array_equal(got[~band], want[~band])
 
 
-@pytest.mark.parametrize("idx", [0, 2, 4])
+@pytest.mark.parametrize("idx", [0, 2, 4, 8])
 def test_placed_solid(g, orc, idx):
     """Placement applied in the kernel: compare with the oracle on points
     transformed on the host (the transforms round differently, so distances
