@@ -606,13 +606,14 @@ def main():
     pinned = [torch.from_numpy(f).pin_memory() for f in tr.fields()]
     hs = torch.empty(n, dtype=torch.float64).pin_memory()
     hh = torch.empty(n, dtype=torch.int32).pin_memory()
+    chunk = max(1, n // 4)   # four chunks: copies of one overlap the step of another
     for _ in range(2):
-        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=n)
+        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=chunk)
     k_e2e = max(3, args.steps // 40)
     barrier()
     t0 = time.perf_counter()
     for _ in range(k_e2e):
-        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=n)
+        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=chunk)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e)
 
     batched = None if args.no_batched else batched_leg(pkg, scenes, rank, max(10, args.steps // 40))
@@ -640,7 +641,8 @@ def main():
             "refine": {"fp64_evals_per_track": evals, "fallback_tracks": fallback},
             "roofline": roof,
             "e2e": {"value": ws * n / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": 48 * n,
-                    "d2h_bytes_per_step": 12 * n, "api": "geo_dist_to_boundary_host (pinned host buffers)"},
+                    "d2h_bytes_per_step": 12 * n,
+                    "api": "geo_dist_to_boundary_host (pinned host buffers, 4 chunks pipelined over copy-in, step and copy-out streams)"},
             "gpu_launches": args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -171,10 +171,13 @@ geo_status geo_safety(geo_volume v, const double* x, const double* y, const doub
                       double* safety, int32_t mode, void* stream);
 
 /* Same as geo_dist_to_boundary but every array is HOST memory (pageable or
- * pinned); the library stages the basket through a device workspace in
- * chunks of at most `chunk` tracks (0 = 1<<20), copying on `stream`, and
- * synchronises `stream` before returning.  The workspace is allocated on the
- * first call and kept with the volume (grown when `chunk` grows). */
+ * pinned; pinned overlaps best); the library stages the basket through a
+ * device workspace of two buffers of `chunk` tracks (0 = 1<<18) as a
+ * pipeline: chunk c+1 is copied in on an internal stream while chunk c is
+ * stepped on `stream` and chunk c-1 copied out on a second internal stream.
+ * Returns after synchronising.  The workspace, streams and events are made
+ * on the first call and kept with the volume (the buffers grow when `chunk`
+ * grows); calls on one volume are serialised by a lock. */
 geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double* y,
                                      const double* z, const double* dx, const double* dy,
                                      const double* dz, int64_t n, double* step, int32_t* hit,

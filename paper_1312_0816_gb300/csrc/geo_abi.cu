@@ -24,9 +24,13 @@ struct geo_volume_s {
     int32_t* vox_ids = nullptr;
     unsigned int* status = nullptr;
     std::vector<ShapeRec64> h64;      // host copy of the daughter records
-    // staging workspace of geo_dist_to_boundary_host
+    // staging workspace of geo_dist_to_boundary_host: two buffers of
+    // ws_tracks tracks, a copy-in and a copy-out stream, and events
     void* ws = nullptr;
     int64_t ws_tracks = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
     std::mutex ws_mu;
 };
 
@@ -418,6 +422,9 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
         return GEO_ERR_SHAPE_PARAMS;
     }
     vw.nd = n_daughters;
+    vw.segs = mother->kind == GEO_TUBS ? 1 : 0;
+    for (int j = 0; j < n_daughters; ++j)
+        if (daughters[j].kind == GEO_TUBS) vw.segs = 1;
 
     cudaError_t e = cudaSuccess;
     const size_t b64 = sizeof(ShapeRec64) * size_t(std::max(n_daughters, 1));
@@ -476,6 +483,10 @@ geo_status geo_destroy_volume(geo_volume v) {
     cudaFree(v->vox_ids);
     cudaFree(v->status);
     cudaFree(v->ws);
+    if (v->s_in) cudaStreamDestroy(v->s_in);
+    if (v->s_out) cudaStreamDestroy(v->s_out);
+    for (cudaEvent_t e : {v->ev_start, v->ev_in[0], v->ev_in[1], v->ev_k[0], v->ev_k[1], v->ev_out[0], v->ev_out[1]})
+        if (e) cudaEventDestroy(e);
     if (prev >= 0 && prev != v->device) cudaSetDevice(prev);
     delete v;
     return GEO_OK;
@@ -544,44 +555,73 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
     if (n < 0 || chunk < 0) return GEO_ERR_INVALID_ARG;
     if (n == 0) return GEO_OK;
     if (!x || !y || !z || !dx || !dy || !dz || !step || !hit) return GEO_ERR_INVALID_ARG;
-    if (chunk == 0) chunk = int64_t(1) << 20;
+    if (chunk == 0) chunk = int64_t(1) << 18;
     if (chunk > n) chunk = n;
     std::lock_guard<std::mutex> lock(v->ws_mu);
     cudaError_t e = cudaSuccess;
+    if (!v->s_in) {
+        if ((e = cudaStreamCreateWithFlags(&v->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&v->s_out, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_status(e);
+        for (cudaEvent_t* ev : {&v->ev_start, &v->ev_in[0], &v->ev_in[1], &v->ev_k[0], &v->ev_k[1], &v->ev_out[0],
+                                &v->ev_out[1]})
+            if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
+    }
+    const size_t per_track = 7 * sizeof(double) + sizeof(int32_t);
     if (v->ws_tracks < chunk) {
         if (v->ws) {
             cudaFree(v->ws);
             v->ws = nullptr;
             v->ws_tracks = 0;
         }
-        if ((e = cudaMalloc(&v->ws, size_t(chunk) * (7 * sizeof(double) + sizeof(int32_t)))) != cudaSuccess)
-            return cuda_status(e);
+        if ((e = cudaMalloc(&v->ws, 2 * size_t(chunk) * per_track)) != cudaSuccess) return cuda_status(e);
         v->ws_tracks = chunk;
     }
-    double* w = static_cast<double*>(v->ws);
     const int64_t cap = v->ws_tracks;
-    double* f[7] = {w, w + cap, w + 2 * cap, w + 3 * cap, w + 4 * cap, w + 5 * cap, w + 6 * cap};
-    int32_t* whit = reinterpret_cast<int32_t*>(w + 7 * cap);
+    double* f[2][7];
+    int32_t* whit[2];
+    for (int bfr = 0; bfr < 2; ++bfr) {
+        double* w = reinterpret_cast<double*>(static_cast<char*>(v->ws) + bfr * size_t(cap) * per_track);
+        for (int k = 0; k < 7; ++k) f[bfr][k] = w + k * cap;
+        whit[bfr] = reinterpret_cast<int32_t*>(w + 7 * cap);
+    }
     const double* src[6] = {x, y, z, dx, dy, dz};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int sms = num_sms_of(v->device);
-    for (int64_t off = 0; off < n; off += chunk) {
+    // three-stage pipeline over chunks, two buffers: copy in (s_in), the
+    // step (the caller's stream), copy out (s_out); chunk c+1 is copied in
+    // while chunk c is stepped and chunk c-1 copied out
+    if ((e = cudaEventRecord(v->ev_start, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(v->s_in, v->ev_start, 0)) != cudaSuccess)
+        return cuda_status(e);
+    int64_t c = 0;
+    for (int64_t off = 0; off < n; off += chunk, ++c) {
+        const int bf = int(c & 1);
         const int64_t m = std::min(chunk, n - off);
+        if (c >= 2 && (e = cudaStreamWaitEvent(v->s_in, v->ev_out[bf], 0)) != cudaSuccess) return cuda_status(e);
         for (int k = 0; k < 6; ++k)
-            if ((e = cudaMemcpyAsync(f[k], src[k] + off, size_t(m) * sizeof(double), cudaMemcpyHostToDevice, s)) !=
-                cudaSuccess)
+            if ((e = cudaMemcpyAsync(f[bf][k], src[k] + off, size_t(m) * sizeof(double), cudaMemcpyHostToDevice,
+                                     v->s_in)) != cudaSuccess)
                 return cuda_status(e);
-        const Basket b{f[0], f[1], f[2], f[3], f[4], f[5], m};
-        e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, f[6], whit, nullptr, s, sms)
-                               : launch_dist_refine(v->view, b, f[6], whit, nullptr, s, sms);
+        if ((e = cudaEventRecord(v->ev_in[bf], v->s_in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, v->ev_in[bf], 0)) != cudaSuccess)
+            return cuda_status(e);
+        const Basket b{f[bf][0], f[bf][1], f[bf][2], f[bf][3], f[bf][4], f[bf][5], m};
+        e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, f[bf][6], whit[bf], nullptr, s, sms)
+                               : launch_dist_refine(v->view, b, f[bf][6], whit[bf], nullptr, s, sms);
         if (e != cudaSuccess) return cuda_status(e);
-        if ((e = cudaMemcpyAsync(step + off, f[6], size_t(m) * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
-                cudaSuccess ||
-            (e = cudaMemcpyAsync(hit + off, whit, size_t(m) * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
-                cudaSuccess)
+        if ((e = cudaEventRecord(v->ev_k[bf], s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(v->s_out, v->ev_k[bf], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(step + off, f[bf][6], size_t(m) * sizeof(double), cudaMemcpyDeviceToHost,
+                                 v->s_out)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(hit + off, whit[bf], size_t(m) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 v->s_out)) != cudaSuccess ||
+            (e = cudaEventRecord(v->ev_out[bf], v->s_out)) != cudaSuccess)
             return cuda_status(e);
     }
-    return cuda_status(cudaStreamSynchronize(s));
+    if ((e = cudaStreamSynchronize(v->s_out)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_status(e);
+    return GEO_OK;
 }
 
 geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_basket* baskets, int32_t n_baskets,

@@ -73,6 +73,7 @@ struct __align__(16) VolView {
     // voxel grid (uniform over the mother's bounding box)
     int32_t voxelized;
     int32_t grid[3];
+    int32_t segs;              // 1 if the mother or a daughter is a tube segment
     double lo[3];
     double cell[3];
     double inv_cell[3];

@@ -20,11 +20,12 @@ __device__ __forceinline__ bool valid_track(double px, double py, double pz, dou
 // the current best, master->local transform, DistFromOutside, strict '<'
 // (mother first, then the lowest index win ties).  Track assumed valid and
 // inside the mother.
+template <bool SEGS = true>
 __device__ __forceinline__ void nav_all64(const ShapeRec64& m, const ShapeRec64* __restrict__ tab, int nd,
                                           double px, double py, double pz, double qx, double qy, double qz,
                                           double& best, int& h) {
     const double p[3] = {px, py, pz}, q[3] = {qx, qy, qz};
-    best = dist_in64(m, p, q);
+    best = dist_in64<false, SEGS>(m, p, q);
     h = -1;
     const double dd = qx * qx + qy * qy + qz * qz;
     const double dn = sqrt(dd);
@@ -41,7 +42,7 @@ __device__ __forceinline__ void nav_all64(const ShapeRec64& m, const ShapeRec64*
         if (ww * dd - proj * proj > rb * rb) continue;  // line misses the sphere
         double x[3], u[3];
         to_local64(r, px, py, pz, qx, qy, qz, x, u);
-        const double s = dist_out64(r, x, u);
+        const double s = dist_out64<false, SEGS>(r, x, u);
         if (LT(s, best)) {
             best = s;
             h = j;

@@ -73,7 +73,7 @@ __device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : 1
 
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
 
-template <bool SMEM, int TRAV>
+template <bool SMEM, int TRAV, bool SEGS>
 __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
                                                              int32_t* __restrict__ hit,
                                                              double* __restrict__ bpoint,
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                 double best = 0.0;
                 int h = -2, nev = 0;
                 rs.status = 1;
-                if (live) refine_pass1<TRAV>(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+                if (live) refine_pass1<TRAV, SEGS>(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
                 int task = 0, bin = -1;
                 if (rs.status == 0) {
                     task = first_task(rs);
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
                     const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
                     double best;
                     int h, nev;
-                    refine_rest(v, tab64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
+                    refine_rest<SEGS>(v, tab64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
                     store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
                     if (nref) nref[i] = nev;
                 }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
             for (int q = c; q < total; q += kCons) {
                 const int e = st_.task[q];
                 const int o = e & (kProd - 1), jj = (e >> 8) - 1;
-                st_.res[o] = eval64(v, tab64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
+                st_.res[o] = eval64<SEGS>(v, tab64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
                                     st_.pd[4][o], st_.pd[5][o]);
             }
             __syncwarp();
@@ -400,28 +400,32 @@ static int grid_refine(K kernel, int64_t n, int smem, int num_sms) {
     return int(need < cap ? need : cap);
 }
 
+template <typename K>
+static cudaError_t launch_refine(K kernel, int smem, const VolView& v, const Basket& b, double* step, int32_t* hit,
+                                 double* bpoint, int32_t* nref, cudaStream_t s, int num_sms) {
+    cudaError_t e = prep(kernel, smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid_refine(kernel, b.n, smem, num_sms), kThreads, smem, s>>>(v, b, step, hit, bpoint, nref);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms) {
     static_assert(sizeof(Stage) % 16 == 0, "stage size keeps the tables 16-byte aligned");
     const int stages = 2 * int(sizeof(Stage));
     const int smem = stages + (v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0);
+    // SEGS: the instantiation with the tube segment's code only for volumes
+    // that hold one, so the others keep the leaner kernel
     if (v.voxelized) {
-        cudaError_t e = prep(k_dist_refine<false, 1>, smem);
-        if (e != cudaSuccess) return e;
-        k_dist_refine<false, 1><<<grid_refine(k_dist_refine<false, 1>, b.n, smem, num_sms), kThreads, smem, s>>>(
-            v, b, step, hit, bpoint, nref);
-    } else if (v.smem_refine) {
-        cudaError_t e = prep(k_dist_refine<true, 0>, smem);
-        if (e != cudaSuccess) return e;
-        k_dist_refine<true, 0><<<grid_refine(k_dist_refine<true, 0>, b.n, smem, num_sms), kThreads, smem, s>>>(
-            v, b, step, hit, bpoint, nref);
-    } else {
-        cudaError_t e = prep(k_dist_refine<false, 0>, smem);
-        if (e != cudaSuccess) return e;
-        k_dist_refine<false, 0><<<grid_refine(k_dist_refine<false, 0>, b.n, smem, num_sms), kThreads, smem, s>>>(
-            v, b, step, hit, bpoint, nref);
+        if (v.segs) return launch_refine(k_dist_refine<false, 1, true>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
+        return launch_refine(k_dist_refine<false, 1, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
     }
-    return cudaGetLastError();
+    if (v.smem_refine) {
+        if (v.segs) return launch_refine(k_dist_refine<true, 0, true>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
+        return launch_refine(k_dist_refine<true, 0, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
+    }
+    if (v.segs) return launch_refine(k_dist_refine<false, 0, true>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
+    return launch_refine(k_dist_refine<false, 0, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
 }
 
 cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,

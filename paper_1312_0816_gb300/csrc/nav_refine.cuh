@@ -143,7 +143,7 @@ struct RefineState {
 // FP32 pass: bounds of the mother and of every daughter.  When status == 1
 // on return, best/h already hold the final answer.  TRAVERSAL: 0 = every
 // daughter, 1 = the uniform grid, 2 = chosen per volume at run time.
-template <int TRAVERSAL>
+template <int TRAVERSAL, bool SEGS = true>
 __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32* __restrict__ tab32,
                                              const ShapeRec64* __restrict__ tab64, double px, double py,
                                              double pz, double qx, double qy, double qz, RefineState& st,
@@ -169,7 +169,7 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
     if (!(dd > 1e-30f && dd < 1e30f)) {
         // direction magnitude outside the range the FP32 bounds assume
         const double p[3] = {px, py, pz};
-        if (contains64(v.m64, p)) nav_all64(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
+        if (contains64(v.m64, p)) nav_all64<SEGS>(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
         else { best = 0.0; h = -2; }
         nev = 1000;
         return;
@@ -222,16 +222,17 @@ __device__ __forceinline__ int first_task(const RefineState& st) {
 
 // FP64 evaluation of one solid for one track (the mother's DistFromInside or
 // a daughter's transform + DistFromOutside).
+template <bool SEGS = true>
 __device__ __forceinline__ double eval64(const VolView& v, const ShapeRec64* __restrict__ tab64, int j, double px,
                                          double py, double pz, double qx, double qy, double qz) {
     if (j < 0) {
         const double p[3] = {px, py, pz}, q[3] = {qx, qy, qz};
-        return dist_in64(v.m64, p, q);
+        return dist_in64<false, SEGS>(v.m64, p, q);
     }
     const ShapeRec64& r = tab64[j];
     double x[3], u[3];
     to_local64(r, px, py, pz, qx, qy, qz, x, u);
-    return dist_out64(r, x, u);
+    return dist_out64<false, SEGS>(r, x, u);
 }
 
 // FP64 refinement in ascending bound order, given the value s_first of the
@@ -239,6 +240,7 @@ __device__ __forceinline__ double eval64(const VolView& v, const ShapeRec64* __r
 // lowest index.  The bounds are compared in FP32 against best_up >= best, so
 // at least every solid that could tie or win is refined (a solid refined in
 // excess cannot change the answer).
+template <bool SEGS = true>
 static __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec64* __restrict__ tab64,
                                          const RefineState& st, double s_first, double px, double py, double pz,
                                          double qx, double qy, double qz, double& best, int& h, int& nev) {
@@ -265,7 +267,7 @@ static __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec
         if (k >= k0 && k < st.c.n) {
             const float L = st.c.L[k];
             if (!mdone && st.Lm <= L) {
-                const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
+                const double sm = eval64<SEGS>(v, tab64, -1, px, py, pz, qx, qy, qz);
                 ++nev;
                 mdone = true;
                 if (LE(sm, best)) {
@@ -276,7 +278,7 @@ static __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec
             }
             if (L <= best_up) {
                 const int j = st.c.j[k];
-                const double s = eval64(v, tab64, j, px, py, pz, qx, qy, qz);
+                const double s = eval64<SEGS>(v, tab64, j, px, py, pz, qx, qy, qz);
                 ++nev;
                 // same order as the sequential loop: bit-pattern order of
                 // non-negative steps, ties to the mother, then the lowest index
@@ -289,7 +291,7 @@ static __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec
         }
     }
     if (!mdone && st.Lm <= best_up) {
-        const double sm = eval64(v, tab64, -1, px, py, pz, qx, qy, qz);
+        const double sm = eval64<SEGS>(v, tab64, -1, px, py, pz, qx, qy, qz);
         ++nev;
         if (LE(sm, best)) {
             best = sm;
@@ -298,7 +300,7 @@ static __device__ __noinline__ void refine_rest(const VolView& v, const ShapeRec
         }
     }
     if (st.c.dropped <= best_up) {
-        nav_all64(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
+        nav_all64<SEGS>(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
         nev += 1000;   // marks a fallback in the statistics
     }
 }

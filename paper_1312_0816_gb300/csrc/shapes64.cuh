@@ -263,6 +263,14 @@ __device__ __forceinline__ double tubs_out64(const double* d, const double* x, c
     return best;
 }
 
+// Out-of-line entry of the tube segment, so that its code stays out of the
+// kernels' hot paths (a segment is evaluated only where one is placed).
+template <bool FACE, bool REENTRY>
+__device__ __noinline__ double tubs_out64_call(const double* d, double x0, double x1, double x2, double u0, double u1,
+                                               double u2, int* face) {
+    const double x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
+    return tubs_out64<FACE, REENTRY>(d, x, u, face);
+}
 template <bool FACE = false, bool REENTRY = false>
 __device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
     if (FACE) *face = -1;
@@ -307,12 +315,13 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     return best;
 }
 
-template <bool FACE = false>
+// SEGS = false: the volume holds no tube segment, and its code is left out.
+template <bool FACE = false, bool SEGS = true>
 __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* x, const double* u,
                                              int* face = nullptr) {
     if (r.kind == KBOX) return box_out64<FACE>(r.d, x, u, face);
     if (r.kind == KTUBE) return tube_out64<FACE>(r.d, x, u, face);
-    if (r.kind == KTUBS) return tubs_out64<FACE>(r.d, x, u, face);
+    if (SEGS && r.kind == KTUBS) return tubs_out64_call<FACE, false>(r.d, x[0], x[1], x[2], u[0], u[1], u[2], face);
     return cone_out64<FACE>(r.d, x, u, face);
 }
 
@@ -330,7 +339,7 @@ __device__ __forceinline__ double reentry64(const ShapeRec64& r, const double* x
         return box_out64<FACE>(r.d, x, u, face);
     }
     if (r.kind == KTUBE) return tube_out64<FACE, true>(r.d, x, u, face);
-    if (r.kind == KTUBS) return tubs_out64<FACE, true>(r.d, x, u, face);
+    if (r.kind == KTUBS) return tubs_out64_call<FACE, true>(r.d, x[0], x[1], x[2], u[0], u[1], u[2], face);
     return cone_out64<FACE, true>(r.d, x, u, face);
 }
 
@@ -346,12 +355,85 @@ __device__ __forceinline__ double slab_exit(double xk, double uk, double h) {
 // minimum is taken on the bit patterns and the result clamped at +0.
 __device__ __forceinline__ double clamp0(double t) { return NONNEG(t) && !IS_ZERO(t) ? t : 0.0; }
 
+// Tube segment, DistFromInside: the tube's exits and the wedge's.
 template <bool FACE = false>
+__device__ __forceinline__ double tubs_in64(const double* d, const double* x, const double* u, int* face = nullptr) {
+    double t = d_inf();
+    int f = -1;
+    auto take = [&](double c, int fc) {
+        if (LT(c, t)) {
+            t = c;
+            if (FACE) f = fc;
+        }
+    };
+    const double rho2 = rho2_of(x);
+    const double A0 = DOT2(u[0], u[0], u[1], u[1]);
+    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    double s;
+    take(clamp0(slab_exit(x[2], u[2], d[2])), IS_POS(u[2]) ? 5 : 4);
+    s = root_rising(A0, B0, SUB(rho2, d[4]));
+    if (NONNEG(s)) take(clamp0(s), 6);
+    if (d[0] > 0.0) {
+        s = root_falling(A0, B0, SUB(rho2, d[3]));
+        if (NONNEG(s)) take(clamp0(s), 7);
+    }
+    if (d[10] == 0.0) {
+        // the wedge: each half-plane holds s where c + s w >= 0
+        const double c1 = DOT2(d[5], x[0], d[6], x[1]), w1 = DOT2(d[5], u[0], d[6], u[1]);
+        const double c2 = DOT2(d[7], x[0], d[8], x[1]), w2 = DOT2(d[7], u[0], d[8], u[1]);
+        const double e1 = IS_NEG(w1) ? DIV(-c1, w1) : d_inf();   // where the track leaves half-plane 1
+        const double e2 = IS_NEG(w2) ? DIV(-c2, w2) : d_inf();
+        if (d[9] != 0.0) {
+            // intersection: leaves the wedge when it leaves either (when
+            // dphi = pi the two planes coincide, and the face is the one
+            // on whose side of the axis the track leaves)
+            if (d[11] != 0.0) {
+                const double ec = MINP(clamp0(e1), clamp0(e2));
+                const double xh = FMA(ec, u[0], x[0]), yh = FMA(ec, u[1], x[1]);
+                take(ec, NONNEG(DOT2(d[6], xh, -d[5], yh)) ? 8 : 9);
+            } else {
+                take(clamp0(e1), 8);
+                take(clamp0(e2), 9);
+            }
+        } else {
+            // union: of the half-lines holding the start (c >= 0), a
+            // rising one (w >= 0) never ends; a falling one ends at e; a
+            // rising one that starts later (at -c/w > 0) continues the
+            // union if it starts before that end
+            const bool in1 = NONNEG(c1), in2 = NONNEG(c2);
+            const bool up1 = !IS_NEG(w1), up2 = !IS_NEG(w2);
+            if (!((in1 && up1) || (in2 && up2))) {
+                // every half-plane holding the start ends: the later end
+                const double x1 = in1 ? clamp0(e1) : 0.0, x2 = in2 ? clamp0(e2) : 0.0;
+                const bool second = in2 && (!in1 || LT(x1, x2));
+                const double E = second ? x2 : x1;
+                // a half-plane not holding the start but entered by then
+                // continues the union
+                const double a1 = (!in1 && IS_POS(w1)) ? DIV(-c1, w1) : d_inf();
+                const double a2 = (!in2 && IS_POS(w2)) ? DIV(-c2, w2) : d_inf();
+                if (!(LE(a1, E) || LE(a2, E))) take(E, second ? 9 : 8);
+            }
+        }
+    }
+    if (FACE) *face = f;
+    return t;
+}
+
+// Out-of-line entry of the tube segment's DistFromInside (see tubs_out64_call).
+template <bool FACE>
+__device__ __noinline__ double tubs_in64_call(const double* d, double x0, double x1, double x2, double u0, double u1,
+                                              double u2, int* face) {
+    const double x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
+    return tubs_in64<FACE>(d, x, u, face);
+}
+
+template <bool FACE = false, bool SEGS = true>
 __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u,
                                             int* face = nullptr) {
     // the exit is the least of the constraints' exit parameters (minimum on
     // the bit patterns of values >= 0; equal values are equal bit patterns)
     const double* d = r.d;
+    if (SEGS && r.kind == KTUBS) return tubs_in64_call<FACE>(d, x[0], x[1], x[2], u[0], u[1], u[2], face);
     double t;
     int f = -1;
     auto take = [&](double c, int fc) {
@@ -371,7 +453,7 @@ __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
     double s;
-    if (r.kind == KTUBE || r.kind == KTUBS) {
+    if (r.kind == KTUBE) {
         t = d_inf();
         take(clamp0(slab_exit(x[2], u[2], d[2])), IS_POS(u[2]) ? 5 : 4);
         s = root_rising(A0, B0, SUB(rho2, d[4]));
@@ -379,44 +461,6 @@ __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x
         if (d[0] > 0.0) {
             s = root_falling(A0, B0, SUB(rho2, d[3]));
             if (NONNEG(s)) take(clamp0(s), 7);
-        }
-        if (r.kind == KTUBS && d[10] == 0.0) {
-            // the wedge: each half-plane holds s where c + s w >= 0
-            const double c1 = DOT2(d[5], x[0], d[6], x[1]), w1 = DOT2(d[5], u[0], d[6], u[1]);
-            const double c2 = DOT2(d[7], x[0], d[8], x[1]), w2 = DOT2(d[7], u[0], d[8], u[1]);
-            const double e1 = IS_NEG(w1) ? DIV(-c1, w1) : d_inf();   // where the track leaves half-plane 1
-            const double e2 = IS_NEG(w2) ? DIV(-c2, w2) : d_inf();
-            if (d[9] != 0.0) {
-                // intersection: leaves the wedge when it leaves either (when
-                // dphi = pi the two planes coincide, and the face is the one
-                // on whose side of the axis the track leaves)
-                if (d[11] != 0.0) {
-                    const double ec = MINP(clamp0(e1), clamp0(e2));
-                    const double xh = FMA(ec, u[0], x[0]), yh = FMA(ec, u[1], x[1]);
-                    take(ec, NONNEG(DOT2(d[6], xh, -d[5], yh)) ? 8 : 9);
-                } else {
-                    take(clamp0(e1), 8);
-                    take(clamp0(e2), 9);
-                }
-            } else {
-                // union: of the half-lines holding the start (c >= 0), a
-                // rising one (w >= 0) never ends; a falling one ends at e; a
-                // rising one that starts later (at -c/w > 0) continues the
-                // union if it starts before that end
-                const bool in1 = NONNEG(c1), in2 = NONNEG(c2);
-                const bool up1 = !IS_NEG(w1), up2 = !IS_NEG(w2);
-                if (!((in1 && up1) || (in2 && up2))) {
-                    // every half-plane holding the start ends: the later end
-                    const double x1 = in1 ? clamp0(e1) : 0.0, x2 = in2 ? clamp0(e2) : 0.0;
-                    const bool second = in2 && (!in1 || LT(x1, x2));
-                    const double E = second ? x2 : x1;
-                    // a half-plane not holding the start but entered by then
-                    // continues the union
-                    const double a1 = (!in1 && IS_POS(w1)) ? DIV(-c1, w1) : d_inf();
-                    const double a2 = (!in2 && IS_POS(w2)) ? DIV(-c2, w2) : d_inf();
-                    if (!(LE(a1, E) || LE(a2, E))) take(E, second ? 9 : 8);
-                }
-            }
         }
         if (FACE) *face = f;
         return t;

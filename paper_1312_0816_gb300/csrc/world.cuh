@@ -29,6 +29,7 @@
 #include "geo_internal.h"
 #include "nav_common.cuh"
 #include "nav_refine.cuh"
+#include "queries.cuh"
 #include "shapes64.cuh"
 
 namespace geonav {
@@ -67,27 +68,33 @@ __device__ __forceinline__ void world_to_node(const double* G, double px, double
     }
 }
 
-// FP64 bounding-sphere test of a point (brad is enlarged, so conservative)
-__device__ __forceinline__ bool near_daughter(const ShapeRec64& r, const double* x) {
-    const double w0 = x[0] - r.t[0], w1 = x[1] - r.t[1], w2 = x[2] - r.t[2];
-    return w0 * w0 + w1 * w1 + w2 * w2 <= r.brad * r.brad;
+// The lowest-index daughter of v other than `skip` whose closed solid holds
+// the point x (v's frame), -1 if none.  A daughter is excluded in FP32 when
+// the point lies outside its inflated bounding sphere or its inflated FP32
+// copy (then the exact point is outside by more than the FP64 rounding); the
+// rest are tested in FP64, in index order (as Contains in queries.cuh).
+__device__ __forceinline__ int first_containing(const VolView& v, const double* x, int skip, double* xl) {
+    const float p32[3] = {f64_to_f32_trunc(x[0]), f64_to_f32_trunc(x[1]), f64_to_f32_trunc(x[2])};
+    for (int j = 0; j < v.nd; ++j) {
+        if (j == skip) continue;
+        const ShapeRec32& r = v.d32[j];
+        float o[3], xs[3];
+        const float c2 = offset32(r, p32, o);
+        if (c2 > r.brad * r.brad * (1.f + kSafMargin)) continue;
+        local32(r, o, xs);
+        if (!contains32(r, xs)) continue;
+        const ShapeRec64& r64 = v.d64[j];
+        point_to_local64(r64, x[0], x[1], x[2], xl);
+        if (contains64(r64, xl)) return j;
+    }
+    return -1;
 }
 
 // Down from `node` (x in its frame) while a daughter contains the point.
 static __device__ int world_descend(const WorldView& w, int node, double* x) {
     for (int level = 0; level < kMaxWorldDepth; ++level) {
-        const VolView& v = w.vols[w.lv[node]];
-        int next = -1;
         double xn[3];
-        for (int j = 0; j < v.nd; ++j) {
-            const ShapeRec64& r = v.d64[j];
-            if (!near_daughter(r, x)) continue;
-            point_to_local64(r, x[0], x[1], x[2], xn);
-            if (contains64(r, xn)) {
-                next = j;
-                break;
-            }
-        }
+        const int next = first_containing(w.vols[w.lv[node]], x, -1, xn);
         if (next < 0) return node;
         node = w.first[node] + next;
         x[0] = xn[0];
@@ -116,17 +123,12 @@ static __device__ void world_relocate(const WorldView& w, int node, int hit, dou
 #pragma unroll
         for (int k = 0; k < 3; ++k)
             xp[k] = FMA(rl.R[3 * k], b[0], FMA(rl.R[3 * k + 1], b[1], FMA(rl.R[3 * k + 2], b[2], rl.t[k])));
-        for (int j = 0; j < vp.nd; ++j) {
-            if (j == left) continue;
-            const ShapeRec64& r = vp.d64[j];
-            if (!near_daughter(r, xp)) continue;
-            double xl[3];
-            point_to_local64(r, xp[0], xp[1], xp[2], xl);
-            if (contains64(r, xl)) {
-                nout = world_descend(w, w.first[P] + j, xl);
-                fout = -2;
-                return;
-            }
+        double xl[3];
+        const int j = first_containing(vp, xp, left, xl);
+        if (j >= 0) {
+            nout = world_descend(w, w.first[P] + j, xl);
+            fout = -2;
+            return;
         }
         if (contains64(vp.m64, xp)) {
             nout = P;
