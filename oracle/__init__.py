@@ -41,7 +41,7 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int32)
-        scene = [ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, dp]
+        scene = [ctypes.c_int, dp, ctypes.c_int, ip, dp, dp, dp, dp]
         L.orc_navigate.argtypes = scene + [ctypes.c_int64] + [dp] * 6 + [dp, ip, dp, dp, ip, ctypes.c_int]
         L.orc_navigate.restype = None
         L.orc_contains_nav.argtypes = scene + [ctypes.c_int64, dp, dp, dp, ip, ctypes.c_int]
@@ -50,9 +50,9 @@ def lib():
         L.orc_safety_nav.restype = None
         L.orc_adjoint.argtypes = scene + [ctypes.c_int64] + [dp] * 6 + [dp, dp, ip, dp, dp, ip]
         L.orc_adjoint.restype = None
-        L.orc_shape_batch.argtypes = [ctypes.c_int, dp, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ip]
+        L.orc_shape_batch.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ip]
         L.orc_shape_batch.restype = None
-        world = [ctypes.c_int, ip, dp, ip, ip, ip, dp, dp, dp, ip, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip]
+        world = [ctypes.c_int, ip, dp, ip, ip, ip, dp, dp, dp, ip, dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip]
         L.orc_world_nodes.argtypes = world
         L.orc_world_nodes.restype = ctypes.c_int
         L.orc_world_locate.argtypes = world + [ctypes.c_int64, dp, dp, dp, ip]
@@ -80,8 +80,9 @@ def _scene_args(scene):
     pr, prp = _d(scene.params.reshape(-1))
     ro, rop = _d(scene.rot.reshape(-1))
     tr, trp = _d(scene.trans.reshape(-1))
-    keep += [mp, k, pr, ro, tr]
-    return keep, [int(scene.mother_kind), mpp, int(scene.n_daughters), kp, prp, rop, trp]
+    pd, pdp = _d(np.concatenate([np.asarray(scene.pdata, dtype=np.float64), [0.0]]))
+    keep += [mp, k, pr, ro, tr, pd]
+    return keep, [int(scene.mother_kind), mpp, int(scene.n_daughters), kp, prp, rop, trp, pdp]
 
 
 def _track_args(tracks, fields=6):
@@ -149,17 +150,25 @@ _WHAT = {"dist_out": 0, "dist_in": 1, "contains": 2, "safety_out": 3, "safety_in
 
 
 def shape(kind: int, params, x, u=None, what: str = "dist_out"):
-    """One solid in its own frame; x, u are (n, 3).  Returns values (and the
-    hit face for the two distance queries)."""
+    """One solid in its own frame; x, u are (n, 3); params is its row, or a
+    polycone spec (an object with z, rmin, rmax, sphi, dphi).  Returns values
+    (and the hit face for the two distance queries)."""
     p = np.zeros(5)
-    p[: len(params)] = params
+    planes = np.zeros(1)
+    if hasattr(params, "rmax"):
+        planes = np.concatenate([np.asarray(params.z, float), np.asarray(params.rmin, float),
+                                 np.asarray(params.rmax, float)])
+        p[:4] = (params.sphi, params.dphi, len(params.z), 0)
+    else:
+        p[: len(params)] = params
     x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
     n = x.shape[0]
     u = np.zeros_like(x) if u is None else np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 3))
     out = np.empty(n)
     face = np.empty(n, dtype=np.int32)
     pa, pp = _d(p)
-    lib().orc_shape_batch(int(kind), pp, n, _d(x)[1], _d(u)[1], _WHAT[what], _d(out)[1], _i(face)[1])
+    pl, plp = _d(planes)
+    lib().orc_shape_batch(int(kind), pp, plp, n, _d(x)[1], _d(u)[1], _WHAT[what], _d(out)[1], _i(face)[1])
     if what in ("dist_out", "dist_in"):
         return out, face
     return out
@@ -172,8 +181,9 @@ def _world_args(world, max_nodes=MAX_NODES):
     f = world.flat()
     keep, args = [], []
     nlv = len(world.volumes)
+    f["pdata"] = np.concatenate([f["pdata"], [0.0]])
     for key, conv in (("mkind", _i), ("mparams", _d), ("nd", _i), ("doff", _i), ("kinds", _i), ("params", _d),
-                      ("rot", _d), ("trans", _d), ("child", _i)):
+                      ("rot", _d), ("trans", _d), ("child", _i), ("pdata", _d)):
         a, ptr = conv(np.asarray(f[key]).reshape(-1))
         keep.append(a)
         args.append(ptr)

@@ -35,6 +35,14 @@
  *     the wedge is the intersection (dphi <= pi) or the union (dphi > pi) of
  *     the half-planes n1.(x,y) >= 0, n1 = (-sin sphi, cos sphi), and
  *     n2.(x,y) >= 0, n2 = (sin(sphi+dphi), -cos(sphi+dphi)); it holds the axis.
+ *   Polycone (Sec. 3.1, the sequence of connected cone and tube sections):
+ *     nz z-planes z[0] < ... < z[nz-1] with inner and outer radii rmin[k] <=
+ *     rmax[k] at plane k; section k (between planes k and k+1) is the cone
+ *     whose radii vary linearly from plane k to plane k+1, and the solid is
+ *     the union of its sections cut to the wedge [sphi, sphi+dphi] (as for
+ *     the tube segment).  Neighbouring sections share the annulus of their
+ *     common plane, so the inner planes are no surfaces.  The shape routines
+ *     read the block [sphi, dphi, nz, z[nz], rmin[nz], rmax[nz]].
  *   Placement p_mother = R p_local + t, R row-major.
  *   Miss = +inf.  Ties: mother first, then lowest daughter index.
  *   Track outside the mother: step 0, hit -2.  Zero/non-finite input: NaN, -2.
@@ -60,6 +68,9 @@
 #define F_IN 7
 #define F_PHI1 8   /* tube segment: the face at sphi        */
 #define F_PHI2 9   /* tube segment: the face at sphi + dphi */
+#define K_PCON 4   /* polycone: block (sphi, dphi, nz, z[], rmin[], rmax[]) */
+#define F_SEC 16   /* polycone: outer surface of section k = 16 + 2k, inner 17 + 2k */
+#define MAXZ 32    /* polycone: at most 32 planes */
 
 typedef struct {
     double lo, hi;
@@ -68,8 +79,13 @@ typedef struct {
                          (+inf for planes): conditioning of that endpoint */
 } ivl;
 
-#define MAXI 8
+#define MAXI 64
 typedef struct { int n; ivl v[MAXI]; } iset;
+
+static void set_copy(iset *dst, const iset *src) {
+    dst->n = src->n;
+    memcpy(dst->v, src->v, (size_t)src->n * sizeof(ivl));
+}
 
 static void set_all(iset *s) {
     s->n = 1;
@@ -102,7 +118,7 @@ static void set_and(iset *a, const iset *b) {
         }
         if (x->hi < y->hi) i++; else j++;
     }
-    *a = r;
+    set_copy(a, &r);
 }
 
 /* a <- a union b (both sorted, disjoint); touching pieces are merged. */
@@ -124,17 +140,18 @@ static void set_or(iset *a, const iset *b) {
             r.v[r.n++] = all[k];
         }
     }
-    *a = r;
+    set_copy(a, &r);
 }
 
 /* Optional record of every finite crossing computed while building a line
  * set (before intersection): used only for the error bound of the step. */
-typedef struct { int n; double t[16]; int f[16]; double c[16]; } xrec;
+#define MAXX 256
+typedef struct { int n; double t[MAXX]; int f[MAXX]; double c[MAXX]; } xrec;
 static void rec_set(xrec *R, const iset *s) {
     if (!R) return;
     for (int i = 0; i < s->n; i++) {
-        if (isfinite(s->v[i].lo) && R->n < 16) { R->t[R->n] = s->v[i].lo; R->f[R->n] = s->v[i].flo; R->c[R->n++] = s->v[i].clo; }
-        if (isfinite(s->v[i].hi) && R->n < 16) { R->t[R->n] = s->v[i].hi; R->f[R->n] = s->v[i].fhi; R->c[R->n++] = s->v[i].chi; }
+        if (isfinite(s->v[i].lo) && R->n < MAXX) { R->t[R->n] = s->v[i].lo; R->f[R->n] = s->v[i].flo; R->c[R->n++] = s->v[i].clo; }
+        if (isfinite(s->v[i].hi) && R->n < MAXX) { R->t[R->n] = s->v[i].hi; R->f[R->n] = s->v[i].fhi; R->c[R->n++] = s->v[i].chi; }
     }
 }
 
@@ -275,20 +292,104 @@ static void cone_line(double dz, double r1, double r2, dd *a, dd *b) {
  * intersection of the two half-planes (dphi <= pi) and whether it is all of
  * the plane (dphi >= 2 pi). */
 #define ORC_PI 3.14159265358979323846
-typedef struct { double n1[2], n2[2]; int convex, full; } wedge;
-static wedge wedge_of(const double *p) {
+typedef struct { double n1[2], n2[2]; int convex, full, half; } wedge;
+static wedge wedge_at(double sphi, double dphi) {
     wedge w;
-    double f1 = p[3], f2 = p[3] + p[4];
+    double f1 = sphi, f2 = sphi + dphi;
     w.n1[0] = -sin(f1); w.n1[1] = cos(f1);
     w.n2[0] = sin(f2);  w.n2[1] = -cos(f2);
-    w.convex = p[4] <= ORC_PI;
-    w.full = !(p[4] < 2.0 * ORC_PI);
+    w.convex = dphi <= ORC_PI;
+    w.full = !(dphi < 2.0 * ORC_PI);
+    w.half = dphi == ORC_PI;
     return w;
+}
+/* the wedge of a tube segment (p[3], p[4]) or of a polycone (p[0], p[1]) */
+static wedge wedge_of(int kind, const double *p) {
+    return kind == K_PCON ? wedge_at(p[0], p[1]) : wedge_at(p[3], p[4]);
 }
 static int wedge_has(const wedge *w, double x, double y) {
     if (w->full) return 1;
     int a = w->n1[0] * x + w->n1[1] * y >= 0.0, b = w->n2[0] * x + w->n2[1] * y >= 0.0;
     return w->convex ? (a && b) : (a || b);
+}
+
+/* S <- S intersect the wedge w: each half-plane n.(x + s u) >= 0 is a
+ * half-line of s; the wedge is their intersection or union. */
+static void and_wedge(const wedge *w, const double *x, const double *u, iset *S, xrec *R) {
+    if (w->full) return;
+    iset t, h2;
+    half_set(w->n1[0] * x[0] + w->n1[1] * x[1], w->n1[0] * u[0] + w->n1[1] * u[1], 0.0, 1, F_PHI1, &t);
+    rec_set(R, &t);
+    half_set(w->n2[0] * x[0] + w->n2[1] * x[1], w->n2[0] * u[0] + w->n2[1] * u[1], 0.0, 1, F_PHI2, &h2);
+    rec_set(R, &h2);
+    if (w->convex) set_and(&t, &h2); else set_or(&t, &h2);
+    set_and(S, &t);
+    /* dphi = pi: the two planes coincide, and a phi endpoint lies on the
+     * face on whose side of the axis it is */
+    for (int i = 0; i < S->n && w->half; i++) {
+        for (int e = 0; e < 2; e++) {
+            int *f = e ? &S->v[i].fhi : &S->v[i].flo;
+            double tt = e ? S->v[i].hi : S->v[i].lo;
+            if ((*f != F_PHI1 && *f != F_PHI2) || !isfinite(tt)) continue;
+            double px = x[0] + tt * u[0], py = x[1] + tt * u[1];
+            *f = (w->n1[1] * px - w->n1[0] * py >= 0.0) ? F_PHI1 : F_PHI2;
+        }
+    }
+}
+
+/* Coefficients of rho^2 - R(z)^2 along the line, R the radius line through
+ * (r0 at z0) and (r1 at z1): R(z(s)) = R0 + Rs s with z(s) = x_z + s u_z. */
+static void radius_quad(double z0, double z1, double r0, double r1, const double *x, const double *u,
+                        dd A, dd B, dd C, dd *Aq, dd *Bq, dd *Cq) {
+    dd b = dd_div(two_sum(r1, -r0), two_sum(z1, -z0));
+    dd R0 = dd_add(dd_of(r0), dd_mul(b, two_sum(x[2], -z0)));
+    dd Rs = dd_mul(b, dd_of(u[2]));
+    *Aq = dd_sub(A, dd_mul(Rs, Rs));
+    *Bq = dd_sub(B, dd_mul(R0, Rs));
+    *Cq = dd_sub(C, dd_mul(R0, R0));
+}
+
+/* { s : za <= x_z + s u_z <= zb }.  A plane z = c is crossed at
+ * (c - x_z) / u_z, the expression half_set uses as well, so that two
+ * sections sharing a plane meet at the same s. */
+static void zslab(const double *x, const double *u, double za, double zb, int fa, int fb, iset *s) {
+    if (u[2] == 0.0) {
+        if (x[2] >= za && x[2] <= zb) set_all(s); else set_empty(s);
+        return;
+    }
+    double ta = (za - x[2]) / u[2], tb = (zb - x[2]) / u[2];
+    if (u[2] > 0.0) set_one(s, ta, fa, INFINITY, tb, fb, INFINITY);
+    else set_one(s, tb, fb, INFINITY, ta, fa, INFINITY);
+}
+
+/* Polycone: the union over sections of slab AND rho <= Rout(z) AND
+ * rho >= Rin(z), then cut to the wedge.  Inner planes carry no face tag
+ * (they are no surface); the end planes are -z (4) and +z (5). */
+static void pcon_line_set(const double *p, const double *x, const double *u, dd A, dd B, dd C,
+                          iset *S, xrec *R) {
+    const int nz = (int)p[2];
+    const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+    iset sec, t, hs;
+    set_empty(S);
+    for (int k = 0; k + 1 < nz; k++) {
+        const int fa = k == 0 ? F_ZM : F_NONE, fb = k + 2 == nz ? F_ZP : F_NONE;
+        dd Aq, Bq, Cq;
+        zslab(x, u, z[k], z[k + 1], fa, fb, &sec); rec_set(R, &sec);
+        radius_quad(z[k], z[k + 1], rx[k], rx[k + 1], x, u, A, B, C, &Aq, &Bq, &Cq);
+        quad_le0(Aq, Bq, Cq, F_SEC + 2 * k, &t); rec_set(R, &t); set_and(&sec, &t);
+        if (rn[k] > 0.0 || rn[k + 1] > 0.0) {
+            /* rho >= Rin(z), squared (exact on the slab, where Rin >= 0);
+             * an inner radius of 0 adds its whole plane, as for the cone */
+            radius_quad(z[k], z[k + 1], rn[k], rn[k + 1], x, u, A, B, C, &Aq, &Bq, &Cq);
+            quad_le0(dd_neg(Aq), dd_neg(Bq), dd_neg(Cq), F_SEC + 2 * k + 1, &t); rec_set(R, &t);
+            if (rn[k] == 0.0) { half_set(x[2], u[2], z[k], 0, fa, &hs); set_or(&t, &hs); }
+            if (rn[k + 1] == 0.0) { half_set(x[2], u[2], z[k + 1], 1, fb, &hs); set_or(&t, &hs); }
+            set_and(&sec, &t);
+        }
+        set_or(S, &sec);
+    }
+    wedge w = wedge_at(p[0], p[1]);
+    and_wedge(&w, x, u, S, R);
 }
 
 /* The exact line set S for a solid in its local frame. */
@@ -304,6 +405,10 @@ static void line_set_rec(int kind, const double *p, const double *x, const doubl
     dd A = dd_add(two_prod(u[0], u[0]), two_prod(u[1], u[1]));
     dd B = dd_add(two_prod(x[0], u[0]), two_prod(x[1], u[1]));
     dd C = dd_add(two_prod(x[0], x[0]), two_prod(x[1], x[1]));
+    if (kind == K_PCON) {
+        pcon_line_set(p, x, u, A, B, C, S, R);
+        return;
+    }
     if (kind == K_TUBE || kind == K_TUBS) {
         double rmin = p[0], rmax = p[1], dz = p[2];
         slab_set(x[2], u[2], dz, F_ZM, F_ZP, S); rec_set(R, S);
@@ -314,28 +419,8 @@ static void line_set_rec(int kind, const double *p, const double *x, const doubl
             quad_le0(dd_neg(A), dd_neg(B), dd_neg(Ci), F_IN, &t); rec_set(R, &t); set_and(S, &t);
         }
         if (kind == K_TUBS) {
-            wedge w = wedge_of(p);
-            if (!w.full) {
-                /* each half-plane n.(x + s u) >= 0 is a half-line of s */
-                iset h2;
-                half_set(w.n1[0] * x[0] + w.n1[1] * x[1], w.n1[0] * u[0] + w.n1[1] * u[1], 0.0, 1, F_PHI1, &t);
-                rec_set(R, &t);
-                half_set(w.n2[0] * x[0] + w.n2[1] * x[1], w.n2[0] * u[0] + w.n2[1] * u[1], 0.0, 1, F_PHI2, &h2);
-                rec_set(R, &h2);
-                if (w.convex) set_and(&t, &h2); else set_or(&t, &h2);
-                set_and(S, &t);
-                /* dphi = pi: the two planes coincide, and a phi endpoint lies
-                 * on the face on whose side of the axis it is */
-                for (int i = 0; i < S->n && p[4] == ORC_PI; i++) {
-                    for (int e = 0; e < 2; e++) {
-                        int *f = e ? &S->v[i].fhi : &S->v[i].flo;
-                        double tt = e ? S->v[i].hi : S->v[i].lo;
-                        if ((*f != F_PHI1 && *f != F_PHI2) || !isfinite(tt)) continue;
-                        double px = x[0] + tt * u[0], py = x[1] + tt * u[1];
-                        *f = (w.n1[1] * px - w.n1[0] * py >= 0.0) ? F_PHI1 : F_PHI2;
-                    }
-                }
-            }
+            wedge w = wedge_of(kind, p);
+            and_wedge(&w, x, u, S, R);
         }
         return;
     }
@@ -429,16 +514,38 @@ double orc_dist_in(int kind, const double *p, const double *x, const double *u) 
     return dist_in_info(kind, p, x, u).s;
 }
 
+/* (r, z) in the polycone's cross-section (the meridian half-plane, r >= 0):
+ * in some section whose z-range holds z, between its interpolated radii. */
+static int pcon_in2(const double *p, double r, double z0) {
+    const int nz = (int)p[2];
+    const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+    if (!(r >= 0.0)) return 0;
+    double r2 = r * r;
+    for (int k = 0; k + 1 < nz; k++) {
+        if (!(z0 >= z[k] && z0 <= z[k + 1])) continue;
+        double f = (z0 - z[k]) / (z[k + 1] - z[k]);
+        double rmin = rn[k] + (rn[k + 1] - rn[k]) * f;
+        double rmax = rx[k] + (rx[k + 1] - rx[k]) * f;
+        if (r2 <= rmax * rmax && r2 >= rmin * rmin) return 1;
+    }
+    return 0;
+}
+
 /* Closed-solid membership, straight from the definitions. */
 int orc_contains(int kind, const double *p, const double *x) {
     if (kind == K_BOX)
         return fabs(x[0]) <= p[0] && fabs(x[1]) <= p[1] && fabs(x[2]) <= p[2];
     double r2 = x[0] * x[0] + x[1] * x[1];
+    if (kind == K_PCON) {
+        if (!pcon_in2(p, sqrt(r2), x[2])) return 0;
+        wedge w = wedge_of(kind, p);
+        return wedge_has(&w, x[0], x[1]);
+    }
     if (kind == K_TUBE || kind == K_TUBS) {
         if (fabs(x[2]) > p[2]) return 0;
         if (!(r2 <= p[1] * p[1] && r2 >= p[0] * p[0])) return 0;
         if (kind == K_TUBE) return 1;
-        wedge w = wedge_of(p);
+        wedge w = wedge_of(kind, p);
         return wedge_has(&w, x[0], x[1]);
     }
     double dz = p[0];
@@ -464,6 +571,27 @@ static double seg_dist(double px, double pz, double ax, double az, double bx, do
     return sqrt(cx * cx + cz * cz);
 }
 
+/* 2-D distance from (r, z) to the boundary edges of the polycone's
+ * cross-section: the two end caps, the outer edge of every section, and
+ * its inner edge unless that lies on the axis (both inner radii 0) and
+ * axis == 0. */
+static double pcon_edges(const double *p, double r, double z0, int axis) {
+    const int nz = (int)p[2];
+    const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+    double d = seg_dist(r, z0, rn[0], z[0], rx[0], z[0]);
+    double e = seg_dist(r, z0, rn[nz - 1], z[nz - 1], rx[nz - 1], z[nz - 1]);
+    if (e < d) d = e;
+    for (int k = 0; k + 1 < nz; k++) {
+        e = seg_dist(r, z0, rx[k], z[k], rx[k + 1], z[k + 1]);
+        if (e < d) d = e;
+        if (axis || rn[k] > 0.0 || rn[k + 1] > 0.0) {
+            e = seg_dist(r, z0, rn[k], z[k], rn[k + 1], z[k + 1]);
+            if (e < d) d = e;
+        }
+    }
+    return d;
+}
+
 /* Safety: exact distance to the nearest boundary point.  inside=1 gives the
  * distance for a point inside the solid, inside=0 for a point outside
  * (0 when the point is in fact on the other side). */
@@ -484,8 +612,40 @@ double orc_safety(int kind, const double *p, const double *x, int inside) {
         if (c < 0.0) c = 0.0;
         return sqrt(a * a + b * b + c * c);
     }
+    if (kind == K_PCON) {
+        wedge w = wedge_of(kind, p);
+        double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+        /* distance to a phi face: its plane's normal distance h, and the 2-D
+         * distance of the point's projection (r along the face's direction,
+         * z) to the cross-section */
+        double face[2] = { INFINITY, INFINITY };
+        if (!w.full) {
+            double e1[2] = { w.n1[1], -w.n1[0] }, e2[2] = { -w.n2[1], w.n2[0] };
+            for (int i = 0; i < 2; i++) {
+                const double *n = i ? w.n2 : w.n1, *e = i ? e2 : e1;
+                double h = n[0] * x[0] + n[1] * x[1];
+                double r = e[0] * x[0] + e[1] * x[1];
+                double d2 = pcon_in2(p, r, x[2]) ? 0.0 : pcon_edges(p, r, x[2], 1);
+                face[i] = sqrt(h * h + d2 * d2);
+            }
+        }
+        if (in) {
+            /* the edges of the cross-section other than those on the axis
+             * (inside a whole turn the axis is no surface; with a wedge the
+             * phi faces hold it) */
+            double d = pcon_edges(p, rho, x[2], 0);
+            if (face[0] < d) d = face[0];
+            if (face[1] < d) d = face[1];
+            return d;
+        }
+        /* azimuth in the wedge: the 2-D distance to the cross-section in
+         * the point's meridian half-plane; outside it: a phi face (for every
+         * radius and height the nearest azimuth of the wedge is an end) */
+        if (w.full || wedge_has(&w, x[0], x[1])) return pcon_edges(p, rho, x[2], 1);
+        return face[0] < face[1] ? face[0] : face[1];
+    }
     if (kind == K_TUBS) {
-        wedge w = wedge_of(p);
+        wedge w = wedge_of(kind, p);
         double rmin = p[0], rmax = p[1], dz = p[2];
         double rho = sqrt(x[0] * x[0] + x[1] * x[1]), az = fabs(x[2]);
         /* distance to the phi face at unit direction e (the rectangle
@@ -550,16 +710,33 @@ static void surface_grad(int kind, const double *p, int f, const double *xs, dou
         return;
     }
     if (f == F_PHI1 || f == F_PHI2) {
-        /* F = -n.(x, y) for the face's normal n; theta = (..., sphi, dphi) */
-        wedge w = wedge_of(p);
+        /* F = -n.(x, y) for the face's normal n; theta = (..., sphi, dphi),
+         * the row slots 3, 4 of a tube segment and 0, 1 of a polycone */
+        wedge w = wedge_of(kind, p);
+        const int is = kind == K_PCON ? 0 : 3;
         if (f == F_PHI1) {
             g[0] = -w.n1[0]; g[1] = -w.n1[1];
-            dF[3] = w.n1[1] * xs[0] - w.n1[0] * xs[1];          /* e1 . (x, y) */
+            dF[is] = w.n1[1] * xs[0] - w.n1[0] * xs[1];          /* e1 . (x, y) */
         } else {
             g[0] = -w.n2[0]; g[1] = -w.n2[1];
             double de = -(-w.n2[1] * xs[0] + w.n2[0] * xs[1]);  /* -e2 . (x, y) */
-            dF[3] = de; dF[4] = de;
+            dF[is] = de; dF[is + 1] = de;
         }
+        return;
+    }
+    if (kind == K_PCON) {
+        /* end planes F = z[0] - z, z - z[nz-1]; section surfaces F = +-(rho^2
+         * - R(z)^2).  The plane table gets no gradient (dF = 0). */
+        const int nz = (int)p[2];
+        const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+        if (f == F_ZM || f == F_ZP) { g[2] = f == F_ZP ? 1.0 : -1.0; return; }
+        if (f < F_SEC) return;
+        const int k = (f - F_SEC) / 2, outer = ((f - F_SEC) % 2) == 0;
+        const double *r = outer ? rx : rn;
+        double b = (r[k + 1] - r[k]) / (z[k + 1] - z[k]);
+        double Rz = r[k] + b * (xs[2] - z[k]);
+        double sg = outer ? 1.0 : -1.0;
+        g[0] = sg * 2.0 * xs[0]; g[1] = sg * 2.0 * xs[1]; g[2] = sg * (-2.0 * Rz * b);
         return;
     }
     int tubelike = kind == K_TUBE || kind == K_TUBS;
@@ -599,7 +776,25 @@ static void surface_grad(int kind, const double *p, int f, const double *xs, dou
 typedef struct {
     int mkind; const double *mparams;
     int nd; const int32_t *kinds; const double *params, *rot, *trans;
+    const double *pdata;   /* polycone plane table */
 } orc_scene;
+
+/* Parameter block of a solid as the shape routines read it: its row of five,
+ * or for a polycone [sphi, dphi, nz, z[nz], rmin[nz], rmax[nz]] gathered
+ * from the plane table (row = (sphi, dphi, nz, offset, 0); the table holds
+ * at the offset nz z-values, then the nz inner, then the nz outer radii). */
+#define PBUF (3 + 3 * MAXZ)
+static const double *shape_block(int kind, const double *row, const double *pdata, double *buf) {
+    if (kind != K_PCON) return row;
+    const int nz = (int)row[2];
+    const int64_t off = (int64_t)row[3];
+    if (nz < 2 || nz > MAXZ || off < 0 || !pdata) abort();
+    buf[0] = row[0]; buf[1] = row[1]; buf[2] = row[2];
+    memcpy(buf + 3, pdata + off, (size_t)(3 * nz) * sizeof(double));
+    return buf;
+}
+#define MOTHER(sc, buf) shape_block((sc)->mkind, (sc)->mparams, (sc)->pdata, buf)
+#define DAUGHTER(sc, j, buf) shape_block((sc)->kinds[j], (sc)->params + 5 * (j), (sc)->pdata, buf)
 
 /* x = R^T (p - t), u = R^T d: master -> local (Sec. 3.1). */
 static void to_local(const orc_scene *sc, int j, const double *pw, const double *dw,
@@ -620,6 +815,15 @@ static int bad_input(const double *pw, const double *dw) {
 
 static double shape_scale(int kind, const double *p) {
     if (kind == K_BOX) { double m = p[0]; if (p[1] > m) m = p[1]; if (p[2] > m) m = p[2]; return m; }
+    if (kind == K_PCON) {
+        const int nz = (int)p[2];
+        double m = 0.0;
+        for (int k = 0; k < nz; k++) {
+            if (fabs(p[3 + k]) > m) m = fabs(p[3 + k]);
+            if (p[3 + 2 * nz + k] > m) m = p[3 + 2 * nz + k];
+        }
+        return m;
+    }
     if (kind == K_TUBE || kind == K_TUBS) return p[1] > p[2] ? p[1] : p[2];
     double m = p[0]; if (p[2] > m) m = p[2]; if (p[4] > m) m = p[4]; return m;
 }
@@ -641,23 +845,26 @@ static navres navigate_one_b(const orc_scene *sc, const double *pw, const double
     r.second = INFINITY; r.face = F_NONE; r.err = 0.0;
     const int entered = blocked == -2;
     if (bad_input(pw, dw)) { r.step = NAN; r.hit = -2; return r; }
-    if (!entered && !orc_contains(sc->mkind, sc->mparams, pw)) { r.step = 0.0; r.hit = -2; return r; }
-    hitinfo m = entered ? dist_in_entered_info(sc->mkind, sc->mparams, pw, dw)
-                        : dist_in_info(sc->mkind, sc->mparams, pw, dw);
-    double best = m.s, chord = m.chord, tnorm = 0.0, scale = shape_scale(sc->mkind, sc->mparams);
+    double mb[PBUF], db[PBUF];
+    const double *mp = MOTHER(sc, mb);
+    if (!entered && !orc_contains(sc->mkind, mp, pw)) { r.step = 0.0; r.hit = -2; return r; }
+    hitinfo m = entered ? dist_in_entered_info(sc->mkind, mp, pw, dw)
+                        : dist_in_info(sc->mkind, mp, pw, dw);
+    double best = m.s, chord = m.chord, tnorm = 0.0, scale = shape_scale(sc->mkind, mp);
     int hit = -1, face = m.face;
     double second = INFINITY;
     for (int j = 0; j < sc->nd; j++) {
         double x[3], u[3];
         to_local(sc, j, pw, dw, x, u);
-        hitinfo h = j == blocked ? dist_reentry_info(sc->kinds[j], sc->params + 5 * j, x, u)
-                                 : dist_out_info(sc->kinds[j], sc->params + 5 * j, x, u);
+        const double *pj = DAUGHTER(sc, j, db);
+        hitinfo h = j == blocked ? dist_reentry_info(sc->kinds[j], pj, x, u)
+                                 : dist_out_info(sc->kinds[j], pj, x, u);
         if (h.s < best) {
             second = best;
             best = h.s; hit = j; face = h.face; chord = h.chord;
             const double *t = sc->trans + 3 * j;
             tnorm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-            scale = shape_scale(sc->kinds[j], sc->params + 5 * j);
+            scale = shape_scale(sc->kinds[j], pj);
         } else if (h.s < second) {
             second = h.s;
         }
@@ -681,10 +888,10 @@ static navres navigate_one_b(const orc_scene *sc, const double *pw, const double
             double x[3], u[3], g[3], dF[5];
             int kind; const double *prm;
             if (hit == -1) {
-                kind = sc->mkind; prm = sc->mparams;
+                kind = sc->mkind; prm = mp;
                 for (int k = 0; k < 3; k++) { x[k] = pw[k]; u[k] = dw[k]; }
             } else {
-                kind = sc->kinds[hit]; prm = sc->params + 5 * hit;
+                kind = sc->kinds[hit]; prm = DAUGHTER(sc, hit, db);
                 to_local(sc, hit, pw, dw, x, u);
             }
             xrec R; R.n = 0;
@@ -716,22 +923,25 @@ static navres navigate_one(const orc_scene *sc, const double *pw, const double *
 }
 
 static int contains_nav(const orc_scene *sc, const double *pw) {
-    if (!orc_contains(sc->mkind, sc->mparams, pw)) return -2;
+    double buf[PBUF];
+    if (!orc_contains(sc->mkind, MOTHER(sc, buf), pw)) return -2;
     for (int j = 0; j < sc->nd; j++) {
         double x[3], u[3], zero[3] = { 0, 0, 0 };
         to_local(sc, j, pw, zero, x, u);
-        if (orc_contains(sc->kinds[j], sc->params + 5 * j, x)) return j;
+        if (orc_contains(sc->kinds[j], DAUGHTER(sc, j, buf), x)) return j;
     }
     return -1;
 }
 
 static double safety_nav(const orc_scene *sc, const double *pw) {
-    if (!orc_contains(sc->mkind, sc->mparams, pw)) return 0.0;
-    double s = orc_safety(sc->mkind, sc->mparams, pw, 1);
+    double buf[PBUF];
+    const double *mp = MOTHER(sc, buf);
+    if (!orc_contains(sc->mkind, mp, pw)) return 0.0;
+    double s = orc_safety(sc->mkind, mp, pw, 1);
     for (int j = 0; j < sc->nd; j++) {
         double x[3], u[3], zero[3] = { 0, 0, 0 };
         to_local(sc, j, pw, zero, x, u);
-        double d = orc_safety(sc->kinds[j], sc->params + 5 * j, x, 0);
+        double d = orc_safety(sc->kinds[j], DAUGHTER(sc, j, buf), x, 0);
         if (d < s) s = d;
     }
     return s;
@@ -754,11 +964,12 @@ static int adjoint_one(const orc_scene *sc, const double *pw, const double *dw,
     if (nr.hit < -1 || nr.face == F_NONE || !isfinite(nr.step)) return 0;
     int kind; const double *p; double x[3], u[3];
     const double *R = NULL;
+    double buf[PBUF];
     if (nr.hit == -1) {
-        kind = sc->mkind; p = sc->mparams;
+        kind = sc->mkind; p = MOTHER(sc, buf);
         for (int k = 0; k < 3; k++) { x[k] = pw[k]; u[k] = dw[k]; }
     } else {
-        kind = sc->kinds[nr.hit]; p = sc->params + 5 * nr.hit;
+        kind = sc->kinds[nr.hit]; p = DAUGHTER(sc, nr.hit, buf);
         to_local(sc, nr.hit, pw, dw, x, u);
         R = sc->rot + 9 * nr.hit;
     }
@@ -839,8 +1050,8 @@ static void run_threads(job *base, int64_t n, int nthreads) {
 }
 
 #define SCENE_ARGS int mkind, const double *mparams, int nd, const int32_t *kinds, \
-                   const double *params, const double *rot, const double *trans
-#define MAKE_SCENE orc_scene sc = { mkind, mparams, nd, kinds, params, rot, trans }
+                   const double *params, const double *rot, const double *trans, const double *pdata
+#define MAKE_SCENE orc_scene sc = { mkind, mparams, nd, kinds, params, rot, trans, pdata }
 
 void orc_navigate(SCENE_ARGS, int64_t n,
                   const double *px, const double *py, const double *pz,
@@ -889,9 +1100,12 @@ void orc_adjoint(SCENE_ARGS, int64_t n,
     }
 }
 
-/* Single-shape batch calls for the shape-level tests. */
-void orc_shape_batch(int kind, const double *p, int64_t n, const double *x, const double *u,
-                     int what, double *out, int32_t *face) {
+/* Single-shape batch calls for the shape-level tests (row: the solid's row
+ * of five; pdata: the plane table of a polycone). */
+void orc_shape_batch(int kind, const double *row, const double *pdata, int64_t n, const double *x,
+                     const double *u, int what, double *out, int32_t *face) {
+    double buf[PBUF];
+    const double *p = shape_block(kind, row, pdata, buf);
     for (int64_t i = 0; i < n; i++) {
         const double *xi = x + 3 * i, *ui = u + 3 * i;
         if (what == 0) { hitinfo h = dist_out_info(kind, p, xi, ui); out[i] = h.s; if (face) face[i] = h.face; }
@@ -946,6 +1160,7 @@ typedef struct {
     const int32_t *nd, *doff;                                    /* per lv: daughters, offset     */
     const int32_t *kinds; const double *params, *rot, *trans;    /* daughters, concatenated       */
     const int32_t *child;                                        /* per daughter: lv placed there */
+    const double *pdata;                                         /* polycone plane table          */
     int root;
     /* node table */
     int nnodes;
@@ -958,6 +1173,7 @@ static orc_scene world_scene(const orc_world *W, int v) {
     s.mkind = W->mkind[v]; s.mparams = W->mparams + 5 * v;
     s.nd = W->nd[v]; s.kinds = W->kinds + o; s.params = W->params + 5 * o;
     s.rot = W->rot + 9 * o; s.trans = W->trans + 3 * o;
+    s.pdata = W->pdata;
     return s;
 }
 
@@ -1003,7 +1219,9 @@ static int descend(const orc_world *W, int node, const double *x0) {
         for (int j = 0; j < W->nd[v] && next < 0; j++) {
             double xl[3];
             into_child(W, v, j, x, xl, NULL, NULL);
-            if (orc_contains(W->kinds[W->doff[v] + j], W->params + 5 * (W->doff[v] + j), xl)) {
+            double buf[PBUF];
+            const int o = W->doff[v] + j;
+            if (orc_contains(W->kinds[o], shape_block(W->kinds[o], W->params + 5 * o, W->pdata, buf), xl)) {
                 next = W->first[node] + j;
                 xn[0] = xl[0]; xn[1] = xl[1]; xn[2] = xl[2];
             }
@@ -1031,7 +1249,9 @@ static void node_frame(const orc_world *W, int node, const double *pw, const dou
 static int world_locate_one(const orc_world *W, const double *pw) {
     for (int k = 0; k < 3; k++)
         if (!isfinite(pw[k])) return -2;
-    if (!orc_contains(W->mkind[W->root], W->mparams + 5 * W->root, pw)) return -1;
+    double buf[PBUF];
+    const int v = W->root;
+    if (!orc_contains(W->mkind[v], shape_block(W->mkind[v], W->mparams + 5 * v, W->pdata, buf), pw)) return -1;
     return descend(W, 0, pw);
 }
 
@@ -1061,12 +1281,18 @@ static int world_step_one(const orc_world *W, int node, int blocked, const doubl
             if (j == left) continue;
             double xl[3];
             into_child(W, v, j, xp, xl, NULL, NULL);
-            if (orc_contains(W->kinds[W->doff[v] + j], W->params + 5 * (W->doff[v] + j), xl)) {
+            double buf[PBUF];
+            const int o = W->doff[v] + j;
+            if (orc_contains(W->kinds[o], shape_block(W->kinds[o], W->params + 5 * o, W->pdata, buf), xl)) {
                 *blocked_out = -2;
                 return descend(W, W->first[P] + j, xl);
             }
         }
-        if (orc_contains(W->mkind[v], W->mparams + 5 * v, xp)) { *blocked_out = left; return P; }
+        double buf[PBUF];
+        if (orc_contains(W->mkind[v], shape_block(W->mkind[v], W->mparams + 5 * v, W->pdata, buf), xp)) {
+            *blocked_out = left;
+            return P;
+        }
         xb[0] = xp[0]; xb[1] = xp[1]; xb[2] = xp[2];
     }
     return -1;   /* left the root */
@@ -1074,9 +1300,9 @@ static int world_step_one(const orc_world *W, int node, int blocked, const doubl
 
 #define WORLD_ARGS int nlv, const int32_t *mkind, const double *mparams, const int32_t *nd, \
                    const int32_t *doff, const int32_t *kinds, const double *params, const double *rot, \
-                   const double *trans, const int32_t *child, int root, int max_nodes, int32_t *t_lv, \
-                   int32_t *t_parent, int32_t *t_slot, int32_t *t_first
-#define MAKE_WORLD orc_world W = { nlv, mkind, mparams, nd, doff, kinds, params, rot, trans, child, root, \
+                   const double *trans, const int32_t *child, const double *pdata, int root, int max_nodes, \
+                   int32_t *t_lv, int32_t *t_parent, int32_t *t_slot, int32_t *t_first
+#define MAKE_WORLD orc_world W = { nlv, mkind, mparams, nd, doff, kinds, params, rot, trans, child, pdata, root, \
                                    0, t_lv, t_parent, t_slot, t_first }
 
 /* Node table only; returns the node count (-1 past max_nodes). */

@@ -12,6 +12,10 @@ the ROOT geometry library, Sec. 3.1):
 * Box  (kind 0): params = (dx, dy, dz, 0, 0)            half-lengths
 * Tube (kind 1): params = (rmin, rmax, dz, 0, 0)        radii and half-z
 * Cone (kind 2): params = (dz, rmin1, rmax1, rmin2, rmax2), radii 1 at -dz, 2 at +dz
+* Tube segment (kind 3): params = (rmin, rmax, dz, sphi, dphi)
+* Polycone (kind 4): params = (sphi, dphi, nz, offset, 0); the scene's plane
+  table `pdata` holds at `offset` the nz plane positions z (increasing), then
+  the nz inner radii, then the nz outer radii (a `Pcon` in a row spec)
 
 A daughter is placed by a rotation R (row-major 3x3, local -> mother) and a
 translation t: p_mother = R p_local + t.
@@ -27,8 +31,28 @@ import math
 
 import numpy as np
 
-BOX, TUBE, CONE, TUBS = 0, 1, 2, 3
-KIND_NAMES = {BOX: "box", TUBE: "tube", CONE: "cone", TUBS: "tube segment"}
+BOX, TUBE, CONE, TUBS, PCON = 0, 1, 2, 3, 4
+KIND_NAMES = {BOX: "box", TUBE: "tube", CONE: "cone", TUBS: "tube segment", PCON: "polycone"}
+MAX_PLANES = 32
+
+
+@dataclasses.dataclass
+class Pcon:
+    """A polycone: nz planes z[0] < ... < z[nz-1] with radii rmin[k] <= rmax[k],
+    cut to the azimuths [sphi, sphi + dphi]."""
+
+    z: tuple
+    rmin: tuple
+    rmax: tuple
+    sphi: float = 0.0
+    dphi: float = 2.0 * math.pi
+
+    def planes(self) -> np.ndarray:
+        return np.concatenate([np.asarray(self.z, float), np.asarray(self.rmin, float), np.asarray(self.rmax, float)])
+
+    @property
+    def nz(self) -> int:
+        return len(self.z)
 
 
 @dataclasses.dataclass
@@ -42,10 +66,16 @@ class Scene:
     params: np.ndarray                  # (nd, 5) float64
     rot: np.ndarray                     # (nd, 9) float64, row-major local->mother
     trans: np.ndarray                   # (nd, 3) float64
+    pdata: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))   # polycone planes
 
     @property
     def n_daughters(self) -> int:
         return int(self.kinds.shape[0])
+
+    def planes_of(self, row) -> np.ndarray:
+        """(3, nz) array z / rmin / rmax of a polycone row."""
+        nz, off = int(row[2]), int(row[3])
+        return self.pdata[off: off + 3 * nz].reshape(3, nz)
 
     def identity_mask(self) -> np.ndarray:
         eye = np.eye(3).reshape(9)
@@ -60,6 +90,9 @@ class Scene:
                 r[j] = math.sqrt(p[j, 0] ** 2 + p[j, 1] ** 2 + p[j, 2] ** 2)
             elif k in (TUBE, TUBS):
                 r[j] = math.sqrt(p[j, 1] ** 2 + p[j, 2] ** 2)
+            elif k == PCON:
+                z, _, rx = self.planes_of(p[j])
+                r[j] = float(np.sqrt(rx * rx + z * z).max())
             else:
                 r[j] = math.sqrt(max(p[j, 2], p[j, 4]) ** 2 + p[j, 0] ** 2)
         return r
@@ -116,13 +149,25 @@ _EYE = np.eye(3).reshape(9)
 def _scene(name, mkind, mparams, rows):
     kinds = np.array([r[0] for r in rows], dtype=np.int32)
     params = np.zeros((len(rows), 5))
+    pdata = []
+
+    def row_of(spec):
+        out = np.zeros(5)
+        if isinstance(spec, Pcon):
+            off = sum(len(a) for a in pdata)
+            pdata.append(spec.planes())
+            out[:4] = (spec.sphi, spec.dphi, spec.nz, off)
+        else:
+            out[: len(spec)] = spec
+        return out
+
+    mp = row_of(mparams)
     for j, r in enumerate(rows):
-        params[j, : len(r[1])] = r[1]
+        params[j] = row_of(r[1])
     rot = np.array([r[2] for r in rows], dtype=np.float64).reshape(len(rows), 9)
     trans = np.array([r[3] for r in rows], dtype=np.float64).reshape(len(rows), 3)
-    mp = np.zeros(5)
-    mp[: len(mparams)] = mparams
-    return Scene(name, int(mkind), mp, kinds, params, rot, trans)
+    pd = np.concatenate(pdata) if pdata else np.zeros(0)
+    return Scene(name, int(mkind), mp, kinds, params, rot, trans, pd)
 
 
 # --------------------------------------------------------------------------
@@ -199,6 +244,38 @@ def seg4() -> Scene:
     return _scene("seg4", BOX, (100.0, 100.0, 100.0), rows)
 
 
+def pcon4() -> Scene:
+    """Box mother (half 100 mm) with four polycones (Sec. 3.1: connected cone
+    and tube sections): a solid bobbin (flanges, slopes and a waist: not
+    convex), a shell whose hole widens in the middle, a polycone cut to a
+    non-convex wedge with inner apexes on its end planes, and a cone segment
+    (two planes, a convex wedge); two of them rotated."""
+    rows = [
+        (PCON, Pcon((-30.0, -25.0, -20.0, 20.0, 25.0, 30.0), (0.0,) * 6, (25.0, 25.0, 10.0, 10.0, 25.0, 25.0)),
+         _EYE, (-50.0, -50.0, 0.0)),
+        (PCON, Pcon((-25.0, -5.0, 5.0, 25.0), (5.0, 10.0, 10.0, 5.0), (15.0, 20.0, 20.0, 15.0)),
+         euler_zxz(0.4, 0.9, 1.7), (50.0, -50.0, 0.0)),
+        (PCON, Pcon((-20.0, 0.0, 20.0), (0.0, 5.0, 0.0), (20.0, 25.0, 15.0), -1.0, 4.2), _EYE, (-50.0, 50.0, 0.0)),
+        (PCON, Pcon((-20.0, 20.0), (0.0, 5.0), (20.0, 10.0), 0.5, 1.3), euler_zxz(2.2, 0.5, 0.3),
+         (50.0, 50.0, 0.0)),
+    ]
+    return _scene("pcon4", BOX, (100.0, 100.0, 100.0), rows)
+
+
+def pconm() -> Scene:
+    """A polycone mother with a waist (not convex: z from -100 to 100 mm,
+    outer radius 80 mm narrowing to 40 mm at z = 0) holding a tube on the
+    axis, two boxes in the flanges and a cone segment."""
+    rows = [
+        (TUBE, (0.0, 10.0, 60.0), _EYE, (0.0, 0.0, 0.0)),
+        (BOX, (15.0, 10.0, 12.0), euler_zxz(0.3, 0.7, 1.1), (45.0, 10.0, -70.0)),
+        (BOX, (10.0, 10.0, 10.0), _EYE, (-40.0, -30.0, 70.0)),
+        (PCON, Pcon((-10.0, 10.0), (0.0, 5.0), (15.0, 8.0), 0.5, 1.3), euler_zxz(1.0, 0.4, 0.2), (0.0, 55.0, 75.0)),
+    ]
+    return _scene("pconm", PCON, Pcon((-100.0, -40.0, 0.0, 40.0, 100.0), (0.0,) * 5, (80.0, 80.0, 40.0, 80.0, 80.0)),
+                  rows)
+
+
 def grid512(seed: int = 5) -> Scene:
     """Box mother (half 800 mm) with 512 daughters on an 8x8x8 grid (pitch 200 mm):
     boxes or tubes by a seeded coin, random rotations."""
@@ -266,7 +343,8 @@ def batched64(seed: int = 3, n_volumes: int = 64, total: int = 1 << 22):
     return vols, baskets
 
 
-SCENES = {"box4": box4, "toy40": toy40, "toy8": toy8, "diff3": diff3, "grid512": grid512, "seg4": seg4}
+SCENES = {"box4": box4, "toy40": toy40, "toy8": toy8, "diff3": diff3, "grid512": grid512, "seg4": seg4,
+          "pcon4": pcon4, "pconm": pconm}
 
 
 # --------------------------------------------------------------------------
@@ -291,7 +369,19 @@ def _sample_mother(rng, scene: Scene, n: int):
         r = np.sqrt(rng.uniform(rmin * rmin, rmax * rmax, n))
         ph = rng.uniform(0.0, 2.0 * math.pi, n)
         return r * np.cos(ph), r * np.sin(ph), rng.uniform(-dz, dz, n)
-    raise ValueError("track sampling supports box and tube mothers")
+    if scene.mother_kind == PCON:
+        # inside by construction, not uniform in volume: a section, a height
+        # in it, a radius between its interpolated radii, an azimuth in the
+        # wedge
+        z, rn, rx = scene.planes_of(mp)
+        k = rng.integers(0, z.shape[0] - 1, n)
+        f = rng.uniform(0.0, 1.0, n)
+        lo = rn[k] + (rn[k + 1] - rn[k]) * f
+        hi = rx[k] + (rx[k + 1] - rx[k]) * f
+        r = np.sqrt(rng.uniform(lo * lo, hi * hi))
+        ph = mp[0] + mp[1] * rng.uniform(0.0, 1.0, n)
+        return r * np.cos(ph), r * np.sin(ph), z[k] + (z[k + 1] - z[k]) * f
+    raise ValueError("track sampling supports box, tube and polycone mothers")
 
 
 def keepout_mask(scene: Scene, x, y, z, margin: float = 1e-6) -> np.ndarray:
@@ -318,6 +408,10 @@ def keepout_mask(scene: Scene, x, y, z, margin: float = 1e-6) -> np.ndarray:
         else:
             if k in (TUBE, TUBS):   # a segment lies inside its whole tube
                 rlo, rhi, hz = p[j, 0], p[j, 1], p[j, 2]
+            elif k == PCON:         # a polycone lies inside its bounding tube
+                zp, rn, rx = scene.planes_of(p[j])
+                rlo, rhi, hz = float(rn.min()), float(rx.max()), 0.5 * float(zp[-1] - zp[0])
+                lz = lz - 0.5 * float(zp[-1] + zp[0])
             else:
                 rlo, rhi, hz = min(p[j, 1], p[j, 3]), max(p[j, 2], p[j, 4]), p[j, 0]
             rr = lx * lx + ly * ly
@@ -430,10 +524,34 @@ def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) ->
             vb[rows[f], free[f]] *= 1e-6
             q[b] = qb
             v[b] = vb
+        # polycones: a section; a line tangent to its outer or inner cone
+        # (mode 0), a point on that cone (1) or on the rim of one of its planes
+        # (2); azimuths in the wedge, half of modes 1 and 2 on a phi face
+        pcn = np.nonzero(kind == PCON)[0]
+        for i in pcn:
+            zp, rn, rx = scene.planes_of(prm[i])
+            k = int(rng.integers(0, zp.shape[0] - 1))
+            f = float(rng.choice([0.0, 1.0])) if mode[i] == 2 else float(rng.uniform())
+            rr = rx if (rng.uniform() < 0.6 or rn[k] + rn[k + 1] == 0.0) else rn
+            r = rr[k] + (rr[k + 1] - rr[k]) * f
+            zc = zp[k] + (zp[k + 1] - zp[k]) * f
+            slope = (rr[k + 1] - rr[k]) / (zp[k + 1] - zp[k])
+            fr = float(rng.uniform())
+            if mode[i] != 0 and prm[i, 1] < 2.0 * math.pi and rng.uniform() < 0.5:
+                fr = float(rng.choice([0.0, 1.0]))
+            ph = prm[i, 0] + prm[i, 1] * fr
+            radial = np.array([math.cos(ph), math.sin(ph), 0.0])
+            q[i] = radial * r + np.array([0.0, 0.0, zc])
+            if mode[i] == 0:
+                tang = np.array([-math.sin(ph), math.cos(ph), 0.0])
+                gen = np.array([slope * radial[0], slope * radial[1], 1.0])
+                gen /= np.linalg.norm(gen)
+                a = rng.uniform(-1.0, 1.0)
+                v[i] = tang * math.sqrt(max(0.0, 1.0 - a * a)) + gen * a
         # tubes, tube segments and cones: tangent lines (mode 0) or rim
         # points (1, 2); on a segment the points lie in its wedge, half of the
         # rim points on the edges of its phi faces
-        c = ~b
+        c = ~b & (kind != PCON)
         if c.any():
             pc = prm[c]
             kc = kind[c]
@@ -506,15 +624,29 @@ class World:
     root: int = 0
 
     def flat(self) -> dict:
+        """The volumes' arrays concatenated; polycone rows point into one
+        concatenated plane table."""
         nd = np.array([v.n_daughters for v in self.volumes], dtype=np.int32)
         doff = np.concatenate([[0], np.cumsum(nd)[:-1]]).astype(np.int32)
+        mparams, params, pdata, base = [], [], [], 0
+        for v in self.volumes:
+            mp = v.mother_params.astype(np.float64).copy()
+            if v.mother_kind == PCON:
+                mp[3] += base
+            pr = v.params.astype(np.float64).copy().reshape(-1, 5)
+            pr[v.kinds == PCON, 3] += base
+            mparams.append(mp)
+            params.append(pr)
+            pdata.append(np.asarray(v.pdata, dtype=np.float64))
+            base += v.pdata.shape[0]
         cat = lambda f, w: (np.concatenate([f(v) for v in self.volumes]) if nd.sum() else np.zeros((0, w)))
         return {
             "mkind": np.array([v.mother_kind for v in self.volumes], dtype=np.int32),
-            "mparams": np.stack([v.mother_params for v in self.volumes]).astype(np.float64),
+            "mparams": np.stack(mparams),
             "nd": nd, "doff": doff,
             "kinds": np.concatenate([v.kinds for v in self.volumes]).astype(np.int32),
-            "params": cat(lambda v: v.params, 5).reshape(-1, 5).astype(np.float64),
+            "params": np.concatenate(params).reshape(-1, 5),
+            "pdata": np.concatenate(pdata) if base else np.zeros(0),
             "rot": cat(lambda v: v.rot, 9).reshape(-1, 9).astype(np.float64),
             "trans": cat(lambda v: v.trans, 3).reshape(-1, 3).astype(np.float64),
             "child": np.concatenate([np.asarray(c, dtype=np.int32) for c in self.child]).astype(np.int32),
@@ -526,13 +658,17 @@ class World:
             assert len(self.child[v]) == vol.n_daughters
             for j, c in enumerate(self.child[v]):
                 cv = self.volumes[c]
-                assert cv.mother_kind == vol.kinds[j] and np.array_equal(cv.mother_params, vol.params[j]), (v, j)
+                assert cv.mother_kind == vol.kinds[j], (v, j)
+                if vol.kinds[j] == PCON:
+                    assert np.array_equal(cv.mother_params[:3], vol.params[j, :3]), (v, j)
+                    assert np.array_equal(cv.planes_of(cv.mother_params), vol.planes_of(vol.params[j])), (v, j)
+                else:
+                    assert np.array_equal(cv.mother_params, vol.params[j]), (v, j)
 
 
 def leaf(kind, params, name="leaf") -> Scene:
-    p = np.zeros(5)
-    p[: len(params)] = params
-    return Scene(name, int(kind), p, np.zeros(0, np.int32), np.zeros((0, 5)), np.zeros((0, 9)), np.zeros((0, 3)))
+    """A logical volume with no daughters (params: a row, or a Pcon)."""
+    return _scene(name, kind, params, [])
 
 
 def _rot_z(phi):
@@ -584,6 +720,45 @@ def world_toy(seed: int = 1) -> World:
     for cx, cy in ((1350.0, 0.0), (-1350.0, 0.0), (0.0, 1350.0), (0.0, -1350.0)):
         rows.append((BOX, (100.0, 100.0, 400.0), _EYE, (cx, cy, 0.0)))
     hall = add(_scene("hall", BOX, (1600.0, 1600.0, 2000.0), rows), [det, rack, rack, rack, rack])
+    w = World(vols, child, root=hall)
+    w.check()
+    return w
+
+
+def world_pcon() -> World:
+    """A box hall (half 400 mm) holding: the polycone vessel of `pconm`
+    (rotated; its tube, two boxes and cone segment as leaves), a box holding
+    a polycone shell whose wall holds a small box, and a polycone bobbin
+    leaf.  Non-overlapping by construction."""
+    vols, child = [], []
+
+    def add(scene, kids):
+        vols.append(scene)
+        child.append(list(kids))
+        return len(vols) - 1
+
+    vessel_sc = pconm()
+    kids = []
+    for j in range(vessel_sc.n_daughters):
+        k, row = int(vessel_sc.kinds[j]), vessel_sc.params[j]
+        if k == PCON:
+            z, rn, rx = vessel_sc.planes_of(row)
+            kids.append(add(leaf(PCON, Pcon(tuple(z), tuple(rn), tuple(rx), row[0], row[1]), f"v{j}"), []))
+        else:
+            kids.append(add(leaf(k, row, f"v{j}"), []))
+    vessel = add(vessel_sc, kids)
+    wall_box = add(leaf(BOX, (4.0, 4.0, 10.0), "wall_box"), [])
+    shell_pc = Pcon((-60.0, -20.0, 20.0, 60.0), (20.0, 30.0, 30.0, 20.0), (40.0, 50.0, 50.0, 40.0))
+    shell = add(_scene("pshell", PCON, shell_pc, [(BOX, (4.0, 4.0, 10.0), _EYE, (40.0, 0.0, 0.0))]), [wall_box])
+    holder = add(_scene("holder", BOX, (80.0, 80.0, 80.0), [(PCON, shell_pc, euler_zxz(0.3, 0.0, 0.0), (0.0, 0.0, 0.0))]),
+                 [shell])
+    bob_pc = Pcon((-30.0, -25.0, -20.0, 20.0, 25.0, 30.0), (0.0,) * 6, (25.0, 25.0, 10.0, 10.0, 25.0, 25.0))
+    bobbin = add(leaf(PCON, bob_pc, "bobbin"), [])
+    rows = [(PCON, Pcon((-100.0, -40.0, 0.0, 40.0, 100.0), (0.0,) * 5, (80.0, 80.0, 40.0, 80.0, 80.0)),
+             euler_zxz(0.5, 1.1, 0.2), (-150.0, 0.0, 0.0)),
+            (BOX, (80.0, 80.0, 80.0), _EYE, (200.0, 150.0, 0.0)),
+            (PCON, bob_pc, euler_zxz(1.2, 0.6, 0.0), (150.0, -200.0, 100.0))]
+    hall = add(_scene("phall", BOX, (400.0, 400.0, 400.0), rows), [vessel, holder, bobbin])
     w = World(vols, child, root=hall)
     w.check()
     return w

@@ -86,7 +86,8 @@ def test_cauchy_mean_chord(orc, kind, params, mean):
 
 # ------------------------------------------------------------ invariants ---
 
-SCENES = [("box4", 0), ("toy40", 1), ("toy8", 1), ("diff3", None), ("seg4", None)]
+SCENES = [("box4", 0), ("toy40", 1), ("toy8", 1), ("diff3", None), ("seg4", None), ("pcon4", None),
+          ("pconm", None)]
 
 
 def _scene(name, seed):

@@ -135,12 +135,13 @@ def test_exit_through_grandparent(orc):
     assert seq[:3] == [(5.0, 1), (0.0, 0), (900.0, -1)]
 
 
-def test_toy_world_invariants(orc):
+@pytest.mark.parametrize("make,min_total", [(scenes.world_toy, 2000), (scenes.world_pcon, 500)], ids=["toy", "pcon"])
+def test_toy_world_invariants(orc, make, min_total):
     """After every step the track is in another node (entering moves down the
     tree, leaving never returns the node left), and a point advanced 1e-6 mm
     past the boundary locates to the new node unless it lies within 1e-6 mm
     of another surface."""
-    w = scenes.world_toy()
+    w = make()
     t = orc.world_nodes(w)
     parent = t["parent"]
 
@@ -168,16 +169,17 @@ def test_toy_world_invariants(orc):
         tr = scenes.Tracks(tr.x + np.where(ok, s, 0) * tr.dx, tr.y + np.where(ok, s, 0) * tr.dy,
                            tr.z + np.where(ok, s, 0) * tr.dz, tr.dx, tr.dy, tr.dz)
         node = np.where(ok, nn, -1).astype(np.int32)
-    assert total > 2000 and 0 < down < total
+    assert total > min_total and 0 < down < total
     assert agree / total > 0.995
 
 
-def test_transport_makes_progress(orc):
+@pytest.mark.parametrize("make", [scenes.world_toy, scenes.world_pcon], ids=["toy", "pcon"])
+def test_transport_makes_progress(orc, make):
     """Transporting tracks step after step through the toy world: no track
     ping-pongs across a surface (never more than two zero steps in a row),
     every track eventually leaves the root, and the path length of a track
     equals the distance from its start to where it left the hall."""
-    w = scenes.world_toy()
+    w = make()
     tr = scenes.world_points(w, 3000, 22)
     x0 = np.stack([tr.x, tr.y, tr.z], 1)
     node = orc.world_locate(w, tr)
