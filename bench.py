@@ -293,6 +293,38 @@ def voxel_leg(pkg, scenes, rank, steps):
     return out
 
 
+def segments_leg(pkg, scenes, rank, steps):
+    """The navigator step (Fig. 1) in volumes holding tube segments and
+    polycones (Sec. 3.1's segmented and multi-section shapes): seg4 (box
+    mother, four tube segments), pcon4 (box mother, four polycones) and pconm
+    (a polycone mother with a waist holding a tube, two boxes and a cone
+    segment); 2^20 tracks, 4 rotating copies (201 MB > L2), both modes."""
+    import torch
+
+    out = {}
+    n = 1 << 20
+    for name in ("seg4", "pcon4", "pconm"):
+        sc = scenes.SCENES[name]()
+        tr = scenes.sample_tracks(sc, n, 61 + 1000 * rank)
+        vol = pkg.geo_build_volume(sc)
+        base = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in tr.fields()]
+        g = torch.Generator(device="cuda")
+        g.manual_seed(13)
+        copies = [base] + [[f[p].contiguous() for f in base]
+                           for p in (torch.randperm(n, device="cuda", generator=g) for _ in range(3))]
+        step = torch.empty(n, dtype=torch.float64, device="cuda")
+        hit = torch.empty(n, dtype=torch.int32, device="cuda")
+        row = {}
+        for mode, key, k in ((1, "fp32_refine", steps), (0, "fp64_plain", max(3, steps // 4))):
+            ms = _event_time(lambda it: pkg.geo_dist_to_boundary(vol, *copies[it % 4], mode=mode, step=step, hit=hit), k)
+            row[key] = {"value": n / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "steps": k}
+        row["speedup_of_refine"] = row["fp64_plain"]["ms_per_step"] / row["fp32_refine"]["ms_per_step"]
+        out[name] = row
+        vol.close()
+    out["workload"] = "2^20 tracks uniform in the mother's exclusive part, isotropic, 4 rotating copies (201 MB > L2)"
+    return out
+
+
 def _event_time(fn, k):
     import torch
 
@@ -382,20 +414,29 @@ def queries_leg(pkg, scenes, rank, steps, sc):
 def shapes_leg(pkg, steps, q_sqrt, q_div):
     """Each solid's queries on their own (the per-shape algorithms of Sec. 3.1
     that Fig. 2 times per shape): DistFromOutside and DistFromInside of a box,
-    a tube shell and a hollow cone, for baskets of 1024 tracks (launch-bound:
+    a tube shell, a hollow cone, a tube segment and polycones (a cone segment
+    and a six-plane bobbin), for baskets of 1024 tracks (launch-bound:
     microseconds per call) and 2^20 tracks (8 rotating copies, 403 MB > L2);
-    FP64 work per track from the routines' instruction mix (placement
-    transform included), as a fraction of the FP64 peak."""
+    for box, tube and cone the FP64 work per track from the routines'
+    instruction mix (placement transform included), as a fraction of the
+    FP64 peak."""
     import torch
+    from paper_1312_0816_gb300.scenes import Pcon
 
     solids = {"box": (0, (10.0, 20.0, 30.0)), "tube": (1, (5.0, 20.0, 30.0)),
-              "cone": (2, (30.0, 5.0, 10.0, 8.0, 20.0)), "tube_segment": (3, (5.0, 20.0, 30.0, 0.4, 4.0))}
+              "cone": (2, (30.0, 5.0, 10.0, 8.0, 20.0)), "tube_segment": (3, (5.0, 20.0, 30.0, 0.4, 4.0)),
+              "cone_segment": (4, Pcon((-30.0, 30.0), (5.0, 8.0), (10.0, 20.0), 0.4, 4.0)),
+              "polycone_6": (4, Pcon((-30.0, -25.0, -20.0, 20.0, 25.0, 30.0), (0.0,) * 6,
+                                     (25.0, 25.0, 10.0, 10.0, 25.0, 25.0)))}
     out = {"workload": "points uniform in 1.5x the solid's extent (inside and outside), isotropic directions; "
                        "identity placement; steps %d" % steps}
     rng = np.random.default_rng(5)
     for name, (kind, prm) in solids.items():
-        ext = np.array(prm[:3]) if kind == 0 else (np.array([prm[1], prm[1], prm[2]]) if kind in (1, 3)
-                                                   else np.array([max(prm[2], prm[4])] * 2 + [prm[0]]))
+        if kind == 4:
+            ext = np.array([max(prm.rmax)] * 2 + [max(abs(prm.z[0]), abs(prm.z[-1]))])
+        else:
+            ext = np.array(prm[:3]) if kind == 0 else (np.array([prm[1], prm[1], prm[2]]) if kind in (1, 3)
+                                                       else np.array([max(prm[2], prm[4])] * 2 + [prm[0]]))
         row = {}
         for n in (1024, 1 << 20):
             x = rng.uniform(-1.5, 1.5, size=(n, 3)) * ext
@@ -481,6 +522,7 @@ def main():
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
     ap.add_argument("--no-world", action="store_true")
+    ap.add_argument("--no-segments", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -622,6 +664,7 @@ def main():
     queries = None if args.no_queries else queries_leg(pkg, scenes, rank, max(10, args.steps // 100), sc)
     shapes = None if args.no_shapes else shapes_leg(pkg, max(10, args.steps // 100), q_sqrt, q_div)
     world = None if args.no_world else world_leg(pkg, scenes, rank, max(10, args.steps // 100))
+    segments = None if args.no_segments else segments_leg(pkg, scenes, rank, max(10, args.steps // 100))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -652,6 +695,7 @@ def main():
             "contains_safety": queries,
             "shapes": shapes,
             "world": world,
+            "segments": segments,
         }
         print(json.dumps(line), flush=True)
     vol.close()

@@ -25,6 +25,19 @@
  *       to the closed wedge of azimuths [sphi, sphi + dphi], 0 < dphi <= 2 pi
  *       (2 pi: the whole tube); the wedge holds the z axis.  Its surfaces are
  *       tagged 8 (the face at sphi) and 9 (the face at sphi + dphi).
+ *     Polycone (GEO_PCON; Sec. 3.1's sequence of connected cone and tube
+ *       sections) p = (sphi, dphi, nz, 0, 0) with `planes` = nz plane
+ *       heights z[k], then the nz inner radii rmin[k], then the nz outer
+ *       radii rmax[k] (3 nz doubles): 2 <= nz <= GEO_MAX_PLANES, z strictly
+ *       increasing, 0 <= rmin[k] <= rmax[k], rmax[k] + rmax[k+1] > 0.
+ *       Section k (between planes k and k+1) is the cone whose radii vary
+ *       linearly from plane k to plane k+1; the solid is the union of the
+ *       sections cut to the wedge [sphi, sphi + dphi] as for the tube
+ *       segment.  Inner planes are no surfaces.  Surfaces: 4 / 5 the planes
+ *       z[0] / z[nz-1], 8 / 9 the phi faces, 16 + 2k the outer and 17 + 2k
+ *       the inner surface of section k.  A cone segment (rmin1, rmax1,
+ *       rmin2, rmax2, dz, sphi, dphi) is the polycone of the two planes
+ *       -dz, +dz.
  *   - A daughter is placed by a rotation R (row-major, local -> mother) and a
  *     translation t:  p_mother = R p_local + t.  The mother's frame is the
  *     frame of the tracks (its rot must be the identity and trans zero).
@@ -67,7 +80,9 @@ typedef enum {
     GEO_ERR_UNSUPPORTED = 6     /* valid request this build does not implement      */
 } geo_status;
 
-typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2, GEO_TUBS = 3 } geo_kind;
+typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2, GEO_TUBS = 3, GEO_PCON = 4 } geo_kind;
+
+#define GEO_MAX_PLANES 32
 
 /* GEO_FP64: every operation in FP64.
  * GEO_FP32_REFINE: a conservative FP32 pass bounds every candidate from below;
@@ -77,13 +92,16 @@ typedef enum { GEO_FP64 = 0, GEO_FP32_REFINE = 1 } geo_mode;
 
 /* One placed solid.  kind: geo_kind.  p: shape parameters (see above).
  * rot: row-major 3x3 rotation local -> mother, orthonormal with det +1 within
- * 1e-12.  trans: translation (mm). */
+ * 1e-12.  trans: translation (mm).  planes: for GEO_PCON a host array of
+ * 3 * nz doubles (see above), read during the call that receives the struct
+ * and not kept; ignored for the other kinds. */
 typedef struct {
     int32_t kind;
     int32_t reserved;   /* must be 0 */
     double p[5];
     double rot[9];
     double trans[3];
+    const double* planes;
 } geo_placed_shape;
 
 /* Build options.  voxelize != 0 builds a uniform-grid candidate list over the
@@ -112,8 +130,10 @@ typedef enum {
  * per track; an identity placement queries the solid in its own frame).
  * Writes out[n] (device FP64) and, if face is not NULL, face[n] (device
  * int32): the surface crossed by a distance (box 0..5 = -x,+x,-y,+y,-z,+z;
- * tube and cone 4/5 = -z/+z planes, 6 outer, 7 inner; -1 none), -1 for the
- * other queries.  dx,dy,dz may be NULL for the safeties and Contains.
+ * tube and cone 4/5 = -z/+z planes, 6 outer, 7 inner; segments 8/9 the phi
+ * faces; polycone sections 16 + 2k / 17 + 2k; -1 none), -1 for the other
+ * queries.  A polycone's plane table travels in the kernel's parameters (the
+ * call allocates nothing).  dx,dy,dz may be NULL for the safeties and Contains.
  * Non-finite input, or a zero direction for a distance: NaN.  The values are
  * those of the navigator's FP64 routines.  Errors: bad kind or parameters of
  * the solid (as geo_build_volume), bad query, host pointers. */
@@ -125,7 +145,10 @@ geo_status geo_shape_query(const geo_placed_shape* shape, int32_t what, const do
  * daughter volumes).  `mother` and `daughters[0..n_daughters)` are host
  * structs, copied; the caller may free them on return.  n_daughters may be 0.
  * Validation: kinds, finiteness, dz > 0, 0 <= rmin <= rmax (rmin1<=rmax1,
- * rmin2<=rmax2, rmax1+rmax2 > 0 for cones), orthonormal rotations.  Allocates
+ * rmin2<=rmax2, rmax1+rmax2 > 0 for cones), 0 < dphi <= 2 pi for segments,
+ * the polycone rules above (GEO_ERR_INVALID_ARG for planes == NULL or nz
+ * out of range, GEO_ERR_SHAPE_PARAMS for the rest), orthonormal rotations.
+ * Polycones' plane tables are copied to the device with the volume.  Allocates
  * device memory and copies on `stream`, then synchronises that stream.
  * On success *out owns the tables; on failure *out is NULL. */
 geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_shape* daughters,

@@ -1,9 +1,9 @@
 """GB300-native vector navigator: distance to the next boundary, Contains and
-Safety for baskets of tracks inside one mother volume (Box, Tube, Cone
-daughters), after "Vectorising the detector geometry to optimize particle
-transport".  The compute path is libgeonav.so (hand-written CUDA for sm_103a)
+Safety for baskets of tracks inside one mother volume (Box, Tube, Cone, tube
+segment and polycone daughters), after "Vectorising the detector geometry to
+optimize particle transport".  The compute path is libgeonav.so (hand-written CUDA for sm_103a)
 behind the C ABI of include/geo.h; `geonav` is its Python binding."""
-from .geonav import (GEO_BOX, GEO_CONE, GEO_FP32_REFINE, GEO_FP64, GEO_TUBE, GEO_TUBS, GeoError, Volume,  # noqa: F401
+from .geonav import (GEO_BOX, GEO_CONE, GEO_FP32_REFINE, GEO_FP64, GEO_PCON, GEO_TUBE, GEO_TUBS, GeoError, Volume,  # noqa: F401
                      geo_build_volume, geo_contains, geo_destroy_volume, geo_dist_to_boundary,
                      geo_dist_to_boundary_host, geo_dist_to_boundary_stats, geo_check_device_status, geo_probe_pipe,
                      geo_safety, geo_status_string, geo_volume_info, load, Batch, geo_build_batch,

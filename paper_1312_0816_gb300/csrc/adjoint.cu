@@ -50,18 +50,41 @@ __device__ __forceinline__ void surface_grad64(const ShapeRec64& r, int face, co
         dF[3] = dF[4] = 0.0;
         return;
     }
-    if (face == 8 || face == 9) {                    // tube segment: F = -n.(x, y)
+    if (face == 8 || face == 9) {                    // segments: F = -n.(x, y)
         const double* d = r.d;
         const double nx = face == 8 ? d[5] : d[7], ny = face == 8 ? d[6] : d[8];
         g[0] = -nx;
         g[1] = -ny;
         g[2] = 0.0;
         // d/dsphi of the face at sphi: e1.(x, y); of the face at sphi + dphi:
-        // -e2.(x, y), for sphi and dphi alike
+        // -e2.(x, y), for sphi and dphi alike; (sphi, dphi) are the parameter
+        // slots 3, 4 of a tube segment and 0, 1 of a polycone
         const double de = face == 8 ? ny * xs[0] - nx * xs[1] : -(-ny * xs[0] + nx * xs[1]);
-        dF[0] = dF[1] = dF[2] = 0.0;
-        dF[3] = de;
-        dF[4] = face == 8 ? 0.0 : de;
+        const int is = r.kind == KPCON ? 0 : 3;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dF[k] = k == is ? de : (k == is + 1 && face == 9 ? de : 0.0);
+        return;
+    }
+    if (r.kind == KPCON) {
+        // end planes F = z[0] - z, z - z[nz-1]; section k: F = +-(rho^2 -
+        // R(z)^2); the plane table gets no gradient
+        dF[0] = dF[1] = dF[2] = dF[3] = dF[4] = 0.0;
+        g[0] = g[1] = g[2] = 0.0;
+        if (face == 4 || face == 5) {
+            g[2] = face == 5 ? 1.0 : -1.0;
+            return;
+        }
+        if (face < 16) return;
+        const double* T = pcon_table(r.d);
+        const int n = int(r.d[1]), k = (face - 16) >> 1;
+        const bool outer = ((face - 16) & 1) == 0;
+        const double* rr = T + (outer ? 2 * n : n);
+        const double b = T[3 * n + (outer ? n - 1 : 0) + k];
+        const double R = rr[k] + b * (xs[2] - T[k]);
+        const double sg = outer ? 1.0 : -1.0;
+        g[0] = sg * 2.0 * xs[0];
+        g[1] = sg * 2.0 * xs[1];
+        g[2] = -sg * 2.0 * R * b;
         return;
     }
     const bool tube = r.kind == KTUBE || r.kind == KTUBS;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -23,7 +24,10 @@ struct geo_volume_s {
     int32_t* vox_off = nullptr;
     int32_t* vox_ids = nullptr;
     unsigned int* status = nullptr;
+    double* planes = nullptr;         // polycone plane tables (device)
     std::vector<ShapeRec64> h64;      // host copy of the daughter records
+    std::vector<double> h_planes;     // host copy of the plane tables
+    std::vector<int64_t> pl_off;      // [nd + 1]: table offset of daughter j (last: the mother), -1 if none
     // staging workspace of geo_dist_to_boundary_host: two buffers of
     // ws_tracks tracks, a copy-in and a copy-out stream, and events
     void* ws = nullptr;
@@ -74,13 +78,29 @@ bool finite_all(const double* a, int n) {
     return true;
 }
 
+// number of planes of a polycone (its p[2])
+int pcon_nz(const geo_placed_shape& s) { return int(s.p[2]); }
+
 // Shape parameter validation (readings of the ROOT conventions, see geo.h).
 geo_status check_shape(const geo_placed_shape& s, bool is_mother) {
-    if (s.kind < GEO_BOX || s.kind > GEO_TUBS) return GEO_ERR_INVALID_ARG;
+    if (s.kind < GEO_BOX || s.kind > GEO_PCON) return GEO_ERR_INVALID_ARG;
     if (s.reserved != 0) return GEO_ERR_INVALID_ARG;
     if (!finite_all(s.p, 5) || !finite_all(s.rot, 9) || !finite_all(s.trans, 3)) return GEO_ERR_SHAPE_PARAMS;
     const double* p = s.p;
+    if (s.kind == GEO_PCON) {
+        if (!s.planes || !(p[2] >= 2 && p[2] <= kMaxPlanes && p[2] == std::floor(p[2]))) return GEO_ERR_INVALID_ARG;
+        const int n = pcon_nz(s);
+        const double *z = s.planes, *rn = z + n, *rx = rn + n;
+        if (!finite_all(s.planes, 3 * n) || p[3] != 0 || p[4] != 0 || !(p[1] > 0 && p[1] <= 2.0 * kPi))
+            return GEO_ERR_SHAPE_PARAMS;
+        for (int k = 0; k < n; ++k) {
+            if (!(rn[k] >= 0 && rn[k] <= rx[k])) return GEO_ERR_SHAPE_PARAMS;
+            if (k + 1 < n && !(z[k + 1] > z[k] && rx[k] + rx[k + 1] > 0)) return GEO_ERR_SHAPE_PARAMS;
+        }
+    }
     switch (s.kind) {
+        case GEO_PCON:
+            break;
         case GEO_BOX:
             if (!(p[0] > 0 && p[1] > 0 && p[2] > 0)) return GEO_ERR_SHAPE_PARAMS;
             break;
@@ -116,13 +136,59 @@ geo_status check_shape(const geo_placed_shape& s, bool is_mother) {
 double bounding_radius(const geo_placed_shape& s) {
     const double* p = s.p;
     if (s.kind == GEO_BOX) return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    if (s.kind == GEO_PCON) {
+        const int n = pcon_nz(s);
+        double r = 0;
+        for (int k = 0; k < n; ++k) r = std::max(r, std::hypot(s.planes[2 * n + k], s.planes[k]));
+        return r;
+    }
     if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) return std::sqrt(p[1] * p[1] + p[2] * p[2]);
     const double r = std::max(p[2], p[4]);
     return std::sqrt(r * r + p[0] * p[0]);
 }
 
-// derived FP64 constants (layout in geo_internal.h)
-ShapeRec64 make_rec64(const geo_placed_shape& s) {
+// The tube bounding a polycone: radii from the least inner to the largest
+// outer radius over its z-range; placed at the range's centre (centered ==
+// false), or about the shape's own origin with a half-length covering both
+// ends (centered == true, for a mother, whose FP32 copies are used in its
+// own frame).
+geo_placed_shape bounding_tube(const geo_placed_shape& s, bool centered) {
+    const int n = pcon_nz(s);
+    const double *z = s.planes, *rn = z + n, *rx = rn + n;
+    geo_placed_shape t = s;
+    t.kind = GEO_TUBE;
+    t.planes = nullptr;
+    double lo = rn[0], hi = rx[0];
+    for (int k = 1; k < n; ++k) {
+        lo = std::min(lo, rn[k]);
+        hi = std::max(hi, rx[k]);
+    }
+    const double zc = 0.5 * (z[0] + z[n - 1]);
+    t.p[0] = lo;
+    t.p[1] = hi;
+    t.p[2] = centered ? std::max(std::fabs(z[0]), std::fabs(z[n - 1])) : 0.5 * (z[n - 1] - z[0]);
+    t.p[3] = t.p[4] = 0.0;
+    if (!centered)
+        for (int k = 0; k < 3; ++k) t.trans[k] = s.trans[k] + s.rot[3 * k + 2] * zc;
+    return t;
+}
+
+// plane table of a polycone (layout in geo_internal.h)
+std::vector<double> pcon_table_host(const geo_placed_shape& s) {
+    const int n = pcon_nz(s);
+    std::vector<double> T(size_t(pcon_table_len(n)));
+    std::copy(s.planes, s.planes + 3 * n, T.begin());
+    const double *z = s.planes, *rn = z + n, *rx = rn + n;
+    for (int k = 0; k + 1 < n; ++k) {
+        T[3 * n + k] = (rn[k + 1] - rn[k]) / (z[k + 1] - z[k]);
+        T[3 * n + (n - 1) + k] = (rx[k + 1] - rx[k]) / (z[k + 1] - z[k]);
+    }
+    return T;
+}
+
+// derived FP64 constants (layout in geo_internal.h); table: the device
+// address of a polycone's plane table
+ShapeRec64 make_rec64(const geo_placed_shape& s, const double* table = nullptr) {
     ShapeRec64 r;
     std::memset(&r, 0, sizeof r);
     std::memcpy(r.R, s.rot, sizeof r.R);
@@ -132,16 +198,29 @@ ShapeRec64 make_rec64(const geo_placed_shape& s) {
     const double* p = s.p;
     if (s.kind == GEO_BOX) {
         r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
-    } else if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) {
-        r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
-        r.d[3] = p[0] * p[0]; r.d[4] = p[1] * p[1];
-        if (s.kind == GEO_TUBS) {
-            const double f1 = p[3], f2 = p[3] + p[4];
+    } else if (s.kind == GEO_TUBE || s.kind == GEO_TUBS || s.kind == GEO_PCON) {
+        double sphi = p[3], dphi = p[4];
+        if (s.kind == GEO_PCON) {
+            const int n = pcon_nz(s);
+            const double *rn = s.planes + n, *rx = rn + n;
+            const long long bits = static_cast<long long>(reinterpret_cast<uintptr_t>(table));
+            std::memcpy(&r.d[0], &bits, sizeof bits);
+            r.d[1] = n;
+            r.d[2] = rn[0] * rn[0]; r.d[3] = rx[0] * rx[0];
+            r.d[4] = rn[n - 1] * rn[n - 1]; r.d[12] = rx[n - 1] * rx[n - 1];
+            sphi = p[0];
+            dphi = p[1];
+        } else {
+            r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
+            r.d[3] = p[0] * p[0]; r.d[4] = p[1] * p[1];
+        }
+        if (s.kind != GEO_TUBE) {
+            const double f1 = sphi, f2 = sphi + dphi;
             r.d[5] = -std::sin(f1); r.d[6] = std::cos(f1);   // n1: wedge side of the face at sphi
             r.d[7] = std::sin(f2);  r.d[8] = -std::cos(f2);  // n2: wedge side of the face at sphi + dphi
-            r.d[9] = p[4] <= kPi ? 1.0 : 0.0;                // the wedge is n1 >= 0 AND n2 >= 0
-            r.d[10] = p[4] < 2.0 * kPi ? 0.0 : 1.0;          // a whole turn: no wedge
-            r.d[11] = p[4] == kPi ? 1.0 : 0.0;               // a half turn: the two planes coincide
+            r.d[9] = dphi <= kPi ? 1.0 : 0.0;                // the wedge is n1 >= 0 AND n2 >= 0
+            r.d[10] = dphi < 2.0 * kPi ? 0.0 : 1.0;          // a whole turn: no wedge
+            r.d[11] = dphi == kPi ? 1.0 : 0.0;               // a half turn: the two planes coincide
         }
     } else {
         const double dz = p[0];
@@ -161,8 +240,10 @@ ShapeRec64 make_rec64(const geo_placed_shape& s) {
 }
 
 // FP32 record of a solid grown (grow > 0) or shrunk (grow < 0) by |grow| mm.
-// Returns false when a shrunk solid degenerates.
-bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32& r) {
+// Returns false when a shrunk solid degenerates.  A polycone is bounded by its
+// tube (centered: about its origin, for a mother).
+bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32& r, bool centered = false) {
+    if (s.kind == GEO_PCON && grow >= 0) return make_rec32(bounding_tube(s, centered), grow, delta, r);
     std::memset(&r, 0, sizeof r);
     for (int k = 0; k < 9; ++k) r.R[k] = float(s.rot[k]);
     bool eye = true;
@@ -178,9 +259,9 @@ bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32
             r.e[k] = float(p[k] + g);
             if (!(p[k] + g > 0)) return false;
         }
-    } else if (s.kind == GEO_TUBS && g < 0) {
-        // a shrunk whole tube is no subset of a segment: an empty solid, so
-        // the filter never decides "surely inside" for a segment mother
+    } else if ((s.kind == GEO_TUBS || s.kind == GEO_PCON) && g < 0) {
+        // a shrunk whole tube is no subset of a segment (nor of a polycone):
+        // an empty solid, so the filter never decides "surely inside" there
         r.kind = GEO_TUBE;
         r.e[0] = 0.f; r.e[1] = -1.f; r.e[2] = -1.f; r.e[3] = 0.f;
     } else if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) {
@@ -233,6 +314,7 @@ double mother_scale(const geo_placed_shape& m) { return bounding_radius(m); }
 //    expressed as a change of radius:              16 eps32 brad^2 (1+b^2) / r
 //    with r taken no smaller than sqrt(eps32) brad / 2 (apexes, tiny holes).
 double inflation(const geo_placed_shape& s, double S) {
+    if (s.kind == GEO_PCON) return inflation(bounding_tube(s, false), S);
     const double br = bounding_radius(s);
     const double* p = s.p;
     double d = kEps32 * (48.0 * S + 16.0 * br);
@@ -266,9 +348,10 @@ geo_status cuda_status(cudaError_t e);
 geo_status build_voxels(const geo_placed_shape& m, const geo_placed_shape* d, int nd, double S,
                         const geo_build_opts* opts, cudaStream_t s, geo_volume v) {
     double half[3];
-    const double* p = m.p;
-    if (m.kind == GEO_BOX) { half[0] = p[0]; half[1] = p[1]; half[2] = p[2]; }
-    else if (m.kind == GEO_TUBE || m.kind == GEO_TUBS) { half[0] = half[1] = p[1]; half[2] = p[2]; }
+    const geo_placed_shape mb = m.kind == GEO_PCON ? bounding_tube(m, true) : m;
+    const double* p = mb.p;
+    if (mb.kind == GEO_BOX) { half[0] = p[0]; half[1] = p[1]; half[2] = p[2]; }
+    else if (mb.kind == GEO_TUBE || mb.kind == GEO_TUBS) { half[0] = half[1] = p[1]; half[2] = p[2]; }
     else { half[0] = half[1] = std::max(p[2], p[4]); half[2] = p[0]; }
     int g[3];
     const int gauto = std::max(1, std::min(64, int(std::lround(2.0 * std::cbrt(double(std::max(nd, 1)))))));
@@ -284,7 +367,7 @@ geo_status build_voxels(const geo_placed_shape& m, const geo_placed_shape* d, in
     }
     std::vector<std::vector<int32_t>> lists(static_cast<size_t>(ncells));
     for (int j = 0; j < nd; ++j) {
-        const geo_placed_shape& sh = d[j];
+        const geo_placed_shape sh = d[j].kind == GEO_PCON ? bounding_tube(d[j], false) : d[j];
         double he[3];
         const double* q = sh.p;
         if (sh.kind == GEO_BOX) { he[0] = q[0]; he[1] = q[1]; he[2] = q[2]; }
@@ -363,6 +446,11 @@ geo_status check_basket(const double* x, const double* y, const double* z, int64
 namespace geonav {
 const VolView* volume_view(geo_volume v) { return v ? &v->view : nullptr; }
 const ShapeRec64* volume_host_daughters(geo_volume v) { return v ? v->h64.data() : nullptr; }
+const double* volume_host_table(geo_volume v, int j) {
+    if (!v || j < -1 || j >= v->view.nd) return nullptr;
+    const int64_t o = v->pl_off[j < 0 ? size_t(v->view.nd) : size_t(j)];
+    return o >= 0 ? v->h_planes.data() + o : nullptr;
+}
 int volume_device(geo_volume v) { return v ? v->device : -1; }
 int sm_count(int device) { return num_sms_of(device); }
 }  // namespace geonav
@@ -402,35 +490,58 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
     if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
 
     const double S = mother_scale(*mother);
-    std::vector<ShapeRec64> h64(n_daughters);
-    std::vector<ShapeRec32> h32(n_daughters);
-    for (int j = 0; j < n_daughters; ++j) {
-        h64[j] = make_rec64(daughters[j]);
-        const double dl = inflation(daughters[j], S);
-        if (!make_rec32(daughters[j], dl, dl, h32[j])) return GEO_ERR_SHAPE_PARAMS;
-    }
-
     geo_volume v = new (std::nothrow) geo_volume_s;
     if (!v) return GEO_ERR_OOM;
     v->device = dev;
+    // the polycones' plane tables, daughters first, then the mother
+    v->pl_off.assign(size_t(n_daughters) + 1, -1);
+    for (int j = 0; j <= n_daughters; ++j) {
+        const geo_placed_shape& sh = j < n_daughters ? daughters[j] : *mother;
+        if (sh.kind != GEO_PCON) continue;
+        v->pl_off[j] = int64_t(v->h_planes.size());
+        const std::vector<double> T = pcon_table_host(sh);
+        v->h_planes.insert(v->h_planes.end(), T.begin(), T.end());
+    }
+    cudaError_t e = cudaSuccess;
+    if (!v->h_planes.empty() && (e = cudaMalloc(&v->planes, sizeof(double) * v->h_planes.size())) != cudaSuccess) {
+        delete v;
+        return cuda_status(e);
+    }
+    auto table_of = [&](int j) { return v->pl_off[j] >= 0 ? v->planes + v->pl_off[j] : nullptr; };
+
+    std::vector<ShapeRec64> h64(n_daughters);
+    std::vector<ShapeRec32> h32(n_daughters);
+    for (int j = 0; j < n_daughters; ++j) {
+        h64[j] = make_rec64(daughters[j], table_of(j));
+        const double dl = inflation(daughters[j], S);
+        if (!make_rec32(daughters[j], dl, dl, h32[j])) {
+            geo_destroy_volume(v);
+            return GEO_ERR_SHAPE_PARAMS;
+        }
+    }
     VolView& vw = v->view;
     std::memset(&vw, 0, sizeof vw);
-    vw.m64 = make_rec64(*mother);
+    vw.m64 = make_rec64(*mother, table_of(n_daughters));
     const double dm = inflation(*mother, S);
-    if (!make_rec32(*mother, -dm, dm, vw.m32) || !make_rec32(*mother, dm, dm, vw.m32u)) {
-        delete v;
+    if (!make_rec32(*mother, -dm, dm, vw.m32) || !make_rec32(*mother, dm, dm, vw.m32u, true)) {
+        geo_destroy_volume(v);
         return GEO_ERR_SHAPE_PARAMS;
     }
     vw.nd = n_daughters;
-    vw.segs = mother->kind == GEO_TUBS ? 1 : 0;
+    vw.segs = (mother->kind == GEO_TUBS || mother->kind == GEO_PCON) ? 1 : 0;
     for (int j = 0; j < n_daughters; ++j)
-        if (daughters[j].kind == GEO_TUBS) vw.segs = 1;
+        if (daughters[j].kind == GEO_TUBS || daughters[j].kind == GEO_PCON) vw.segs = 1;
 
-    cudaError_t e = cudaSuccess;
     const size_t b64 = sizeof(ShapeRec64) * size_t(std::max(n_daughters, 1));
     const size_t b32 = sizeof(ShapeRec32) * size_t(std::max(n_daughters, 1));
     if ((e = cudaMalloc(&v->d64, b64)) != cudaSuccess || (e = cudaMalloc(&v->d32, b32)) != cudaSuccess ||
         (e = cudaMalloc(&v->status, sizeof(unsigned int))) != cudaSuccess) {
+        geo_destroy_volume(v);
+        return cuda_status(e);
+    }
+    if (!v->h_planes.empty() &&
+        (e = cudaMemcpyAsync(v->planes, v->h_planes.data(), sizeof(double) * v->h_planes.size(),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess) {
         geo_destroy_volume(v);
         return cuda_status(e);
     }
@@ -479,6 +590,7 @@ geo_status geo_destroy_volume(geo_volume v) {
     cudaDeviceSynchronize();
     cudaFree(v->d64);
     cudaFree(v->d32);
+    cudaFree(v->planes);
     cudaFree(v->vox_off);
     cudaFree(v->vox_ids);
     cudaFree(v->status);
@@ -768,9 +880,15 @@ geo_status geo_shape_query(const geo_placed_shape* shape, int32_t what, const do
     if (!is_device_ptr(out) || (face && !is_device_ptr(face))) return GEO_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
-    const ShapeRec64 r = make_rec64(*shape);
+    ShapeArg a;
+    std::memset(&a, 0, sizeof a);
+    a.r = make_rec64(*shape);
+    if (shape->kind == GEO_PCON) {
+        const std::vector<double> T = pcon_table_host(*shape);
+        std::copy(T.begin(), T.end(), a.table);
+    }
     const Basket b{x, y, z, dist ? dx : nullptr, dist ? dy : nullptr, dist ? dz : nullptr, n};
-    return cuda_status(launch_shape_query(r, what, b, out, face, static_cast<cudaStream_t>(stream),
+    return cuda_status(launch_shape_query(a, what, b, out, face, static_cast<cudaStream_t>(stream),
                                           num_sms_of(dev)));
 }
 

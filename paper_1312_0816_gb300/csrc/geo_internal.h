@@ -7,7 +7,15 @@
 
 namespace geonav {
 
-constexpr int KBOX = 0, KTUBE = 1, KCONE = 2, KTUBS = 3;
+constexpr int KBOX = 0, KTUBE = 1, KCONE = 2, KTUBS = 3, KPCON = 4;
+constexpr int kMaxPlanes = GEO_MAX_PLANES;
+
+// Plane table of one polycone of n planes (m = n - 1 sections), FP64:
+//  [0, n) z, [n, 2n) rmin, [2n, 3n) rmax, [3n, 3n+m) inner slopes b_in,
+//  [3n+m, 3n+2m) outer slopes b_out; section k's radius lines are
+//  R(z) = r[k] + b[k] (z - z[k]).
+constexpr int pcon_table_len(int n) { return 3 * n + 2 * (n - 1); }
+constexpr int kPconTableMax = pcon_table_len(kMaxPlanes);
 
 // FP64 record of one placed solid, 256 B, read warp-uniformly (broadcast).
 //  R: row-major local->mother rotation, t: translation.
@@ -23,6 +31,10 @@ constexpr int KBOX = 0, KTUBE = 1, KCONE = 2, KTUBS = 3;
 //         same for n2; d[10] = 1 for a whole turn (no wedge); d[11] = 1 for
 //         a half turn (both faces in one plane)
 //   (radius lines R(z) = a + b z, R(-dz) = r1, R(+dz) = r2)
+//   polycone: d[0] the device address of its plane table (bit pattern),
+//         d[1] nz, d[2] rmin[0]^2, d[3] rmax[0]^2, d[4] rmin[nz-1]^2,
+//         d[12] rmax[nz-1]^2, d[5..11] the wedge as for the tube segment;
+//         p = (sphi, dphi, nz, 0, 0)
 //  brad: bounding-sphere radius about t, enlarged by a relative 1e-12 + 1e-9 mm
 //  so that the FP64 sphere cull is conservative.
 struct __align__(16) ShapeRec64 {
@@ -73,7 +85,7 @@ struct __align__(16) VolView {
     // voxel grid (uniform over the mother's bounding box)
     int32_t voxelized;
     int32_t grid[3];
-    int32_t segs;              // 1 if the mother or a daughter is a tube segment
+    int32_t segs;              // 1 if the mother or a daughter is a tube segment or a polycone
     double lo[3];
     double cell[3];
     double inv_cell[3];
@@ -127,7 +139,13 @@ cudaError_t launch_contains_filter(const VolView& v, const Basket& b, int32_t* w
                                    int num_sms);
 cudaError_t launch_safety_filter(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms);
 
-cudaError_t launch_shape_query(const ShapeRec64& r, int what, const Basket& b, double* out, int32_t* face,
+// One solid for geo_shape_query: its record and, for a polycone, its plane
+// table (the record's table address is not used: the kernel reads `table`).
+struct ShapeArg {
+    ShapeRec64 r;
+    double table[kPconTableMax];
+};
+cudaError_t launch_shape_query(const ShapeArg& a, int what, const Basket& b, double* out, int32_t* face,
                                cudaStream_t s, int num_sms);
 size_t adjoint_smem_bytes(int nd);
 size_t adjoint_workspace_bytes(int nd, int64_t n, int num_sms);
@@ -138,6 +156,7 @@ cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit
 // accessors of the opaque volume handle (defined in geo_abi.cu)
 const VolView* volume_view(geo_volume v);
 const ShapeRec64* volume_host_daughters(geo_volume v);   // host copy, nd records
+const double* volume_host_table(geo_volume v, int j);    // host plane table of daughter j (-1: mother), or null
 int volume_device(geo_volume v);
 int sm_count(int device);
 

@@ -68,8 +68,9 @@ __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity
     healthy = false;
 }
 
-// FP64 task bins: 0 the mother, then box, tube (and tube segment), cone
-__device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : 1 + kind; }
+// FP64 task bins: 0 the mother, then box, tube (and tube segment), cone (and
+// polycone)
+__device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : (kind == KPCON ? 3 : 1 + kind); }
 
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
 

@@ -1,6 +1,7 @@
 // shapes64.cuh -- FP64 device routines for the shape queries of Sec. 3.1
-// (distance to enter, distance to leave, inside check, safety) of Box, Tube
-// and Cone, plus the master->local transform of Sec. 3.1.
+// (distance to enter, distance to leave, inside check, safety) of Box, Tube,
+// Cone, the tube segment and the polycone, plus the master->local transform
+// of Sec. 3.1.
 //
 // Formulation: "candidate surfaces".  DistFromOutside of a closed solid is the
 // smallest s >= 0 at which the ray crosses INTO the solid through one of its
@@ -111,11 +112,52 @@ __device__ __forceinline__ bool wedge_has64(const double* d, double x, double y)
     return d[9] != 0.0 ? (a && b) : (a || b);
 }
 
+// ------------------------------------------------------------- polycone ---
+// The plane table T (layout in geo_internal.h) is read with plain loads: it
+// lives in global memory, or in a kernel's parameters for one-shape queries.
+__device__ __forceinline__ const double* pcon_table(const double* d) {
+    return reinterpret_cast<const double*>(__double_as_longlong(d[0]));
+}
+
+// the last section k (0 <= k <= n-2) with z[k] <= v
+__device__ __forceinline__ int pcon_section(const double* z, int n, double v) {
+    int lo = 0, hi = n - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (z[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// radius line of a section at height v: r0 + b (v - z0)
+__device__ __forceinline__ double rline(double r0, double b, double z0, double v) { return FMA(b, SUB(v, z0), r0); }
+
+// (rho^2 = r2, z = v) in the cross-section: in a section whose z-range holds
+// v (on a plane: either of the two sharing it), between its radius lines
+__device__ __forceinline__ bool pcon_in2(const double* T, int n, double r2, double v) {
+    const double *z = T, *rn = T + n, *rx = T + 2 * n, *bi = T + 3 * n, *bo = bi + (n - 1);
+    if (!(v >= z[0] && v <= z[n - 1])) return false;
+    const int k0 = pcon_section(z, n, v);
+    for (int k = k0; k >= 0 && k >= k0 - 1; --k) {
+        if (!(v >= z[k] && v <= z[k + 1])) continue;
+        const double ro = rline(rx[k], bo[k], z[k], v), ri = rline(rn[k], bi[k], z[k], v);
+        if (LE(r2, MUL(ro, ro)) && (!(rn[k] > 0.0 || rn[k + 1] > 0.0) || LE(MUL(ri, ri), r2))) return true;
+    }
+    return false;
+}
+
+// out of line, so that the hot kernels do not carry the polycone's code
+static __device__ __noinline__ bool pcon_contains64(const double* d, const double* T, double x0, double x1, double x2) {
+    return pcon_in2(T, int(d[1]), DOT2(x0, x0, x1, x1), x2) && wedge_has64(d, x0, x1);
+}
+
 // ------------------------------------------------------------- contains ---
 __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x) {
     const double* d = r.d;
     if (r.kind == KBOX) return ABS_LE(x[0], d[0]) && ABS_LE(x[1], d[1]) && ABS_LE(x[2], d[2]);
     const double rho2 = rho2_of(x);
+    if (r.kind == KPCON) return pcon_contains64(d, pcon_table(d), x[0], x[1], x[2]);
     if (r.kind == KTUBE) return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2);
     if (r.kind == KTUBS)
         return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2) && wedge_has64(d, x[0], x[1]);
@@ -315,13 +357,118 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     return best;
 }
 
-// SEGS = false: the volume holds no tube segment, and its code is left out.
+// Polycone: the end planes (entered from outside the z-range at a point of
+// the end annulus in the wedge), the phi faces (as for the tube segment, at a
+// point of the cross-section), and every section's outer cone crossed inwards
+// and inner cone crossed outwards at a height inside the section's z-range
+// and an azimuth in the wedge.  Sections are visited in the order the track
+// meets them, from the one holding its start, and the visit stops at the
+// first section beyond the best candidate so far (the segment search).
+template <bool FACE = false, bool REENTRY = false>
+__device__ __forceinline__ double pcon_out64(const double* d, const double* T, const double* x, const double* u,
+                                             int* face = nullptr) {
+    if (FACE) *face = -1;
+    const int n = int(d[1]);
+    const double *z = T, *rn = T + n, *rx = T + 2 * n, *bi = T + 3 * n, *bo = bi + (n - 1);
+    const double rho2 = rho2_of(x);
+    if (!REENTRY && pcon_in2(T, n, rho2, x[2]) && wedge_has64(d, x[0], x[1])) return 0.0;
+    double best = d_inf();
+    {   // the end plane the track approaches from outside the z-range
+        const bool lo = x[2] < z[0] && IS_POS(u[2]), hi = x[2] > z[n - 1] && IS_NEG(u[2]);
+        const double t = DIV(SUB(lo ? z[0] : z[n - 1], x[2]), (lo || hi) ? u[2] : 1.0);
+        const double xh = FMA(t, u[0], x[0]), yh = FMA(t, u[1], x[1]);
+        const double r2 = DOT2(xh, xh, yh, yh);
+        if ((lo || hi) && LE(r2, lo ? d[3] : d[12]) && LE(lo ? d[2] : d[4], r2) && wedge_has64(d, xh, yh)) {
+            best = t;
+            if (FACE) *face = lo ? 4 : 5;
+        }
+    }
+    if (d[10] == 0.0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double nx = d[5 + 2 * i], ny = d[6 + 2 * i];
+            const double ex = i == 0 ? ny : -ny, ey = i == 0 ? -nx : nx;   // the face's direction
+            const double wn = DOT2(nx, u[0], ny, u[1]);
+            if (!IS_POS(wn)) continue;                                       // not moving to the wedge side
+            const double s = DIV(-DOT2(nx, x[0], ny, x[1]), wn);
+            if (!(REENTRY ? IS_POS(s) : NONNEG(s)) || !LT(s, best)) continue;
+            const double xh = FMA(s, u[0], x[0]), yh = FMA(s, u[1], x[1]);
+            if (NONNEG(DOT2(ex, xh, ey, yh)) && pcon_in2(T, n, DOT2(xh, xh, yh, yh), FMA(s, u[2], x[2]))) {
+                best = s;
+                if (FACE) *face = 8 + i;
+            }
+        }
+    }
+    const double A0 = DOT2(u[0], u[0], u[1], u[1]);
+    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    auto section = [&](int k) {
+        const double zk = z[k], zk1 = z[k + 1], dz0 = SUB(x[2], zk);
+        {   // outer cone, crossed inwards
+            const double ro0 = FMA(bo[k], dz0, rx[k]), rs = MUL(bo[k], u[2]);
+            const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
+            if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best)) {
+                const double zh = FMA(s, u[2], x[2]);
+                if (zh >= zk && zh <= zk1 && wedge_has64(d, FMA(s, u[0], x[0]), FMA(s, u[1], x[1]))) {
+                    best = s;
+                    if (FACE) *face = 16 + 2 * k;
+                }
+            }
+        }
+        if (rn[k] > 0.0 || rn[k + 1] > 0.0) {   // inner cone, crossed outwards (out of the hole)
+            const double ri0 = FMA(bi[k], dz0, rn[k]), rs = MUL(bi[k], u[2]);
+            const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
+            if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best)) {
+                const double zh = FMA(s, u[2], x[2]);
+                if (zh >= zk && zh <= zk1 && wedge_has64(d, FMA(s, u[0], x[0]), FMA(s, u[1], x[1]))) {
+                    best = s;
+                    if (FACE) *face = 17 + 2 * k;
+                }
+            }
+        }
+    };
+    // heights the track reaches before `best`, with a margin far above rounding
+    auto reach = [&]() {
+        const double zr = FMA(best, u[2], x[2]);
+        return zr + copysign(1e-12 * (fabs(zr) + 1.0), u[2]);
+    };
+    if (IS_ZERO(u[2])) {
+        if (x[2] >= z[0] && x[2] <= z[n - 1]) {
+            const int k = pcon_section(z, n, x[2]);
+            section(k);
+            if (k > 0 && x[2] == z[k]) section(k - 1);
+        }
+    } else if (IS_POS(u[2])) {
+        for (int k = pcon_section(z, n, x[2]); k < n - 1; ++k) {
+            if (z[k] > reach()) break;
+            section(k);
+        }
+    } else {
+        for (int k = pcon_section(z, n, x[2]); k >= 0; --k) {
+            if (z[k + 1] < reach()) break;
+            section(k);
+        }
+    }
+    return best;
+}
+
+// Out-of-line entry of the polycone (see tubs_out64_call).
+template <bool FACE, bool REENTRY>
+__device__ __noinline__ double pcon_out64_call(const double* d, const double* T, double x0, double x1, double x2,
+                                               double u0, double u1, double u2, int* face) {
+    const double x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
+    return pcon_out64<FACE, REENTRY>(d, T, x, u, face);
+}
+
+// SEGS = false: the volume holds no tube segment or polycone, and their code
+// is left out.
 template <bool FACE = false, bool SEGS = true>
 __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* x, const double* u,
                                              int* face = nullptr) {
     if (r.kind == KBOX) return box_out64<FACE>(r.d, x, u, face);
     if (r.kind == KTUBE) return tube_out64<FACE>(r.d, x, u, face);
     if (SEGS && r.kind == KTUBS) return tubs_out64_call<FACE, false>(r.d, x[0], x[1], x[2], u[0], u[1], u[2], face);
+    if (SEGS && r.kind == KPCON)
+        return pcon_out64_call<FACE, false>(r.d, pcon_table(r.d), x[0], x[1], x[2], u[0], u[1], u[2], face);
     return cone_out64<FACE>(r.d, x, u, face);
 }
 
@@ -340,6 +487,8 @@ __device__ __forceinline__ double reentry64(const ShapeRec64& r, const double* x
     }
     if (r.kind == KTUBE) return tube_out64<FACE, true>(r.d, x, u, face);
     if (r.kind == KTUBS) return tubs_out64_call<FACE, true>(r.d, x[0], x[1], x[2], u[0], u[1], u[2], face);
+    if (r.kind == KPCON)
+        return pcon_out64_call<FACE, true>(r.d, pcon_table(r.d), x[0], x[1], x[2], u[0], u[1], u[2], face);
     return cone_out64<FACE, true>(r.d, x, u, face);
 }
 
@@ -354,6 +503,48 @@ __device__ __forceinline__ double slab_exit(double xk, double uk, double h) {
 // Exit parameters of a point inside are >= 0 up to the sign of a zero; the
 // minimum is taken on the bit patterns and the result clamped at +0.
 __device__ __forceinline__ double clamp0(double t) { return NONNEG(t) && !IS_ZERO(t) ? t : 0.0; }
+
+// Exit from the wedge of a segment (d as in geo_internal.h): each half-plane
+// holds s where c + s w >= 0; take(exit, face) is called with the candidates.
+template <typename Take>
+__device__ __forceinline__ void wedge_exit64(const double* d, const double* x, const double* u, Take& take) {
+    // the wedge: each half-plane holds s where c + s w >= 0
+    const double c1 = DOT2(d[5], x[0], d[6], x[1]), w1 = DOT2(d[5], u[0], d[6], u[1]);
+    const double c2 = DOT2(d[7], x[0], d[8], x[1]), w2 = DOT2(d[7], u[0], d[8], u[1]);
+    const double e1 = IS_NEG(w1) ? DIV(-c1, w1) : d_inf();   // where the track leaves half-plane 1
+    const double e2 = IS_NEG(w2) ? DIV(-c2, w2) : d_inf();
+    if (d[9] != 0.0) {
+        // intersection: leaves the wedge when it leaves either (when
+        // dphi = pi the two planes coincide, and the face is the one
+        // on whose side of the axis the track leaves)
+        if (d[11] != 0.0) {
+            const double ec = MINP(clamp0(e1), clamp0(e2));
+            const double xh = FMA(ec, u[0], x[0]), yh = FMA(ec, u[1], x[1]);
+            take(ec, NONNEG(DOT2(d[6], xh, -d[5], yh)) ? 8 : 9);
+        } else {
+            take(clamp0(e1), 8);
+            take(clamp0(e2), 9);
+        }
+    } else {
+        // union: of the half-lines holding the start (c >= 0), a
+        // rising one (w >= 0) never ends; a falling one ends at e; a
+        // rising one that starts later (at -c/w > 0) continues the
+        // union if it starts before that end
+        const bool in1 = NONNEG(c1), in2 = NONNEG(c2);
+        const bool up1 = !IS_NEG(w1), up2 = !IS_NEG(w2);
+        if (!((in1 && up1) || (in2 && up2))) {
+            // every half-plane holding the start ends: the later end
+            const double x1 = in1 ? clamp0(e1) : 0.0, x2 = in2 ? clamp0(e2) : 0.0;
+            const bool second = in2 && (!in1 || LT(x1, x2));
+            const double E = second ? x2 : x1;
+            // a half-plane not holding the start but entered by then
+            // continues the union
+            const double a1 = (!in1 && IS_POS(w1)) ? DIV(-c1, w1) : d_inf();
+            const double a2 = (!in2 && IS_POS(w2)) ? DIV(-c2, w2) : d_inf();
+            if (!(LE(a1, E) || LE(a2, E))) take(E, second ? 9 : 8);
+        }
+    }
+}
 
 // Tube segment, DistFromInside: the tube's exits and the wedge's.
 template <bool FACE = false>
@@ -377,44 +568,7 @@ __device__ __forceinline__ double tubs_in64(const double* d, const double* x, co
         s = root_falling(A0, B0, SUB(rho2, d[3]));
         if (NONNEG(s)) take(clamp0(s), 7);
     }
-    if (d[10] == 0.0) {
-        // the wedge: each half-plane holds s where c + s w >= 0
-        const double c1 = DOT2(d[5], x[0], d[6], x[1]), w1 = DOT2(d[5], u[0], d[6], u[1]);
-        const double c2 = DOT2(d[7], x[0], d[8], x[1]), w2 = DOT2(d[7], u[0], d[8], u[1]);
-        const double e1 = IS_NEG(w1) ? DIV(-c1, w1) : d_inf();   // where the track leaves half-plane 1
-        const double e2 = IS_NEG(w2) ? DIV(-c2, w2) : d_inf();
-        if (d[9] != 0.0) {
-            // intersection: leaves the wedge when it leaves either (when
-            // dphi = pi the two planes coincide, and the face is the one
-            // on whose side of the axis the track leaves)
-            if (d[11] != 0.0) {
-                const double ec = MINP(clamp0(e1), clamp0(e2));
-                const double xh = FMA(ec, u[0], x[0]), yh = FMA(ec, u[1], x[1]);
-                take(ec, NONNEG(DOT2(d[6], xh, -d[5], yh)) ? 8 : 9);
-            } else {
-                take(clamp0(e1), 8);
-                take(clamp0(e2), 9);
-            }
-        } else {
-            // union: of the half-lines holding the start (c >= 0), a
-            // rising one (w >= 0) never ends; a falling one ends at e; a
-            // rising one that starts later (at -c/w > 0) continues the
-            // union if it starts before that end
-            const bool in1 = NONNEG(c1), in2 = NONNEG(c2);
-            const bool up1 = !IS_NEG(w1), up2 = !IS_NEG(w2);
-            if (!((in1 && up1) || (in2 && up2))) {
-                // every half-plane holding the start ends: the later end
-                const double x1 = in1 ? clamp0(e1) : 0.0, x2 = in2 ? clamp0(e2) : 0.0;
-                const bool second = in2 && (!in1 || LT(x1, x2));
-                const double E = second ? x2 : x1;
-                // a half-plane not holding the start but entered by then
-                // continues the union
-                const double a1 = (!in1 && IS_POS(w1)) ? DIV(-c1, w1) : d_inf();
-                const double a2 = (!in2 && IS_POS(w2)) ? DIV(-c2, w2) : d_inf();
-                if (!(LE(a1, E) || LE(a2, E))) take(E, second ? 9 : 8);
-            }
-        }
-    }
+    if (d[10] == 0.0) wedge_exit64(d, x, u, take);
     if (FACE) *face = f;
     return t;
 }
@@ -427,6 +581,84 @@ __device__ __noinline__ double tubs_in64_call(const double* d, double x0, double
     return tubs_in64<FACE>(d, x, u, face);
 }
 
+// Polycone, DistFromInside.  The solid is the intersection of four
+// constraints: the z-range, rho <= Rout(z) and rho >= Rin(z) (piecewise
+// linear radii) and the wedge; the exit is the least of their exits.  The
+// first violation of a radius constraint is the first crossing of a
+// section's outer cone outwards (or inner cone inwards) at a height inside
+// that section's z-range; sections are visited from the start's, in the
+// track's direction, up to the least exit so far.
+template <bool FACE = false>
+__device__ __forceinline__ double pcon_in64(const double* d, const double* T, const double* x, const double* u,
+                                            int* face = nullptr) {
+    double t = d_inf();
+    int f = -1;
+    auto take = [&](double c, int fc) {
+        if (LT(c, t)) {
+            t = c;
+            if (FACE) f = fc;
+        }
+    };
+    const int n = int(d[1]);
+    const double *z = T, *rn = T + n, *rx = T + 2 * n, *bi = T + 3 * n, *bo = bi + (n - 1);
+    const double rho2 = rho2_of(x);
+    const double A0 = DOT2(u[0], u[0], u[1], u[1]);
+    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    if (!IS_ZERO(u[2])) {   // the end plane ahead
+        const bool up = IS_POS(u[2]);
+        take(clamp0(DIV(SUB(up ? z[n - 1] : z[0], x[2]), u[2])), up ? 5 : 4);
+    }
+    if (d[10] == 0.0) wedge_exit64(d, x, u, take);
+    auto section = [&](int k) {
+        const double zk = z[k], zk1 = z[k + 1], dz0 = SUB(x[2], zk);
+        {   // outer cone, crossed outwards
+            const double ro0 = FMA(bo[k], dz0, rx[k]), rs = MUL(bo[k], u[2]);
+            const double s = root_rising(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
+            if (NONNEG(s) && LT(clamp0(s), t)) {
+                const double zh = FMA(s, u[2], x[2]);
+                if (zh >= zk && zh <= zk1) take(clamp0(s), 16 + 2 * k);
+            }
+        }
+        if (rn[k] > 0.0 || rn[k + 1] > 0.0) {   // inner cone, crossed inwards (into the hole)
+            const double ri0 = FMA(bi[k], dz0, rn[k]), rs = MUL(bi[k], u[2]);
+            const double s = root_falling(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
+            if (NONNEG(s) && LT(clamp0(s), t)) {
+                const double zh = FMA(s, u[2], x[2]);
+                if (zh >= zk && zh <= zk1) take(clamp0(s), 17 + 2 * k);
+            }
+        }
+    };
+    auto reach = [&]() {
+        const double zr = FMA(t, u[2], x[2]);
+        return zr + copysign(1e-12 * (fabs(zr) + 1.0), u[2]);
+    };
+    if (IS_ZERO(u[2])) {
+        const int k = pcon_section(z, n, x[2]);
+        section(k);
+        if (k > 0 && x[2] == z[k]) section(k - 1);
+    } else if (IS_POS(u[2])) {
+        for (int k = pcon_section(z, n, x[2]); k < n - 1; ++k) {
+            if (z[k] > reach()) break;
+            section(k);
+        }
+    } else {
+        for (int k = pcon_section(z, n, x[2]); k >= 0; --k) {
+            if (z[k + 1] < reach()) break;
+            section(k);
+        }
+    }
+    if (FACE) *face = f;
+    return t;
+}
+
+// Out-of-line entry of the polycone's DistFromInside (see tubs_out64_call).
+template <bool FACE>
+__device__ __noinline__ double pcon_in64_call(const double* d, const double* T, double x0, double x1, double x2,
+                                              double u0, double u1, double u2, int* face) {
+    const double x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
+    return pcon_in64<FACE>(d, T, x, u, face);
+}
+
 template <bool FACE = false, bool SEGS = true>
 __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x, const double* u,
                                             int* face = nullptr) {
@@ -434,6 +666,8 @@ __device__ __forceinline__ double dist_in64(const ShapeRec64& r, const double* x
     // the bit patterns of values >= 0; equal values are equal bit patterns)
     const double* d = r.d;
     if (SEGS && r.kind == KTUBS) return tubs_in64_call<FACE>(d, x[0], x[1], x[2], u[0], u[1], u[2], face);
+    if (SEGS && r.kind == KPCON)
+        return pcon_in64_call<FACE>(d, pcon_table(d), x[0], x[1], x[2], u[0], u[1], u[2], face);
     double t;
     int f = -1;
     auto take = [&](double c, int fc) {
@@ -492,12 +726,52 @@ __device__ __forceinline__ double seg2(double px, double pz, double ax, double a
     return SQRT(DOT2(cx, cx, cz, cz));
 }
 
+// 2-D distance from (r, v) to the boundary edges of a polycone's cross-section:
+// the end caps, the outer edges and the inner edges (those on the axis only
+// when `axis`).
+__device__ __forceinline__ double pcon_edges(const double* T, int n, double r, double v, bool axis) {
+    const double *z = T, *rn = T + n, *rx = T + 2 * n;
+    double s = fmin(seg2(r, v, rn[0], z[0], rx[0], z[0]), seg2(r, v, rn[n - 1], z[n - 1], rx[n - 1], z[n - 1]));
+    for (int k = 0; k < n - 1; ++k) {
+        s = fmin(s, seg2(r, v, rx[k], z[k], rx[k + 1], z[k + 1]));
+        if (axis || rn[k] > 0.0 || rn[k + 1] > 0.0) s = fmin(s, seg2(r, v, rn[k], z[k], rn[k + 1], z[k + 1]));
+    }
+    return s;
+}
+
+// Polycone safety: 2-D distances in the meridian half-plane to the edges of
+// the cross-section (inside: the edges that are surfaces; outside, azimuth in
+// the wedge: all of them), and for a wedge the distance to each phi face
+// (its plane's normal distance and the 2-D distance of the projection to the
+// cross-section; outside the wedge the nearest azimuth is an end).
+static __device__ __noinline__ double pcon_safety64(const double* d, const double* T, double x0, double x1, double x2,
+                                             bool in) {
+    const int n = int(d[1]);
+    const double rho = SQRT(DOT2(x0, x0, x1, x1));
+    double fd[2] = {d_inf(), d_inf()};
+    if (d[10] == 0.0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double nx = d[5 + 2 * i], ny = d[6 + 2 * i];
+            const double ex = i == 0 ? ny : -ny, ey = i == 0 ? -nx : nx;
+            const double h = DOT2(nx, x0, ny, x1);
+            const double rr = DOT2(ex, x0, ey, x1);
+            const double d2 = (NONNEG(rr) && pcon_in2(T, n, MUL(rr, rr), x2)) ? 0.0 : pcon_edges(T, n, rr, x2, true);
+            fd[i] = SQRT(FMA(h, h, MUL(d2, d2)));
+        }
+    }
+    if (in) return fmin(pcon_edges(T, n, rho, x2, false), fmin(fd[0], fd[1]));
+    if (d[10] != 0.0 || wedge_has64(d, x0, x1)) return pcon_edges(T, n, rho, x2, true);
+    return fmin(fd[0], fd[1]);
+}
+
 // Distance to the boundary from a point inside (inside == true) or outside.
 // Returns 0 if the point is on the other side.
 __device__ __forceinline__ double safety64(const ShapeRec64& r, const double* x, bool inside) {
     const bool in = contains64(r, x);
     if (in != inside) return 0.0;
     const double* d = r.d;
+    if (r.kind == KPCON) return pcon_safety64(d, pcon_table(d), x[0], x[1], x[2], in);
     if (r.kind == KBOX) {
         const double a = SUB(fabs(x[0]), d[0]), b = SUB(fabs(x[1]), d[1]), c = SUB(fabs(x[2]), d[2]);
         if (in) return -fmax(a, fmax(b, c));

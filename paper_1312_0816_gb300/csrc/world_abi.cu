@@ -95,6 +95,11 @@ geo_status geo_build_world(const geo_volume* volumes, int32_t n_volumes, const i
             if (c < 0 || c >= n_volumes) return GEO_ERR_INVALID_ARG;
             const ShapeRec64& m = volume_view(volumes[c])->m64;
             if (m.kind != d[j].kind || std::memcmp(m.p, d[j].p, sizeof m.p) != 0) return GEO_ERR_SHAPE_PARAMS;
+            if (m.kind == KPCON) {   // and the same planes
+                const double *a = volume_host_table(volumes[c], -1), *b = volume_host_table(volumes[v], j);
+                if (!a || !b || std::memcmp(a, b, sizeof(double) * 3 * size_t(m.d[1])) != 0)
+                    return GEO_ERR_SHAPE_PARAMS;
+            }
         }
     }
     // breadth-first expansion with world transforms

@@ -17,7 +17,8 @@ from . import build_lib
 GEO_OK = 0
 GEO_FP64 = 0
 GEO_FP32_REFINE = 1
-GEO_BOX, GEO_TUBE, GEO_CONE, GEO_TUBS = 0, 1, 2, 3
+GEO_BOX, GEO_TUBE, GEO_CONE, GEO_TUBS, GEO_PCON = 0, 1, 2, 3, 4
+GEO_MAX_PLANES = 32
 
 _STATUS = {0: "GEO_OK", 1: "GEO_ERR_INVALID_ARG", 2: "GEO_ERR_SHAPE_PARAMS", 3: "GEO_ERR_OOM",
            4: "GEO_ERR_CUDA", 5: "GEO_ERR_DEVICE_ASSERT", 6: "GEO_ERR_UNSUPPORTED"}
@@ -31,7 +32,8 @@ class GeoError(RuntimeError):
 
 class geo_placed_shape(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("p", ctypes.c_double * 5),
-                ("rot", ctypes.c_double * 9), ("trans", ctypes.c_double * 3)]
+                ("rot", ctypes.c_double * 9), ("trans", ctypes.c_double * 3),
+                ("planes", ctypes.POINTER(ctypes.c_double))]
 
 
 class geo_build_opts(ctypes.Structure):
@@ -125,12 +127,31 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _shape_struct(kind, params, rot=None, trans=None) -> geo_placed_shape:
+def _shape_struct(kind, params, rot=None, trans=None, pdata=None, keep=None) -> geo_placed_shape:
+    """params: the solid's row; for a polycone either a spec with z, rmin,
+    rmax, sphi, dphi, or a row (sphi, dphi, nz, offset, 0) into `pdata`.  The
+    plane array is appended to `keep`, which the caller holds until the call
+    that receives the struct returns."""
     s = geo_placed_shape()
     s.kind = int(kind)
     s.reserved = 0
     p = np.zeros(5)
-    p[: len(params)] = params
+    if int(kind) == GEO_PCON:
+        if hasattr(params, "rmax"):
+            planes = np.concatenate([np.asarray(params.z, float), np.asarray(params.rmin, float),
+                                     np.asarray(params.rmax, float)])
+            p[:3] = (params.sphi, params.dphi, len(params.z))
+        else:
+            nz, off = int(params[2]), int(params[3])
+            planes = np.asarray(pdata, dtype=np.float64)[off: off + 3 * nz]
+            p[:3] = (params[0], params[1], nz)
+        planes = np.ascontiguousarray(planes, dtype=np.float64)
+        if keep is None:
+            raise ValueError("a polycone needs a keep list for its plane array")
+        keep.append(planes)
+        s.planes = planes.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    else:
+        p[: len(params)] = params
     s.p[:] = [float(v) for v in p]
     s.rot[:] = [float(v) for v in (np.eye(3).reshape(9) if rot is None else np.asarray(rot).reshape(9))]
     s.trans[:] = [float(v) for v in (np.zeros(3) if trans is None else np.asarray(trans).reshape(3))]
@@ -164,11 +185,13 @@ def geo_build_volume(scene, voxelize: bool = False, grid=(0, 0, 0), stream=None)
     """Builds the device tables of `scene` (an object with mother_kind,
     mother_params, kinds, params, rot, trans -- see scenes.Scene)."""
     L = load()
-    mother = _shape_struct(scene.mother_kind, scene.mother_params)
+    keep = []
+    pdata = getattr(scene, "pdata", None)
+    mother = _shape_struct(scene.mother_kind, scene.mother_params, pdata=pdata, keep=keep)
     nd = int(scene.n_daughters)
     arr = (geo_placed_shape * max(nd, 1))()
     for j in range(nd):
-        arr[j] = _shape_struct(scene.kinds[j], scene.params[j], scene.rot[j], scene.trans[j])
+        arr[j] = _shape_struct(scene.kinds[j], scene.params[j], scene.rot[j], scene.trans[j], pdata=pdata, keep=keep)
     opts = geo_build_opts()
     opts.voxelize = 1 if voxelize else 0
     opts.grid[:] = [int(g) for g in grid]
@@ -267,7 +290,8 @@ def geo_shape_query(kind, params, what, x, y, z, dx=None, dy=None, dz=None, rot=
         out = torch.empty(n, dtype=f64, device=x.device)
     if want_face and face is None:
         face = torch.empty(n, dtype=torch.int32, device=x.device)
-    shape = _shape_struct(kind, params, rot, trans)
+    keep = []
+    shape = _shape_struct(kind, params, rot, trans, keep=keep)
     dist = what in (GEO_Q_DIST_OUT, GEO_Q_DIST_IN)
     dirs = [_dev(a, f64, n, nm) if dist else ctypes.c_void_p(0) for a, nm in ((dx, "dx"), (dy, "dy"), (dz, "dz"))]
     _check(load().geo_shape_query(ctypes.byref(shape), int(what), _dev(x, f64, n, "x"), _dev(y, f64, n, "y"),

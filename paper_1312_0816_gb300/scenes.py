@@ -595,6 +595,14 @@ def adversarial_tracks(scene: Scene, n: int, seed: int, jitter: float = 1e-7) ->
         mp = scene.mother_params
         if scene.mother_kind == BOX:
             inside = np.all(np.abs(start) < 0.999 * mp[:3], axis=1)
+        elif scene.mother_kind == PCON:
+            # the tube inscribed in the polycone (its least outer and largest
+            # inner radius over its z-range) lies inside it; whole turns only
+            zp, rn, rx = scene.planes_of(mp)
+            rr = start[:, 0] ** 2 + start[:, 1] ** 2
+            inside = (rr < (0.999 * rx.min()) ** 2) & (rr > (1.001 * rn.max()) ** 2) & \
+                     (start[:, 2] > zp[0] + 1e-3 * (zp[-1] - zp[0])) & (start[:, 2] < zp[-1] - 1e-3 * (zp[-1] - zp[0]))
+            assert mp[1] >= 2.0 * math.pi
         else:
             inside = (start[:, 0] ** 2 + start[:, 1] ** 2 < (0.999 * mp[1]) ** 2) & \
                      (np.abs(start[:, 2]) < 0.999 * mp[2])

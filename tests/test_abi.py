@@ -50,7 +50,7 @@ def _build(mother, daughters):
 
 
 @pytest.mark.parametrize("mother,daughter,status", [
-    ((0, (100, 100, 100)), (4, (1, 1, 1)), 1),                      # unknown kind
+    ((0, (100, 100, 100)), (5, (1, 1, 1)), 1),                      # unknown kind
     ((0, (100, 100, 100)), (3, (0, 10, 5, 0, 0)), 2),               # tube segment of no angle
     ((0, (100, 100, 100)), (3, (0, 10, 5, 0, 7)), 2),               # tube segment beyond a whole turn
     ((0, (100, 100, 100)), (3, (8, 6, 5, 0, 1)), 2),                # tube segment rmin > rmax
@@ -108,3 +108,40 @@ def test_shape_query_validation():
     assert L.geo_shape_query(ctypes.byref(bad), 0, None, None, None, None, None, None, 0, None, None, None) == 2
     kind = _shape(7, (1, 1, 1))
     assert L.geo_shape_query(ctypes.byref(kind), 0, None, None, None, None, None, None, 0, None, None, None) == 1
+
+
+_KEEP = []
+
+
+def _pcon(z, rmin, rmax, sphi=0.0, dphi=2 * np.pi, **over):
+    from paper_1312_0816_gb300.scenes import Pcon
+
+    s = geonav._shape_struct(4, Pcon(tuple(z), tuple(rmin), tuple(rmax), sphi, dphi), keep=_KEEP)
+    for k, v in over.items():
+        if k == "planes":
+            s.planes = v
+        else:
+            s.p[int(k[1:])] = v
+    return s
+
+
+@pytest.mark.parametrize("shape,status", [
+    (lambda: _pcon((-1, 0, 2), (0, 1, 0), (3, 4, 2)), 0),
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), 0.5, 1.0), 0),                     # a cone segment
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), planes=None), 1),                   # no plane table
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), p2=1.0), 1),                        # one plane
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), p2=2.5), 1),                        # not a count
+    (lambda: _pcon(range(33), (0,) * 33, (1,) * 33), 1),                       # too many planes
+    (lambda: _pcon((-1, -1, 2), (0, 0, 0), (3, 3, 3)), 2),                      # z not increasing
+    (lambda: _pcon((-1, 0, 2), (0, 5, 0), (3, 4, 2)), 2),                       # rmin > rmax
+    (lambda: _pcon((-1, 0, 2), (0, 0, 0), (0, 0, 2)), 2),                       # a section of no radius
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), 0.0, 0.0), 2),                      # no angle
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), 0.0, 7.0), 2),                      # beyond a whole turn
+    (lambda: _pcon((-1, 2), (0, 0), (3, 3), p3=1.0), 2),                        # p[3] must be 0
+    (lambda: _pcon((-1, 2), (0, float("nan")), (3, 3)), 2),                     # NaN radius
+])
+def test_polycone_validation(shape, status):
+    """The polycone's rules (include/geo.h), checked before any device work."""
+    L = geonav.load()
+    s = shape()
+    assert L.geo_shape_query(ctypes.byref(s), 0, None, None, None, None, None, None, 0, None, None, None) == status

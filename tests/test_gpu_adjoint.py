@@ -76,7 +76,8 @@ def central(fstep, base, k, h):
     return (fstep(a) - fstep(b)) / (2 * h)
 
 
-@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("toy8", 1 << 16), ("seg4", 1 << 16)])
+@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("toy8", 1 << 16), ("seg4", 1 << 16),
+                                    ("pcon4", 1 << 16), ("pconm", 1 << 16)])
 def test_track_gradients(g, orc, name, n):
     sc = scenes.SCENES[name]()
     vol = g.geo_build_volume(sc)
@@ -118,10 +119,20 @@ def test_track_gradients(g, orc, name, n):
 
 def _scene_with(sc, trans=None, params=None, mparams=None):
     return scenes.Scene(sc.name, sc.mother_kind, sc.mother_params if mparams is None else mparams, sc.kinds,
-                        sc.params if params is None else params, sc.rot, sc.trans if trans is None else trans)
+                        sc.params if params is None else params, sc.rot, sc.trans if trans is None else trans,
+                        sc.pdata)
 
 
-@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("seg4", 1 << 16)])
+def _slots(kind, row):
+    """Continuous parameter slots of a row: a polycone's (sphi, dphi) only, and
+    no dphi at a whole turn (a shorter turn opens a sliver)."""
+    if kind == scenes.PCON:
+        return (0,) if row[1] >= 2 * np.pi else (0, 1)
+    return range(5)
+
+
+@pytest.mark.parametrize("name,n", [("box4", 1 << 18), ("diff3", 1 << 16), ("seg4", 1 << 16), ("pcon4", 1 << 16),
+                                    ("pconm", 1 << 16)])
 def test_geometry_gradients_match_fd(g, orc, name, n):
     """d(sum over smooth tracks of step)/d(translations, shape parameters)."""
     sc = scenes.SCENES[name]()
@@ -161,7 +172,7 @@ def test_geometry_gradients_match_fd(g, orc, name, n):
             tm[j, k] -= H
             fd = fd_of(_scene_with(sc, trans=tp), _scene_with(sc, trans=tm))
             assert abs(fd - gt[j, k]) <= 1e-6 * max(1.0, abs(fd)) + noise, (j, k, fd, gt[j, k])
-        for k in range(5):
+        for k in _slots(sc.kinds[j], sc.params[j]):
             if sc.params[j, k] == 0.0:
                 continue
             if sc.kinds[j] == scenes.TUBS and k == 4 and sc.params[j, 4] + H > 2 * np.pi:
@@ -172,7 +183,7 @@ def test_geometry_gradients_match_fd(g, orc, name, n):
             fd = fd_of(_scene_with(sc, params=pp), _scene_with(sc, params=pm))
             assert abs(fd - gprm[j, k]) <= 1e-6 * max(1.0, abs(fd)) + noise, (j, k, fd, gprm[j, k])
     nd = sc.n_daughters
-    for k in range(5):
+    for k in _slots(sc.mother_kind, sc.mother_params):
         if sc.mother_params[k] == 0.0:
             continue
         mp, mm = sc.mother_params.copy(), sc.mother_params.copy()

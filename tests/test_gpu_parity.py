@@ -71,6 +71,8 @@ SCENES = {
     "diff3": lambda: scenes.diff3(),
     "grid512": lambda: scenes.grid512(5),
     "seg4": lambda: scenes.seg4(),
+    "pcon4": lambda: scenes.pcon4(),
+    "pconm": lambda: scenes.pconm(),
 }
 _scene_cache = {}
 
@@ -92,7 +94,7 @@ def test_box4_basket_1024(g, orc, mode):
 
 
 @pytest.mark.parametrize("name,n", [("toy40", 65536 + 77), ("toy8", 30011), ("diff3", 30011),
-                                    ("grid512", 8191)])
+                                    ("grid512", 8191), ("pcon4", 30011), ("pconm", 30011)])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_scene_parity(g, orc, name, n, mode):
     """Several blocks of 256 tracks and a ragged tail."""
@@ -116,7 +118,7 @@ def test_refine_equals_fp64_bitwise(g, name):
         assert np.array_equal(b0.view(np.int64), b1.view(np.int64))
 
 
-@pytest.mark.parametrize("name", ["box4", "toy40", "diff3", "grid512"])
+@pytest.mark.parametrize("name", ["box4", "toy40", "diff3", "grid512", "seg4", "pcon4", "pconm"])
 def test_adversarial_parity(g, orc, name):
     sc = scene(name)
     tr = scenes.adversarial_tracks(sc, 20000, 9)

@@ -32,7 +32,8 @@ def g():
 
 def scene_list():
     return [scenes.toy40(1), scenes.toy8(1), scenes.box4(0), scenes.diff3(), scenes.grid512(5),
-            scenes.cell_volume(11, 200, False), scenes.cell_volume(12, 1000, True), scenes.seg4()]
+            scenes.cell_volume(11, 200, False), scenes.cell_volume(12, 1000, True), scenes.seg4(), scenes.pcon4(),
+            scenes.pconm()]
 
 
 def hard_points(orc, sc, n, seed):
@@ -62,7 +63,7 @@ def dev3(tr):
     return [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in (tr.x, tr.y, tr.z)]
 
 
-@pytest.mark.parametrize("idx", range(8))
+@pytest.mark.parametrize("idx", range(10))
 def test_modes_agree_and_match_oracle(g, orc, idx):
     sc = scene_list()[idx]
     vol = g.geo_build_volume(sc)

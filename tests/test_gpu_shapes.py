@@ -1,6 +1,7 @@
 """Per-shape queries (Sec. 3.1, measured per shape in Fig. 2) on the GPU
 against the oracle's shape routines: DistFromOutside, DistFromInside, the two
-safeties and Contains of one Box, Tube or Cone, in its own frame and placed.
+safeties and Contains of one Box, Tube, Cone, tube segment or polycone, in
+its own frame and placed.
 
 Bars: distances within 1e-9 mm (relative to max(1, s)) and the crossed face
 equal, except on a small fraction of rays that graze a surface or cross at an
@@ -32,6 +33,16 @@ SOLIDS = [
     (3, (2.0, 10.0, 8.0, -1.0, math.pi)),             # a half shell (both faces in one plane),
     (3, (0.0, 10.0, 8.0, 2.0, 0.2)),                  # a thin wedge,
     (3, (3.0, 10.0, 8.0, 0.3, 2 * math.pi)),          # a whole turn
+    # polycones: a solid bobbin (not convex), a shell whose hole widens, a
+    # non-convex wedge with inner apexes on its end planes, a cone segment, a
+    # hollow cone segment beyond a half turn, and a zigzag of 12 planes
+    (4, scenes.Pcon((-30.0, -25.0, -20.0, 20.0, 25.0, 30.0), (0.0,) * 6, (25.0, 25.0, 10.0, 10.0, 25.0, 25.0))),
+    (4, scenes.Pcon((-25.0, -5.0, 5.0, 25.0), (5.0, 10.0, 10.0, 5.0), (15.0, 20.0, 20.0, 15.0))),
+    (4, scenes.Pcon((-20.0, 0.0, 20.0), (0.0, 5.0, 0.0), (20.0, 25.0, 15.0), -1.0, 4.2)),
+    (4, scenes.Pcon((-20.0, 20.0), (0.0, 5.0), (20.0, 10.0), 0.5, 1.3)),
+    (4, scenes.Pcon((-15.0, 15.0), (4.0, 8.0), (12.0, 18.0), 2.0, 3.9)),
+    (4, scenes.Pcon(tuple(-33.0 + 6.0 * k for k in range(12)), tuple(2.0 + (k % 2) * 3.0 for k in range(12)),
+                    tuple(10.0 + (k % 2) * 8.0 + k for k in range(12)))),
 ]
 WHAT = {"dist_out": 0, "dist_in": 1, "safety_out": 2, "safety_in": 3, "contains": 4}
 
@@ -49,6 +60,9 @@ def g():
 def extent(kind, p):
     if kind == 0:
         return np.array(p[:3])
+    if kind == 4:
+        r = max(p.rmax)
+        return np.array([r, r, max(abs(p.z[0]), abs(p.z[-1]))])
     if kind in (1, 3):
         return np.array([p[1], p[1], p[2]])
     r = max(p[2], p[4])
@@ -115,7 +129,7 @@ def test_shape_queries_match_oracle(g, orc, idx):
         assert np.array_equal(got[~band], want[~band])
 
 
-@pytest.mark.parametrize("idx", [0, 2, 4, 8])
+@pytest.mark.parametrize("idx", [0, 2, 4, 8, 12, 14])
 def test_placed_solid(g, orc, idx):
     """Placement applied in the kernel: compare with the oracle on points
     transformed on the host (the transforms round differently, so distances

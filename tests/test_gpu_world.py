@@ -74,9 +74,10 @@ def test_node_table_and_locate(g, orc):
     assert list(nb) == [-2, -1]
 
 
-@pytest.mark.parametrize("seed", [5, 6])
-def test_transport_matches_oracle(g, orc, seed):
-    w = scenes.world_toy()
+@pytest.mark.parametrize("make,seed,min_checked", [(scenes.world_toy, 5, 100000), (scenes.world_toy, 6, 100000),
+                                                  (scenes.world_pcon, 5, 50000)], ids=["toy5", "toy6", "pcon5"])
+def test_transport_matches_oracle(g, orc, make, seed, min_checked):
+    w = make()
     W, vols = build(g, w)
     tr = scenes.world_points(w, 50000, seed)
     node = orc.world_locate(w, tr)
@@ -103,15 +104,16 @@ def test_transport_matches_oracle(g, orc, seed):
         tr = scenes.Tracks(tr.x + s * tr.dx, tr.y + s * tr.dy, tr.z + s * tr.dz, tr.dx, tr.dy, tr.dz)
         node = np.where(alive, n0, -1).astype(np.int32)
         flag = np.where(alive, f0, -1).astype(np.int32)
-    assert checked > 100000
+    assert checked > min_checked
     assert exempt_total <= 1e-4 * checked
 
 
-def test_transport_until_every_track_leaves(g):
-    """GPU-only transport of the toy world until every track has left the
-    hall: no ping-pong on a surface (at most two zero steps in a row) and the
+@pytest.mark.parametrize("make", [scenes.world_toy, scenes.world_pcon], ids=["toy", "pcon"])
+def test_transport_until_every_track_leaves(g, make):
+    """GPU-only transport of the world until every track has left the hall:
+    no ping-pong on a surface (at most two zero steps in a row) and the
     summed steps equal the straight distance travelled."""
-    w = scenes.world_toy()
+    w = make()
     W, vols = build(g, w)
     tr = scenes.world_points(w, 1 << 16, 8)
     x = [dev(f) for f in tr.fields()]
