@@ -384,7 +384,8 @@ def adjoint_leg(pkg, scenes, rank, steps):
 
 def queries_leg(pkg, scenes, rank, steps, sc):
     """Contains and Safety over the toy detector, 2^22 points (inputs 100 MB,
-    4 rotating copies > L2)."""
+    4 rotating copies > L2); Safety exact in both modes and the cheaper
+    under-estimate (GEO_SAFETY_ESTIMATE)."""
     import torch
 
     n = 1 << 22
@@ -403,7 +404,7 @@ def queries_leg(pkg, scenes, rank, steps, sc):
         ms = _event_time(lambda it: pkg.geo_contains(vol, *copies[it % 4], mode=mode, where=where), steps)
         out[key] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
                     "algorithmic_gb_s": 28.0 * n / (ms * 1e-3) / 1e9}
-    for mode, key in ((0, "safety_fp64"), (1, "safety_fp32_refine")):
+    for mode, key in ((0, "safety_fp64"), (1, "safety_fp32_refine"), (2, "safety_estimate")):
         ms = _event_time(lambda it: pkg.geo_safety(vol, *copies[it % 4], mode=mode, safety=saf), steps)
         out[key] = {"value": n / (ms * 1e-3), "unit": "points/s", "ms_per_step": ms,
                     "algorithmic_gb_s": 32.0 * n / (ms * 1e-3) / 1e9}

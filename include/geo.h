@@ -87,8 +87,10 @@ typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2, GEO_TUBS = 3, GEO_PCON =
 /* GEO_FP64: every operation in FP64.
  * GEO_FP32_REFINE: a conservative FP32 pass bounds every candidate from below;
  * only candidates that can still win are recomputed with the same FP64
- * routines as GEO_FP64, so both modes return the same answers. */
-typedef enum { GEO_FP64 = 0, GEO_FP32_REFINE = 1 } geo_mode;
+ * routines as GEO_FP64, so both modes return the same answers.
+ * GEO_SAFETY_ESTIMATE (geo_safety only): the cheaper, under-estimating
+ * safety (see geo_safety). */
+typedef enum { GEO_FP64 = 0, GEO_FP32_REFINE = 1, GEO_SAFETY_ESTIMATE = 2 } geo_mode;
 
 /* One placed solid.  kind: geo_kind.  p: shape parameters (see above).
  * rot: row-major 3x3 rotation local -> mother, orthonormal with det +1 within
@@ -189,7 +191,18 @@ geo_status geo_contains(geo_volume v, const double* x, const double* y, const do
  * candidate not culled by its FP64 bounding sphere; GEO_FP32_REFINE bounds
  * every candidate from below in FP32 and evaluates in FP64 only those whose
  * bound does not exceed the smallest FP64 value found (usually one); both
- * modes return the same FP64 minimum. */
+ * modes return the same FP64 minimum.  GEO_SAFETY_ESTIMATE returns a cheaper
+ * lower bound of the safety (never above it, 0 outside the mother or inside
+ * a daughter), in the manner of ROOT's estimated safeties: every solid is
+ * replaced by a simpler bound of its distance -- box and tube the exact
+ * distance, cone the largest distance to a supporting half-plane of its
+ * meridian trapezoid, tube segment and polycone the distance to the tube
+ * enclosing them; the mother (box, tube, cone) its inside distance, a
+ * segment or polycone mother 0 -- each evaluated in FP32 on a copy grown
+ * (mother: shrunk) by the filter's inflation and lowered by a relative
+ * 2^-18, with no FP64 work but the mother's containment test.  The value is
+ * below that bound by at most about the inflation (a few 1e-5 of the
+ * mother's extent). */
 geo_status geo_safety(geo_volume v, const double* x, const double* y, const double* z, int64_t n,
                       double* safety, int32_t mode, void* stream);
 

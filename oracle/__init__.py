@@ -48,6 +48,8 @@ def lib():
         L.orc_contains_nav.restype = None
         L.orc_safety_nav.argtypes = scene + [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int]
         L.orc_safety_nav.restype = None
+        L.orc_safety_estimate_nav.argtypes = scene + [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int]
+        L.orc_safety_estimate_nav.restype = None
         L.orc_adjoint.argtypes = scene + [ctypes.c_int64] + [dp] * 6 + [dp, dp, ip, dp, dp, ip]
         L.orc_adjoint.restype = None
         L.orc_shape_batch.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ip]
@@ -125,6 +127,17 @@ def safety(scene, tracks, nthreads: int = 1):
     kt, targs = _track_args(tracks, 3)
     out = np.empty(n)
     lib().orc_safety_nav(*sargs, n, *targs, _d(out)[1], int(nthreads))
+    return out
+
+
+def safety_estimate(scene, tracks, nthreads: int = 1):
+    """The under-estimating safety: min of the mother's and daughters' simpler
+    bounds (see geo_oracle.c); never above the exact safety."""
+    n = tracks.n
+    ks, sargs = _scene_args(scene)
+    kt, targs = _track_args(tracks, 3)
+    out = np.empty(n)
+    lib().orc_safety_estimate_nav(*sargs, n, *targs, _d(out)[1], int(nthreads))
     return out
 
 

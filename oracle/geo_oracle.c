@@ -948,6 +948,120 @@ static double safety_nav(const orc_scene *sc, const double *pw) {
 }
 
 /* ------------------------------------------------------------------ */
+/* the under-estimating safety (ROOT-style estimate)                     */
+/* ------------------------------------------------------------------ */
+/*
+ * A cheaper safety that may under-estimate (never over-estimate) the
+ * distance: every solid is replaced by a simpler bound.
+ *   Mother, point inside: box and tube the exact inside distance; cone the
+ *     least distance to the supporting lines of its meridian trapezoid (exact
+ *     for a convex section); tube segment and polycone 0 (no bound).
+ *   Daughter, point outside: box and tube the exact distance; cone the
+ *     largest signed distance to a supporting half-plane of its trapezoid
+ *     (z-slab, outer radius line, and the inner radius line when both inner
+ *     radii are positive), at least 0; tube segment the
+ *     distance to its whole tube; polycone the distance to its enclosing tube
+ *     (least inner and largest outer radius over its z-range); each of them
+ *     raised to the distance to the sphere circumscribing that bound (about
+ *     the box's, tube's or cone's origin, about the middle of a polycone's
+ *     z-range), if larger.
+ * Each is at most that solid's exact safety, so the navigator-level value
+ * min(mother, daughters) is at most the exact safety.
+ */
+static double rect_dist(double rho, double z, double rmin, double rmax, double zlo, double zhi) {
+    double dr = rho > rmax ? rho - rmax : (rho < rmin ? rmin - rho : 0.0);
+    double dz = z > zhi ? z - zhi : (z < zlo ? zlo - z : 0.0);
+    return sqrt(dr * dr + dz * dz);
+}
+
+static double estimate_in(int kind, const double *p, const double *x) {
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]), az = fabs(x[2]);
+    double s;
+    if (kind == K_BOX) {
+        s = p[0] - fabs(x[0]);
+        if (p[1] - fabs(x[1]) < s) s = p[1] - fabs(x[1]);
+        if (p[2] - az < s) s = p[2] - az;
+    } else if (kind == K_TUBE) {
+        s = p[1] - rho;
+        if (p[2] - az < s) s = p[2] - az;
+        if (p[0] > 0.0 && rho - p[0] < s) s = rho - p[0];
+    } else if (kind == K_CONE) {
+        double dz = p[0];
+        double bo = (p[4] - p[2]) / (2.0 * dz), bi = (p[3] - p[1]) / (2.0 * dz);
+        double ro = 0.5 * (p[2] + p[4]) + bo * x[2], ri = 0.5 * (p[1] + p[3]) + bi * x[2];
+        s = dz - az;
+        double e = (ro - rho) / sqrt(1.0 + bo * bo);
+        if (e < s) s = e;
+        if (p[1] > 0.0 || p[3] > 0.0) {
+            e = (rho - ri) / sqrt(1.0 + bi * bi);
+            if (e < s) s = e;
+        }
+    } else {
+        s = 0.0;
+    }
+    return s > 0.0 ? s : 0.0;
+}
+
+/* max(bound b, distance from x to the sphere of radius R about (0, 0, zc)) */
+static double with_sphere(double b, const double *x, double zc, double R) {
+    double dz = x[2] - zc;
+    double d = sqrt(x[0] * x[0] + x[1] * x[1] + dz * dz) - R;
+    return d > b ? d : b;
+}
+
+static double estimate_out(int kind, const double *p, const double *x) {
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+    if (kind == K_BOX) {
+        double a = fabs(x[0]) - p[0], b = fabs(x[1]) - p[1], c = fabs(x[2]) - p[2];
+        if (a < 0.0) a = 0.0;
+        if (b < 0.0) b = 0.0;
+        if (c < 0.0) c = 0.0;
+        return with_sphere(sqrt(a * a + b * b + c * c), x, 0.0, sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]));
+    }
+    if (kind == K_TUBE || kind == K_TUBS)
+        return with_sphere(rect_dist(rho, x[2], p[0], p[1], -p[2], p[2]), x, 0.0, sqrt(p[1] * p[1] + p[2] * p[2]));
+    if (kind == K_PCON) {
+        const int nz = (int)p[2];
+        const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+        double lo = rn[0], hi = rx[0];
+        for (int k = 1; k < nz; k++) {
+            if (rn[k] < lo) lo = rn[k];
+            if (rx[k] > hi) hi = rx[k];
+        }
+        double hz = 0.5 * (z[nz - 1] - z[0]);
+        return with_sphere(rect_dist(rho, x[2], lo, hi, z[0], z[nz - 1]), x, 0.5 * (z[0] + z[nz - 1]),
+                           sqrt(hi * hi + hz * hz));
+    }
+    double dz = p[0];
+    double bo = (p[4] - p[2]) / (2.0 * dz), bi = (p[3] - p[1]) / (2.0 * dz);
+    double ro = 0.5 * (p[2] + p[4]) + bo * x[2], ri = 0.5 * (p[1] + p[3]) + bi * x[2];
+    double s = fabs(x[2]) - dz;
+    double e = (rho - ro) / sqrt(1.0 + bo * bo);
+    if (e > s) s = e;
+    if (p[1] > 0.0 && p[3] > 0.0) {
+        e = (ri - rho) / sqrt(1.0 + bi * bi);
+        if (e > s) s = e;
+    }
+    double rm = p[2] > p[4] ? p[2] : p[4];
+    s = with_sphere(s, x, 0.0, sqrt(rm * rm + dz * dz));
+    return s > 0.0 ? s : 0.0;
+}
+
+static double safety_estimate_nav(const orc_scene *sc, const double *pw) {
+    double buf[PBUF];
+    const double *mp = MOTHER(sc, buf);
+    if (!orc_contains(sc->mkind, mp, pw)) return 0.0;
+    double s = estimate_in(sc->mkind, mp, pw);
+    for (int j = 0; j < sc->nd; j++) {
+        double x[3], u[3], zero[3] = { 0, 0, 0 };
+        to_local(sc, j, pw, zero, x, u);
+        double d = estimate_out(sc->kinds[j], DAUGHTER(sc, j, buf), x);
+        if (d < s) s = d;
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------ */
 /* adjoint of the step (implicit function rule on the winning surface)  */
 /* ------------------------------------------------------------------ */
 
@@ -1020,8 +1134,10 @@ static void *run_job(void *arg) {
             if (J->face) J->face[i] = r.face;
         } else if (J->what == 1) {
             J->where[i] = contains_nav(J->sc, pw);
-        } else {
+        } else if (J->what == 2) {
             J->safety[i] = safety_nav(J->sc, pw);
+        } else {
+            J->safety[i] = safety_estimate_nav(J->sc, pw);
         }
     }
     return NULL;
@@ -1078,6 +1194,14 @@ void orc_safety_nav(SCENE_ARGS, int64_t n, const double *px, const double *py,
     MAKE_SCENE;
     job J; memset(&J, 0, sizeof J);
     J.sc = &sc; J.px = px; J.py = py; J.pz = pz; J.safety = safety; J.what = 2;
+    run_threads(&J, n, nthreads);
+}
+
+void orc_safety_estimate_nav(SCENE_ARGS, int64_t n, const double *px, const double *py,
+                             const double *pz, double *safety, int nthreads) {
+    MAKE_SCENE;
+    job J; memset(&J, 0, sizeof J);
+    J.sc = &sc; J.px = px; J.py = py; J.pz = pz; J.safety = safety; J.what = 3;
     run_threads(&J, n, nthreads);
 }
 

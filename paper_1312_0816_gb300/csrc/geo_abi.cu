@@ -44,6 +44,7 @@ struct geo_batch_s {
     int blocks_per_sm = 0;
     int64_t ntiles = 0;
     int64_t max_end = 0;
+    int32_t segs = 0;
     VolView* d_vols = nullptr;
     BatchTile* d_tiles = nullptr;
     unsigned int* d_words = nullptr;   // [0] tile counter, [1] status
@@ -649,7 +650,7 @@ geo_status geo_safety(geo_volume v, const double* x, const double* y, const doub
                       int32_t mode, void* stream) {
     geo_status st = check_volume_device(v);
     if (st != GEO_OK) return st;
-    if (mode != GEO_FP64 && mode != GEO_FP32_REFINE) return GEO_ERR_INVALID_ARG;
+    if (mode != GEO_FP64 && mode != GEO_FP32_REFINE && mode != GEO_SAFETY_ESTIMATE) return GEO_ERR_INVALID_ARG;
     if ((st = check_basket(x, y, z, n)) != GEO_OK) return st;
     if (n == 0) return GEO_OK;
     if (!is_device_ptr(safety)) return GEO_ERR_INVALID_ARG;
@@ -782,6 +783,7 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     b->blocks_per_sm = bps;
     b->ntiles = int64_t(tiles.size());
     b->max_end = max_end;
+    for (int i = 0; i < n_vols; ++i) b->segs = b->segs || vols[i]->view.segs;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_vols, sizeof(VolView) * n_vols)) != cudaSuccess ||
@@ -834,6 +836,8 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
     bv.ntiles = b->ntiles;
     bv.counter = b->d_words;
     bv.status = b->d_words + 1;
+    bv.segs = b->segs;
+    bv.pad = 0;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
     return cuda_status(launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, s, num_sms_of(b->device)));
 }

@@ -113,6 +113,8 @@ struct BatchView {
     int64_t ntiles;
     unsigned int* counter;    // next tile to claim (reset before every launch)
     unsigned int* status;     // device error word of the batch
+    int32_t segs;             // 1 if a volume holds a tube segment or a polycone
+    int32_t pad;
 };
 
 // device error codes written to VolView::status
@@ -129,7 +131,7 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit,
                                 int blocks_per_sm, cudaStream_t s, int num_sms);
-int batched_max_blocks_per_sm();
+int batched_max_blocks_per_sm(bool segs);
 cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, int mode, cudaStream_t s,
                             int num_sms);
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
@@ -138,6 +140,8 @@ cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mo
 cudaError_t launch_contains_filter(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s,
                                    int num_sms);
 cudaError_t launch_safety_filter(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms);
+// the under-estimating safety (the FP32 lower bounds alone)
+cudaError_t launch_safety_estimate(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms);
 
 // One solid for geo_shape_query: its record and, for a polycone, its plane
 // table (the record's table address is not used: the kernel reads `table`).

@@ -139,6 +139,7 @@ cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, i
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,
                           int num_sms) {
     if (mode == GEO_FP32_REFINE) return launch_safety_filter(v, b, saf, s, num_sms);
+    if (mode == GEO_SAFETY_ESTIMATE) return launch_safety_estimate(v, b, saf, s, num_sms);
     GEO_LAUNCH(k_safety_fp64, v, b, saf);
 }
 

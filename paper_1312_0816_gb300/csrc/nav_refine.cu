@@ -222,6 +222,8 @@ struct __align__(16) TileHdr {
     int pad[3];
 };
 
+// SEGS = false: no volume of the batch holds a tube segment or a polycone.
+template <bool SEGS>
 __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
                                                               int32_t* __restrict__ hit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                     const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
                     double best;
                     int h, nev;
-                    refine_rest(vp, vp.d64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
+                    refine_rest<SEGS>(vp, vp.d64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
                     store_result(prev_base + t, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
                 }
             }
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
             for (int q = c; q < total; q += kCons) {
                 const int e = st_.task[q];
                 const int o = e & (kProd - 1), jj = (e >> 8) - 1;
-                st_.res[o] = eval64(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
+                st_.res[o] = eval64<SEGS>(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
                                     st_.pd[4][o], st_.pd[5][o]);
             }
             __syncwarp();
@@ -361,13 +363,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
     }
 }
 
-int batched_max_blocks_per_sm() {
+template <bool SEGS>
+static int batched_blocks_per_sm() {
     static int cached = 0;
     if (cached == 0) {
         const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
         int per_sm = 0;
-        if (cudaFuncSetAttribute(k_dist_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched, kThreads, smem) != cudaSuccess ||
+        if (cudaFuncSetAttribute(k_dist_batched<SEGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched<SEGS>, kThreads, smem) !=
+                cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;
@@ -377,16 +382,27 @@ int batched_max_blocks_per_sm() {
     return cached;
 }
 
+int batched_max_blocks_per_sm(bool segs) {
+    return segs ? batched_blocks_per_sm<true>() : batched_blocks_per_sm<false>();
+}
+
+template <bool SEGS>
+static cudaError_t launch_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
+                                  cudaStream_t s, int num_sms) {
+    const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
+    const int maxb = batched_blocks_per_sm<SEGS>();
+    const int per_sm = (blocks_per_sm <= 0 || blocks_per_sm > maxb) ? maxb : blocks_per_sm;
+    cudaError_t e = cudaFuncSetAttribute(k_dist_batched<SEGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_dist_batched<SEGS><<<per_sm * num_sms, kThreads, smem, s>>>(bv, b, step, hit);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
                                 cudaStream_t s, int num_sms) {
     static_assert(sizeof(TileHdr) % 16 == 0 && sizeof(VolView) % 16 == 0, "16-byte copies");
-    const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
-    const int maxb = batched_max_blocks_per_sm();
-    const int per_sm = (blocks_per_sm <= 0 || blocks_per_sm > maxb) ? maxb : blocks_per_sm;
-    cudaError_t e = cudaFuncSetAttribute(k_dist_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k_dist_batched<<<per_sm * num_sms, kThreads, smem, s>>>(bv, b, step, hit);
-    return cudaGetLastError();
+    return bv.segs ? launch_batched<true>(bv, b, step, hit, blocks_per_sm, s, num_sms)
+                   : launch_batched<false>(bv, b, step, hit, blocks_per_sm, s, num_sms);
 }
 
 template <typename K>

@@ -169,7 +169,7 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
     if (!(dd > 1e-30f && dd < 1e30f)) {
         // direction magnitude outside the range the FP32 bounds assume
         const double p[3] = {px, py, pz};
-        if (contains64(v.m64, p)) nav_all64<SEGS>(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
+        if (contains64<SEGS>(v.m64, p)) nav_all64<SEGS>(v.m64, tab64, v.nd, px, py, pz, qx, qy, qz, best, h);
         else { best = 0.0; h = -2; }
         nev = 1000;
         return;
@@ -183,7 +183,7 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
     bool inside = in_shrunk;
     if (!in_shrunk) {
         const double p[3] = {px, py, pz};
-        inside = contains64(v.m64, p);
+        inside = contains64<SEGS>(v.m64, p);
     }
     if (!inside) {
         best = 0.0;

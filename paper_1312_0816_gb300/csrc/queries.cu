@@ -12,7 +12,7 @@ namespace geonav {
 
 constexpr int kQueryTable32Max = 96 * 1024;   // bytes of FP32 records staged per block
 
-template <bool SMEM>
+template <bool SMEM, bool SEGS>
 __global__ void __launch_bounds__(256) k_contains32(VolView v, Basket b, int32_t* __restrict__ where) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_contains32(VolView v, Basket b, int32_t
         double p[3];
         float p32[3];
         point32(b, i, p, p32);
-        where[i] = contains_filter(v, t32, p, p32);
+        where[i] = contains_filter<SEGS>(v, t32, p, p32);
     }
 }
 
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) k_contains32(VolView v, Basket b, int32_t
 // instruction whatever the number of active lanes).  Each point then
 // finishes on its own thread (rarely with more FP64 work).  Which warp
 // evaluates a task does not change its value, so results are deterministic.
-template <bool SMEM>
+template <bool SMEM, bool SEGS>
 __global__ void __launch_bounds__(256) k_safety32(VolView v, Basket b, double* __restrict__ saf) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) k_safety32(VolView v, Basket b, double* _
         SafetyState st;
         st.Lm = st.L2 = 0.f;
         st.j1 = -1;
-        const bool in = live && safety_pass1(v, t32, p, p32, st);
+        const bool in = live && safety_pass1<SEGS>(v, t32, p, p32, st);
         const int bin = in ? (st.j1 < 0 ? 0 : 1 + t32[st.j1].kind) : -1;
         s_p[0][t] = p[0];
         s_p[1][t] = p[1];
@@ -84,14 +84,14 @@ __global__ void __launch_bounds__(256) k_safety32(VolView v, Basket b, double* _
         for (int q = t; q < total; q += 256) {
             const int o = s_list[q];
             const double po[3] = {s_p[0][o], s_p[1][o], s_p[2][o]};
-            s_res[o] = safety_of(v, s_task[o], po);
+            s_res[o] = safety_of<SEGS>(v, s_task[o], po);
         }
         __syncthreads();
         if (live) {
             double s = 0.0;
             if (in) {
                 int nev;
-                s = safety_finish(v, t32, p, p32, st, s_res[t], tau, &nev);
+                s = safety_finish<SEGS>(v, t32, p, p32, st, s_res[t], tau, &nev);
             }
             saf[i] = s;
         }
@@ -99,26 +99,75 @@ __global__ void __launch_bounds__(256) k_safety32(VolView v, Basket b, double* _
     }
 }
 
-#define GEO_LAUNCH32(KER, ...)                                                                  \
-    do {                                                                                        \
-        const int bytes = v.nd * int(sizeof(ShapeRec32));                                       \
-        if (bytes <= kQueryTable32Max) {                                                        \
-            cudaError_t e = prep(KER<true>, bytes);                                             \
-            if (e != cudaSuccess) return e;                                                     \
-            KER<true><<<blocks_for(KER<true>, b.n, bytes, num_sms), 256, bytes, s>>>(__VA_ARGS__); \
-        } else {                                                                                \
-            KER<false><<<blocks_for(KER<false>, b.n, 0, num_sms), 256, 0, s>>>(__VA_ARGS__);      \
-        }                                                                                       \
-        return cudaGetLastError();                                                              \
-    } while (0)
+// The under-estimating safety (GEO_SAFETY_ESTIMATE): the FP32 pass alone.
+// Every solid's bound is its inflated (mother: deflated) FP32 copy's
+// distance lowered by a relative 2^-18: box and tube the exact distance to
+// the copy, cone the largest supporting half-plane distance, tube segment
+// and polycone their enclosing tube, segment and polycone mothers 0; a
+// daughter's bound is raised to the distance to its copy's bounding sphere
+// where that is larger, so the sphere cull cannot change the minimum.  The
+// minimum is a lower bound of the exact safety; no FP64 work but the
+// mother's containment test where its FP32 copies cannot decide.
+template <bool SMEM, bool SEGS>
+__global__ void __launch_bounds__(256) k_safety_est(VolView v, Basket b, double* __restrict__ saf) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    const ShapeRec32* t32 = v.d32;
+    if (SMEM) {
+        if (!stage_table(smem_raw, v.d32, uint32_t(v.nd) * sizeof(ShapeRec32), &bar, v.status)) return;
+        t32 = reinterpret_cast<const ShapeRec32*>(smem_raw);
+    }
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < b.n; i += stride) {
+        double p[3];
+        float p32[3];
+        point32(b, i, p, p32);
+        float L = 0.f;
+        if (mother_contains<SEGS>(v, p, p32)) {
+            L = safety_in_lb32(v.m32, p32);
+            for (int j = 0; j < v.nd && L > 0.f; ++j) {
+                const ShapeRec32& r = t32[j];
+                float o[3], x[3];
+                const float c2 = offset32(r, p32, o);
+                if (beyond(r, c2, L)) continue;   // the whole copy is farther than L
+                local32(r, o, x);
+                L = fminf(L, fmaxf(safety_out_lb32(r, x), sphere_lb32(r, c2)));
+            }
+        }
+        saf[i] = double(L);
+    }
+}
+
+// the FP32 table staged when it fits; the polycone's code only for volumes
+// holding segments or polycones
+template <bool SEGS, typename K1, typename K0, typename... A>
+static cudaError_t launch32(K1 staged, K0 global, const VolView& v, const Basket& b, cudaStream_t s, int num_sms,
+                            A... args) {
+    const int bytes = v.nd * int(sizeof(ShapeRec32));
+    if (bytes <= kQueryTable32Max) {
+        cudaError_t e = prep(staged, bytes);
+        if (e != cudaSuccess) return e;
+        staged<<<blocks_for(staged, b.n, bytes, num_sms), 256, bytes, s>>>(v, b, args...);
+    } else {
+        global<<<blocks_for(global, b.n, 0, num_sms), 256, 0, s>>>(v, b, args...);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_contains_filter(const VolView& v, const Basket& b, int32_t* where, cudaStream_t s,
                                    int num_sms) {
-    GEO_LAUNCH32(k_contains32, v, b, where);
+    if (v.segs) return launch32<true>(k_contains32<true, true>, k_contains32<false, true>, v, b, s, num_sms, where);
+    return launch32<false>(k_contains32<true, false>, k_contains32<false, false>, v, b, s, num_sms, where);
+}
+
+cudaError_t launch_safety_estimate(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms) {
+    if (v.segs) return launch32<true>(k_safety_est<true, true>, k_safety_est<false, true>, v, b, s, num_sms, saf);
+    return launch32<false>(k_safety_est<true, false>, k_safety_est<false, false>, v, b, s, num_sms, saf);
 }
 
 cudaError_t launch_safety_filter(const VolView& v, const Basket& b, double* saf, cudaStream_t s, int num_sms) {
-    GEO_LAUNCH32(k_safety32, v, b, saf);
+    if (v.segs) return launch32<true>(k_safety32<true, true>, k_safety32<false, true>, v, b, s, num_sms, saf);
+    return launch32<false>(k_safety32<true, false>, k_safety32<false, false>, v, b, s, num_sms, saf);
 }
 
 }  // namespace geonav

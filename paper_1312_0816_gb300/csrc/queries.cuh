@@ -42,10 +42,12 @@ __device__ __forceinline__ void point32(const Basket& b, int64_t i, double* p, f
 // Mother containment: FP32 on the deflated copy (surely inside), on the
 // inflated copy (surely outside), FP64 in between.  Non-finite points fail
 // both FP32 tests and come out outside, as in FP64.
+// SEGS = false: the volume holds no polycone (its code is left out).
+template <bool SEGS = true>
 __device__ __forceinline__ bool mother_contains(const VolView& v, const double* p, const float* p32) {
     if (contains32(v.m32, p32)) return true;
     if (!contains32(v.m32u, p32)) return false;
-    return contains64(v.m64, p);
+    return contains64<SEGS>(v.m64, p);
 }
 
 // Offset from the daughter's centre, its squared length and the local point.
@@ -62,9 +64,10 @@ __device__ __forceinline__ void local32(const ShapeRec32& r, const float* w, flo
 }
 
 // Contains of one point: -2, -1 or the lowest daughter index.
+template <bool SEGS = true>
 __device__ __forceinline__ int contains_filter(const VolView& v, const ShapeRec32* __restrict__ t32,
                                                const double* p, const float* p32) {
-    if (!mother_contains(v, p, p32)) return -2;
+    if (!mother_contains<SEGS>(v, p, p32)) return -2;
     for (int j = 0; j < v.nd; ++j) {
         const ShapeRec32& r = t32[j];
         float o[3], x[3];
@@ -75,19 +78,20 @@ __device__ __forceinline__ int contains_filter(const VolView& v, const ShapeRec3
         const ShapeRec64& r64 = v.d64[j];
         double xl[3];
         point_to_local64(r64, p[0], p[1], p[2], xl);
-        if (contains64(r64, xl)) return j;
+        if (contains64<SEGS>(r64, xl)) return j;
     }
     return -1;
 }
 
 // FP64 safety of candidate k (-1: mother inside-safety, else daughter k's
 // outside-safety), with the plain kernel's routines.
+template <bool SEGS = true>
 __device__ __forceinline__ double safety_of(const VolView& v, int k, const double* p) {
-    if (k < 0) return safety64(v.m64, p, true);
+    if (k < 0) return safety64<SEGS>(v.m64, p, true);
     const ShapeRec64& r = v.d64[k];
     double x[3];
     point_to_local64(r, p[0], p[1], p[2], x);
-    return safety64(r, x, false);
+    return safety64<SEGS>(r, x, false);
 }
 
 // FP32 threshold above which a lower bound proves an FP64 safety larger than
@@ -95,6 +99,13 @@ __device__ __forceinline__ double safety_of(const VolView& v, int k, const doubl
 // margin), and tau above the FP64 rounding of any safety in the mother.
 __device__ __forceinline__ float above(double s, float tau) {
     return fmaf(f64_to_f32_up(s), 1.f + 9.536743e-07f, tau);
+}
+
+// Lower bound of the distance to daughter r from its bounding sphere (the
+// inflated radius covers the FP32 position errors; the square root is
+// lowered by the relative margin).
+__device__ __forceinline__ float sphere_lb32(const ShapeRec32& r, float c2) {
+    return fsqrt(c2) * (1.f - kSafMargin) - r.brad;
 }
 
 // Bounding-sphere cull of daughter r against a bound L: true when the whole
@@ -112,9 +123,10 @@ struct SafetyState {
     int j1;
 };
 
+template <bool SEGS = true>
 __device__ __forceinline__ bool safety_pass1(const VolView& v, const ShapeRec32* __restrict__ t32, const double* p,
                                              const float* p32, SafetyState& st) {
-    if (!mother_contains(v, p, p32)) return false;
+    if (!mother_contains<SEGS>(v, p, p32)) return false;
     const float Lm = safety_in_lb32(v.m32, p32);
     float L1 = Lm, L2 = f_inf();
     int j1 = -1;
@@ -142,6 +154,7 @@ __device__ __forceinline__ bool safety_pass1(const VolView& v, const ShapeRec32*
 // Given s = the FP64 safety of candidate j1: done if the second bound
 // exceeds s; otherwise every other candidate whose bound does not exceed the
 // running minimum is evaluated in FP64.  *nev counts the evaluations.
+template <bool SEGS = true>
 __device__ __forceinline__ double safety_finish(const VolView& v, const ShapeRec32* __restrict__ t32,
                                                 const double* p, const float* p32, const SafetyState& st,
                                                 double s, float tau, int* nev) {
@@ -150,7 +163,7 @@ __device__ __forceinline__ double safety_finish(const VolView& v, const ShapeRec
     if (!(st.L2 > th)) {
         // another candidate may still be below s: visit them all
         if (st.j1 >= 0 && !(st.Lm > th)) {
-            s = fmin(s, safety_of(v, -1, p));
+            s = fmin(s, safety_of<SEGS>(v, -1, p));
             ++ne;
             th = above(s, tau);
         }
@@ -162,7 +175,7 @@ __device__ __forceinline__ double safety_finish(const VolView& v, const ShapeRec
             if (beyond(r, c2, th)) continue;
             local32(r, o, x);
             if (safety_out_lb32(r, x) > th) continue;
-            s = fmin(s, safety_of(v, j, p));
+            s = fmin(s, safety_of<SEGS>(v, j, p));
             ++ne;
             th = above(s, tau);
         }
@@ -172,14 +185,15 @@ __device__ __forceinline__ double safety_finish(const VolView& v, const ShapeRec
 }
 
 // Safety of one point (the two phases back to back).
+template <bool SEGS = true>
 __device__ __forceinline__ double safety_filter(const VolView& v, const ShapeRec32* __restrict__ t32,
                                                 const double* p, const float* p32, float tau, int* nev) {
     SafetyState st;
-    if (!safety_pass1(v, t32, p, p32, st)) {
+    if (!safety_pass1<SEGS>(v, t32, p, p32, st)) {
         *nev = 0;
         return 0.0;
     }
-    return safety_finish(v, t32, p, p32, st, safety_of(v, st.j1, p), tau, nev);
+    return safety_finish<SEGS>(v, t32, p, p32, st, safety_of<SEGS>(v, st.j1, p), tau, nev);
 }
 
 // 2^-36 of the mother's extent: far above the FP64 rounding of any safety

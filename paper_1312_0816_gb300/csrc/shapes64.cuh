@@ -153,11 +153,15 @@ static __device__ __noinline__ bool pcon_contains64(const double* d, const doubl
 }
 
 // ------------------------------------------------------------- contains ---
+// SEGS = false (here and below): the caller's volumes hold no polycone, and
+// its out-of-line code (whose registers a kernel that calls it must provide)
+// is left out.
+template <bool SEGS = true>
 __device__ __forceinline__ bool contains64(const ShapeRec64& r, const double* x) {
     const double* d = r.d;
     if (r.kind == KBOX) return ABS_LE(x[0], d[0]) && ABS_LE(x[1], d[1]) && ABS_LE(x[2], d[2]);
     const double rho2 = rho2_of(x);
-    if (r.kind == KPCON) return pcon_contains64(d, pcon_table(d), x[0], x[1], x[2]);
+    if (SEGS && r.kind == KPCON) return pcon_contains64(d, pcon_table(d), x[0], x[1], x[2]);
     if (r.kind == KTUBE) return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2);
     if (r.kind == KTUBS)
         return ABS_LE(x[2], d[2]) && LE(rho2, d[4]) && LE(d[3], rho2) && wedge_has64(d, x[0], x[1]);
@@ -767,11 +771,12 @@ static __device__ __noinline__ double pcon_safety64(const double* d, const doubl
 
 // Distance to the boundary from a point inside (inside == true) or outside.
 // Returns 0 if the point is on the other side.
+template <bool SEGS = true>
 __device__ __forceinline__ double safety64(const ShapeRec64& r, const double* x, bool inside) {
-    const bool in = contains64(r, x);
+    const bool in = contains64<SEGS>(r, x);
     if (in != inside) return 0.0;
     const double* d = r.d;
-    if (r.kind == KPCON) return pcon_safety64(d, pcon_table(d), x[0], x[1], x[2], in);
+    if (SEGS && r.kind == KPCON) return pcon_safety64(d, pcon_table(d), x[0], x[1], x[2], in);
     if (r.kind == KBOX) {
         const double a = SUB(fabs(x[0]), d[0]), b = SUB(fabs(x[1]), d[1]), c = SUB(fabs(x[2]), d[2]);
         if (in) return -fmax(a, fmax(b, c));

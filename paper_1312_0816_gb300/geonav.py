@@ -17,6 +17,7 @@ from . import build_lib
 GEO_OK = 0
 GEO_FP64 = 0
 GEO_FP32_REFINE = 1
+GEO_SAFETY_ESTIMATE = 2   # geo_safety only: the cheaper under-estimate
 GEO_BOX, GEO_TUBE, GEO_CONE, GEO_TUBS, GEO_PCON = 0, 1, 2, 3, 4
 GEO_MAX_PLANES = 32
 
@@ -261,8 +262,9 @@ def geo_contains(vol: Volume, x, y, z, mode: int = GEO_FP32_REFINE, where=None, 
 
 
 def geo_safety(vol: Volume, x, y, z, mode: int = GEO_FP32_REFINE, safety=None, stream=None):
-    """Navigator-level Safety (exact Euclidean; same FP64 value in both
-    modes)."""
+    """Navigator-level Safety: exact Euclidean in GEO_FP64 and GEO_FP32_REFINE
+    (the same FP64 value), or the cheaper lower bound with
+    GEO_SAFETY_ESTIMATE."""
     import torch
 
     n = int(x.numel())

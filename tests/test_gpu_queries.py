@@ -110,3 +110,67 @@ def test_mother_only_volume(g, orc):
         got = g.geo_safety(vol, *x, mode=m).cpu().numpy()
         assert np.max(np.abs(got - orc.safety(sc, tr))) <= STEP_TOL
     vol.close()
+
+
+EPS32 = 2.0 ** -24
+
+
+def _radius_and_slope(kind, row, pcon_planes=None):
+    """Bounding radius of the solid's FP32 copy and its largest radius slope
+    squared (a segment or polycone is copied as its enclosing tube)."""
+    if kind == scenes.BOX:
+        return float(np.sqrt(np.sum(np.asarray(row[:3]) ** 2))), 0.0
+    if kind in (scenes.TUBE, scenes.TUBS):
+        return float(np.hypot(row[1], row[2])), 0.0
+    if kind == scenes.PCON:
+        z, _, rx = pcon_planes
+        return float(np.hypot(rx.max(), 0.5 * (z[-1] - z[0]))), 0.0
+    dz = row[0]
+    b2 = max(((row[4] - row[2]) / (2 * dz)) ** 2, ((row[3] - row[1]) / (2 * dz)) ** 2)
+    return float(np.hypot(max(row[2], row[4]), dz)), b2
+
+
+def inflation_bound(sc):
+    """An upper bound of the FP32 inflation of the volume's solids, from the
+    builder's rule: eps32 (48 S + 16 br) for the rounding of positions and of
+    the shape arithmetic, plus a discriminant term that its radius floor
+    bounds by 32 sqrt(eps32) br (1 + b^2); S is the mother's extent."""
+    if sc.mother_kind == scenes.PCON:
+        z, _, rx = sc.planes_of(sc.mother_params)
+        S = float(np.sqrt(rx * rx + z * z).max())
+    else:
+        S, _ = _radius_and_slope(sc.mother_kind, sc.mother_params)
+    worst = 0.0
+    solids = [(sc.mother_kind, sc.mother_params)] + [(int(k), sc.params[j]) for j, k in enumerate(sc.kinds)]
+    for kind, row in solids:
+        br, b2 = _radius_and_slope(kind, row, sc.planes_of(row) if kind == scenes.PCON else None)
+        d = EPS32 * (48 * S + 16 * br)
+        if kind != scenes.BOX:
+            d += 32 * np.sqrt(EPS32) * br * (1 + b2)
+        worst = max(worst, d)
+    return worst
+
+
+@pytest.mark.parametrize("idx", range(10))
+def test_safety_estimate(g, orc, idx):
+    """GEO_SAFETY_ESTIMATE: never above the exact safety nor above the defined
+    bound (the oracle's estimate), and below that bound by at most twice the
+    FP32 inflation plus a relative 2^-16; 0 for non-finite points."""
+    sc = scene_list()[idx]
+    vol = g.geo_build_volume(sc)
+    tol_abs = 2.0 * inflation_bound(sc)
+    uniform = scenes.sample_tracks(sc, 50000, 20 + idx, exclusive=False)
+    for tr in (uniform, hard_points(orc, sc, 20000, 30 + idx)):
+        est = g.geo_safety(vol, *dev3(tr), mode=2).cpu().numpy()
+        want = orc.safety_estimate(sc, tr, nthreads=8)
+        exact = orc.safety(sc, tr, nthreads=8)
+        finite = np.isfinite(tr.x) & np.isfinite(tr.y) & np.isfinite(tr.z)
+        assert np.all(est[~finite] == 0.0)
+        assert np.all(est >= 0.0)
+        assert np.all(est <= exact + 1e-12 * (1.0 + exact)), sc.name
+        assert np.all(est <= want + 1e-12 * (1.0 + want)), sc.name
+        assert np.all(est >= want - tol_abs - 2.0 ** -16 * want), (sc.name, float(np.max(want - est)), tol_abs)
+        if tr is uniform and sc.mother_kind not in (scenes.TUBS, scenes.PCON):
+            pos = exact > 0
+            assert np.mean(est[pos] / exact[pos]) > 0.9, sc.name   # a useful bound, not just a valid one
+    vol.close()
