@@ -955,7 +955,11 @@ static double safety_nav(const orc_scene *sc, const double *pw) {
  * distance: every solid is replaced by a simpler bound.
  *   Mother, point inside: box and tube the exact inside distance; cone the
  *     least distance to the supporting lines of its meridian trapezoid (exact
- *     for a convex section); tube segment and polycone 0 (no bound).
+ *     for a convex section); a whole-turn polycone whose z-range holds its
+ *     origin the inside distance of its inscribed tube (radii from the
+ *     largest inner to the least outer radius, half-length the nearer end
+ *     plane's distance to the origin), 0 outside that tube; tube segments
+ *     and other polycones 0 (no bound).
  *   Daughter, point outside: box and tube the exact distance; cone the
  *     largest signed distance to a supporting half-plane of its trapezoid
  *     (z-slab, outer radius line, and the inner radius line when both inner
@@ -996,6 +1000,19 @@ static double estimate_in(int kind, const double *p, const double *x) {
             e = (rho - ri) / sqrt(1.0 + bi * bi);
             if (e < s) s = e;
         }
+    } else if (kind == K_PCON && !(p[1] < 2.0 * ORC_PI)) {
+        const int nz = (int)p[2];
+        const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+        double lo = rn[0], hi = rx[0];
+        for (int k = 1; k < nz; k++) {
+            if (rn[k] > lo) lo = rn[k];
+            if (rx[k] < hi) hi = rx[k];
+        }
+        if (!(z[0] < 0.0 && z[nz - 1] > 0.0 && lo < hi)) return 0.0;
+        double hz = -z[0] < z[nz - 1] ? -z[0] : z[nz - 1];
+        s = hi - rho;
+        if (hz - az < s) s = hz - az;
+        if (lo > 0.0 && rho - lo < s) s = rho - lo;
     } else {
         s = 0.0;
     }

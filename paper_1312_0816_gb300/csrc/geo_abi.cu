@@ -174,6 +174,31 @@ geo_placed_shape bounding_tube(const geo_placed_shape& s, bool centered) {
     return t;
 }
 
+// A tube inside a whole-turn polycone, about its origin: radii from the
+// largest inner to the least outer radius (every section's radii lie between
+// its planes' values), half-length the smaller distance from the origin to an
+// end plane.  false when there is none (a wedge, the origin outside the
+// z-range, or no common radius).
+bool inscribed_tube(const geo_placed_shape& s, geo_placed_shape& t) {
+    const int n = pcon_nz(s);
+    const double *z = s.planes, *rn = z + n, *rx = rn + n;
+    if (s.p[1] < 2.0 * kPi || !(z[0] < 0.0 && z[n - 1] > 0.0)) return false;
+    double lo = rn[0], hi = rx[0];
+    for (int k = 1; k < n; ++k) {
+        lo = std::max(lo, rn[k]);
+        hi = std::min(hi, rx[k]);
+    }
+    if (!(lo < hi)) return false;
+    t = s;
+    t.kind = GEO_TUBE;
+    t.planes = nullptr;
+    t.p[0] = lo;
+    t.p[1] = hi;
+    t.p[2] = std::min(-z[0], z[n - 1]);
+    t.p[3] = t.p[4] = 0.0;
+    return true;
+}
+
 // plane table of a polycone (layout in geo_internal.h)
 std::vector<double> pcon_table_host(const geo_placed_shape& s) {
     const int n = pcon_nz(s);
@@ -245,6 +270,9 @@ ShapeRec64 make_rec64(const geo_placed_shape& s, const double* table = nullptr) 
 // tube (centered: about its origin, for a mother).
 bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32& r, bool centered = false) {
     if (s.kind == GEO_PCON && grow >= 0) return make_rec32(bounding_tube(s, centered), grow, delta, r);
+    geo_placed_shape in;
+    // a shrunk polycone: its inscribed tube shrunk (when that survives)
+    if (s.kind == GEO_PCON && inscribed_tube(s, in) && make_rec32(in, grow, delta, r)) return true;
     std::memset(&r, 0, sizeof r);
     for (int k = 0; k < 9; ++k) r.R[k] = float(s.rot[k]);
     bool eye = true;
@@ -261,8 +289,9 @@ bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32
             if (!(p[k] + g > 0)) return false;
         }
     } else if ((s.kind == GEO_TUBS || s.kind == GEO_PCON) && g < 0) {
-        // a shrunk whole tube is no subset of a segment (nor of a polycone):
-        // an empty solid, so the filter never decides "surely inside" there
+        // a shrunk whole tube is no subset of a segment (nor of a polycone
+        // without an inscribed tube): an empty solid, so the filter never
+        // decides "surely inside" there
         r.kind = GEO_TUBE;
         r.e[0] = 0.f; r.e[1] = -1.f; r.e[2] = -1.f; r.e[3] = 0.f;
     } else if (s.kind == GEO_TUBE || s.kind == GEO_TUBS) {

@@ -31,10 +31,10 @@ def test_never_above_the_exact_safety(orc, name, seed):
     assert np.all(est >= 0.0)
     # the two formulas round differently: a few ulps of the extent
     assert np.all(est <= exact + 1e-12 * (1.0 + exact))
-    if sc.mother_kind in (scenes.TUBS, scenes.PCON):
+    if sc.mother_kind == scenes.TUBS:
         assert np.all(est == 0.0)     # such a mother has no bound
     else:
-        assert np.mean(est > 0.0) > 0.5
+        assert np.mean(est > 0.0) > 0.3
 
 
 def test_exact_where_every_bound_is_exact(orc):
@@ -115,10 +115,17 @@ def test_polycone_enclosing_tube(orc):
     assert est[2] == pytest.approx(15.0, rel=1e-15) and exact[2] == pytest.approx(15.0, rel=1e-15)
 
 
-def test_segment_and_polycone_mothers_give_zero(orc):
-    sc = scenes.pconm()
-    tr = scenes.sample_tracks(sc, 5000, 54)
-    assert np.all(orc.safety_estimate(sc, tr) == 0.0)
+def test_polycone_mother_inscribed_tube(orc):
+    """pconm (outer radius 80 narrowing to 40 at z = 0, z -100..100, no
+    daughter near the axis at z = +-90): its inscribed tube is r <= 40,
+    |z| <= 100, so at (10, 0, 90) the mother's bound is min(40 - 10, 100 - 90)
+    = 10, at (60, 0, 90), outside the tube, 0."""
+    sc = scenes.Scene("m", scenes.PCON, scenes.pconm().mother_params, np.zeros(0, np.int32), np.zeros((0, 5)),
+                      np.zeros((0, 9)), np.zeros((0, 3)), scenes.pconm().pdata)
+    tr = tracks_from(np.array([[10.0, 0, 90.0], [60.0, 0, 90.0]]), np.tile([1.0, 0, 0], (2, 1)))
+    est, exact = orc.safety_estimate(sc, tr), orc.safety(sc, tr)
+    assert est[0] == 10.0 and exact[0] == 10.0
+    assert est[1] == 0.0 and exact[1] == pytest.approx(10.0, rel=1e-15)
 
 
 def test_cone_mother_inside_is_exact(orc):
