@@ -43,6 +43,11 @@ SOLIDS = [
     (4, scenes.Pcon((-15.0, 15.0), (4.0, 8.0), (12.0, 18.0), 2.0, 3.9)),
     (4, scenes.Pcon(tuple(-33.0 + 6.0 * k for k in range(12)), tuple(2.0 + (k % 2) * 3.0 for k in range(12)),
                     tuple(10.0 + (k % 2) * 8.0 + k for k in range(12)))),
+    # limits: pointed tips, a pinch in a non-convex wedge, the largest plane count
+    (4, scenes.Pcon((-20.0, 0.0, 20.0), (0.0, 0.0, 0.0), (0.0, 15.0, 0.0))),
+    (4, scenes.Pcon((-20.0, 0.0, 20.0), (5.0, 10.0, 5.0), (15.0, 10.0, 15.0), 0.3, 5.0)),
+    (4, scenes.Pcon(tuple(-31.0 + 2.0 * k for k in range(32)), tuple(1.0 + (k % 3) for k in range(32)),
+                    tuple(6.0 + 4.0 * (k % 2) + 0.2 * k for k in range(32)))),
 ]
 WHAT = {"dist_out": 0, "dist_in": 1, "safety_out": 2, "safety_in": 3, "contains": 4}
 

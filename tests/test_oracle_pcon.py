@@ -27,7 +27,15 @@ BOB = Pcon((-30.0, -25.0, -20.0, 20.0, 25.0, 30.0), (0.0,) * 6, (25.0, 25.0, 10.
 SHELL = Pcon((-25.0, -5.0, 5.0, 25.0), (5.0, 10.0, 10.0, 5.0), (15.0, 20.0, 20.0, 15.0))
 WEDGE = Pcon((-20.0, 0.0, 20.0), (0.0, 5.0, 0.0), (20.0, 25.0, 15.0), -1.0, 4.2)
 CONS = Pcon((-20.0, 20.0), (0.0, 5.0), (20.0, 10.0), 0.5, 1.3)
-ALL = [BOB, SHELL, WEDGE, CONS]
+# limits and degenerate forms: pointed tips (outer radius 0 on the end
+# planes), a pinch (the two sections meet in a circle at z = 0), the
+# largest plane count
+TIPS = Pcon((-20.0, 0.0, 20.0), (0.0, 0.0, 0.0), (0.0, 15.0, 0.0))
+PINCH = Pcon((-20.0, 0.0, 20.0), (5.0, 10.0, 5.0), (15.0, 10.0, 15.0), 0.3, 5.0)
+ZIG32 = Pcon(tuple(-31.0 + 2.0 * k for k in range(32)), tuple(1.0 + (k % 3) for k in range(32)),
+             tuple(6.0 + 4.0 * (k % 2) + 0.2 * k for k in range(32)))
+ALL = [BOB, SHELL, WEDGE, CONS, TIPS, PINCH, ZIG32]
+IDS = ["bobbin", "shell", "wedge", "cons", "tips", "pinch", "zig32"]
 
 
 def rays(n, seed, box=60.0):
@@ -202,7 +210,7 @@ def test_cauchy_mean_chord_convex_polycone(orc):
 
 # ------------------------------------------------- against the membership test
 
-@pytest.mark.parametrize("pc", ALL, ids=["bobbin", "shell", "wedge", "cons"])
+@pytest.mark.parametrize("pc", ALL, ids=IDS)
 def test_distances_against_membership_march(orc, pc):
     """Before DistFromOutside every point of the ray is outside, just after it
     inside; before DistFromInside every point is inside, just after it
@@ -272,7 +280,7 @@ def surface_points(pc, n, seed):
     return np.concatenate(out)
 
 
-@pytest.mark.parametrize("pc", ALL, ids=["bobbin", "shell", "wedge", "cons"])
+@pytest.mark.parametrize("pc", ALL, ids=IDS)
 def test_safety_against_sampled_surface(orc, pc):
     """Exact safety <= distance to every surface point, and within the
     sampling resolution of the nearest sampled one."""
