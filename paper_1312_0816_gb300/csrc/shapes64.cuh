@@ -367,11 +367,7 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
 // and inner cone crossed outwards at a height inside the section's z-range
 // and an azimuth in the wedge.  Sections are visited in the order the track
 // meets them, from the one holding its start, and the visit stops at the
-// first section beyond the best candidate so far (the segment search).  A
-// section whose z-range the track crosses (before the best candidate) only
-// farther from the axis than the section's largest outer radius is skipped
-// without its roots: no crossing of its surfaces lies in its range there
-// (the test keeps a relative margin of 1e-9 over every rounding).
+// first section beyond the best candidate so far (the segment search).
 template <bool FACE = false, bool REENTRY = false>
 __device__ __forceinline__ double pcon_out64(const double* d, const double* T, const double* x, const double* u,
                                              int* face = nullptr) {
@@ -409,27 +405,8 @@ __device__ __forceinline__ double pcon_out64(const double* d, const double* T, c
     }
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
-    // closest approach of the line to the axis, and 1/u_z
-    const double tax = IS_POS(A0) ? DIV(-B0, A0) : 0.0;
-    const double iuz = IS_ZERO(u[2]) ? 0.0 : DIV(1.0, u[2]);
     auto section = [&](int k) {
         const double zk = z[k], zk1 = z[k + 1], dz0 = SUB(x[2], zk);
-        {   // cull: the least rho^2 over the part of the track in the section
-            double lo = 0.0, hi = best;
-            if (!IS_ZERO(u[2])) {
-                const double ta = MUL(SUB(zk, x[2]), iuz), tb = MUL(SUB(zk1, x[2]), iuz);
-                const double w = 1e-9 * (fabs(ta) + fabs(tb) + 1.0);
-                lo = fmax(lo, SUB(fmin(ta, tb), w));
-                hi = fmin(hi, ADD(fmax(ta, tb), w));
-            }
-            if (lo <= hi) {
-                const double t = fmin(fmax(tax, lo), hi);
-                const double r2 = FMA(t, FMA(A0, t, ADD(B0, B0)), rho2);
-                const double rm = fmax(rx[k], rx[k + 1]);
-                const double mag = FMA(fabs(t), FMA(A0, fabs(t), 2.0 * fabs(B0)), rho2) + MUL(rm, rm);
-                if (r2 > FMA(rm, rm, 1e-9 * mag)) return;
-            }
-        }
         {   // outer cone, crossed inwards
             const double ro0 = FMA(bo[k], dz0, rx[k]), rs = MUL(bo[k], u[2]);
             const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
@@ -614,12 +591,7 @@ __device__ __noinline__ double tubs_in64_call(const double* d, double x0, double
 // first violation of a radius constraint is the first crossing of a
 // section's outer cone outwards (or inner cone inwards) at a height inside
 // that section's z-range; sections are visited from the start's, in the
-// track's direction, up to the least exit so far.  A section is skipped when
-// the part of the track in it (before the least exit so far) stays nearer
-// the axis than its least outer radius and farther than its largest inner
-// radius (rho^2 along the line is convex: its largest value is at an end,
-// its least at the closest approach), with a relative margin of 1e-9 over
-// every rounding.
+// track's direction, up to the least exit so far.
 template <bool FACE = false>
 __device__ __forceinline__ double pcon_in64(const double* d, const double* T, const double* x, const double* u,
                                             int* face = nullptr) {
@@ -641,29 +613,8 @@ __device__ __forceinline__ double pcon_in64(const double* d, const double* T, co
         take(clamp0(DIV(SUB(up ? z[n - 1] : z[0], x[2]), u[2])), up ? 5 : 4);
     }
     if (d[10] == 0.0) wedge_exit64(d, x, u, take);
-    const double tax = IS_POS(A0) ? DIV(-B0, A0) : 0.0;
-    const double iuz = IS_ZERO(u[2]) ? 0.0 : DIV(1.0, u[2]);
     auto section = [&](int k) {
         const double zk = z[k], zk1 = z[k + 1], dz0 = SUB(x[2], zk);
-        {   // cull
-            double lo = 0.0, hi = t;
-            if (!IS_ZERO(u[2])) {
-                const double ta = MUL(SUB(zk, x[2]), iuz), tb = MUL(SUB(zk1, x[2]), iuz);
-                const double w = 1e-9 * (fabs(ta) + fabs(tb) + 1.0);
-                lo = fmax(lo, SUB(fmin(ta, tb), w));
-                hi = fmin(hi, ADD(fmax(ta, tb), w));
-            }
-            if (!(lo <= hi)) return;
-            if (hi < d_inf()) {
-                auto r2at = [&](double q) { return FMA(q, FMA(A0, q, ADD(B0, B0)), rho2); };
-                auto mag = [&](double q) { return FMA(fabs(q), FMA(A0, fabs(q), 2.0 * fabs(B0)), rho2); };
-                const double tm = fmin(fmax(tax, lo), hi);
-                const double rmax2 = fmax(r2at(lo), r2at(hi)), rmin2 = r2at(tm);
-                const double ro = fmin(rx[k], rx[k + 1]), ri = fmax(rn[k], rn[k + 1]);
-                const double m = 1e-9 * (fmax(mag(lo), mag(hi)) + MUL(ro, ro) + MUL(ri, ri));
-                if (rmax2 < FMA(ro, ro, -m) && rmin2 > FMA(ri, ri, m)) return;
-            }
-        }
         {   // outer cone, crossed outwards
             const double ro0 = FMA(bo[k], dz0, rx[k]), rs = MUL(bo[k], u[2]);
             const double s = root_rising(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
