@@ -74,10 +74,8 @@ __device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : (
 
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
 
-// SEGS: one block per SM, so that the segment and polycone routines the
-// kernel calls get their registers (two blocks would cap it at 80 and spill)
 template <bool SMEM, int TRAV, bool SEGS>
-__global__ void __launch_bounds__(kThreads, SEGS ? 1 : 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
+__global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
                                                              int32_t* __restrict__ hit,
                                                              double* __restrict__ bpoint,
                                                              int32_t* __restrict__ nref) {
@@ -226,7 +224,7 @@ struct __align__(16) TileHdr {
 
 // SEGS = false: no volume of the batch holds a tube segment or a polycone.
 template <bool SEGS>
-__global__ void __launch_bounds__(kThreads, SEGS ? 1 : 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
+__global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
                                                               int32_t* __restrict__ hit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full[2], done[2];
