@@ -47,25 +47,6 @@ __device__ __forceinline__ float lower_bound(float t, float delta, float inv_dn)
     return t - (16.f * kEps32f * fabsf(t) + delta * inv_dn);
 }
 
-// Tubes and cones: true when the forward ray (t >= tmin) stays farther from
-// the axis than the copy's largest radius (plus its tolerance), so that
-// enter32 would find nothing.  The least rho^2 of the ray is compared with a
-// margin above its FP32 rounding and above the tangency allowance of the
-// root test (16 eps32 of the discriminant).
-__device__ __forceinline__ bool beyond_axis32(const ShapeRec32& r, const float* x, const float* u, float tmin) {
-    const float* e = r.e;
-    const float rm2 = r.kind == KTUBE ? e[1] : fmaxf(e[7], e[9]);
-    const float ro = fsqrt(rm2) + r.delta;
-    const float A = fmaf(u[0], u[0], u[1] * u[1]);
-    const float B = fmaf(x[0], u[0], x[1] * u[1]);
-    const float C = fmaf(x[0], x[0], x[1] * x[1]);
-    const float t = A > 0.f ? fmaxf(-fdiv(B, A), tmin) : tmin;
-    const float at = fabsf(t);
-    const float r2 = fmaf(t, fmaf(A, t, B + B), C);
-    const float err = 16.f * kEps32f * fmaf(at, fmaf(A, at, 2.f * fabsf(B)), C);
-    return r2 - err > ro * ro * (1.f + 64.f * kEps32f);
-}
-
 // FP32 lower bound of one daughter's DistFromOutside (bounding-sphere test,
 // transform in the frame shifted to the closest approach, inflated solid),
 // inserted into the candidate list when it can beat the mother's exit.
@@ -89,7 +70,6 @@ __device__ __forceinline__ void bound_daughter(const ShapeRec32& r, int j, const
             u[k] = fmaf(r.R[6 + k], d32[2], fmaf(r.R[3 + k], d32[1], r.R[k] * d32[0]));
         }
     }
-    if (r.kind != KBOX && beyond_axis32(r, x, u, -s0)) return;
     const float tp = enter32(r, x, u, -s0);
     if (!(tp < f_inf())) return;
     const float L = lower_bound(s0 + tp, r.delta, inv_dn);
