@@ -77,7 +77,7 @@ typedef enum {
     GEO_ERR_OOM = 3,            /* device allocation failed (builder only)          */
     GEO_ERR_CUDA = 4,           /* a CUDA runtime call failed                       */
     GEO_ERR_DEVICE_ASSERT = 5,  /* a kernel reported a failed internal check        */
-    GEO_ERR_UNSUPPORTED = 6     /* valid request this build does not implement      */
+    GEO_ERR_UNSUPPORTED = 6     /* valid request the library does not implement     */
 } geo_status;
 
 typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2, GEO_TUBS = 3, GEO_PCON = 4 } geo_kind;
