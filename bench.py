@@ -325,6 +325,89 @@ def segments_leg(pkg, scenes, rank, steps):
     return out
 
 
+def sweep_leg(pkg, scenes, rank, steps, vol, base):
+    """Fig. 3's axis, time per track against basket size, on the toy detector:
+    baskets of N = 16 .. 2^20 consecutive tracks of the 2^20-track basket;
+    per N the tracks/s of one geo_dist_to_boundary call per basket (stream
+    launches: launch-bound for small N; the basket is L2-resident, 50 MB) and
+    of 2^22 tracks as 2^22/N baskets in one batched launch replayed as a CUDA
+    graph (four copies of the basket, 201 MB > L2).  Also the paper's
+    1024-track basket of four boxes in a box (microseconds per call, stream
+    launch and graph replay, both modes) and the paper's own 8-daughter toy
+    detector at 2^20 tracks (both modes)."""
+    import torch
+
+    from paper_1312_0816_gb300 import autotune
+
+    n = int(base[0].numel())
+    out = {"workload": "toy detector (40 daughters); basket sizes 16..2^20; the 1024-track box4 basket; "
+                       "toy8 at 2^20 tracks"}
+    step = torch.empty(n, dtype=torch.float64, device="cuda")
+    hit = torch.empty(n, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(7 + rank)
+    big = [torch.cat([f] * 4) for f in base]
+    nb = int(big[0].numel())
+    bstep = torch.empty(nb, dtype=torch.float64, device="cuda")
+    bhit = torch.empty(nb, dtype=torch.int32, device="cuda")
+    sweep = {}
+    for N in (16, 64, 256, 1024, 4096, 65536, 1 << 20):
+        offs = rng.integers(0, n - N + 1, size=64)
+        k = max(10, min(200, (1 << 22) // N))
+        ms = _event_time(lambda it: pkg.geo_dist_to_boundary(
+            vol, *[f[int(offs[it % 64]): int(offs[it % 64]) + N] for f in base], mode=1,
+            step=step[:N], hit=hit[:N]), k)
+        rows = np.array([(0, j * N, N) for j in range(nb // N)], dtype=np.int64)
+        batch = pkg.geo_build_batch([vol], rows, tile_order=1)
+        msb = autotune.time_graph(batch, big, bstep, bhit, reps=max(3, steps // 4))
+        batch.close()
+        sweep[str(N)] = {"per_call": {"value": N / (ms * 1e-3), "unit": "tracks/s", "us_per_call": ms * 1e3},
+                         "batched_2p22": {"value": nb / (msb * 1e-3), "unit": "tracks/s", "ms_per_launch": msb,
+                                          "baskets": int(len(rows))}}
+    out["basket_sizes"] = sweep
+    # the paper's 1024-track basket (box mother, four boxes)
+    sc1 = scenes.box4(0)
+    t1 = scenes.sample_tracks(sc1, 1024, 0)
+    v1 = pkg.geo_build_volume(sc1)
+    x1 = [torch.from_numpy(f).cuda() for f in t1.fields()]
+    s1 = torch.empty(1024, dtype=torch.float64, device="cuda")
+    h1 = torch.empty(1024, dtype=torch.int32, device="cuda")
+    box4 = {}
+    for mode, key in ((0, "fp64_plain"), (1, "fp32_refine")):
+        ms = _event_time(lambda it: pkg.geo_dist_to_boundary(v1, *x1, mode=mode, step=s1, hit=h1), 200)
+        box4[key] = {"us_per_call": ms * 1e3, "value": 1024 / (ms * 1e-3), "unit": "tracks/s"}
+        try:
+            pkg.geo_dist_to_boundary(v1, *x1, mode=mode, step=s1, hit=h1)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                with torch.cuda.graph(g, stream=st):
+                    pkg.geo_dist_to_boundary(v1, *x1, mode=mode, step=s1, hit=h1)
+            box4[key]["us_per_graph_replay"] = _event_time(lambda it: g.replay(), 200) * 1e3
+        except RuntimeError as e:
+            torch.cuda.synchronize()
+            box4[key]["us_per_graph_replay"] = None
+            box4[key]["graph_error"] = str(e).splitlines()[0][:200]
+    v1.close()
+    out["box4_1024"] = box4
+    # the paper's own toy detector composition (8 daughters)
+    sc8 = scenes.toy8(1)
+    t8 = scenes.sample_tracks(sc8, 1 << 20, 8 + 1000 * rank)
+    v8 = pkg.geo_build_volume(sc8)
+    x8 = [torch.from_numpy(f).cuda() for f in t8.fields()]
+    g8 = torch.Generator(device="cuda")
+    g8.manual_seed(21)
+    c8 = [x8] + [[f[p].contiguous() for f in x8] for p in (torch.randperm(1 << 20, device="cuda", generator=g8)
+                                                          for _ in range(3))]
+    toy8 = {}
+    for mode, key, kk in ((1, "fp32_refine", steps), (0, "fp64_plain", max(3, steps // 4))):
+        ms = _event_time(lambda it: pkg.geo_dist_to_boundary(v8, *c8[it % 4], mode=mode, step=step, hit=hit), kk)
+        toy8[key] = {"value": (1 << 20) / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms}
+    v8.close()
+    out["toy8_2p20"] = toy8
+    return out
+
+
 def _event_time(fn, k):
     import torch
 
@@ -524,6 +607,7 @@ def main():
     ap.add_argument("--no-shapes", action="store_true")
     ap.add_argument("--no-world", action="store_true")
     ap.add_argument("--no-segments", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -666,6 +750,7 @@ def main():
     shapes = None if args.no_shapes else shapes_leg(pkg, max(10, args.steps // 100), q_sqrt, q_div)
     world = None if args.no_world else world_leg(pkg, scenes, rank, max(10, args.steps // 100))
     segments = None if args.no_segments else segments_leg(pkg, scenes, rank, max(10, args.steps // 100))
+    sweep = None if args.no_sweep else sweep_leg(pkg, scenes, rank, max(10, args.steps // 100), vol, base)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -697,6 +782,7 @@ def main():
             "shapes": shapes,
             "world": world,
             "segments": segments,
+            "sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     vol.close()
