@@ -445,8 +445,12 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
     return launch_refine(k_dist_refine<false, 0, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
 }
 
+// Small baskets take the warp-per-track FP64 kernel (the same answers: both
+// modes return the plain FP64 bits); the filter pays off only when its
+// threads are many.
 cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                                cudaStream_t s, int num_sms) {
+    if (small_basket(v, b.n, num_sms)) return launch_dist_warp(v, b, step, hit, bpoint, s, num_sms);
     return launch_dist_refine_stats(v, b, step, hit, bpoint, nullptr, s, num_sms);
 }
 

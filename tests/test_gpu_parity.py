@@ -129,6 +129,30 @@ def test_adversarial_parity(g, orc, name):
     compare(ref, step, hit, max_exempt=0.35)
 
 
+@pytest.mark.parametrize("name", ["toy40", "box4", "seg4", "pcon4", "pconm"])
+def test_small_basket_warp_path(g, name):
+    """Baskets of at most 64 tracks per SM take the warp-per-track kernel
+    (lanes over daughters, shuffle minimum over (step, index)): the same bits
+    as the thread-per-track kernels give the same tracks inside a large
+    basket, in both modes."""
+    sc = scene(name)
+    tr = scenes.sample_tracks(sc, 40000, 31)
+    adv = scenes.adversarial_tracks(sc, 3000, 32)
+    for big in (tr, adv):
+        n_small = 3000
+        small = scenes.Tracks(*(f[:n_small].copy() for f in big.fields()))
+        for mode in (0, 1):
+            s_big, h_big, b_big = run_nav(g, sc, big, mode, bpoint=True) if big.n > 20000 else (None, None, None)
+            if s_big is None:
+                # pad the adversarial rays into a large basket with random ones
+                joined = scenes.Tracks(*(np.concatenate([a, b]) for a, b in zip(big.fields(), tr.fields())))
+                s_big, h_big, b_big = run_nav(g, sc, joined, mode, bpoint=True)
+            s_sm, h_sm, b_sm = run_nav(g, sc, small, mode, bpoint=True)
+            assert np.array_equal(s_sm.view(np.int64), s_big[:n_small].view(np.int64)), (name, mode)
+            assert np.array_equal(h_sm, h_big[:n_small]), (name, mode)
+            assert np.array_equal(b_sm.view(np.int64), b_big[:, :n_small].view(np.int64)), (name, mode)
+
+
 @pytest.mark.parametrize("case", golden("closed_forms.json")["nav_cases"], ids=lambda c: c["why"][:40])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_golden_navigator_cases(g, case, mode):
