@@ -127,7 +127,8 @@ cudaError_t launch_dist_fp64(const VolView& v, const Basket& b, double* step, in
                              double* bpoint, cudaStream_t s, int num_sms);
 cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                double* bpoint, cudaStream_t s, int num_sms);
-// small baskets (n <= 64 per SM, no voxels): one warp per track
+// small baskets (at most 8 tracks per SM, at most 32 daughters, no voxels):
+// one warp per track
 bool small_basket(const VolView& v, int64_t n, int num_sms);
 cudaError_t launch_dist_warp(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                              cudaStream_t s, int num_sms);

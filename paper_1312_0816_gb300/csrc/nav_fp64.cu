@@ -197,8 +197,15 @@ __global__ void __launch_bounds__(256) k_safety_fp64(VolView v, Basket b, double
         return cudaGetLastError();                                                           \
     } while (0)
 
-// one warp per track while a warp per track still fits in one wave of the GPU
-bool small_basket(const VolView& v, int64_t n, int num_sms) { return !v.voxelized && n <= int64_t(64) * num_sms; }
+// One warp per track when the basket is small (at most 8 tracks per SM: the
+// latency of a track's serial daughter loop would set the time) and the
+// daughters fit one pass of the lanes (at most 32).  With more daughters, or
+// more tracks, the warp's FP64 instructions -- charged in full whatever the
+// lanes that take part -- outweigh the latency it hides (the 40-daughter toy
+// detector: 53 us per call instead of 36 us at 16..1024 tracks).
+bool small_basket(const VolView& v, int64_t n, int num_sms) {
+    return !v.voxelized && v.nd <= 32 && n <= int64_t(8) * num_sms;
+}
 
 cudaError_t launch_dist_warp(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                              cudaStream_t s, int num_sms) {

@@ -129,17 +129,17 @@ def test_adversarial_parity(g, orc, name):
     compare(ref, step, hit, max_exempt=0.35)
 
 
-@pytest.mark.parametrize("name", ["toy40", "box4", "seg4", "pcon4", "pconm"])
+@pytest.mark.parametrize("name", ["toy8", "box4", "diff3", "seg4", "pcon4", "pconm"])
 def test_small_basket_warp_path(g, name):
-    """Baskets of at most 64 tracks per SM take the warp-per-track kernel
-    (lanes over daughters, shuffle minimum over (step, index)): the same bits
-    as the thread-per-track kernels give the same tracks inside a large
-    basket, in both modes."""
+    """Baskets of at most 8 tracks per SM in volumes of at most 32 daughters
+    take the warp-per-track kernel (lanes over daughters, shuffle minimum over
+    (step, index)): the same bits as the thread-per-track kernels give the
+    same tracks inside a large basket, in both modes."""
     sc = scene(name)
     tr = scenes.sample_tracks(sc, 40000, 31)
     adv = scenes.adversarial_tracks(sc, 3000, 32)
     for big in (tr, adv):
-        n_small = 3000
+        n_small = 1000
         small = scenes.Tracks(*(f[:n_small].copy() for f in big.fields()))
         for mode in (0, 1):
             s_big, h_big, b_big = run_nav(g, sc, big, mode, bpoint=True) if big.n > 20000 else (None, None, None)
