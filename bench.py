@@ -328,8 +328,9 @@ def segments_leg(pkg, scenes, rank, steps):
 def sweep_leg(pkg, scenes, rank, steps, vol, base):
     """Fig. 3's axis, time per track against basket size, on the toy detector:
     baskets of N = 16 .. 2^20 consecutive tracks of the 2^20-track basket;
-    per N the tracks/s of one geo_dist_to_boundary call per basket (stream
-    launches: launch-bound for small N; the basket is L2-resident, 50 MB) and
+    per N the tracks/s of one geo_dist_to_boundary call per basket (32 calls
+    at different offsets captured in a CUDA graph, so the time is the
+    device's: launch-bound for small N; the basket is L2-resident, 50 MB) and
     of 2^22 tracks as 2^22/N baskets in one batched launch replayed as a CUDA
     graph (four copies of the basket, 201 MB > L2).  Also the paper's
     1024-track basket of four boxes in a box (microseconds per call, stream
@@ -351,11 +352,18 @@ def sweep_leg(pkg, scenes, rank, steps, vol, base):
     bhit = torch.empty(nb, dtype=torch.int32, device="cuda")
     sweep = {}
     for N in (16, 64, 256, 1024, 4096, 65536, 1 << 20):
-        offs = rng.integers(0, n - N + 1, size=64)
-        k = max(10, min(200, (1 << 22) // N))
-        ms = _event_time(lambda it: pkg.geo_dist_to_boundary(
-            vol, *[f[int(offs[it % 64]): int(offs[it % 64]) + N] for f in base], mode=1,
-            step=step[:N], hit=hit[:N]), k)
+        offs = rng.integers(0, n - N + 1, size=32)
+        calls = 32 if N < (1 << 20) else 1
+        args = [[f[int(o): int(o) + N] for f in base] for o in offs[:calls]]
+        pkg.geo_dist_to_boundary(vol, *args[0], mode=1, step=step[:N], hit=hit[:N])
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                for a in args:
+                    pkg.geo_dist_to_boundary(vol, *a, mode=1, step=step[:N], hit=hit[:N])
+        ms = _event_time(lambda it: g.replay(), max(5, min(100, (1 << 22) // (N * calls)))) / calls
         rows = np.array([(0, j * N, N) for j in range(nb // N)], dtype=np.int64)
         batch = pkg.geo_build_batch([vol], rows, tile_order=1)
         msb = autotune.time_graph(batch, big, bstep, bhit, reps=max(3, steps // 4))

@@ -232,7 +232,8 @@ typedef struct {
 } geo_basket;
 
 /* tile_order: 0 = largest estimated cost first (tracks x daughters), 1 = in
- * basket order.  blocks_per_sm: resident blocks of the persistent launch
+ * basket order (the packed tiles of ragged tails after the baskets' full
+ * tiles, volume by volume).  blocks_per_sm: resident blocks of the persistent launch
  * (0 = as many as fit).  Values other than these give GEO_ERR_INVALID_ARG. */
 typedef struct {
     int32_t tile_order;
@@ -241,9 +242,11 @@ typedef struct {
 
 typedef struct geo_batch_s* geo_batch;
 
-/* Builds a batch: copies the baskets, splits them into tiles of at most 256
- * tracks, orders the tiles, and uploads the per-volume views, the tile list
- * and a tile counter to the device (the batch owns them).  The volumes must
+/* Builds a batch: copies the baskets, splits them into tiles of 256
+ * consecutive tracks, gathers the ragged remainders of each volume's baskets
+ * into packed tiles of up to 256 tracks (listing their indices), orders the
+ * tiles, and uploads the per-volume views, the tile list, the packed
+ * indices and a tile counter to the device (the batch owns them).  The volumes must
  * stay alive while the batch is used.  All volumes must live on the current
  * device.  Synchronises `stream`. */
 geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_basket* baskets,

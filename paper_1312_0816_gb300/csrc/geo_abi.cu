@@ -45,6 +45,7 @@ struct geo_batch_s {
     int64_t ntiles = 0;
     int64_t max_end = 0;
     int32_t segs = 0;
+    int64_t* d_idx = nullptr;   // track indices of packed tiles
     VolView* d_vols = nullptr;
     BatchTile* d_tiles = nullptr;
     unsigned int* d_words = nullptr;   // [0] tile counter, [1] status
@@ -778,21 +779,42 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
     for (int i = 0; i < n_vols; ++i)
         if (!vols[i] || vols[i]->device != dev) return GEO_ERR_INVALID_ARG;
+    // Every basket's full 256-track stretches become tiles of consecutive
+    // tracks; the ragged tails of a volume's baskets are gathered, in basket
+    // order, into packed tiles that list their tracks' indices, so that
+    // baskets of a few tracks still fill the producers' 256 threads.
     std::vector<BatchTile> tiles;
     std::vector<int64_t> cost;
+    std::vector<std::vector<int64_t>> tails(static_cast<size_t>(n_vols));
     int64_t max_end = 0;
     for (int k = 0; k < n_baskets; ++k) {
         const geo_basket& bk = baskets[k];
         if (bk.reserved != 0 || bk.volume < 0 || bk.volume >= n_vols || bk.offset < 0 || bk.count < 0)
             return GEO_ERR_INVALID_ARG;
         max_end = std::max(max_end, bk.offset + bk.count);
-        for (int64_t off = 0; off < bk.count; off += 256) {
+        const int64_t full = bk.count / 256 * 256;
+        for (int64_t off = 0; off < full; off += 256) {
             BatchTile t;
             t.vol = bk.volume;
-            t.count = int32_t(std::min<int64_t>(256, bk.count - off));
+            t.count = 256;
             t.base = bk.offset + off;
             tiles.push_back(t);
-            cost.push_back(int64_t(t.count) * (vols[bk.volume]->view.nd + 1));
+            cost.push_back(int64_t(256) * (vols[bk.volume]->view.nd + 1));
+        }
+        for (int64_t q = bk.offset + full; q < bk.offset + bk.count; ++q) tails[size_t(bk.volume)].push_back(q);
+    }
+    std::vector<int64_t> idx;
+    for (int v = 0; v < n_vols; ++v) {
+        const std::vector<int64_t>& tv = tails[size_t(v)];
+        for (size_t a = 0; a < tv.size(); a += 256) {
+            const size_t m = std::min<size_t>(256, tv.size() - a);
+            BatchTile t;
+            t.vol = v;
+            t.count = -int32_t(m);
+            t.base = int64_t(idx.size());
+            idx.insert(idx.end(), tv.begin() + std::ptrdiff_t(a), tv.begin() + std::ptrdiff_t(a + m));
+            tiles.push_back(t);
+            cost.push_back(int64_t(m) * (vols[v]->view.nd + 1));
         }
     }
     if (order == 0) {
@@ -818,6 +840,9 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     if ((e = cudaMalloc(&b->d_vols, sizeof(VolView) * n_vols)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_words, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (!idx.empty() && (e = cudaMalloc(&b->d_idx, sizeof(int64_t) * idx.size())) != cudaSuccess) ||
+        (!idx.empty() && (e = cudaMemcpyAsync(b->d_idx, idx.data(), sizeof(int64_t) * idx.size(),
+                                              cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
         (e = cudaMemcpyAsync(b->d_vols, views.data(), sizeof(VolView) * n_vols, cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
         (!tiles.empty() && (e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(),
@@ -840,6 +865,7 @@ geo_status geo_destroy_batch(geo_batch b) {
     cudaFree(b->d_vols);
     cudaFree(b->d_tiles);
     cudaFree(b->d_words);
+    cudaFree(b->d_idx);
     if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
     delete b;
     return GEO_OK;
@@ -867,6 +893,7 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
     bv.status = b->d_words + 1;
     bv.segs = b->segs;
     bv.pad = 0;
+    bv.idx = b->d_idx;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
     return cuda_status(launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, s, num_sms_of(b->device)));
 }

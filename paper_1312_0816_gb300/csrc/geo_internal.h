@@ -99,7 +99,8 @@ struct Basket {
     int64_t n;
 };
 
-// One tile of the batched launch: up to 256 consecutive tracks of one basket.
+// One tile of the batched launch: up to 256 consecutive tracks of one basket,
+// or (count < 0) up to 256 tracks of one volume listed from BatchView::idx[base].
 struct BatchTile {
     int32_t vol;
     int32_t count;
@@ -115,6 +116,7 @@ struct BatchView {
     unsigned int* status;     // device error word of the batch
     int32_t segs;             // 1 if a volume holds a tube segment or a polycone
     int32_t pad;
+    const int64_t* idx;       // track indices of packed tiles (count < 0), or null
 };
 
 // device error codes written to VolView::status

@@ -212,7 +212,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b
 // them so), with the same producer / consumer pipeline.  The tile header of a
 // stage carries a copy of the tile's volume view; the solid tables are read
 // from global memory through L1 (a table change per tile would otherwise
-// need a restage while the other stage still uses the previous one).
+// need a restage while the other stage still uses the previous one).  A
+// packed tile (negative count) lists its tracks' indices in bv.idx from its
+// base on (the ragged tails of a volume's baskets gathered into full tiles).
 struct __align__(16) TileHdr {
     VolView vol;
     int64_t base;
@@ -244,8 +246,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
 
     if (t < kProd) {
         // ------------------------------------------------------ producers --
-        int64_t prev_base = 0;
-        int prev_count = 0;
+        int64_t prev_i = 0;      // this thread's track in the previous tile
+        bool prev_live = false;
         for (int k = 0;; ++k) {
             Stage& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
@@ -264,15 +266,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
             }
             producer_barrier();
             const int tile = hd.tile;
+            int64_t cur_i = 0;
+            bool cur_live = false;
             if (tile >= 0) {
                 if (t < kWords)
                     reinterpret_cast<int4*>(&hd.vol)[t] = reinterpret_cast<const int4*>(bv.vols + hd.vol_index)[t];
                 const int64_t base = hd.base;
-                const int count = hd.count;
+                const bool packed = hd.count < 0;
+                const int count = packed ? -hd.count : hd.count;
                 producer_barrier();
                 const VolView& v = hd.vol;
                 const bool live = t < count;
-                const int64_t i = base + t;
+                const int64_t i = live ? (packed ? bv.idx[base + t] : base + t) : 0;
+                cur_i = i;
+                cur_live = live;
                 double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
                 if (live) {
                     px = b.x[i]; py = b.y[i]; pz = b.z[i];
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 Stage& sp = S[kp & 1];
                 const VolView& vp = H[kp & 1].vol;
                 mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), bv.status, healthy);
-                if (t < prev_count && sp.n[t] >= 0) {
+                if (prev_live && sp.n[t] >= 0) {
                     RefineState rs;
                     rs.status = 0;
                     rs.c.n = sp.n[t];
@@ -334,12 +341,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                     double best;
                     int h, nev;
                     refine_rest<SEGS>(vp, vp.d64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
-                    store_result(prev_base + t, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
+                    store_result(prev_i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
                 }
             }
             if (tile < 0) break;
-            prev_base = hd.base;
-            prev_count = hd.count;
+            prev_live = cur_live;
+            prev_i = cur_i;
         }
     } else {
         // ------------------------------------------------------ consumers --

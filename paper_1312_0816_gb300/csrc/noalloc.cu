@@ -135,6 +135,7 @@ extern "C" geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vol
     bv.status = &d->words[1];
     bv.segs = 0;
     bv.pad = 0;
+    bv.idx = nullptr;   // plain tiles only
     for (int i = 0; i < n_vols; ++i) bv.segs = bv.segs || volume_view(vols[i])->segs;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
     e = launch_dist_batched(bv, bk, step, hit, 0, s, sm_count(dev));
