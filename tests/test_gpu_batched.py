@@ -149,3 +149,24 @@ def test_autotuner_picks_a_candidate_and_caches(g, small_batch, tmp_path, monkey
     s0, h0 = g.geo_dist_to_boundary_batched(ref, *x)
     torch.cuda.synchronize()
     assert torch.equal(s, s0) and torch.equal(h, h0)
+
+
+def test_batched_segments_and_polycones(g):
+    """Volumes with tube segments and polycones (the batched kernel's
+    instantiation with their code) mixed with plain ones, baskets of 1 to 700
+    tracks (packed ragged tails): the same bits as one call per basket."""
+    vols = [scenes.seg4(), scenes.pcon4(), scenes.pconm(), scenes.toy8(1)]
+    rng = np.random.default_rng(11)
+    baskets = [(int(rng.integers(0, 4)), int(rng.integers(1, 700))) for _ in range(60)]
+    tr, rows = scenes.batched_tracks(vols, baskets, 12)
+    volh = [g.geo_build_volume(v) for v in vols]
+    for order in (0, 1):
+        batch = g.geo_build_batch(volh, rows, tile_order=order)
+        s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
+        torch.cuda.synchronize()
+        s, h = s.cpu().numpy(), h.cpu().numpy()
+        s64, h64 = per_basket(g, vols, volh, tr, rows, 0)
+        assert np.array_equal(h, h64)
+        assert np.array_equal(s.view(np.int64), s64.view(np.int64))
+        batch.close()
+

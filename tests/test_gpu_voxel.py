@@ -32,7 +32,8 @@ def run(g, vol, tr, mode):
 
 
 @pytest.mark.parametrize("name,grid", [("grid512", (0, 0, 0)), ("grid512", (8, 8, 8)), ("grid512", (32, 16, 8)),
-                                       ("toy40", (0, 0, 0)), ("diff3", (4, 4, 4))])
+                                       ("toy40", (0, 0, 0)), ("diff3", (4, 4, 4)), ("seg4", (4, 4, 4)),
+                                       ("pcon4", (4, 4, 4)), ("pconm", (4, 4, 8))])
 def test_voxel_modes_equal_plain_loop(g, name, grid):
     sc = scenes.SCENES[name]()
     plain = g.geo_build_volume(sc)
