@@ -779,7 +779,7 @@ def main():
             "roofline": roof,
             "e2e": {"value": ws * n / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": 48 * n,
                     "d2h_bytes_per_step": 12 * n,
-                    "api": "geo_dist_to_boundary_host (pinned host buffers, 4 chunks pipelined over copy-in, step and copy-out streams)"},
+                    "api": "geo_dist_to_boundary_host (pinned host buffers, 4 chunks pipelined over a copy-in stream, two alternating step streams and a copy-out stream)"},
             "gpu_launches": args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -210,8 +210,10 @@ geo_status geo_safety(geo_volume v, const double* x, const double* y, const doub
  * pinned; pinned overlaps best); the library stages the basket through a
  * device workspace of two buffers of `chunk` tracks (0 = 1<<18) as a
  * pipeline: chunk c+1 is copied in on an internal stream while chunk c is
- * stepped on `stream` and chunk c-1 copied out on a second internal stream.
- * Returns after synchronising.  The workspace, streams and events are made
+ * stepped and chunk c-1 copied out on a second internal stream; even chunks
+ * are stepped on `stream`, odd ones on a third internal stream (joined to
+ * `stream` at the end), so that consecutive steps overlap.  Returns after
+ * synchronising.  The workspace, streams and events are made
  * on the first call and kept with the volume (the buffers grow when `chunk`
  * grows); calls on one volume are serialised by a lock. */
 geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double* y,

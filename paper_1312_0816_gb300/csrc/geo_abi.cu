@@ -32,9 +32,9 @@ struct geo_volume_s {
     // ws_tracks tracks, a copy-in and a copy-out stream, and events
     void* ws = nullptr;
     int64_t ws_tracks = 0;
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_k2 = nullptr;
     cudaEvent_t ev_start = nullptr, ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr};
+                ev_out[2] = {nullptr, nullptr}, ev_join = nullptr;
     std::mutex ws_mu;
 };
 
@@ -628,7 +628,9 @@ geo_status geo_destroy_volume(geo_volume v) {
     cudaFree(v->ws);
     if (v->s_in) cudaStreamDestroy(v->s_in);
     if (v->s_out) cudaStreamDestroy(v->s_out);
-    for (cudaEvent_t e : {v->ev_start, v->ev_in[0], v->ev_in[1], v->ev_k[0], v->ev_k[1], v->ev_out[0], v->ev_out[1]})
+    if (v->s_k2) cudaStreamDestroy(v->s_k2);
+    for (cudaEvent_t e : {v->ev_start, v->ev_in[0], v->ev_in[1], v->ev_k[0], v->ev_k[1], v->ev_out[0], v->ev_out[1],
+                          v->ev_join})
         if (e) cudaEventDestroy(e);
     if (prev >= 0 && prev != v->device) cudaSetDevice(prev);
     delete v;
@@ -704,10 +706,11 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
     cudaError_t e = cudaSuccess;
     if (!v->s_in) {
         if ((e = cudaStreamCreateWithFlags(&v->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaStreamCreateWithFlags(&v->s_out, cudaStreamNonBlocking)) != cudaSuccess)
+            (e = cudaStreamCreateWithFlags(&v->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&v->s_k2, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_status(e);
         for (cudaEvent_t* ev : {&v->ev_start, &v->ev_in[0], &v->ev_in[1], &v->ev_k[0], &v->ev_k[1], &v->ev_out[0],
-                                &v->ev_out[1]})
+                                &v->ev_out[1], &v->ev_join})
             if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
     }
     const size_t per_track = 7 * sizeof(double) + sizeof(int32_t);
@@ -732,14 +735,19 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int sms = num_sms_of(v->device);
     // three-stage pipeline over chunks, two buffers: copy in (s_in), the
-    // step (the caller's stream), copy out (s_out); chunk c+1 is copied in
-    // while chunk c is stepped and chunk c-1 copied out
+    // step, copy out (s_out); chunk c+1 is copied in while chunk c is stepped
+    // and chunk c-1 copied out.  The steps of even chunks run on the caller's
+    // stream and those of odd chunks on a second internal stream, so that a
+    // chunk's kernel can start on the SMs the previous one is leaving (its
+    // tail) instead of waiting for it.
     if ((e = cudaEventRecord(v->ev_start, s)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(v->s_in, v->ev_start, 0)) != cudaSuccess)
+        (e = cudaStreamWaitEvent(v->s_in, v->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(v->s_k2, v->ev_start, 0)) != cudaSuccess)
         return cuda_status(e);
     int64_t c = 0;
     for (int64_t off = 0; off < n; off += chunk, ++c) {
         const int bf = int(c & 1);
+        const cudaStream_t ks = bf ? v->s_k2 : s;
         const int64_t m = std::min(chunk, n - off);
         if (c >= 2 && (e = cudaStreamWaitEvent(v->s_in, v->ev_out[bf], 0)) != cudaSuccess) return cuda_status(e);
         for (int k = 0; k < 6; ++k)
@@ -747,13 +755,13 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
                                      v->s_in)) != cudaSuccess)
                 return cuda_status(e);
         if ((e = cudaEventRecord(v->ev_in[bf], v->s_in)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s, v->ev_in[bf], 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(ks, v->ev_in[bf], 0)) != cudaSuccess)
             return cuda_status(e);
         const Basket b{f[bf][0], f[bf][1], f[bf][2], f[bf][3], f[bf][4], f[bf][5], m};
-        e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, f[bf][6], whit[bf], nullptr, s, sms)
-                               : launch_dist_refine(v->view, b, f[bf][6], whit[bf], nullptr, s, sms);
+        e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, f[bf][6], whit[bf], nullptr, ks, sms)
+                               : launch_dist_refine(v->view, b, f[bf][6], whit[bf], nullptr, ks, sms);
         if (e != cudaSuccess) return cuda_status(e);
-        if ((e = cudaEventRecord(v->ev_k[bf], s)) != cudaSuccess ||
+        if ((e = cudaEventRecord(v->ev_k[bf], ks)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(v->s_out, v->ev_k[bf], 0)) != cudaSuccess ||
             (e = cudaMemcpyAsync(step + off, f[bf][6], size_t(m) * sizeof(double), cudaMemcpyDeviceToHost,
                                  v->s_out)) != cudaSuccess ||
@@ -762,7 +770,10 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
             (e = cudaEventRecord(v->ev_out[bf], v->s_out)) != cudaSuccess)
             return cuda_status(e);
     }
-    if ((e = cudaStreamSynchronize(v->s_out)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    // the caller's stream follows the whole call (the second stream joined)
+    if ((e = cudaEventRecord(v->ev_join, v->s_k2)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, v->ev_join, 0)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(v->s_out)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_status(e);
     return GEO_OK;
 }
