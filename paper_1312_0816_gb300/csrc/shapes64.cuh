@@ -441,14 +441,14 @@ __device__ __forceinline__ double pcon_out64(const double* d, const double* T, c
             section(k);
             if (k > 0 && x[2] == z[k]) section(k - 1);
         }
-    } else if (IS_POS(u[2])) {
-        for (int k = pcon_section(z, n, x[2]); k < n - 1; ++k) {
-            if (z[k] > reach()) break;
-            section(k);
-        }
     } else {
-        for (int k = pcon_section(z, n, x[2]); k >= 0; --k) {
-            if (z[k + 1] < reach()) break;
+        // one loop for both directions (lanes moving up and down share its
+        // iterations instead of running two loops one after the other)
+        const bool up = IS_POS(u[2]);
+        const int dk = up ? 1 : -1;
+        for (int k = pcon_section(z, n, x[2]); k >= 0 && k < n - 1; k += dk) {
+            const double r = reach();
+            if (up ? z[k] > r : z[k + 1] < r) break;
             section(k);
         }
     }
@@ -640,14 +640,12 @@ __device__ __forceinline__ double pcon_in64(const double* d, const double* T, co
         const int k = pcon_section(z, n, x[2]);
         section(k);
         if (k > 0 && x[2] == z[k]) section(k - 1);
-    } else if (IS_POS(u[2])) {
-        for (int k = pcon_section(z, n, x[2]); k < n - 1; ++k) {
-            if (z[k] > reach()) break;
-            section(k);
-        }
     } else {
-        for (int k = pcon_section(z, n, x[2]); k >= 0; --k) {
-            if (z[k + 1] < reach()) break;
+        const bool up = IS_POS(u[2]);
+        const int dk = up ? 1 : -1;
+        for (int k = pcon_section(z, n, x[2]); k >= 0 && k < n - 1; k += dk) {
+            const double r = reach();
+            if (up ? z[k] > r : z[k + 1] < r) break;
             section(k);
         }
     }
