@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 N_TRACKS = 1 << 20
 N_COPIES = 8          # rotating basket copies: 8 x 60 MB > 2 x 129 MB L2
+E2E_COPIES = 4        # pinned host copies for the end-to-end timing: 4 x 60 MB > L2
 METRIC = "tracks/s dist-to-boundary, FP32+FP64-refine vs plain FP64 on GPU; % roofline"
 WORKLOAD = "toy detector: tube mother r0-1000 half-z 1500 mm, 40 daughters (8 tube shells, 24 rotated boxes, " \
            "8 cones), 2^20 tracks uniform in the mother's exclusive part, isotropic, seed 1"
@@ -737,18 +738,22 @@ def main():
                                "fp64_div_per_s": r_div, "fp64_sqrt_per_s": r_sqrt,
                                "div_in_dfma": q_div, "sqrt_in_dfma": q_sqrt}}
 
-    # end to end through the host-memory entry point (pinned buffers)
-    pinned = [torch.from_numpy(f).pin_memory() for f in tr.fields()]
-    hs = torch.empty(n, dtype=torch.float64).pin_memory()
-    hh = torch.empty(n, dtype=torch.int32).pin_memory()
-    chunk = max(1, n // 4)   # four chunks: copies of one overlap the step of another
-    for _ in range(2):
-        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=chunk)
+    # end to end through the host-memory entry point: pinned host buffers,
+    # which the step reads and writes in place over the host link; E2E_COPIES
+    # permuted copies in rotation (more than L2 holds), each with its outputs
+    pinned, houts = [], []
+    for c in range(E2E_COPIES):
+        perm = np.random.default_rng(1000 + c).permutation(n)
+        pinned.append([torch.from_numpy(np.ascontiguousarray(f[perm])).pin_memory() for f in tr.fields()])
+        houts.append((torch.empty(n, dtype=torch.float64).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory()))
+    for c in range(E2E_COPIES):
+        pkg.geo_dist_to_boundary_host(vol, *pinned[c], mode=1, step=houts[c][0], hit=houts[c][1])
     k_e2e = max(3, args.steps // 40)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        pkg.geo_dist_to_boundary_host(vol, *pinned, mode=1, step=hs, hit=hh, chunk=chunk)
+    for it in range(k_e2e):
+        c = it % E2E_COPIES
+        pkg.geo_dist_to_boundary_host(vol, *pinned[c], mode=1, step=houts[c][0], hit=houts[c][1])
     e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e)
 
     batched = None if args.no_batched else batched_leg(pkg, scenes, rank, max(10, args.steps // 40))
@@ -779,7 +784,9 @@ def main():
             "roofline": roof,
             "e2e": {"value": ws * n / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": 48 * n,
                     "d2h_bytes_per_step": 12 * n,
-                    "api": "geo_dist_to_boundary_host (pinned host buffers, 4 chunks pipelined over a copy-in stream, two alternating step streams and a copy-out stream)"},
+                    "api": "geo_dist_to_boundary_host on pinned host buffers (the step reads the tracks and writes "
+                           "the results in place over the host link; %d permuted copies in rotation, %.0f MB > L2; "
+                           "synchronised every call)" % (E2E_COPIES, E2E_COPIES * n * 60 / 1e6)},
             "gpu_launches": args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,

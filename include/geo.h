@@ -206,11 +206,16 @@ geo_status geo_contains(geo_volume v, const double* x, const double* y, const do
 geo_status geo_safety(geo_volume v, const double* x, const double* y, const double* z, int64_t n,
                       double* safety, int32_t mode, void* stream);
 
-/* Same as geo_dist_to_boundary but every array is HOST memory (pageable or
- * pinned; pinned overlaps best); the library stages the basket through a
- * device workspace of two buffers of `chunk` tracks (0 = 1<<18) as a
+/* Same as geo_dist_to_boundary but every array is HOST memory; a device
+ * pointer among them gives GEO_ERR_INVALID_ARG.  When all eight arrays are
+ * page-locked (cudaHostAlloc, cudaHostRegister; pinned torch tensors), one
+ * step runs on them in place: the kernel reads the tracks and writes the
+ * results across the host link, with no staging copies, and `chunk` is
+ * unused.  Otherwise (pageable memory) the library stages the basket through a
+ * device workspace of three buffers of `chunk` tracks (0 = 1<<18) as a
  * pipeline: chunk c+1 is copied in on an internal stream while chunk c is
- * stepped and chunk c-1 copied out on a second internal stream; even chunks
+ * stepped and chunk c-1 copied out on a second internal stream, and a buffer
+ * is refilled as soon as its chunk has been copied out; even chunks
  * are stepped on `stream`, odd ones on a third internal stream (joined to
  * `stream` at the end), so that consecutive steps overlap.  Returns after
  * synchronising.  The workspace, streams and events are made

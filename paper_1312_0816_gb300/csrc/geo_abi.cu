@@ -28,13 +28,14 @@ struct geo_volume_s {
     std::vector<ShapeRec64> h64;      // host copy of the daughter records
     std::vector<double> h_planes;     // host copy of the plane tables
     std::vector<int64_t> pl_off;      // [nd + 1]: table offset of daughter j (last: the mother), -1 if none
-    // staging workspace of geo_dist_to_boundary_host: two buffers of
+    // staging workspace of geo_dist_to_boundary_host: kStageBufs buffers of
     // ws_tracks tracks, a copy-in and a copy-out stream, and events
+    static constexpr int kStageBufs = 3;
     void* ws = nullptr;
     int64_t ws_tracks = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr, s_k2 = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr}, ev_join = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_in[kStageBufs] = {}, ev_k[kStageBufs] = {}, ev_out[kStageBufs] = {},
+                ev_join = nullptr;
     std::mutex ws_mu;
 };
 
@@ -455,6 +456,18 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc,
+// cudaHostRegister), which kernels can read and write in place over the host
+// link; nullptr for pageable memory.
+const void* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 geo_status check_volume_device(geo_volume v) {
     if (!v) return GEO_ERR_INVALID_ARG;
     int dev = -1;
@@ -629,9 +642,11 @@ geo_status geo_destroy_volume(geo_volume v) {
     if (v->s_in) cudaStreamDestroy(v->s_in);
     if (v->s_out) cudaStreamDestroy(v->s_out);
     if (v->s_k2) cudaStreamDestroy(v->s_k2);
-    for (cudaEvent_t e : {v->ev_start, v->ev_in[0], v->ev_in[1], v->ev_k[0], v->ev_k[1], v->ev_out[0], v->ev_out[1],
-                          v->ev_join})
+    for (cudaEvent_t e : {v->ev_start, v->ev_join})
         if (e) cudaEventDestroy(e);
+    for (int k = 0; k < geo_volume_s::kStageBufs; ++k)
+        for (cudaEvent_t e : {v->ev_in[k], v->ev_k[k], v->ev_out[k]})
+            if (e) cudaEventDestroy(e);
     if (prev >= 0 && prev != v->device) cudaSetDevice(prev);
     delete v;
     return GEO_OK;
@@ -700,17 +715,45 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
     if (n < 0 || chunk < 0) return GEO_ERR_INVALID_ARG;
     if (n == 0) return GEO_OK;
     if (!x || !y || !z || !dx || !dy || !dz || !step || !hit) return GEO_ERR_INVALID_ARG;
+    const void* hp[8] = {x, y, z, dx, dy, dz, step, hit};
+    const void* mp[8];
+    bool mapped = true;
+    for (int k = 0; k < 8; ++k) {
+        if (is_device_ptr(hp[k])) return GEO_ERR_INVALID_ARG;
+        mp[k] = mapped_host_ptr(hp[k]);
+        mapped = mapped && mp[k] != nullptr;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int sms = num_sms_of(v->device);
+    cudaError_t e = cudaSuccess;
+    if (mapped) {
+        // every array page-locked: one step over the arrays in place (the
+        // kernel's loads and stores cross the host link; no staging copies)
+        const Basket b{static_cast<const double*>(mp[0]), static_cast<const double*>(mp[1]),
+                       static_cast<const double*>(mp[2]), static_cast<const double*>(mp[3]),
+                       static_cast<const double*>(mp[4]), static_cast<const double*>(mp[5]), n};
+        double* ostep = const_cast<double*>(static_cast<const double*>(mp[6]));
+        int32_t* ohit = const_cast<int32_t*>(static_cast<const int32_t*>(mp[7]));
+        e = (mode == GEO_FP64) ? launch_dist_fp64(v->view, b, ostep, ohit, nullptr, s, sms)
+                               : launch_dist_refine(v->view, b, ostep, ohit, nullptr, s, sms);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? GEO_OK : cuda_status(e);
+    }
     if (chunk == 0) chunk = int64_t(1) << 18;
     if (chunk > n) chunk = n;
     std::lock_guard<std::mutex> lock(v->ws_mu);
-    cudaError_t e = cudaSuccess;
     if (!v->s_in) {
         if ((e = cudaStreamCreateWithFlags(&v->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaStreamCreateWithFlags(&v->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaStreamCreateWithFlags(&v->s_k2, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_status(e);
-        for (cudaEvent_t* ev : {&v->ev_start, &v->ev_in[0], &v->ev_in[1], &v->ev_k[0], &v->ev_k[1], &v->ev_out[0],
-                                &v->ev_out[1], &v->ev_join})
+        std::vector<cudaEvent_t*> evs = {&v->ev_start, &v->ev_join};
+        for (int k = 0; k < geo_volume_s::kStageBufs; ++k) {
+            evs.push_back(&v->ev_in[k]);
+            evs.push_back(&v->ev_k[k]);
+            evs.push_back(&v->ev_out[k]);
+        }
+        for (cudaEvent_t* ev : evs)
             if ((e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_status(e);
     }
     const size_t per_track = 7 * sizeof(double) + sizeof(int32_t);
@@ -720,36 +763,38 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
             v->ws = nullptr;
             v->ws_tracks = 0;
         }
-        if ((e = cudaMalloc(&v->ws, 2 * size_t(chunk) * per_track)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMalloc(&v->ws, geo_volume_s::kStageBufs * size_t(chunk) * per_track)) != cudaSuccess)
+            return cuda_status(e);
         v->ws_tracks = chunk;
     }
     const int64_t cap = v->ws_tracks;
-    double* f[2][7];
-    int32_t* whit[2];
-    for (int bfr = 0; bfr < 2; ++bfr) {
+    constexpr int NB = geo_volume_s::kStageBufs;
+    double* f[NB][7];
+    int32_t* whit[NB];
+    for (int bfr = 0; bfr < NB; ++bfr) {
         double* w = reinterpret_cast<double*>(static_cast<char*>(v->ws) + bfr * size_t(cap) * per_track);
         for (int k = 0; k < 7; ++k) f[bfr][k] = w + k * cap;
         whit[bfr] = reinterpret_cast<int32_t*>(w + 7 * cap);
     }
     const double* src[6] = {x, y, z, dx, dy, dz};
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int sms = num_sms_of(v->device);
-    // three-stage pipeline over chunks, two buffers: copy in (s_in), the
+    // three-stage pipeline over chunks and NB buffers: copy in (s_in), the
     // step, copy out (s_out); chunk c+1 is copied in while chunk c is stepped
-    // and chunk c-1 copied out.  The steps of even chunks run on the caller's
-    // stream and those of odd chunks on a second internal stream, so that a
-    // chunk's kernel can start on the SMs the previous one is leaving (its
-    // tail) instead of waiting for it.
+    // and chunk c-1 copied out, and a buffer is refilled once its chunk has
+    // been copied out (with three buffers the copy-in of chunk c+2 need not
+    // wait for the step of chunk c).  The steps of even chunks run on the
+    // caller's stream and those of odd chunks on a second internal stream, so
+    // that a chunk's kernel can start on the SMs the previous one is leaving
+    // (its tail) instead of waiting for it.
     if ((e = cudaEventRecord(v->ev_start, s)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(v->s_in, v->ev_start, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(v->s_k2, v->ev_start, 0)) != cudaSuccess)
         return cuda_status(e);
     int64_t c = 0;
     for (int64_t off = 0; off < n; off += chunk, ++c) {
-        const int bf = int(c & 1);
-        const cudaStream_t ks = bf ? v->s_k2 : s;
+        const int bf = int(c % NB);
+        const cudaStream_t ks = (c & 1) ? v->s_k2 : s;
         const int64_t m = std::min(chunk, n - off);
-        if (c >= 2 && (e = cudaStreamWaitEvent(v->s_in, v->ev_out[bf], 0)) != cudaSuccess) return cuda_status(e);
+        if (c >= NB && (e = cudaStreamWaitEvent(v->s_in, v->ev_out[bf], 0)) != cudaSuccess) return cuda_status(e);
         for (int k = 0; k < 6; ++k)
             if ((e = cudaMemcpyAsync(f[bf][k], src[k] + off, size_t(m) * sizeof(double), cudaMemcpyHostToDevice,
                                      v->s_in)) != cudaSuccess)

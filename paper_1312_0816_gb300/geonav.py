@@ -399,9 +399,17 @@ def geo_world_step(world: World, x, y, z, dx, dy, dz, node, flag=None, mode: int
 
 def geo_dist_to_boundary_host(vol: Volume, x, y, z, dx, dy, dz, mode: int = GEO_FP32_REFINE, step=None, hit=None,
                               chunk: int = 0, stream=None):
-    """Host-memory variant: numpy float64 arrays (or pinned CPU tensors) in,
-    numpy/pinned outputs filled; synchronises the stream."""
+    """Host-memory variant: numpy float64 arrays or CPU tensors in, outputs
+    filled (numpy arrays, or pinned tensors when the inputs are pinned
+    tensors and no outputs are given); synchronises the stream.  With every
+    array pinned the step runs on them in place; otherwise the library stages
+    them through device buffers in chunks."""
     n = int(len(x))
+    if step is None and hit is None and all(hasattr(a, "is_pinned") and a.is_pinned() for a in (x, y, z, dx, dy, dz)):
+        import torch
+
+        step = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        hit = torch.empty(n, dtype=torch.int32, pin_memory=True)
 
     def ptr(a):
         if hasattr(a, "data_ptr"):

@@ -249,13 +249,48 @@ def test_safety_parity(g, orc, mode):
         assert np.max(np.abs(got - want)) <= STEP_TOL, name
 
 
-def test_host_entry_matches_device(g):
+@pytest.mark.parametrize("mode,chunk", [(1, 30000), (1, 7001), (0, 50000), (1, 0)])
+def test_host_entry_matches_device(g, mode, chunk):
+    """The host-buffer pipeline: 4 chunks (one buffer reused), 15 ragged
+    chunks (every buffer reused several times), 2 chunks, one chunk."""
     sc = scene("toy40")
     tr = scenes.sample_tracks(sc, 100000, 16)
-    s0, h0 = run_nav(g, sc, tr, 1)
-    s1, h1 = g.geo_dist_to_boundary_host(vol(g, sc), *tr.fields(), mode=1, chunk=30000)
+    s0, h0 = run_nav(g, sc, tr, mode)
+    s1, h1 = g.geo_dist_to_boundary_host(vol(g, sc), *tr.fields(), mode=mode, chunk=chunk)
     assert np.array_equal(s0.view(np.int64), s1.view(np.int64))
     assert np.array_equal(h0, h1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_host_entry_in_place(g, mode):
+    """Pinned host arrays: the step reads and writes them in place (no
+    staging); a ragged basket, a small one (the warp-per-track path), and
+    pinned inputs with a pageable output (staged again)."""
+    import torch
+
+    sc = scene("toy40")
+    v = vol(g, sc)
+    for n in (100003, 77):
+        tr = scenes.sample_tracks(sc, n, 18)
+        s0, h0 = run_nav(g, sc, tr, mode)
+        pinned = [torch.from_numpy(f).pin_memory() for f in tr.fields()]
+        s1, h1 = g.geo_dist_to_boundary_host(v, *pinned, mode=mode)
+        assert s1.is_pinned() and h1.is_pinned()
+        assert np.array_equal(s0.view(np.int64), s1.numpy().view(np.int64))
+        assert np.array_equal(h0, h1.numpy())
+        s2, h2 = g.geo_dist_to_boundary_host(v, *pinned, mode=mode, step=np.empty(n),
+                                             hit=torch.empty(n, dtype=torch.int32).pin_memory())
+        assert np.array_equal(s0.view(np.int64), s2.view(np.int64)) and np.array_equal(h0, h2.numpy())
+
+
+def test_host_entry_rejects_device_arrays(g):
+    import torch
+
+    sc = scene("toy40")
+    tr = scenes.sample_tracks(sc, 1000, 19)
+    d = [torch.from_numpy(f).cuda() for f in tr.fields()]
+    with pytest.raises(g.GeoError):
+        g.geo_dist_to_boundary_host(vol(g, sc), *d, mode=1, step=np.empty(1000), hit=np.empty(1000, np.int32))
 
 
 def test_full_size_toy_detector_sampled(g, orc):
