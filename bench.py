@@ -57,7 +57,7 @@ FP64_BPOINT = 3
 # counted as 4)
 FP32_SPHERE, FP32_TRANSFORM = 16, 18
 FP32_SHAPE = {0: 45, 1: 90, 2: 110}
-KERNEL_SOURCES = ("nav_refine.cu", "nav_refine.cuh", "shapes32.cuh", "shapes64.cuh", "nav_common.cuh",
+KERNEL_SOURCES = ("nav_refine.cu", "refine_kernel.cuh", "nav_refine.cuh", "shapes32.cuh", "shapes64.cuh", "nav_common.cuh",
                   "stage.cuh", "geo_internal.h")
 
 

@@ -84,6 +84,10 @@ typedef enum { GEO_BOX = 0, GEO_TUBE = 1, GEO_CONE = 2, GEO_TUBS = 3, GEO_PCON =
 
 #define GEO_MAX_PLANES 32
 
+/* Tracks per tile of the FP32-filter kernels and of the batched launches
+ * (geo_build_batch, geo_dist_to_boundary_batched_noalloc). */
+#define GEO_TILE_TRACKS 384
+
 /* GEO_FP64: every operation in FP64.
  * GEO_FP32_REFINE: a conservative FP32 pass bounds every candidate from below;
  * only candidates that can still win are recomputed with the same FP64
@@ -249,9 +253,10 @@ typedef struct {
 
 typedef struct geo_batch_s* geo_batch;
 
-/* Builds a batch: copies the baskets, splits them into tiles of 256
- * consecutive tracks, gathers the ragged remainders of each volume's baskets
- * into packed tiles of up to 256 tracks (listing their indices), orders the
+/* Builds a batch: copies the baskets, splits them into tiles of
+ * GEO_TILE_TRACKS consecutive tracks, gathers the ragged remainders of each
+ * volume's baskets into packed tiles of up to GEO_TILE_TRACKS tracks (listing
+ * their indices), orders the
  * tiles, and uploads the per-volume views, the tile list, the packed
  * indices and a tile counter to the device (the batch owns them).  The volumes must
  * stay alive while the batch is used.  All volumes must live on the current
@@ -283,7 +288,7 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
  * volume views, the tile counter and the status word are kept in a fixed
  * array of device memory owned by the library (about 0.55 MB, present on
  * every device that loads it until the process exits).  Limits: at most 64
- * volumes and 32768 tiles of 256 tracks (about 8.4 M tracks) per call; larger
+ * volumes and 32768 tiles of GEO_TILE_TRACKS tracks (about 12.6 M tracks) per call; larger
  * requests return GEO_ERR_INVALID_ARG.  vols: volumes built earlier with
  * geo_build_volume, on the current device.  baskets: HOST array, as for
  * geo_build_batch.  x..dz, step, hit: device arrays as for

@@ -4,7 +4,7 @@ segment and polycone daughters), after "Vectorising the detector geometry to
 optimize particle transport".  The compute path is libgeonav.so (hand-written CUDA for sm_103a)
 behind the C ABI of include/geo.h; `geonav` is its Python binding."""
 from .geonav import (GEO_BOX, GEO_CONE, GEO_FP32_REFINE, GEO_FP64, GEO_PCON, GEO_SAFETY_ESTIMATE, GEO_TUBE,  # noqa: F401
-                     GEO_TUBS, GeoError, Volume,
+                     GEO_TUBS, GEO_MAX_PLANES, GEO_TILE_TRACKS, GeoError, Volume,
                      geo_build_volume, geo_contains, geo_destroy_volume, geo_dist_to_boundary,
                      geo_dist_to_boundary_host, geo_dist_to_boundary_stats, geo_check_device_status, geo_probe_pipe,
                      geo_safety, geo_status_string, geo_volume_info, load, Batch, geo_build_batch,

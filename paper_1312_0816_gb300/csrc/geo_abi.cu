@@ -68,6 +68,14 @@ int num_sms_of(int dev) {
     return cache[dev];
 }
 
+// shared memory of one SM
+int sm_smem(int dev) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || v <= 0)
+        v = 100 * 1024;
+    return v;
+}
+
 int smem_budget(int dev) {
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
@@ -615,11 +623,13 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
         }
     }
     vw.smem64 = (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64)) <= smem_budget(dev)) ? 1 : 0;
-    // the refine kernel keeps ~53 KB of stage buffers and wants two blocks per
-    // SM, so its staged tables are capped at 56 KB; larger tables are read
-    // through L1 from global memory
+    // the refine kernel wants two blocks per SM: its staged tables get what
+    // half of an SM's shared memory leaves beside its two stage buffers (less
+    // the per-block reservation and static shared memory); larger tables are
+    // read through L1 from global memory
+    const int64_t stages = int64_t(refine_stage_bytes());
     vw.smem_refine = (int64_t(n_daughters) * int64_t(sizeof(ShapeRec64) + sizeof(ShapeRec32)) <=
-                      std::min(smem_budget(dev) - 56 * 1024, 56 * 1024))
+                      std::min(int64_t(smem_budget(dev)) - stages, int64_t(sm_smem(dev)) / 2 - 2048 - stages))
                          ? 1
                          : 0;
     *out = v;
@@ -835,10 +845,11 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
     for (int i = 0; i < n_vols; ++i)
         if (!vols[i] || vols[i]->device != dev) return GEO_ERR_INVALID_ARG;
-    // Every basket's full 256-track stretches become tiles of consecutive
-    // tracks; the ragged tails of a volume's baskets are gathered, in basket
-    // order, into packed tiles that list their tracks' indices, so that
-    // baskets of a few tracks still fill the producers' 256 threads.
+    // Every basket's full kTileTracks-track stretches become tiles of
+    // consecutive tracks; the ragged tails of a volume's baskets are
+    // gathered, in basket order, into packed tiles that list their tracks'
+    // indices, so that baskets of a few tracks still fill the producer
+    // threads.
     std::vector<BatchTile> tiles;
     std::vector<int64_t> cost;
     std::vector<std::vector<int64_t>> tails(static_cast<size_t>(n_vols));
@@ -848,22 +859,22 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
         if (bk.reserved != 0 || bk.volume < 0 || bk.volume >= n_vols || bk.offset < 0 || bk.count < 0)
             return GEO_ERR_INVALID_ARG;
         max_end = std::max(max_end, bk.offset + bk.count);
-        const int64_t full = bk.count / 256 * 256;
-        for (int64_t off = 0; off < full; off += 256) {
+        const int64_t full = bk.count / kTileTracks * kTileTracks;
+        for (int64_t off = 0; off < full; off += kTileTracks) {
             BatchTile t;
             t.vol = bk.volume;
-            t.count = 256;
+            t.count = kTileTracks;
             t.base = bk.offset + off;
             tiles.push_back(t);
-            cost.push_back(int64_t(256) * (vols[bk.volume]->view.nd + 1));
+            cost.push_back(int64_t(kTileTracks) * (vols[bk.volume]->view.nd + 1));
         }
         for (int64_t q = bk.offset + full; q < bk.offset + bk.count; ++q) tails[size_t(bk.volume)].push_back(q);
     }
     std::vector<int64_t> idx;
     for (int v = 0; v < n_vols; ++v) {
         const std::vector<int64_t>& tv = tails[size_t(v)];
-        for (size_t a = 0; a < tv.size(); a += 256) {
-            const size_t m = std::min<size_t>(256, tv.size() - a);
+        for (size_t a = 0; a < tv.size(); a += kTileTracks) {
+            const size_t m = std::min<size_t>(kTileTracks, tv.size() - a);
             BatchTile t;
             t.vol = v;
             t.count = -int32_t(m);

@@ -9,6 +9,8 @@ namespace geonav {
 
 constexpr int KBOX = 0, KTUBE = 1, KCONE = 2, KTUBS = 3, KPCON = 4;
 constexpr int kMaxPlanes = GEO_MAX_PLANES;
+// tracks per tile of the FP32-filter kernels (one per producer thread)
+constexpr int kTileTracks = GEO_TILE_TRACKS;
 
 // Plane table of one polycone of n planes (m = n - 1 sections), FP64:
 //  [0, n) z, [n, 2n) rmin, [2n, 3n) rmax, [3n, 3n+m) inner slopes b_in,
@@ -99,8 +101,9 @@ struct Basket {
     int64_t n;
 };
 
-// One tile of the batched launch: up to 256 consecutive tracks of one basket,
-// or (count < 0) up to 256 tracks of one volume listed from BatchView::idx[base].
+// One tile of the batched launch: up to kTileTracks consecutive tracks of one
+// basket, or (count < 0) up to kTileTracks tracks of one volume listed from
+// BatchView::idx[base].
 struct BatchTile {
     int32_t vol;
     int32_t count;
@@ -123,6 +126,12 @@ struct BatchView {
 constexpr unsigned ST_TMA_TIMEOUT = 1u;
 constexpr unsigned ST_BAD_INDEX = 2u;
 constexpr unsigned ST_SYNC_TIMEOUT = 4u;
+
+// shared memory of the refine kernel's two stage buffers (host)
+size_t refine_stage_bytes();
+// the refine kernel in its latency configuration (small baskets)
+cudaError_t launch_dist_refine_latency(const VolView& v, const Basket& b, double* step, int32_t* hit,
+                                       double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
 
 // launchers (host), each returns cudaGetLastError() of its launch
 cudaError_t launch_dist_fp64(const VolView& v, const Basket& b, double* step, int32_t* hit,

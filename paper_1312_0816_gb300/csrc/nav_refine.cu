@@ -20,191 +20,11 @@
 #include "nav_common.cuh"
 #include "nav_refine.cuh"
 #include "stage.cuh"
+#include "refine_kernel.cuh"
 
 namespace geonav {
 
-// Warp-specialised persistent kernel.  A block holds 8 producer warps (one
-// track per thread per tile of 256) and 4 consumer warps (one per SM
-// sub-partition: the FP64 units are per sub-partition, and the microbenchmark
-// shows one warp with a dependent FP64 chain keeps one busy).
-//  producers: FP32 pass of tile k, then bin each track's first FP64 task by
-//             solid kind (mother, box, tube, cone) into stage k%2, arrive on
-//             full[k%2]; then wait done[(k-1)%2] and finish tile k-1 (rare
-//             extra refinements, stores).
-//  consumers: wait full[k%2], evaluate the binned tasks of tile k in FP64 (a
-//             warp takes 32 consecutive tasks, so nearly always one kind),
-//             arrive on done[k%2].
-// The FP64 pipe therefore works on tile k while the FP32 pass of tile k+1 runs.
-// Every wait is bounded; a wait that runs out records ST_SYNC_TIMEOUT.
-constexpr int kProd = 256;
-constexpr int kCons = 128;
-constexpr int kThreads = kProd + kCons;
-
-struct Stage {
-    double pd[6][kProd];        // the tile's positions and directions (FP64)
-    double res[kProd];          // FP64 value of each track's first task
-    float L[kCand][kProd];      // stashed FP32 state for the producers' second half
-    int j[kCand][kProd];
-    float Lm[kProd];
-    float dropped[kProd];
-    int n[kProd];               // candidate count, -1: answer already final
-    int task[kProd];            // binned tasks: owner | (solid + 1) << 8
-    int cnt[4];
-};
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait; after one timeout the caller stops waiting altogether (its
-// results are then unreliable and the status word says so).
-constexpr uint32_t kSyncPolls = 1u << 20;
-__device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned int* status,
-                                                  bool& healthy) {
-    if (!healthy) return;
-    for (uint32_t it = 0; it < kSyncPolls; ++it)
-        if (mbar_try_wait(bar, parity)) return;
-    atomicOr(status, ST_SYNC_TIMEOUT);
-    healthy = false;
-}
-
-// FP64 task bins: 0 the mother, then box, tube (and tube segment), cone (and
-// polycone)
-__device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : (kind == KPCON ? 3 : 1 + kind); }
-
-__device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(kProd) : "memory"); }
-
-template <bool SMEM, int TRAV, bool SEGS>
-__global__ void __launch_bounds__(kThreads, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
-                                                             int32_t* __restrict__ hit,
-                                                             double* __restrict__ bpoint,
-                                                             int32_t* __restrict__ nref) {
-    // dynamic shared memory: the two stages, then (SMEM) the solid tables
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t bar;
-    __shared__ uint64_t full[2], done[2];
-    Stage* S = reinterpret_cast<Stage*>(smem_raw);
-    unsigned char* tables = smem_raw + 2 * sizeof(Stage);
-    const ShapeRec32* tab32 = v.d32;
-    const ShapeRec64* tab64 = v.d64;
-    if (SMEM) {
-        const uint32_t b32 = uint32_t(v.nd) * sizeof(ShapeRec32);
-        if (!stage_tables(tables, v.d32, b32, tables + b32, v.d64, uint32_t(v.nd) * sizeof(ShapeRec64), &bar,
-                          v.status))
-            return;
-        tab32 = reinterpret_cast<const ShapeRec32*>(tables);
-        tab64 = reinterpret_cast<const ShapeRec64*>(tables + b32);
-    }
-    const int t = threadIdx.x;
-    if (t == 0) {
-        mbar_init(&full[0], kProd / 32);
-        mbar_init(&full[1], kProd / 32);
-        mbar_init(&done[0], kCons / 32);
-        mbar_init(&done[1], kCons / 32);
-    }
-    __syncthreads();
-    const int64_t ntiles = (b.n + kProd - 1) / kProd;
-    const int K = int((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);   // tiles of this block
-    const int lane = t & 31;
-    bool healthy = true;
-
-    if (t < kProd) {
-        // ------------------------------------------------------ producers --
-        for (int k = 0; k <= K; ++k) {
-            if (k < K) {
-                Stage& st_ = S[k & 1];
-                const int64_t i = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * kProd + t;
-                const bool live = i < b.n;
-                double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
-                if (live) {
-                    px = b.x[i]; py = b.y[i]; pz = b.z[i];
-                    qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
-                }
-                st_.pd[0][t] = px; st_.pd[1][t] = py; st_.pd[2][t] = pz;
-                st_.pd[3][t] = qx; st_.pd[4][t] = qy; st_.pd[5][t] = qz;
-                RefineState rs;
-                double best = 0.0;
-                int h = -2, nev = 0;
-                rs.status = 1;
-                if (live) refine_pass1<TRAV, SEGS>(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
-                int task = 0, bin = -1;
-                if (rs.status == 0) {
-                    task = first_task(rs);
-                    bin = task < 0 ? 0 : kind_bin(tab64[task].kind);
-                }
-                if (t < 4) st_.cnt[t] = 0;
-                producer_barrier();
-                const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
-                producer_barrier();
-                int start = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < bin) start += st_.cnt[q];
-                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << 8);
-                // stash the FP32 state; final answers are stored right away
-                if (rs.status == 0) {
-#pragma unroll
-                    for (int q = 0; q < kCand; ++q) {
-                        st_.L[q][t] = rs.c.L[q];
-                        st_.j[q][t] = rs.c.j[q];
-                    }
-                    st_.Lm[t] = rs.Lm;
-                    st_.dropped[t] = rs.c.dropped;
-                    st_.n[t] = rs.c.n;
-                } else {
-                    st_.n[t] = -1;
-                    if (live) {
-                        store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
-                        if (nref) nref[i] = nev;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[k & 1]);
-            }
-            if (k >= 1) {
-                const int kp = k - 1;
-                Stage& sp = S[kp & 1];
-                mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), v.status, healthy);
-                const int64_t i = (int64_t(blockIdx.x) + int64_t(kp) * gridDim.x) * kProd + t;
-                if (i < b.n && sp.n[t] >= 0) {
-                    RefineState rs;
-                    rs.status = 0;
-                    rs.c.n = sp.n[t];
-#pragma unroll
-                    for (int q = 0; q < kCand; ++q) {
-                        rs.c.L[q] = sp.L[q][t];
-                        rs.c.j[q] = sp.j[q][t];
-                    }
-                    rs.c.dropped = sp.dropped[t];
-                    rs.Lm = sp.Lm[t];
-                    const double px = sp.pd[0][t], py = sp.pd[1][t], pz = sp.pd[2][t];
-                    const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
-                    double best;
-                    int h, nev;
-                    refine_rest<SEGS>(v, tab64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
-                    store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
-                    if (nref) nref[i] = nev;
-                }
-            }
-        }
-    } else {
-        // ------------------------------------------------------ consumers --
-        const int c = t - kProd;
-        for (int k = 0; k < K; ++k) {
-            Stage& st_ = S[k & 1];
-            mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), v.status, healthy);
-            const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
-            for (int q = c; q < total; q += kCons) {
-                const int e = st_.task[q];
-                const int o = e & (kProd - 1), jj = (e >> 8) - 1;
-                st_.res[o] = eval64<SEGS>(v, tab64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
-                                    st_.pd[4][o], st_.pd[5][o]);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&done[k & 1]);
-        }
-    }
-}
+size_t refine_stage_bytes() { return 2 * sizeof(Stage<kProd>); }
 
 // ---------------------------------------------------------------------------
 // Batched persistent launch: tiles of many logical volumes, claimed in order
@@ -230,8 +50,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                                                               int32_t* __restrict__ hit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full[2], done[2];
-    Stage* S = reinterpret_cast<Stage*>(smem_raw);
-    TileHdr* H = reinterpret_cast<TileHdr*>(smem_raw + 2 * sizeof(Stage));
+    Stage<kProd>* S = reinterpret_cast<Stage<kProd>*>(smem_raw);
+    TileHdr* H = reinterpret_cast<TileHdr*>(smem_raw + 2 * sizeof(Stage<kProd>));
     const int t = threadIdx.x;
     const int lane = t & 31;
     bool healthy = true;
@@ -249,7 +69,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
         int64_t prev_i = 0;      // this thread's track in the previous tile
         bool prev_live = false;
         for (int k = 0;; ++k) {
-            Stage& st_ = S[k & 1];
+            Stage<kProd>& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
             if (t == 0) {
                 const unsigned q = atomicAdd(bv.counter, 1u);
@@ -264,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 }
                 st_.cnt[0] = st_.cnt[1] = st_.cnt[2] = st_.cnt[3] = 0;
             }
-            producer_barrier();
+            producer_barrier<kProd>();
             const int tile = hd.tile;
             int64_t cur_i = 0;
             bool cur_live = false;
@@ -274,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 const int64_t base = hd.base;
                 const bool packed = hd.count < 0;
                 const int count = packed ? -hd.count : hd.count;
-                producer_barrier();
+                producer_barrier<kProd>();
                 const VolView& v = hd.vol;
                 const bool live = t < count;
                 const int64_t i = live ? (packed ? bv.idx[base + t] : base + t) : 0;
@@ -298,12 +118,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                     bin = task < 0 ? 0 : kind_bin(v.d64[task].kind);
                 }
                 const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
-                producer_barrier();
+                producer_barrier<kProd>();
                 int start = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (q < bin) start += st_.cnt[q];
-                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << 8);
+                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << kOwnerBits);
                 if (rs.status == 0) {
 #pragma unroll
                     for (int q = 0; q < kCand; ++q) {
@@ -322,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
             if (lane == 0) mbar_arrive(&full[k & 1]);
             if (k >= 1) {
                 const int kp = k - 1;
-                Stage& sp = S[kp & 1];
+                Stage<kProd>& sp = S[kp & 1];
                 const VolView& vp = H[kp & 1].vol;
                 mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), bv.status, healthy);
                 if (prev_live && sp.n[t] >= 0) {
@@ -352,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
         // ------------------------------------------------------ consumers --
         const int c = t - kProd;
         for (int k = 0;; ++k) {
-            Stage& st_ = S[k & 1];
+            Stage<kProd>& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), bv.status, healthy);
             if (!healthy || hd.tile < 0) break;
@@ -360,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
             const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
             for (int q = c; q < total; q += kCons) {
                 const int e = st_.task[q];
-                const int o = e & (kProd - 1), jj = (e >> 8) - 1;
+                const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
                 st_.res[o] = eval64<SEGS>(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
                                     st_.pd[4][o], st_.pd[5][o]);
             }
@@ -374,7 +194,7 @@ template <bool SEGS>
 static int batched_blocks_per_sm() {
     static int cached = 0;
     if (cached == 0) {
-        const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
+        const int smem = 2 * int(sizeof(Stage<kProd>) + sizeof(TileHdr));
         int per_sm = 0;
         if (cudaFuncSetAttribute(k_dist_batched<SEGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
                 cudaSuccess ||
@@ -396,7 +216,7 @@ int batched_max_blocks_per_sm(bool segs) {
 template <bool SEGS>
 static cudaError_t launch_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
                                   cudaStream_t s, int num_sms) {
-    const int smem = 2 * int(sizeof(Stage) + sizeof(TileHdr));
+    const int smem = 2 * int(sizeof(Stage<kProd>) + sizeof(TileHdr));
     const int maxb = batched_blocks_per_sm<SEGS>();
     const int per_sm = (blocks_per_sm <= 0 || blocks_per_sm > maxb) ? maxb : blocks_per_sm;
     cudaError_t e = cudaFuncSetAttribute(k_dist_batched<SEGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -412,44 +232,14 @@ cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* st
                    : launch_batched<false>(bv, b, step, hit, blocks_per_sm, s, num_sms);
 }
 
-template <typename K>
-static int grid_refine(K kernel, int64_t n, int smem, int num_sms) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    const int64_t need = (n + kProd - 1) / kProd;
-    const int64_t cap = int64_t(per_sm) * num_sms;
-    return int(need < cap ? need : cap);
-}
-
-template <typename K>
-static cudaError_t launch_refine(K kernel, int smem, const VolView& v, const Basket& b, double* step, int32_t* hit,
-                                 double* bpoint, int32_t* nref, cudaStream_t s, int num_sms) {
-    cudaError_t e = prep(kernel, smem);
-    if (e != cudaSuccess) return e;
-    kernel<<<grid_refine(kernel, b.n, smem, num_sms), kThreads, smem, s>>>(v, b, step, hit, bpoint, nref);
-    return cudaGetLastError();
-}
-
+// A basket that gives each of the two resident blocks per SM at most one
+// tile of 256 tracks takes the latency configuration, larger ones the
+// throughput configuration.
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms) {
-    static_assert(sizeof(Stage) % 16 == 0, "stage size keeps the tables 16-byte aligned");
-    const int stages = 2 * int(sizeof(Stage));
-    const int smem = stages + (v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0);
-    // SEGS: the instantiation with the tube segment's code only for volumes
-    // that hold one, so the others keep the leaner kernel
-    if (v.voxelized) {
-        if (v.segs) return launch_refine(k_dist_refine<false, 1, true>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
-        return launch_refine(k_dist_refine<false, 1, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
-    }
-    if (v.smem_refine) {
-        if (v.segs) return launch_refine(k_dist_refine<true, 0, true>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
-        return launch_refine(k_dist_refine<true, 0, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
-    }
-    if (v.segs) return launch_refine(k_dist_refine<false, 0, true>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
-    return launch_refine(k_dist_refine<false, 0, false>, smem, v, b, step, hit, bpoint, nref, s, num_sms);
+    if (b.n <= int64_t(2) * num_sms * kLatProd)
+        return launch_dist_refine_latency(v, b, step, hit, bpoint, nref, s, num_sms);
+    return launch_refine_cfg<kProd, kCons>(v, b, step, hit, bpoint, nref, s, num_sms);
 }
 
 // Small baskets take the warp-per-track FP64 kernel (the same answers: both

@@ -25,8 +25,7 @@ using namespace geonav;
 namespace {
 
 constexpr int kNoAllocMaxVolumes = 64;
-constexpr int kNoAllocMaxTiles = 32768;   // tiles of at most 256 tracks
-constexpr int kTileTracks = 256;
+constexpr int kNoAllocMaxTiles = 32768;   // tiles of at most kTileTracks tracks
 
 struct NoAllocScratch {
     VolView vols[kNoAllocMaxVolumes];
@@ -102,7 +101,7 @@ extern "C" geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vol
     NoAllocScratch* d = nullptr;
     geo_status st = scratch_on(dev, &d);
     if (st != GEO_OK) return st;
-    // tiles of at most 256 tracks, largest estimated cost (tracks x daughters) first
+    // tiles of at most kTileTracks tracks, largest estimated cost (tracks x daughters) first
     int64_t m = 0;
     for (int k = 0; k < n_baskets; ++k) {
         const geo_basket& bk = baskets[k];

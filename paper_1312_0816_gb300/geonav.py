@@ -20,6 +20,7 @@ GEO_FP32_REFINE = 1
 GEO_SAFETY_ESTIMATE = 2   # geo_safety only: the cheaper under-estimate
 GEO_BOX, GEO_TUBE, GEO_CONE, GEO_TUBS, GEO_PCON = 0, 1, 2, 3, 4
 GEO_MAX_PLANES = 32
+GEO_TILE_TRACKS = 384   # include/geo.h: tracks per tile of the filter kernels and batched launches
 
 _STATUS = {0: "GEO_OK", 1: "GEO_ERR_INVALID_ARG", 2: "GEO_ERR_SHAPE_PARAMS", 3: "GEO_ERR_OOM",
            4: "GEO_ERR_CUDA", 5: "GEO_ERR_DEVICE_ASSERT", 6: "GEO_ERR_UNSUPPORTED"}

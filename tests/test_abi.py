@@ -31,6 +31,21 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(geonav, name), name
 
 
+def test_binding_constants_match_the_header():
+    """Every #define and enum constant of include/geo.h has the same value in
+    the binding."""
+    src = open(os.path.join(ROOT, "include", "geo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"#define\s+(GEO_[A-Z0-9_]+)\s+(\d+)", src)}
+    for body in re.findall(r"typedef enum\s*\{(.*?)\}", src, flags=re.S):
+        consts.update({k: int(v) for k, v in re.findall(r"(GEO_[A-Z0-9_]+)\s*=\s*(\d+)", body)})
+    assert {"GEO_MAX_PLANES", "GEO_TILE_TRACKS", "GEO_PCON", "GEO_SAFETY_ESTIMATE"} <= set(consts)
+    for k, v in consts.items():
+        if k.startswith("GEO_ERR_") or k == "GEO_OK":
+            continue
+        assert getattr(geonav, k) == v, k
+
+
 def test_status_strings():
     for s in range(7):
         assert geonav.geo_status_string(s)

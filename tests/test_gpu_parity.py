@@ -97,7 +97,8 @@ def test_box4_basket_1024(g, orc, mode):
                                     ("grid512", 8191), ("pcon4", 30011), ("pconm", 30011)])
 @pytest.mark.parametrize("mode", [0, 1])
 def test_scene_parity(g, orc, name, n, mode):
-    """Several blocks of 256 tracks and a ragged tail."""
+    """Several tiles of tracks (GEO_TILE_TRACKS, and the plain kernel's blocks of
+    256) and a ragged tail."""
     sc = scene(name)
     tr = scenes.sample_tracks(sc, n, 101)
     ref = orc.navigate(sc, tr, nthreads=8)
@@ -116,6 +117,24 @@ def test_refine_equals_fp64_bitwise(g, name):
         assert np.array_equal(h0, h1)
         assert np.array_equal(s0.view(np.int64), s1.view(np.int64))
         assert np.array_equal(b0.view(np.int64), b1.view(np.int64))
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_refine_block_configurations(g, name):
+    """Both block configurations of the filter kernel -- 8 + 4 warps with
+    tiles of 256 tracks while a basket gives each of two blocks per SM at most
+    one tile, 12 + 2 warps with tiles of GEO_TILE_TRACKS beyond -- return the
+    plain FP64 bits, on either side of the switch and with a ragged tail."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    edge = 2 * sms * 256
+    sc = scene(name)
+    base = scenes.sample_tracks(sc, edge + 3 * g.GEO_TILE_TRACKS + 17, 21)
+    for n in (edge, edge + 1, base.n):
+        tr = scenes.Tracks(*(f[:n] for f in base.fields()))
+        s0, h0 = run_nav(g, sc, tr, 0)
+        s1, h1 = run_nav(g, sc, tr, 1)
+        assert np.array_equal(h0, h1), n
+        assert np.array_equal(s0.view(np.int64), s1.view(np.int64)), n
 
 
 @pytest.mark.parametrize("name", ["box4", "toy40", "diff3", "grid512", "seg4", "pcon4", "pconm"])

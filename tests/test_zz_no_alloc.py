@@ -48,7 +48,7 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
         pytest.skip("no CUDA device")
     sc = scenes.box4(0)
     vol = g.geo_build_volume(sc)
-    n = 32768 * 256 + 1   # one track more than 32768 full tiles
+    n = 32768 * g.GEO_TILE_TRACKS + 1   # one track more than 32768 full tiles
     x = [torch.zeros(1, dtype=torch.float64, device="cuda").expand(n).contiguous() for _ in range(6)]
     step = torch.empty(n, dtype=torch.float64, device="cuda")
     hit = torch.empty(n, dtype=torch.int32, device="cuda")
