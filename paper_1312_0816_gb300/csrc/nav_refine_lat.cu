@@ -1,7 +1,7 @@
 // nav_refine_lat.cu -- the refine kernel in its latency configuration (8
-// producer + 4 consumer warps, tiles of 256 tracks) for baskets that give
-// every resident block at most one tile; a translation unit of its own so
-// that the two configurations compile in parallel.
+// producer + 4 consumer warps, tiles of 256 tracks) for baskets of at most
+// two tiles per resident block; a translation unit of its own so that the
+// two configurations compile in parallel.
 #include "refine_kernel.cuh"
 
 namespace geonav {

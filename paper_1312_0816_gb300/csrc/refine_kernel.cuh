@@ -33,9 +33,9 @@ namespace geonav {
 // C consumer threads):
 //  * 12 + 2 warps, tiles of kTileTracks = 384: throughput (many tiles per
 //    block; the batched launch);
-//  * 8 + 4 warps, tiles of 256: baskets that give every block at most one
-//    tile, where the latency of a tile's FP64 phase with 2 consumer warps
-//    would set the time (1024 tracks: 32 us per call instead of 46 us).
+//  * 8 + 4 warps, tiles of 256: baskets of at most two tiles per block,
+//    where the latency of a tile's FP64 phase with 2 consumer warps would
+//    set the time (1024 tracks: 32 us per call instead of 46 us).
 constexpr int kProd = kTileTracks;   // the batched launch
 constexpr int kCons = 64;
 constexpr int kThreads = kProd + kCons;

@@ -122,11 +122,11 @@ def test_refine_equals_fp64_bitwise(g, name):
 @pytest.mark.parametrize("name", list(SCENES))
 def test_refine_block_configurations(g, name):
     """Both block configurations of the filter kernel -- 8 + 4 warps with
-    tiles of 256 tracks while a basket gives each of two blocks per SM at most
-    one tile, 12 + 2 warps with tiles of GEO_TILE_TRACKS beyond -- return the
-    plain FP64 bits, on either side of the switch and with a ragged tail."""
+    tiles of 256 tracks while a basket has at most two tiles for each of two
+    blocks per SM, 12 + 2 warps with tiles of GEO_TILE_TRACKS beyond -- return
+    the plain FP64 bits, on either side of the switch and with a ragged tail."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    edge = 2 * sms * 256
+    edge = 4 * sms * 256
     sc = scene(name)
     base = scenes.sample_tracks(sc, edge + 3 * g.GEO_TILE_TRACKS + 17, 21)
     for n in (edge, edge + 1, base.n):
