@@ -5,7 +5,7 @@
 // U of the mother exit, master->local transform in a frame shifted to the
 // track's closest approach to the daughter's origin, and a LOWER bound L_j of
 // DistFromOutside from the daughter's inflated FP32 copy (shapes32.cuh).  The
-// K smallest bounds are kept in registers, sorted.
+// kCand = 2 smallest bounds are kept in registers, sorted.
 // Pass 2 (FP64, few solids): candidates are refined in ascending order of
 // their bounds, the mother (bound L_m of its exit) taking its place in that
 // order, with the same FP64 routines as the plain kernel; refinement stops as

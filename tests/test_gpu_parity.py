@@ -119,6 +119,36 @@ def test_refine_equals_fp64_bitwise(g, name):
         assert np.array_equal(b0.view(np.int64), b1.view(np.int64))
 
 
+@pytest.mark.parametrize("n", [5000, 200003])
+def test_refine_fallback_to_the_full_loop(g, orc, n):
+    """Five identical overlapping boxes (and one box apart): the entering
+    distances of the five tie bit for bit, so their FP32 bounds tie too and
+    the candidate list (two entries) has to evict one whose bound equals the
+    best; those tracks take the full FP64 loop.  The answers are the oracle's
+    (a tie goes to the lowest index) and the plain FP64 kernel's bits, in both
+    block configurations of the filter kernel."""
+    eye = np.eye(3).reshape(9)
+    box = (0, (20.0, 30.0, 40.0), eye, (0.0, 0.0, 0.0))
+    other = (0, (10.0, 10.0, 10.0), eye, (0.0, 150.0, 0.0))
+    sc = scene_from_spec((0, (400.0, 400.0, 400.0)), [other, box, box, box, box, box], name="ties")
+    rng = np.random.default_rng(23)
+    side = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    p = np.stack([60.0 * side, rng.uniform(-25.0, 25.0, n), rng.uniform(-35.0, 35.0, n)], axis=1)
+    d = rng.normal(scale=0.3, size=(n, 3))
+    d[:, 0] = -side
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    tr = tracks_from(p, d)
+    ref = orc.navigate(sc, tr, nthreads=8)
+    s0, h0 = run_nav(g, sc, tr, 0)
+    s1, h1 = run_nav(g, sc, tr, 1)
+    assert np.array_equal(h0, h1) and np.array_equal(s0.view(np.int64), s1.view(np.int64))
+    assert np.array_equal(h1, ref["hit"])
+    assert np.max(np.abs(s1 - ref["step"])) <= STEP_TOL
+    assert np.mean(h1 == 1) > 0.5 and not np.any(h1 >= 2)   # every box hit goes to the first copy
+    _, _, nref = g.geo_dist_to_boundary_stats(vol(g, sc), *dev(tr))
+    assert np.mean(nref.cpu().numpy() >= 1000) > 0.5
+
+
 @pytest.mark.parametrize("name", list(SCENES))
 def test_refine_block_configurations(g, name):
     """Both block configurations of the filter kernel -- 8 + 4 warps with
