@@ -12,21 +12,70 @@ namespace geonav {
 
 constexpr int kQueryTable32Max = 96 * 1024;   // bytes of FP32 records staged per block
 
+// Contains: per tile of 256 points, the FP32 tests run per thread and give
+// each point its first candidate (the first daughter whose inflated copy
+// holds it); the FP64 decisions for those candidates are binned by solid
+// kind and taken by whole warps over the binned list, as in the Safety
+// kernel below (the FP64 pipe charges a warp instruction whatever its active
+// lanes, and a thread-per-point loop runs the FP64 test once for every
+// daughter that any lane of the warp stops at).  A point whose candidate
+// fails goes on with the remaining candidates on its own thread (rare).
 template <bool SMEM, bool SEGS>
 __global__ void __launch_bounds__(256) k_contains32(VolView v, Basket b, int32_t* __restrict__ where) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bar;
+    __shared__ double s_p[3][256];
+    __shared__ int s_task[256];
+    __shared__ int s_list[256];
+    __shared__ unsigned char s_in[256];
+    __shared__ int s_cnt[5];
     const ShapeRec32* t32 = v.d32;
     if (SMEM) {
         if (!stage_table(smem_raw, v.d32, uint32_t(v.nd) * sizeof(ShapeRec32), &bar, v.status)) return;
         t32 = reinterpret_cast<const ShapeRec32*>(smem_raw);
     }
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < b.n; i += stride) {
-        double p[3];
-        float p32[3];
-        point32(b, i, p, p32);
-        where[i] = contains_filter<SEGS>(v, t32, p, p32);
+    const int t = threadIdx.x;
+    const int64_t ntiles = (b.n + 255) / 256;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t i = tile * 256 + t;
+        const bool live = i < b.n;
+        double p[3] = {0.0, 0.0, 0.0};
+        float p32[3] = {0.f, 0.f, 0.f};
+        if (live) point32(b, i, p, p32);
+        int w = -2, j1 = -1;
+        if (live && mother_contains<SEGS>(v, p, p32)) {
+            w = -1;
+            j1 = contains_next(v, t32, p32, 0);
+        }
+        const int kd = j1 >= 0 ? v.d64[j1].kind : -1;
+        const int bin = (kd >= 0 && kd < 5) ? kd : -1;
+        s_p[0][t] = p[0];
+        s_p[1][t] = p[1];
+        s_p[2][t] = p[2];
+        s_task[t] = j1;
+        if (t < 5) s_cnt[t] = 0;
+        __syncthreads();
+        const int slot = bin >= 0 ? atomicAdd(&s_cnt[bin], 1) : 0;
+        __syncthreads();
+        int start = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            if (q < bin) start += s_cnt[q];
+        if (bin >= 0) s_list[start + slot] = t;
+        const int total = s_cnt[0] + s_cnt[1] + s_cnt[2] + s_cnt[3] + s_cnt[4];
+        __syncthreads();
+        for (int q = t; q < total; q += 256) {
+            const int o = s_list[q];
+            const double po[3] = {s_p[0][o], s_p[1][o], s_p[2][o]};
+            s_in[o] = contains_daughter64<SEGS>(v, s_task[o], po) ? 1 : 0;
+        }
+        __syncthreads();
+        if (live) {
+            if (bin >= 0) w = s_in[t] ? j1 : contains_rest<SEGS>(v, t32, p, p32, j1);
+            else if (j1 >= 0) w = contains_filter<SEGS>(v, t32, p, p32);   // a kind outside the bins
+            where[i] = w;
+        }
+        __syncthreads();   // the tile's shared arrays are rewritten next
     }
 }
 

@@ -63,24 +63,50 @@ __device__ __forceinline__ void local32(const ShapeRec32& r, const float* w, flo
     for (int k = 0; k < 3; ++k) x[k] = fmaf(r.R[6 + k], w[2], fmaf(r.R[3 + k], w[1], r.R[k] * w[0]));
 }
 
-// Contains of one point: -2, -1 or the lowest daughter index.
-template <bool SEGS = true>
-__device__ __forceinline__ int contains_filter(const VolView& v, const ShapeRec32* __restrict__ t32,
-                                               const double* p, const float* p32) {
-    if (!mother_contains<SEGS>(v, p, p32)) return -2;
-    for (int j = 0; j < v.nd; ++j) {
+// The first daughter from index `from` on whose inflated FP32 copy holds the
+// point (-1: none).  A point inside a daughter is inside its copy, so no
+// daughter skipped here can contain it.
+__device__ __forceinline__ int contains_next(const VolView& v, const ShapeRec32* __restrict__ t32, const float* p32,
+                                             int from) {
+    for (int j = from; j < v.nd; ++j) {
         const ShapeRec32& r = t32[j];
         float o[3], x[3];
         const float c2 = offset32(r, p32, o);
         if (c2 > r.brad * r.brad * (1.f + kSafMargin)) continue;   // outside the bounding sphere
         local32(r, o, x);
-        if (!contains32(r, x)) continue;
-        const ShapeRec64& r64 = v.d64[j];
-        double xl[3];
-        point_to_local64(r64, p[0], p[1], p[2], xl);
-        if (contains64<SEGS>(r64, xl)) return j;
+        if (contains32(r, x)) return j;
     }
     return -1;
+}
+
+// The FP64 decision for daughter j, with the plain kernel's routines.
+template <bool SEGS = true>
+__device__ __forceinline__ bool contains_daughter64(const VolView& v, int j, const double* p) {
+    const ShapeRec64& r64 = v.d64[j];
+    double xl[3];
+    point_to_local64(r64, p[0], p[1], p[2], xl);
+    return contains64<SEGS>(r64, xl);
+}
+
+// After the FP64 test of candidate j failed: the remaining candidates in
+// index order (rare: the inflated copies of daughters seldom overlap).
+template <bool SEGS = true>
+__device__ __forceinline__ int contains_rest(const VolView& v, const ShapeRec32* __restrict__ t32, const double* p,
+                                             const float* p32, int j) {
+    for (j = contains_next(v, t32, p32, j + 1); j >= 0; j = contains_next(v, t32, p32, j + 1))
+        if (contains_daughter64<SEGS>(v, j, p)) return j;
+    return -1;
+}
+
+// Contains of one point: -2, -1 or the lowest daughter index.
+template <bool SEGS = true>
+__device__ __forceinline__ int contains_filter(const VolView& v, const ShapeRec32* __restrict__ t32,
+                                               const double* p, const float* p32) {
+    if (!mother_contains<SEGS>(v, p, p32)) return -2;
+    const int j = contains_next(v, t32, p32, 0);
+    if (j < 0) return -1;
+    if (contains_daughter64<SEGS>(v, j, p)) return j;
+    return contains_rest<SEGS>(v, t32, p, p32, j);
 }
 
 // FP64 safety of candidate k (-1: mother inside-safety, else daughter k's
