@@ -68,21 +68,31 @@ __device__ __forceinline__ void world_to_node(const double* G, double px, double
     }
 }
 
-// The lowest-index daughter of v other than `skip` whose closed solid holds
-// the point x (v's frame), -1 if none.  A daughter is excluded in FP32 when
-// the point lies outside its inflated bounding sphere or its inflated FP32
-// copy (then the exact point is outside by more than the FP64 rounding); the
-// rest are tested in FP64, in index order (as Contains in queries.cuh).
-__device__ __forceinline__ int first_containing(const VolView& v, const double* x, int skip, double* xl) {
-    const float p32[3] = {f64_to_f32_trunc(x[0]), f64_to_f32_trunc(x[1]), f64_to_f32_trunc(x[2])};
-    for (int j = 0; j < v.nd; ++j) {
+// The first daughter of v from index `from` on, other than `skip`, whose
+// inflated FP32 copy holds the FP32 point (-1: none).  A daughter is excluded
+// when the point lies outside its inflated bounding sphere or its inflated
+// copy (then the exact point is outside by more than the FP64 rounding).
+__device__ __forceinline__ int next_candidate(const VolView& v, const float* p32, int skip, int from) {
+    for (int j = from; j < v.nd; ++j) {
         if (j == skip) continue;
         const ShapeRec32& r = v.d32[j];
         float o[3], xs[3];
         const float c2 = offset32(r, p32, o);
         if (c2 > r.brad * r.brad * (1.f + kSafMargin)) continue;
         local32(r, o, xs);
-        if (!contains32(r, xs)) continue;
+        if (contains32(r, xs)) return j;
+    }
+    return -1;
+}
+
+// The lowest-index daughter of v other than `skip` whose closed solid holds
+// the point x (v's frame), -1 if none: the candidates of the FP32 tests are
+// tested in FP64 in index order (as Contains in queries.cuh).  The FP64 test
+// sits outside the candidate search, so the lanes of a warp take it together
+// instead of once for every daughter at which one of them stops.
+__device__ __forceinline__ int first_containing(const VolView& v, const double* x, int skip, double* xl) {
+    const float p32[3] = {f64_to_f32_trunc(x[0]), f64_to_f32_trunc(x[1]), f64_to_f32_trunc(x[2])};
+    for (int j = next_candidate(v, p32, skip, 0); j >= 0; j = next_candidate(v, p32, skip, j + 1)) {
         const ShapeRec64& r64 = v.d64[j];
         point_to_local64(r64, x[0], x[1], x[2], xl);
         if (contains64(r64, xl)) return j;
