@@ -54,12 +54,15 @@ def lib():
         L.orc_adjoint.restype = None
         L.orc_shape_batch.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int, dp, ip]
         L.orc_shape_batch.restype = None
+        L.orc_shape_batch_err.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int, ctypes.c_double,
+                                          dp, dp]
+        L.orc_shape_batch_err.restype = None
         world = [ctypes.c_int, ip, dp, ip, ip, ip, dp, dp, dp, ip, dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip]
         L.orc_world_nodes.argtypes = world
         L.orc_world_nodes.restype = ctypes.c_int
         L.orc_world_locate.argtypes = world + [ctypes.c_int64, dp, dp, dp, ip]
         L.orc_world_locate.restype = ctypes.c_int
-        L.orc_world_step.argtypes = world + [ctypes.c_int64] + [dp] * 6 + [ip, ip, dp, ip, ip]
+        L.orc_world_step.argtypes = world + [ctypes.c_int64] + [dp] * 6 + [ip, ip, dp, ip, ip, dp, ip, ip]
         L.orc_world_step.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -187,6 +190,31 @@ def shape(kind: int, params, x, u=None, what: str = "dist_out"):
     return out
 
 
+def shape_err(kind: int, params, x, u, what: str = "dist_out", tnorm: float = 0.0):
+    """For a distance query of one solid: the answer's a-priori FP64 error
+    bound (tnorm: distance of the solid's placement from the frame the query
+    was posed in) and the gap to the nearest crossing of another of its
+    surfaces.  Returns (err, gap)."""
+    p = np.zeros(5)
+    planes = np.zeros(1)
+    if hasattr(params, "rmax"):
+        planes = np.concatenate([np.asarray(params.z, float), np.asarray(params.rmin, float),
+                                 np.asarray(params.rmax, float)])
+        p[:4] = (params.sphi, params.dphi, len(params.z), 0)
+    else:
+        p[: len(params)] = params
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, 3))
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 3))
+    n = x.shape[0]
+    err = np.empty(n)
+    gap = np.empty(n)
+    pa, pp = _d(p)
+    pl, plp = _d(planes)
+    lib().orc_shape_batch_err(int(kind), pp, plp, n, _d(x)[1], _d(u)[1], _WHAT[what], float(tnorm), _d(err)[1],
+                              _d(gap)[1])
+    return err, gap
+
+
 MAX_NODES = 1 << 20
 
 
@@ -222,13 +250,15 @@ def world_locate(world, tracks):
     return node
 
 
-def world_step(world, tracks, node_in, blocked_in=None):
+def world_step(world, tracks, node_in, blocked_in=None, info=False):
     """The step of Fig. 1 in each track's node, then the track's node after
     the step (-1 left the root, -2 not inside its node or invalid) and its
     flag: j >= 0 = daughter j of the node was just left (its re-entry
     distance replaces DistFromOutside), -2 = the node was just entered
     through its surface, -1 = none (after Locate).  Returns step, node,
-    flag."""
+    flag, and with info=True a dict of the step's a-priori FP64 error bound
+    (err, the node's placements included), the winner in the node's volume
+    (hit) and its surface (face)."""
     keep, table, args = _world_args(world)
     kt, targs = _track_args(tracks)
     nin, nptr = _i(node_in)
@@ -238,5 +268,11 @@ def world_step(world, tracks, node_in, blocked_in=None):
     step = np.empty(tracks.n)
     node = np.empty(tracks.n, dtype=np.int32)
     blk = np.empty(tracks.n, dtype=np.int32)
-    assert lib().orc_world_step(*args, tracks.n, *targs, nptr, bptr, _d(step)[1], _i(node)[1], _i(blk)[1]) > 0
+    err = np.empty(tracks.n)
+    hit = np.empty(tracks.n, dtype=np.int32)
+    face = np.empty(tracks.n, dtype=np.int32)
+    assert lib().orc_world_step(*args, tracks.n, *targs, nptr, bptr, _d(step)[1], _i(node)[1], _i(blk)[1],
+                                _d(err)[1], _i(hit)[1], _i(face)[1]) > 0
+    if info:
+        return step, node, blk, {"err": err, "hit": hit, "face": face}
     return step, node, blk

@@ -835,12 +835,110 @@ typedef struct {
     double err;    /* a-priori FP64 error bound of the step                      */
 } navres;
 
+/* Radius line R(z) = ra + rb z of a quadric face (rho = R(z)); 0 for a face
+ * that is a plane. */
+static int face_line(int kind, const double *p, int f, double *ra, double *rb) {
+    if (kind == K_BOX || f == F_ZM || f == F_ZP || f == F_PHI1 || f == F_PHI2 || f < 0) return 0;
+    if (kind == K_TUBE || kind == K_TUBS) {
+        if (f != F_OUT && f != F_IN) return 0;
+        *ra = f == F_OUT ? p[1] : p[0];
+        *rb = 0.0;
+        return 1;
+    }
+    if (kind == K_CONE) {
+        if (f != F_OUT && f != F_IN) return 0;
+        const double r1 = f == F_OUT ? p[2] : p[1], r2 = f == F_OUT ? p[4] : p[3];
+        *rb = (r2 - r1) / (2.0 * p[0]);
+        *ra = 0.5 * (r1 + r2);
+        return 1;
+    }
+    if (f < F_SEC) return 0;
+    const int nz = (int)p[2];
+    const double *z = p + 3, *rn = z + nz, *rx = rn + nz;
+    const int k = (f - F_SEC) / 2;
+    const double *r = ((f - F_SEC) % 2) == 0 ? rx : rn;
+    if (k + 1 >= nz) return 0;
+    *rb = (r[k + 1] - r[k]) / (z[k + 1] - z[k]);
+    *ra = r[k] - *rb * z[k];
+    return 1;
+}
+
 /* blocked >= 0: that daughter was just left through its surface; it enters
  * the minimum with its re-entry distance instead of DistFromOutside (0).
  * blocked == -2: the track has just entered the mother through its surface;
  * the mother's exit is that of the component being entered, and a start
- * point a rounding outside the mother is not "outside". */
-static navres navigate_one_b(const orc_scene *sc, const double *pw, const double *dw, int blocked) {
+ * point a rounding outside the mother is not "outside".
+ * frame: how many placements (levels of a geometry tree) were applied, in
+ * FP64, to bring the track into this volume's frame, and fscale (mm) the
+ * size of the coordinates they moved (0, 0 for a track given in the frame). */
+/* A-priori FP64 error bound (in units of the step, |d|) of the crossing of
+ * solid (kind, prm) at parameter s of its local line x + s u, for a track at
+ * distance pn from the origin of the volume's frame with direction norm dn,
+ * the solid placed at distance tnorm, below `frame` FP64 placement levels that
+ * moved coordinates of size fscale:
+ *   E = eps [ 8 ((pn + tnorm + s dn)(1 + frame) + frame fscale) cond / dn
+ *             + 16 qcoef ],  eps = 2^-53,
+ * over every surface crossing of the solid that coincides with s within
+ * 1e-6 (1 + s) (edges, rims, apexes: which surface is crossed first is
+ * decided by rounding there):
+ *   cond = max(1 + L/l, 1 + |g||d|/|g.d|): a position error moves the hit by
+ *     itself over |d| cos(incidence) (g the surface gradient at the hit), and
+ *     a quadric root by L/l more (L the solid's size, l the half-chord);
+ *   qcoef = sum|terms| / |F'(s)| of the quadric rho^2 - R(z)^2 = A s^2 +
+ *     2 B s + C along the line: rounding its terms moves the root by a few eps
+ *     times this (a far-away small solid: |x| >> its size), with sum|terms|
+ *     <= (|x_perp| + |s||u_perp|)^2 + (|ra| + |rb| (|x_z| + |s||u_z|))^2 and
+ *     |F'(s)| = |g.u|. */
+static double crossing_err(int kind, const double *prm, const double *x, const double *u, double s, double pn,
+                           double dn, double tnorm, int frame, double fscale) {
+    double cond = 1.0, qcoef = 0.0;
+    if (isfinite(s)) {
+        double g[3], dF[5];
+        xrec R; R.n = 0;
+        iset S;
+        line_set_rec(kind, prm, x, u, &S, &R);
+        const double sh = shape_scale(kind, prm);
+        for (int e = 0; e < R.n; e++) {
+            if (!(fabs(R.t[e] - s) <= 1e-6 * (1.0 + s)) || R.f[e] == F_NONE) continue;
+            const double te = R.t[e];
+            const double xs[3] = { x[0] + te * u[0], x[1] + te * u[1], x[2] + te * u[2] };
+            surface_grad(kind, prm, R.f[e], xs, g, dF);
+            const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            const double gd = fabs(g[0] * u[0] + g[1] * u[1] + g[2] * u[2]);
+            const double c2 = gd > 0.0 ? 1.0 + gn * dn / gd : INFINITY;
+            if (c2 > cond) cond = c2;
+            if (!isinf(R.c[e])) {
+                const double c1 = 1.0 + sh / (R.c[e] * dn);
+                if (c1 > cond) cond = c1;
+            }
+            double ra, rb;
+            if (face_line(kind, prm, R.f[e], &ra, &rb)) {
+                const double ate = fabs(te);
+                const double m1 = sqrt(x[0] * x[0] + x[1] * x[1]) + ate * sqrt(u[0] * u[0] + u[1] * u[1]);
+                const double m2 = fabs(ra) + fabs(rb) * (fabs(x[2]) + ate * fabs(u[2]));
+                const double q = gd > 0.0 ? (m1 * m1 + m2 * m2) / gd : INFINITY;
+                if (q > qcoef) qcoef = q;
+            }
+        }
+    }
+    const double eps = ldexp(1.0, -53);
+    const double sd = isfinite(s) ? s * dn : 0.0;
+    return eps * (8.0 * ((pn + tnorm + sd) * (1.0 + frame) + frame * fscale) * cond / dn + 16.0 * qcoef);
+}
+
+/* blocked >= 0: that daughter was just left through its surface; it enters
+ * the minimum with its re-entry distance instead of DistFromOutside (0).
+ * blocked == -2: the track has just entered the mother through its surface;
+ * the mother's exit is that of the component being entered, and a start
+ * point a rounding outside the mother is not "outside".
+ * frame: how many placements (levels of a geometry tree) were applied, in
+ * FP64, to bring the track into this volume's frame, and fscale (mm) the
+ * size of the coordinates they moved (0, 0 for a track given in the frame).
+ * err bounds the FP64 error of the step: the largest crossing_err() of the
+ * winner and of every candidate within 1e-6 (1 + s) of it (one of those may
+ * win under another rounding). */
+static navres navigate_one_f(const orc_scene *sc, const double *pw, const double *dw, int blocked, int frame,
+                             double fscale) {
     navres r;
     r.second = INFINITY; r.face = F_NONE; r.err = 0.0;
     const int entered = blocked == -2;
@@ -850,72 +948,48 @@ static navres navigate_one_b(const orc_scene *sc, const double *pw, const double
     if (!entered && !orc_contains(sc->mkind, mp, pw)) { r.step = 0.0; r.hit = -2; return r; }
     hitinfo m = entered ? dist_in_entered_info(sc->mkind, mp, pw, dw)
                         : dist_in_info(sc->mkind, mp, pw, dw);
-    double best = m.s, chord = m.chord, tnorm = 0.0, scale = shape_scale(sc->mkind, mp);
+    double best = m.s;
     int hit = -1, face = m.face;
     double second = INFINITY;
+    double cs[sc->nd > 0 ? sc->nd : 1];   /* every daughter's candidate step */
     for (int j = 0; j < sc->nd; j++) {
         double x[3], u[3];
         to_local(sc, j, pw, dw, x, u);
         const double *pj = DAUGHTER(sc, j, db);
         hitinfo h = j == blocked ? dist_reentry_info(sc->kinds[j], pj, x, u)
                                  : dist_out_info(sc->kinds[j], pj, x, u);
+        cs[j] = h.s;
         if (h.s < best) {
             second = best;
-            best = h.s; hit = j; face = h.face; chord = h.chord;
-            const double *t = sc->trans + 3 * j;
-            tnorm = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-            scale = shape_scale(sc->kinds[j], pj);
+            best = h.s; hit = j; face = h.face;
         } else if (h.s < second) {
             second = h.s;
         }
     }
     r.step = best; r.hit = hit; r.second = second; r.face = face;
-    {
-        /* A-priori FP64 error bound of the step:
-         *   E = 8 eps (|p| + |t_j| + s|d|) * cond,  eps = 2^-53,
-         *   cond = max(1 + L/l, 1 + |g||d| / |g.d|)
-         * with L the solid's largest dimension, l the half-chord of a winning
-         * quadric root, and g the winning surface's gradient at the hit point:
-         * |g||d|/|g.d| is the sensitivity of the hit parameter to a move of
-         * the start point (grazing incidence, on planes as on quadrics). */
-        double pn = sqrt(pw[0] * pw[0] + pw[1] * pw[1] + pw[2] * pw[2]);
-        double dn = sqrt(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
-        double cond = isinf(chord) ? 1.0 : 1.0 + scale / (chord * dn);
-        if (isfinite(best)) {
-            /* every surface crossing of the winning solid that coincides with
-             * the step within 1e-6 (1 + s) (edges, rims, apexes: whichever
-             * surface is crossed first is decided by rounding there) */
-            double x[3], u[3], g[3], dF[5];
-            int kind; const double *prm;
-            if (hit == -1) {
-                kind = sc->mkind; prm = mp;
-                for (int k = 0; k < 3; k++) { x[k] = pw[k]; u[k] = dw[k]; }
-            } else {
-                kind = sc->kinds[hit]; prm = DAUGHTER(sc, hit, db);
-                to_local(sc, hit, pw, dw, x, u);
-            }
-            xrec R; R.n = 0;
-            iset S;
-            line_set_rec(kind, prm, x, u, &S, &R);
-            double sh = shape_scale(kind, prm);
-            for (int e = 0; e < R.n; e++) {
-                if (!(fabs(R.t[e] - best) <= 1e-6 * (1.0 + best)) || R.f[e] == F_NONE) continue;
-                double te = R.t[e];
-                double xs[3] = { x[0] + te * u[0], x[1] + te * u[1], x[2] + te * u[2] };
-                surface_grad(kind, prm, R.f[e], xs, g, dF);
-                double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-                double gd = fabs(g[0] * u[0] + g[1] * u[1] + g[2] * u[2]);
-                double c2 = gd > 0.0 ? 1.0 + gn * dn / gd : INFINITY;
-                if (c2 > cond) cond = c2;
-                if (!isinf(R.c[e])) {
-                    double c1 = 1.0 + sh / (R.c[e] * dn);
-                    if (c1 > cond) cond = c1;
-                }
-            }
-        }
-        r.err = 8.0 * ldexp(1.0, -53) * (pn + tnorm + best * dn) * cond;
+    const double pn = sqrt(pw[0] * pw[0] + pw[1] * pw[1] + pw[2] * pw[2]);
+    const double dn = sqrt(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+    const double win = 1e-6 * (1.0 + best);
+    double err = 0.0;
+    if (hit == -1 || (isfinite(best) && fabs(m.s - best) <= win)) {
+        const double e = crossing_err(sc->mkind, mp, pw, dw, m.s, pn, dn, 0.0, frame, fscale);
+        if (e > err) err = e;
     }
+    for (int j = 0; j < sc->nd; j++) {
+        if (j != hit && !(isfinite(best) && fabs(cs[j] - best) <= win)) continue;
+        double x[3], u[3];
+        to_local(sc, j, pw, dw, x, u);
+        const double *t = sc->trans + 3 * j;
+        const double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        const double e = crossing_err(sc->kinds[j], DAUGHTER(sc, j, db), x, u, cs[j], pn, dn, tn, frame, fscale);
+        if (e > err) err = e;
+    }
+    r.err = err;
     return r;
+}
+
+static navres navigate_one_b(const orc_scene *sc, const double *pw, const double *dw, int blocked) {
+    return navigate_one_f(sc, pw, dw, blocked, 0, 0.0);
 }
 
 static navres navigate_one(const orc_scene *sc, const double *pw, const double *dw) {
@@ -1257,6 +1331,34 @@ void orc_shape_batch(int kind, const double *row, const double *pdata, int64_t n
     }
 }
 
+/* For the distance queries (what 0: DistFromOutside, 1: DistFromInside) of
+ * one solid: the a-priori FP64 error bound of each answer (crossing_err(),
+ * the solid placed at distance tnorm from the frame the query came from),
+ * and the gap between the answer and the nearest crossing of another of the
+ * solid's surfaces (which surface is crossed is decided by rounding when the
+ * gap is within that bound: edges, rims, apexes). */
+void orc_shape_batch_err(int kind, const double *row, const double *pdata, int64_t n, const double *x,
+                         const double *u, int what, double tnorm, double *err, double *gap) {
+    double buf[PBUF];
+    const double *p = shape_block(kind, row, pdata, buf);
+    for (int64_t i = 0; i < n; i++) {
+        const double *xi = x + 3 * i, *ui = u + 3 * i;
+        hitinfo h = what == 0 ? dist_out_info(kind, p, xi, ui) : dist_in_info(kind, p, xi, ui);
+        const double pn = sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+        const double dn = sqrt(ui[0] * ui[0] + ui[1] * ui[1] + ui[2] * ui[2]);
+        err[i] = crossing_err(kind, p, xi, ui, h.s, pn, dn, tnorm, 0, 0.0);
+        double g = INFINITY;
+        if (isfinite(h.s)) {
+            xrec R; R.n = 0;
+            iset S;
+            line_set_rec(kind, p, xi, ui, &S, &R);
+            for (int e = 0; e < R.n; e++)
+                if (R.f[e] != F_NONE && R.f[e] != h.face && fabs(R.t[e] - h.s) < g) g = fabs(R.t[e] - h.s);
+        }
+        gap[i] = g;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* geometry tree: a step followed by final localisation                 */
 /* ------------------------------------------------------------------ */
@@ -1396,14 +1498,33 @@ static int world_locate_one(const orc_world *W, const double *pw) {
     return descend(W, 0, pw);
 }
 
+/* levels of placements between the root and node, and the size of the
+ * coordinates they move: |world point| + the sum of their |translation| */
+static int node_depth(const orc_world *W, int node, const double *pw, double *fscale) {
+    int depth = 0;
+    double f = sqrt(pw[0] * pw[0] + pw[1] * pw[1] + pw[2] * pw[2]);
+    for (int m = node; m > 0; m = W->parent[m]) {
+        const double *t = W->trans + 3 * (W->doff[W->lv[W->parent[m]]] + W->slot[m]);
+        f += sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        depth++;
+    }
+    *fscale = f;
+    return depth;
+}
+
 static int world_step_one(const orc_world *W, int node, int blocked, const double *pw, const double *dw,
-                          double *step, int *blocked_out) {
+                          double *step, int *blocked_out, navres *info) {
     *blocked_out = -1;
+    if (info) { info->err = 0.0; info->hit = -2; info->face = F_NONE; }
     if (node < 0 || node >= W->nnodes) { *step = NAN; return -2; }
     double x[3], u[3];
     node_frame(W, node, pw, dw, x, u);
     orc_scene s = world_scene(W, W->lv[node]);
-    navres r = navigate_one_b(&s, x, u, blocked == -2 || (blocked >= 0 && blocked < s.nd) ? blocked : -1);
+    double fscale;
+    const int depth = node_depth(W, node, pw, &fscale);
+    navres r = navigate_one_f(&s, x, u, blocked == -2 || (blocked >= 0 && blocked < s.nd) ? blocked : -1, depth,
+                              fscale);
+    if (info) *info = r;
     *step = r.step;
     if (r.hit == -2) return -2;
     const double b[3] = { x[0] + r.step * u[0], x[1] + r.step * u[1], x[2] + r.step * u[2] };
@@ -1463,16 +1584,24 @@ int orc_world_locate(WORLD_ARGS, int64_t n, const double *px, const double *py, 
     return W.nnodes;
 }
 
+/* err, hit, face (each nullable): the step's a-priori FP64 error bound (the
+ * placements down to the node included), the winner in the node's volume
+ * and its surface. */
 int orc_world_step(WORLD_ARGS, int64_t n, const double *px, const double *py, const double *pz,
                    const double *dx, const double *dy, const double *dz, const int32_t *node_in,
-                   const int32_t *blocked_in, double *step, int32_t *node_out, int32_t *blocked_out) {
+                   const int32_t *blocked_in, double *step, int32_t *node_out, int32_t *blocked_out,
+                   double *err, int32_t *hit, int32_t *face) {
     MAKE_WORLD;
     if (world_nodes(&W, max_nodes) < 0) return -1;
     for (int64_t i = 0; i < n; i++) {
         const double pw[3] = { px[i], py[i], pz[i] }, dw[3] = { dx[i], dy[i], dz[i] };
         int b;
-        node_out[i] = world_step_one(&W, node_in[i], blocked_in ? blocked_in[i] : -1, pw, dw, &step[i], &b);
+        navres r;
+        node_out[i] = world_step_one(&W, node_in[i], blocked_in ? blocked_in[i] : -1, pw, dw, &step[i], &b, &r);
         if (blocked_out) blocked_out[i] = b;
+        if (err) err[i] = r.err;
+        if (hit) hit[i] = r.hit;
+        if (face) face[i] = r.face;
     }
     return W.nnodes;
 }

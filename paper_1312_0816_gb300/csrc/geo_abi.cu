@@ -231,6 +231,9 @@ ShapeRec64 make_rec64(const geo_placed_shape& s, const double* table = nullptr) 
     std::memcpy(r.t, s.trans, sizeof r.t);
     std::memcpy(r.p, s.p, sizeof r.p);
     r.kind = s.kind;
+    bool eye = true;
+    for (int k = 0; k < 9; ++k) eye = eye && s.rot[k] == ((k % 4) == 0 ? 1.0 : 0.0);
+    r.flags = eye ? kRec64Identity : 0;
     const double* p = s.p;
     if (s.kind == GEO_BOX) {
         r.d[0] = p[0]; r.d[1] = p[1]; r.d[2] = p[2];
@@ -377,6 +380,17 @@ double inflation(const geo_placed_shape& s, double S) {
     const double floor_r = 0.5 * std::sqrt(kEps32) * br;
     d += 16.0 * kEps32 * br * br * (1.0 + slope2) / std::max(rsmall, floor_r);
     return d;
+}
+
+// A solid whose routines live in the kernels' second instantiation: tube
+// segments, polycones, and cones with a zero radius at an end plane (an apex
+// there, whose crossings are formed about it).
+bool needs_segs_code(const geo_placed_shape& s) {
+    if (s.kind == GEO_TUBS || s.kind == GEO_PCON) return true;
+    if (s.kind != GEO_CONE) return false;
+    const double* p = s.p;
+    const bool hole = p[1] > 0.0 || p[3] > 0.0;
+    return p[2] == 0.0 || p[4] == 0.0 || (hole && (p[1] == 0.0 || p[3] == 0.0));
 }
 
 geo_status cuda_status(cudaError_t e);
@@ -580,9 +594,11 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
         return GEO_ERR_SHAPE_PARAMS;
     }
     vw.nd = n_daughters;
-    vw.segs = (mother->kind == GEO_TUBS || mother->kind == GEO_PCON) ? 1 : 0;
+    // the kernels' instantiation with the out-of-line code of tube segments,
+    // polycones and cones through an apex on an end plane
+    vw.segs = needs_segs_code(*mother) ? 1 : 0;
     for (int j = 0; j < n_daughters; ++j)
-        if (daughters[j].kind == GEO_TUBS || daughters[j].kind == GEO_PCON) vw.segs = 1;
+        if (needs_segs_code(daughters[j])) vw.segs = 1;
 
     const size_t b64 = sizeof(ShapeRec64) * size_t(std::max(n_daughters, 1));
     const size_t b32 = sizeof(ShapeRec32) * size_t(std::max(n_daughters, 1));

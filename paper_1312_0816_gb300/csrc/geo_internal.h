@@ -39,6 +39,11 @@ constexpr int kPconTableMax = pcon_table_len(kMaxPlanes);
 //         p = (sphi, dphi, nz, 0, 0)
 //  brad: bounding-sphere radius about t, enlarged by a relative 1e-12 + 1e-9 mm
 //  so that the FP64 sphere cull is conservative.
+//  flags: kRec64Identity when the rotation is exactly the identity: the
+//  master->local transform is then x = p - t, u = d (3 FP64 operations
+//  instead of 21; every kernel takes the same branch, so all agree bit for
+//  bit).
+constexpr int32_t kRec64Identity = 1;
 struct __align__(16) ShapeRec64 {
     double R[9];
     double t[3];

@@ -156,12 +156,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                     }
                     rs.c.dropped = sp.dropped[t];
                     rs.Lm = sp.Lm[t];
-                    const double px = sp.pd[0][t], py = sp.pd[1][t], pz = sp.pd[2][t];
-                    const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
                     double best;
                     int h, nev;
-                    refine_rest<SEGS>(vp, vp.d64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
-                    store_result(prev_i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
+                    if (!refine_fast(rs, sp.res[t], best, h))
+                        refine_rest<SEGS>(vp, vp.d64, rs, sp.res[t], sp.pd[0][t], sp.pd[1][t], sp.pd[2][t],
+                                          sp.pd[3][t], sp.pd[4][t], sp.pd[5][t], best, h, nev);
+                    store_result(prev_i, b.n, best, h, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, step, hit, nullptr);
                 }
             }
             if (tile < 0) break;

@@ -240,6 +240,27 @@ __device__ __forceinline__ double eval64(const VolView& v, const ShapeRec64* __r
     return dist_out64<false, SEGS>(r, x, u);
 }
 
+// The answer of refine_rest() when no further FP64 evaluation can change it
+// (nearly every track): the first task's value s_first is finite and every
+// other bound -- the remaining candidates, the mother's when it was not the
+// first task, the least evicted one -- lies above its FP32 upper bound.  A
+// solid's FP64 value is at least its bound, so none of them can win or tie.
+// Returns false when refine_rest() has to run.
+__device__ __forceinline__ bool refine_fast(const RefineState& st, double s_first, double& best, int& h) {
+    const bool mother_first = first_task(st) < 0;
+    if (!LT(s_first, d_inf())) return false;
+    const float up = f64_to_f32_up(s_first);
+    const int k0 = mother_first ? 0 : 1;
+#pragma unroll
+    for (int k = 0; k < kCand; ++k)
+        if (k >= k0 && k < st.c.n && st.c.L[k] <= up) return false;
+    if (!mother_first && st.Lm <= up) return false;
+    if (st.c.dropped <= up) return false;
+    best = s_first;
+    h = mother_first ? -1 : st.c.j[0];
+    return true;
+}
+
 // FP64 refinement in ascending bound order, given the value s_first of the
 // first task (first_task()).  Ties resolve as in Fig. 1a: mother, then the
 // lowest index.  The bounds are compared in FP32 against best_up >= best, so

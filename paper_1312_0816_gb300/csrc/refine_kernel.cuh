@@ -159,7 +159,10 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
                 } else {
                     st_.n[t] = -1;
                     if (live) {
-                        store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
+                        // the track is read back from the stage: keeping it in
+                        // registers through the FP32 pass would spill
+                        store_result(i, b.n, best, h, st_.pd[0][t], st_.pd[1][t], st_.pd[2][t], st_.pd[3][t],
+                                     st_.pd[4][t], st_.pd[5][t], step, hit, bpoint);
                         if (nref) nref[i] = nev;
                     }
                 }
@@ -182,12 +185,13 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
                     }
                     rs.c.dropped = sp.dropped[t];
                     rs.Lm = sp.Lm[t];
-                    const double px = sp.pd[0][t], py = sp.pd[1][t], pz = sp.pd[2][t];
-                    const double qx = sp.pd[3][t], qy = sp.pd[4][t], qz = sp.pd[5][t];
                     double best;
-                    int h, nev;
-                    refine_rest<SEGS>(v, tab64, rs, sp.res[t], px, py, pz, qx, qy, qz, best, h, nev);
-                    store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, bpoint);
+                    int h, nev = 1;
+                    if (!refine_fast(rs, sp.res[t], best, h))
+                        refine_rest<SEGS>(v, tab64, rs, sp.res[t], sp.pd[0][t], sp.pd[1][t], sp.pd[2][t], sp.pd[3][t],
+                                          sp.pd[4][t], sp.pd[5][t], best, h, nev);
+                    store_result(i, b.n, best, h, sp.pd[0][t], sp.pd[1][t], sp.pd[2][t], sp.pd[3][t], sp.pd[4][t],
+                                 sp.pd[5][t], step, hit, bpoint);
                     if (nref) nref[i] = nev;
                 }
             }

@@ -55,10 +55,15 @@ __device__ __forceinline__ bool OPPOSITE(double a, double b) {
 __device__ __forceinline__ double MINP(double a, double b) { return LT(b, a) ? b : a; }
 __device__ __forceinline__ double MAXP(double a, double b) { return LT(a, b) ? b : a; }
 
-// x = R^T (p - t), u = R^T d
+// x = R^T (p - t), u = R^T d (an identity rotation: x = p - t, u = d)
 __device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, double py, double pz,
                                            double qx, double qy, double qz, double* x, double* u) {
     const double w0 = SUB(px, r.t[0]), w1 = SUB(py, r.t[1]), w2 = SUB(pz, r.t[2]);
+    if (r.flags & kRec64Identity) {
+        x[0] = w0; x[1] = w1; x[2] = w2;
+        u[0] = qx; u[1] = qy; u[2] = qz;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         x[k] = FMA(r.R[6 + k], w2, FMA(r.R[3 + k], w1, MUL(r.R[k], w0)));
@@ -69,6 +74,10 @@ __device__ __forceinline__ void to_local64(const ShapeRec64& r, double px, doubl
 // x = R^T (p - t) alone (the same operations as to_local64, so the same bits)
 __device__ __forceinline__ void point_to_local64(const ShapeRec64& r, double px, double py, double pz, double* x) {
     const double w0 = SUB(px, r.t[0]), w1 = SUB(py, r.t[1]), w2 = SUB(pz, r.t[2]);
+    if (r.flags & kRec64Identity) {
+        x[0] = w0; x[1] = w1; x[2] = w2;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) x[k] = FMA(r.R[6 + k], w2, FMA(r.R[3 + k], w1, MUL(r.R[k], w0)));
 }
@@ -102,6 +111,33 @@ __device__ __forceinline__ double root_rising(double A, double B, double C) {
     return ok ? s : d_inf();
 }
 
+// The same two roots whatever their sign (the parameter origin need not be
+// the track's start): +inf only when there is none (D < 0, or a linear F that
+// does not fall / rise through zero).
+__device__ __forceinline__ double root_falling_any(double A, double B, double C) {
+    const double D = FMA(B, B, -MUL(A, C));
+    const bool real = NONNEG(D);
+    const double sq = SQRT(real ? D : 0.0);
+    const bool bneg = IS_NEG(B);
+    const double num = bneg ? C : SUB(-B, sq);
+    const double den = bneg ? SUB(sq, B) : A;
+    const bool ok = real && (bneg || !IS_ZERO(A));
+    const double s = DIV(num, ok ? den : 1.0);
+    return ok ? s : d_inf();
+}
+
+__device__ __forceinline__ double root_rising_any(double A, double B, double C) {
+    const double D = FMA(B, B, -MUL(A, C));
+    const bool real = NONNEG(D);
+    const double sq = SQRT(real ? D : 0.0);
+    const bool bpos = IS_POS(B);
+    const double num = bpos ? C : SUB(sq, B);
+    const double den = bpos ? SUB(-B, sq) : A;
+    const bool ok = real && (bpos || !IS_ZERO(A));
+    const double s = DIV(num, ok ? den : 1.0);
+    return ok ? s : d_inf();
+}
+
 __device__ __forceinline__ double rho2_of(const double* x) { return DOT2(x[0], x[0], x[1], x[1]); }
 
 // ---------------------------------------------------- tube segment wedge ---
@@ -110,6 +146,58 @@ __device__ __forceinline__ bool wedge_has64(const double* d, double x, double y)
     if (d[10] != 0.0) return true;
     const bool a = NONNEG(DOT2(d[5], x, d[6], y)), b = NONNEG(DOT2(d[7], x, d[8], y));
     return d[9] != 0.0 ? (a && b) : (a || b);
+}
+
+// Crossing of the cone rho = R(z) = Rc + b (z - zc) with the track, the
+// quadric rho^2 - R(z)^2 formed about the track's point closest to (0, 0, zc)
+// of the axis.  With zc at the cone's apex (Rc = 0) this resolves a track
+// passing close to the apex: there the two roots nearly coincide, and the
+// quadric about the start point, whose terms are as large as the start's
+// distance squared, cannot separate them, while about the closest point its
+// terms are as small as the miss distance.  RISING: the root where rho^2 -
+// R^2 rises through zero, else the falling one.  Returns the parameter (+inf:
+// none) and the crossing's x, y and height above zc.  inv_uu = 1 / |u|^2.
+template <bool RISING>
+__device__ __forceinline__ double cone_root_about(double zc, double Rc, double b, const double* x, const double* u,
+                                                  double A0, double inv_uu, double& xh, double& yh, double& zh) {
+    const double xz = SUB(x[2], zc);
+    const double sc = MUL(-FMA(xz, u[2], DOT2(x[0], u[0], x[1], u[1])), inv_uu);
+    const double c0 = FMA(sc, u[0], x[0]), c1 = FMA(sc, u[1], x[1]), c2 = FMA(sc, u[2], xz);
+    const double Rq = FMA(b, c2, Rc), rs = MUL(b, u[2]);
+    const double A = FMA(-rs, rs, A0), B = FMA(-Rq, rs, DOT2(c0, u[0], c1, u[1]));
+    const double C = FMA(-Rq, Rq, DOT2(c0, c0, c1, c1));
+    const double sg = RISING ? root_rising_any(A, B, C) : root_falling_any(A, B, C);
+    xh = FMA(sg, u[0], c0);
+    yh = FMA(sg, u[1], c1);
+    zh = FMA(sg, u[2], c2);
+    return ADD(sc, sg);
+}
+
+// Crossing of the cone of polycone section [zk, zk1], radius line through
+// (r0 at zk) and (r1 at zk1) with slope b, formed about the apex when the
+// radius vanishes at one of the section's planes, else about (0, 0, zk)
+// (cone_root_about).  Sets the crossing's x, y and whether its height lies
+// in [zk, zk1].
+template <bool RISING>
+__device__ __forceinline__ double pcon_sec_root(double r0, double r1, double b, double zk, double zk1, const double* x,
+                                                const double* u, double A0, double inv_uu, double& xh, double& yh,
+                                                bool& in_z) {
+    const bool top = IS_ZERO(r1) && !IS_ZERO(r0);
+    double zh;
+    const double s = cone_root_about<RISING>(top ? zk1 : zk, top ? r1 : r0, b, x, u, A0, inv_uu, xh, yh, zh);
+    in_z = top ? (zh >= SUB(zk, zk1) && zh <= 0.0) : (zh >= 0.0 && zh <= SUB(zk1, zk));
+    return s;
+}
+
+// A crossing of a phi face's plane lies on the face when it is on the face's
+// side of the axis.  Within rounding of the axis (r2 <= tau2, the squared
+// rounding scale of the crossing point) that side is decided by rounding, and
+// the track instead enters there, where the two faces meet, when the solid
+// holds the axis (no inner radius there) and the track moves into the wedge.
+__device__ __forceinline__ bool on_phi_face(const double* d, double ex, double ey, double xh, double yh, double r2,
+                                            bool axis_in, double tau2, const double* u) {
+    if (LE(r2, tau2)) return axis_in && wedge_has64(d, u[0], u[1]);
+    return NONNEG(DOT2(ex, xh, ey, yh));
 }
 
 // ------------------------------------------------------------- polycone ---
@@ -300,7 +388,9 @@ __device__ __forceinline__ double tubs_out64(const double* d, const double* x, c
             if (!(REENTRY ? IS_POS(s) : NONNEG(s)) || !LT(s, best)) continue;
             const double xh = FMA(s, u[0], x[0]), yh = FMA(s, u[1], x[1]);
             const double r2 = DOT2(xh, xh, yh, yh);
-            if (ABS_LE(FMA(s, u[2], x[2]), dz) && NONNEG(DOT2(ex, xh, ey, yh)) && LE(r2, rmax2) && LE(rmin2, r2)) {
+            const double tau2 = MUL(0x1p-101, FMA(MUL(s, s), A, rho2));
+            if (ABS_LE(FMA(s, u[2], x[2]), dz) && LE(r2, rmax2) && LE(rmin2, r2) &&
+                on_phi_face(d, ex, ey, xh, yh, r2, IS_ZERO(rmin2), tau2, u)) {
                 best = s;
                 if (FACE) *face = 8 + i;
             }
@@ -317,7 +407,27 @@ __device__ __noinline__ double tubs_out64_call(const double* d, double x0, doubl
     const double x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
     return tubs_out64<FACE, REENTRY>(d, x, u, face);
 }
-template <bool FACE = false, bool REENTRY = false>
+// Crossing of a cone's radius line R(z) = b (z - zc) through its apex at the
+// end plane zc = -dz (low) or +dz, formed about the apex (cone_root_about);
+// sets whether its height lies in [-dz, dz].  Out of line: apexes are rare,
+// and the cone routine of the hot kernels keeps its registers.
+static __device__ __noinline__ double cone_apex_root(bool rising, bool low, double dz, double b, double x0, double x1,
+                                                     double x2, double u0, double u1, double u2, bool* in_z) {
+    const double x[3] = {x0, x1, x2}, u[3] = {u0, u1, u2};
+    const double A0 = DOT2(u0, u0, u1, u1);
+    const double inv_uu = DIV(1.0, FMA(u2, u2, A0));
+    double xh, yh, zh;
+    const double zc = low ? -dz : dz;
+    const double s = rising ? cone_root_about<true>(zc, 0.0, b, x, u, A0, inv_uu, xh, yh, zh)
+                            : cone_root_about<false>(zc, 0.0, b, x, u, A0, inv_uu, xh, yh, zh);
+    const double w = ADD(dz, dz);
+    *in_z = low ? (zh >= 0.0 && zh <= w) : (zh <= 0.0 && zh >= -w);
+    return s;
+}
+
+// APEX: the instantiation that forms the crossing of a cone through an apex on
+// an end plane about that apex (volumes holding such a cone run it).
+template <bool FACE = false, bool REENTRY = false, bool APEX = true>
 __device__ __forceinline__ double cone_out64(const double* d, const double* x, const double* u, int* face = nullptr) {
     if (FACE) *face = -1;
     const double dz = d[0];
@@ -342,18 +452,35 @@ __device__ __forceinline__ double cone_out64(const double* d, const double* x, c
     }
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
     const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    // a radius vanishing at an end plane (an apex there): that cone's
+    // crossing is formed about the apex, out of line (cone_apex_root)
+    const bool apex_o = IS_ZERO(d[6]) || IS_ZERO(d[8]), apex_i = hole && (IS_ZERO(d[5]) || IS_ZERO(d[7]));
     {   // outer cone rho^2 - (a + b z)^2, crossed inwards
-        const double rs = MUL(d[2], u[2]);
-        const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+        double s;
+        bool in_z;
+        if (APEX && apex_o) {
+            s = cone_apex_root(false, IS_ZERO(d[6]), dz, d[2], x[0], x[1], x[2], u[0], u[1], u[2], &in_z);
+        } else {
+            const double rs = MUL(d[2], u[2]);
+            s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
+            in_z = ABS_LE(FMA(s, u[2], x[2]), dz);
+        }
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && in_z) {
             best = s;
             if (FACE) *face = 6;
         }
     }
     if (hole) {   // inner cone, crossed outwards
-        const double rs = MUL(d[4], u[2]);
-        const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && ABS_LE(FMA(s, u[2], x[2]), dz)) {
+        double s;
+        bool in_z;
+        if (APEX && apex_i) {
+            s = cone_apex_root(true, IS_ZERO(d[5]), dz, d[4], x[0], x[1], x[2], u[0], u[1], u[2], &in_z);
+        } else {
+            const double rs = MUL(d[4], u[2]);
+            s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
+            in_z = ABS_LE(FMA(s, u[2], x[2]), dz);
+        }
+        if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && in_z) {
             best = s;
             if (FACE) *face = 7;
         }
@@ -397,36 +524,32 @@ __device__ __forceinline__ double pcon_out64(const double* d, const double* T, c
             const double s = DIV(-DOT2(nx, x[0], ny, x[1]), wn);
             if (!(REENTRY ? IS_POS(s) : NONNEG(s)) || !LT(s, best)) continue;
             const double xh = FMA(s, u[0], x[0]), yh = FMA(s, u[1], x[1]);
-            if (NONNEG(DOT2(ex, xh, ey, yh)) && pcon_in2(T, n, DOT2(xh, xh, yh, yh), FMA(s, u[2], x[2]))) {
+            const double r2 = DOT2(xh, xh, yh, yh);
+            const double tau2 = MUL(0x1p-101, FMA(MUL(s, s), DOT2(u[0], u[0], u[1], u[1]), rho2));
+            if (pcon_in2(T, n, r2, FMA(s, u[2], x[2])) && on_phi_face(d, ex, ey, xh, yh, r2, true, tau2, u)) {
                 best = s;
                 if (FACE) *face = 8 + i;
             }
         }
     }
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
-    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    const double inv_uu = DIV(1.0, FMA(u[2], u[2], A0));
     auto section = [&](int k) {
-        const double zk = z[k], zk1 = z[k + 1], dz0 = SUB(x[2], zk);
+        const double zk = z[k], zk1 = z[k + 1];
+        double xh, yh;
+        bool in_z;
         {   // outer cone, crossed inwards
-            const double ro0 = FMA(bo[k], dz0, rx[k]), rs = MUL(bo[k], u[2]);
-            const double s = root_falling(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-            if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best)) {
-                const double zh = FMA(s, u[2], x[2]);
-                if (zh >= zk && zh <= zk1 && wedge_has64(d, FMA(s, u[0], x[0]), FMA(s, u[1], x[1]))) {
-                    best = s;
-                    if (FACE) *face = 16 + 2 * k;
-                }
+            const double s = pcon_sec_root<false>(rx[k], rx[k + 1], bo[k], zk, zk1, x, u, A0, inv_uu, xh, yh, in_z);
+            if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && in_z && wedge_has64(d, xh, yh)) {
+                best = s;
+                if (FACE) *face = 16 + 2 * k;
             }
         }
         if (rn[k] > 0.0 || rn[k + 1] > 0.0) {   // inner cone, crossed outwards (out of the hole)
-            const double ri0 = FMA(bi[k], dz0, rn[k]), rs = MUL(bi[k], u[2]);
-            const double s = root_rising(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-            if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best)) {
-                const double zh = FMA(s, u[2], x[2]);
-                if (zh >= zk && zh <= zk1 && wedge_has64(d, FMA(s, u[0], x[0]), FMA(s, u[1], x[1]))) {
-                    best = s;
-                    if (FACE) *face = 17 + 2 * k;
-                }
+            const double s = pcon_sec_root<true>(rn[k], rn[k + 1], bi[k], zk, zk1, x, u, A0, inv_uu, xh, yh, in_z);
+            if ((REENTRY ? IS_POS(s) : NONNEG(s)) && LT(s, best) && in_z && wedge_has64(d, xh, yh)) {
+                best = s;
+                if (FACE) *face = 17 + 2 * k;
             }
         }
     };
@@ -473,7 +596,7 @@ __device__ __forceinline__ double dist_out64(const ShapeRec64& r, const double* 
     if (SEGS && r.kind == KTUBS) return tubs_out64_call<FACE, false>(r.d, x[0], x[1], x[2], u[0], u[1], u[2], face);
     if (SEGS && r.kind == KPCON)
         return pcon_out64_call<FACE, false>(r.d, pcon_table(r.d), x[0], x[1], x[2], u[0], u[1], u[2], face);
-    return cone_out64<FACE>(r.d, x, u, face);
+    return cone_out64<FACE, false, SEGS>(r.d, x, u, face);
 }
 
 // Distance to enter again a solid the track has just left (its start point
@@ -605,31 +728,24 @@ __device__ __forceinline__ double pcon_in64(const double* d, const double* T, co
     };
     const int n = int(d[1]);
     const double *z = T, *rn = T + n, *rx = T + 2 * n, *bi = T + 3 * n, *bo = bi + (n - 1);
-    const double rho2 = rho2_of(x);
     const double A0 = DOT2(u[0], u[0], u[1], u[1]);
-    const double B0 = DOT2(x[0], u[0], x[1], u[1]);
+    const double inv_uu = DIV(1.0, FMA(u[2], u[2], A0));
     if (!IS_ZERO(u[2])) {   // the end plane ahead
         const bool up = IS_POS(u[2]);
         take(clamp0(DIV(SUB(up ? z[n - 1] : z[0], x[2]), u[2])), up ? 5 : 4);
     }
     if (d[10] == 0.0) wedge_exit64(d, x, u, take);
     auto section = [&](int k) {
-        const double zk = z[k], zk1 = z[k + 1], dz0 = SUB(x[2], zk);
+        const double zk = z[k], zk1 = z[k + 1];
+        double xh, yh;
+        bool in_z;
         {   // outer cone, crossed outwards
-            const double ro0 = FMA(bo[k], dz0, rx[k]), rs = MUL(bo[k], u[2]);
-            const double s = root_rising(FMA(-rs, rs, A0), FMA(-ro0, rs, B0), FMA(-ro0, ro0, rho2));
-            if (NONNEG(s) && LT(clamp0(s), t)) {
-                const double zh = FMA(s, u[2], x[2]);
-                if (zh >= zk && zh <= zk1) take(clamp0(s), 16 + 2 * k);
-            }
+            const double s = pcon_sec_root<true>(rx[k], rx[k + 1], bo[k], zk, zk1, x, u, A0, inv_uu, xh, yh, in_z);
+            if (NONNEG(s) && LT(clamp0(s), t) && in_z) take(clamp0(s), 16 + 2 * k);
         }
         if (rn[k] > 0.0 || rn[k + 1] > 0.0) {   // inner cone, crossed inwards (into the hole)
-            const double ri0 = FMA(bi[k], dz0, rn[k]), rs = MUL(bi[k], u[2]);
-            const double s = root_falling(FMA(-rs, rs, A0), FMA(-ri0, rs, B0), FMA(-ri0, ri0, rho2));
-            if (NONNEG(s) && LT(clamp0(s), t)) {
-                const double zh = FMA(s, u[2], x[2]);
-                if (zh >= zk && zh <= zk1) take(clamp0(s), 17 + 2 * k);
-            }
+            const double s = pcon_sec_root<false>(rn[k], rn[k + 1], bi[k], zk, zk1, x, u, A0, inv_uu, xh, yh, in_z);
+            if (NONNEG(s) && LT(clamp0(s), t) && in_z) take(clamp0(s), 17 + 2 * k);
         }
     };
     auto reach = [&]() {

@@ -1,24 +1,24 @@
 """Parity of the CUDA navigator (through the C ABI) with the CPU oracle.
 
-Bar (stated per test): steps within 1e-9 mm of the oracle and hit index
-bit-exact, except on tracks in the tie band (second-smallest oracle candidate
-within 1e-9 mm of the winner) or the conditioning band (the oracle's a-priori
-FP64 error bound E exceeds 1e-9 mm, i.e. near-tangent roots); those are
-counted and must be rare.  The FP32+refine mode must equal the plain FP64
-mode bit for bit on every track.
+Bar, on every track: the step within max(1e-9 mm, err) of the oracle's, err
+the oracle's a-priori FP64 error bound (pinned against exact crossings in
+test_oracle_errbound.py; it exceeds 1e-9 mm only for ill-conditioned hits:
+grazing incidence, near-tangent roots, far-away small solids), and the hit
+index bit-exact except in the tie band (second-smallest oracle candidate
+within that tolerance of the winner).  The share of conditioning-banded
+tracks is capped on random rays.  The FP32+refine mode must equal the plain
+FP64 mode bit for bit on every track.
 """
 import math
 
 import numpy as np
 import pytest
 
-from helpers import golden, expr, scene_from_spec, tracks_from, tie_band
+from helpers import golden, expr, scene_from_spec, tracks_from, check_steps, STEP_TOL
 from paper_1312_0816_gb300 import scenes
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-STEP_TOL = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -51,17 +51,13 @@ def run_nav(g, sc, tr, mode, bpoint=False):
     return [o.cpu().numpy() for o in out]
 
 
-def compare(ref, step, hit, max_exempt=1e-3):
-    """Returns the number of exempt tracks after asserting the bar on the rest."""
-    assert np.array_equal(np.isnan(step), np.isnan(ref["step"]))
-    exempt = tie_band(ref) | (ref["err"] > STEP_TOL)
-    ok = ~exempt & ~np.isnan(ref["step"])
-    d = np.abs(step - ref["step"])[ok]
-    assert d.size == 0 or d.max() <= STEP_TOL, d.max()
-    bad = np.nonzero(hit[ok] != ref["hit"][ok])[0]
-    assert bad.size == 0, (bad[:10], hit[ok][bad[:10]], ref["hit"][ok][bad[:10]])
-    assert exempt.mean() <= max_exempt, exempt.mean()
-    return int(exempt.sum())
+def compare(ref, step, hit, tracks, sc, orc, max_banded=1e-3, max_graze=0.0):
+    """Every track checked (helpers.check_steps); a track whose answer only
+    FP64 rounding decides must be the oracle's for a start point moved by
+    1e-9 mm, and their share is capped.  Returns the band counts."""
+    st = check_steps(ref, step, hit, tracks, max_banded, orc, sc)
+    assert st["rounding_decided"] <= max_graze * max(st["n"], 1), st
+    return st
 
 
 SCENES = {
@@ -90,7 +86,7 @@ def test_box4_basket_1024(g, orc, mode):
     tr = scenes.sample_tracks(sc, 1024, 0)
     ref = orc.navigate(sc, tr, nthreads=8)
     step, hit = run_nav(g, sc, tr, mode)
-    compare(ref, step, hit)
+    compare(ref, step, hit, tr, sc, orc)
 
 
 @pytest.mark.parametrize("name,n", [("toy40", 65536 + 77), ("toy8", 30011), ("diff3", 30011),
@@ -103,7 +99,7 @@ def test_scene_parity(g, orc, name, n, mode):
     tr = scenes.sample_tracks(sc, n, 101)
     ref = orc.navigate(sc, tr, nthreads=8)
     step, hit = run_nav(g, sc, tr, mode)
-    compare(ref, step, hit)
+    compare(ref, step, hit, tr, sc, orc, max_graze=1e-4)
 
 
 @pytest.mark.parametrize("name", list(SCENES))
@@ -174,8 +170,10 @@ def test_adversarial_parity(g, orc, name):
     ref = orc.navigate(sc, tr, nthreads=8)
     step, hit = run_nav(g, sc, tr, 1)
     # these rays are aimed at edges, rims and faces at grazing incidence, so a
-    # large share is ill-conditioned by construction (exempt from the 1e-9 bar)
-    compare(ref, step, hit, max_exempt=0.35)
+    # large share is ill-conditioned by construction: every one of them is
+    # still checked, at its own bound
+    st = compare(ref, step, hit, tr, sc, orc, max_banded=None, max_graze=0.01)
+    assert st["n"] == tr.n and st["cond_banded"] > 0
 
 
 @pytest.mark.parametrize("name", ["toy8", "box4", "diff3", "seg4", "pcon4", "pconm"])
@@ -242,7 +240,7 @@ def test_edge_cases(g, orc, mode):
     assert np.isnan(step[2]) and hit[2] == -2
     assert np.isnan(step[3]) and np.isnan(step[4])
     assert hit[6] == 0 and step[6] == 0.0
-    compare(ref, step, hit, max_exempt=0.1)
+    compare(ref, step, hit, tr, sc, orc, max_banded=None)
 
 
 @pytest.mark.parametrize("n", [0, 1, 31, 255, 257])
@@ -256,7 +254,7 @@ def test_small_and_empty_baskets(g, orc, n):
     ref = orc.navigate(sc, tr)
     for mode in (0, 1):
         step, hit = run_nav(g, sc, tr, mode)
-        compare(ref, step, hit, max_exempt=0.5)
+        compare(ref, step, hit, tr, sc, orc, max_banded=None)
 
 
 def test_boundary_point(g):
@@ -353,4 +351,4 @@ def test_full_size_toy_detector_sampled(g, orc):
     idx = np.sort(np.random.default_rng(17).choice(tr.n, 20000, replace=False))
     sub = scenes.Tracks(*(f[idx] for f in tr.fields()))
     ref = orc.navigate(sc, sub, nthreads=8)
-    compare(ref, step[idx], hit[idx])
+    compare(ref, step[idx], hit[idx], sub, sc, orc, max_graze=1e-4)

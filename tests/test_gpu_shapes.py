@@ -3,16 +3,23 @@ against the oracle's shape routines: DistFromOutside, DistFromInside, the two
 safeties and Contains of one Box, Tube, Cone, tube segment or polycone, in
 its own frame and placed.
 
-Bars: distances within 1e-9 mm (relative to max(1, s)) and the crossed face
-equal, except on a small fraction of rays that graze a surface or cross at an
-edge (both answers are then correct to rounding); safeties within 1e-9 mm;
-Contains exact outside the 1e-9 mm surface band.
+Bars: every distance within max(1e-9 mm, err) of the oracle's, err the
+oracle's a-priori FP64 error bound of that query (pinned against exact
+crossings in test_oracle_errbound.py), and the crossed face equal unless
+another of the solid's surfaces is crossed within that tolerance (an edge, a
+rim); a point within 1e-9 mm of the surface is inside or outside by rounding,
+so its distances are not unique and only counted.  Where the two answers
+differ by more, the GPU's must be the oracle's for the start point moved by
+1e-9 mm along some axis (a ray grazing a cylinder or cone: FP64 rounding
+decides between touch and miss); those are counted and capped.  Safeties within 1e-9 mm; Contains exact outside the
+1e-9 mm surface band.
 """
 import math
 
 import numpy as np
 import pytest
 
+from helpers import PERTURB, PERTURB_MATCH
 from paper_1312_0816_gb300 import scenes
 
 torch = pytest.importorskip("torch")
@@ -100,15 +107,32 @@ def gpu(g, kind, p, what, x, u, rot=None, trans=None):
     return out.cpu().numpy(), face.cpu().numpy()
 
 
-def check_distance(got, gface, want, wface, max_bad):
-    """Values within TOL; the crossed face must agree where the crossing is
-    more than TOL away (a point on the surface has none that is unique)."""
+def check_distance(orc, kind, p, what, x, u, got, gface, tnorm=0.0):
+    """Every ray checked; returns the number decided by rounding."""
+    want, wface = orc.shape(kind, p, x, u, what)
+    err, gap = orc.shape_err(kind, p, x, u, what, tnorm)
+    tol = np.maximum(TOL, err)
     both_inf = np.isinf(got) & np.isinf(want)
     with np.errstate(invalid="ignore"):
-        close = both_inf | (np.abs(got - want) <= TOL * np.maximum(1.0, np.abs(want)))
-    same_face = (gface == wface) | (want <= TOL)
-    bad = ~(close & same_face)
-    assert bad.mean() <= max_bad, (bad.sum(), got[bad][:5], want[bad][:5], gface[bad][:5], wface[bad][:5])
+        close = both_inf | (np.abs(got - want) <= tol)
+    far = np.nonzero(~close)[0]
+    if far.size:
+        # a grazing contact decided by rounding: the GPU's answer is the
+        # oracle's for the start point moved by 1e-9 mm along some axis
+        ok = np.zeros(far.size, dtype=bool)
+        for k in range(3):
+            for sg in (-1.0, 1.0):
+                xm = x[far].copy()
+                xm[:, k] += sg * PERTURB
+                wm, _ = orc.shape(kind, p, xm, u[far], what)
+                em, _ = orc.shape_err(kind, p, xm, u[far], what, tnorm)
+                with np.errstate(invalid="ignore"):
+                    ok |= (np.isinf(wm) & np.isinf(got[far])) | (np.abs(got[far] - wm) <= np.maximum(PERTURB_MATCH, em))
+        assert np.all(ok), (far[~ok][:5], got[far][~ok][:5], want[far][~ok][:5])
+    free = ~close | both_inf | (want <= tol) | (gap <= tol)
+    fbad = np.nonzero(~free & (gface != wface))[0]
+    assert fbad.size == 0, (fbad[:5], gface[fbad][:5], wface[fbad][:5], got[fbad][:5], want[fbad][:5])
+    return int(far.size)
 
 
 @pytest.mark.parametrize("idx", range(len(SOLIDS)))
@@ -116,14 +140,14 @@ def test_shape_queries_match_oracle(g, orc, idx):
     kind, p = SOLIDS[idx]
     x, u = sample(kind, p, 200000, 100 + idx)
     xs, us = on_surface(orc, kind, p, x[:20000], u[:20000])
-    for pts, dirs, max_bad in ((x, u, 1e-5), (xs, us, 2e-3)):
+    for pts, dirs, max_touch in ((x, u, 1e-5), (xs, us, 2e-3)):
         # within 1e-9 mm of the surface, inside/outside (and so both
-        # distances) is decided by rounding: that band is exempt
+        # distances) is decided by rounding: that band is only counted
         band = orc.shape(kind, p, pts, None, "safety_out") + orc.shape(kind, p, pts, None, "safety_in") < TOL
         for what in ("dist_out", "dist_in"):
             got, gface = gpu(g, kind, p, what, pts, dirs)
-            want, wface = orc.shape(kind, p, pts, dirs, what)
-            check_distance(got[~band], gface[~band], want[~band], wface[~band], max_bad)
+            touch = check_distance(orc, kind, p, what, pts[~band], dirs[~band], got[~band], gface[~band])
+            assert touch <= max_touch * pts.shape[0], touch
         for what in ("safety_out", "safety_in"):
             got, gface = gpu(g, kind, p, what, pts, dirs)
             want = orc.shape(kind, p, pts, None, what)
@@ -137,8 +161,8 @@ def test_shape_queries_match_oracle(g, orc, idx):
 @pytest.mark.parametrize("idx", [0, 2, 4, 8, 12, 14])
 def test_placed_solid(g, orc, idx):
     """Placement applied in the kernel: compare with the oracle on points
-    transformed on the host (the transforms round differently, so distances
-    get a 1e-9 relative tolerance and Contains the surface band)."""
+    transformed on the host (the transforms round differently: the error
+    bound counts the placement's distance)."""
     kind, p = SOLIDS[idx]
     rng = np.random.default_rng(7 + idx)
     R = np.asarray(scenes.haar_rotation(rng)).reshape(3, 3)
@@ -150,8 +174,8 @@ def test_placed_solid(g, orc, idx):
     u_back = uw @ R
     for what in ("dist_out", "dist_in"):
         got, gface = gpu(g, kind, p, what, xw, uw, rot=R, trans=t)
-        want, wface = orc.shape(kind, p, x_back, u_back, what)
-        check_distance(got, gface, want, wface, 1e-4)
+        touch = check_distance(orc, kind, p, what, x_back, u_back, got, gface, tnorm=float(np.linalg.norm(t)))
+        assert touch <= 1e-4 * xw.shape[0], touch
     got, _ = gpu(g, kind, p, "safety_out", xw, uw, rot=R, trans=t)
     want = orc.shape(kind, p, x_back, None, "safety_out")
     assert np.max(np.abs(got - want)) <= 1e-9 * 300

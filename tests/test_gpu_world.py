@@ -4,9 +4,13 @@ oracle, both modes bit for bit identical to each other.
 
 Transport runs several steps; at every step the oracle gets the GPU's state
 (position, node, flag) as input, so differences cannot accumulate.  Bars:
-steps within 1e-9 mm (relative to max(1, s)); node and flag exact except on
-tracks whose oracle answer changes when the start point moves by 1e-9 mm
-(a boundary point within rounding of another surface), which must be rare.
+every step within max(1e-9 mm, err) of the oracle's, err the oracle's
+a-priori FP64 error bound of that step, which adds the rounding of the
+placements that bring the world point into its node level by level (the GPU
+applies one composed transform per node instead; pinned against exact
+crossings in test_oracle_errbound.py); node and flag exact except on tracks
+whose oracle answer changes when the start point moves by 1e-9 mm (a
+boundary point within rounding of another surface), which must be rare.
 """
 import numpy as np
 import pytest
@@ -91,9 +95,10 @@ def test_transport_matches_oracle(g, orc, make, seed, min_checked):
         s1, n1, f1 = gpu_step(g, W, tr, node, flag, 1)
         assert np.array_equal(s0.view(np.int64)[alive], s1.view(np.int64)[alive]), it
         assert np.array_equal(n0, n1) and np.array_equal(f0, f1), it
-        os_, on, of = orc.world_step(w, tr, node, flag)
+        os_, on, of, info = orc.world_step(w, tr, node, flag, info=True)
         d = np.abs(s0 - os_)[alive]
-        assert np.all(d <= 1e-9 * np.maximum(1.0, np.abs(os_[alive]))), (it, d.max())
+        tol = np.maximum(1e-9, info["err"])[alive]
+        assert np.all(d <= tol), (it, np.nonzero(d > tol)[0][:5], d.max())
         diff = alive & ((n0 != on) | (f0 != of))
         if diff.any():
             ex = unstable(orc, w, tr, node, flag, on)
