@@ -281,8 +281,8 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
 
 /* For callers that must not allocate device memory while they run (an
  * application whose allocator owns all device memory, a real-time loop that
- * forbids allocation after start-up, code recorded under global-mode stream
- * capture).  The paper has no counterpart: this is a service of the library.
+ * forbids allocation after start-up).  The paper has no counterpart: this is
+ * a service of the library.
  * Same step and answers as geo_build_batch + geo_dist_to_boundary_batched
  * (GEO_FP32_REFINE), but this call allocates nothing: the tile list, the
  * volume views, the tile counter and the status word are kept in a fixed
@@ -298,7 +298,12 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
  * Every call reuses the same array, so calls that overlap on the GPU (on
  * different streams, or from different host threads) race: serialise them.
  * The counter and status word are cleared by each call; the rest keeps the
- * last call's contents. */
+ * last call's contents.  The tile list and the volume views are copied from
+ * host memory that is not page-locked; such a copy waits for the work already
+ * queued on `stream`, so the call may block the host until that work is done.
+ * A wait of the kernel that runs out, or a tile index outside n_total, is
+ * recorded in the status word of every volume of the call (read it with
+ * geo_check_device_status). */
 geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vols, int32_t n_vols,
                                                 const geo_basket* baskets, int32_t n_baskets,
                                                 const double* x, const double* y, const double* z,
@@ -399,10 +404,30 @@ geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const doubl
                                       double* step, int32_t* hit, int32_t* nref, void* stream);
 
 /* Reads and clears the volume's device status word (errors recorded by
- * kernels, e.g. a bulk-copy wait that ran out of polls).  Synchronises
- * `stream`.  Returns GEO_ERR_DEVICE_ASSERT if any was recorded; *word gets
- * the raw bits when non-NULL. */
+ * kernels: 1 a bulk-copy wait that ran out of polls, 2 a track index outside
+ * the basket, 4 a pipeline wait that ran out of polls; the batched launches
+ * record theirs in every volume of the batch).  Synchronises `stream`.
+ * Returns GEO_ERR_DEVICE_ASSERT if any was recorded; *word gets the raw bits
+ * when non-NULL. */
 geo_status geo_check_device_status(geo_volume v, uint32_t* word, void* stream);
+
+/* ---- test support: failure detection without a GPU fault ----------------
+ * The paper has no counterpart; these exercise the library's failure paths.
+ *
+ * geo_selftest_wait_timeout: launches one warp that waits, with `polls`
+ * (1 .. 2^20) polls, on a shared-memory barrier that no thread arrives at --
+ * the failure path of every bounded wait of the pipeline kernels -- and
+ * records bit 4 in the volume's status word; the kernel then returns, so the
+ * context stays usable.  Asynchronous on `stream`; read the word with
+ * geo_check_device_status.
+ *
+ * geo_debug_fail_alloc: host-side fault injection.  With nth > 0, the nth
+ * allocation the library makes from now on (host objects of volumes, batches
+ * and trees, and their device memory) fails as if memory had run out: the
+ * building call frees what it had taken and returns GEO_ERR_OOM.  0 turns it
+ * off; negative values give GEO_ERR_INVALID_ARG.  Process-wide. */
+geo_status geo_selftest_wait_timeout(geo_volume v, uint32_t polls, void* stream);
+geo_status geo_debug_fail_alloc(int32_t nth);
 
 /* Measurement support (not part of the navigator): issue rate in operations
  * per second of one arithmetic operation over the whole GPU: what = 0 FP32

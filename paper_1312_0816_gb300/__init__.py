@@ -12,4 +12,5 @@ from .geonav import (GEO_BOX, GEO_CONE, GEO_FP32_REFINE, GEO_FP64, GEO_PCON, GEO
                      geo_adjoint_workspace_size, geo_dist_to_boundary_adjoint,
                      geo_shape_query, GEO_Q_DIST_OUT, GEO_Q_DIST_IN, GEO_Q_SAFETY_OUT, GEO_Q_SAFETY_IN,
                      GEO_Q_CONTAINS, World, geo_build_world, geo_destroy_world, geo_world_info,
-                     geo_world_nodes, geo_world_locate, geo_world_step)
+                     geo_world_nodes, geo_world_locate, geo_world_step, geo_selftest_wait_timeout,
+                     geo_debug_fail_alloc)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
@@ -448,8 +449,8 @@ geo_status build_voxels(const geo_placed_shape& m, const geo_placed_shape* d, in
     }
     if (ids.empty()) ids.push_back(0);
     cudaError_t e;
-    if ((e = cudaMalloc(&v->vox_off, sizeof(int32_t) * off.size())) != cudaSuccess ||
-        (e = cudaMalloc(&v->vox_ids, sizeof(int32_t) * ids.size())) != cudaSuccess ||
+    if ((e = lib_malloc(&v->vox_off, sizeof(int32_t) * off.size())) != cudaSuccess ||
+        (e = lib_malloc(&v->vox_ids, sizeof(int32_t) * ids.size())) != cudaSuccess ||
         (e = cudaMemcpyAsync(v->vox_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(v->vox_ids, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice, s)) !=
@@ -519,6 +520,23 @@ const double* volume_host_table(geo_volume v, int j) {
 }
 int volume_device(geo_volume v) { return v ? v->device : -1; }
 int sm_count(int device) { return num_sms_of(device); }
+
+// geo_debug_fail_alloc: > 0 counts down the allocations; the one that brings
+// it to zero fails
+static std::atomic<int> g_fail_alloc{0};
+bool lib_alloc_fails() {
+    int n = g_fail_alloc.load();
+    while (n > 0)
+        if (g_fail_alloc.compare_exchange_weak(n, n - 1)) return n == 1;
+    return false;
+}
+cudaError_t lib_malloc_raw(void** p, size_t bytes) {
+    if (lib_alloc_fails()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 }  // namespace geonav
 
 extern "C" {
@@ -551,13 +569,16 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
             if (opts->grid[k] < 0 || opts->grid[k] > 256) return GEO_ERR_INVALID_ARG;
     }
 
+    geo_volume v = lib_new<geo_volume_s>();
+    if (!v) return GEO_ERR_OOM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        delete v;
+        return GEO_ERR_CUDA;
+    }
 
     const double S = mother_scale(*mother);
-    geo_volume v = new (std::nothrow) geo_volume_s;
-    if (!v) return GEO_ERR_OOM;
     v->device = dev;
     // the polycones' plane tables, daughters first, then the mother
     v->pl_off.assign(size_t(n_daughters) + 1, -1);
@@ -569,7 +590,7 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
         v->h_planes.insert(v->h_planes.end(), T.begin(), T.end());
     }
     cudaError_t e = cudaSuccess;
-    if (!v->h_planes.empty() && (e = cudaMalloc(&v->planes, sizeof(double) * v->h_planes.size())) != cudaSuccess) {
+    if (!v->h_planes.empty() && (e = lib_malloc(&v->planes, sizeof(double) * v->h_planes.size())) != cudaSuccess) {
         delete v;
         return cuda_status(e);
     }
@@ -602,8 +623,8 @@ geo_status geo_build_volume(const geo_placed_shape* mother, const geo_placed_sha
 
     const size_t b64 = sizeof(ShapeRec64) * size_t(std::max(n_daughters, 1));
     const size_t b32 = sizeof(ShapeRec32) * size_t(std::max(n_daughters, 1));
-    if ((e = cudaMalloc(&v->d64, b64)) != cudaSuccess || (e = cudaMalloc(&v->d32, b32)) != cudaSuccess ||
-        (e = cudaMalloc(&v->status, sizeof(unsigned int))) != cudaSuccess) {
+    if ((e = lib_malloc(&v->d64, b64)) != cudaSuccess || (e = lib_malloc(&v->d32, b32)) != cudaSuccess ||
+        (e = lib_malloc(&v->status, sizeof(unsigned int))) != cudaSuccess) {
         geo_destroy_volume(v);
         return cuda_status(e);
     }
@@ -789,7 +810,7 @@ geo_status geo_dist_to_boundary_host(geo_volume v, const double* x, const double
             v->ws = nullptr;
             v->ws_tracks = 0;
         }
-        if ((e = cudaMalloc(&v->ws, geo_volume_s::kStageBufs * size_t(chunk) * per_track)) != cudaSuccess)
+        if ((e = lib_malloc(&v->ws, geo_volume_s::kStageBufs * size_t(chunk) * per_track)) != cudaSuccess)
             return cuda_status(e);
         v->ws_tracks = chunk;
     }
@@ -910,7 +931,7 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     }
     std::vector<VolView> views(n_vols);
     for (int i = 0; i < n_vols; ++i) views[i] = vols[i]->view;
-    geo_batch b = new (std::nothrow) geo_batch_s;
+    geo_batch b = lib_new<geo_batch_s>();
     if (!b) return GEO_ERR_OOM;
     b->device = dev;
     b->n_vols = n_vols;
@@ -920,10 +941,10 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     for (int i = 0; i < n_vols; ++i) b->segs = b->segs || vols[i]->view.segs;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if ((e = cudaMalloc(&b->d_vols, sizeof(VolView) * n_vols)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_words, 2 * sizeof(unsigned int))) != cudaSuccess ||
-        (!idx.empty() && (e = cudaMalloc(&b->d_idx, sizeof(int64_t) * idx.size())) != cudaSuccess) ||
+    if ((e = lib_malloc(&b->d_vols, sizeof(VolView) * n_vols)) != cudaSuccess ||
+        (e = lib_malloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess ||
+        (e = lib_malloc(&b->d_words, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (!idx.empty() && (e = lib_malloc(&b->d_idx, sizeof(int64_t) * idx.size())) != cudaSuccess) ||
         (!idx.empty() && (e = cudaMemcpyAsync(b->d_idx, idx.data(), sizeof(int64_t) * idx.size(),
                                               cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
         (e = cudaMemcpyAsync(b->d_vols, views.data(), sizeof(VolView) * n_vols, cudaMemcpyHostToDevice, s)) !=
@@ -975,7 +996,7 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
     bv.counter = b->d_words;
     bv.status = b->d_words + 1;
     bv.segs = b->segs;
-    bv.pad = 0;
+    bv.nvols = b->n_vols;
     bv.idx = b->d_idx;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
     return cuda_status(launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, s, num_sms_of(b->device)));
@@ -1048,6 +1069,19 @@ geo_status geo_dist_to_boundary_stats(geo_volume v, const double* x, const doubl
     const Basket b{x, y, z, dx, dy, dz, n};
     return cuda_status(launch_dist_refine_stats(v->view, b, step, hit, nullptr, nref,
                                                 static_cast<cudaStream_t>(stream), num_sms_of(v->device)));
+}
+
+geo_status geo_selftest_wait_timeout(geo_volume v, uint32_t polls, void* stream) {
+    geo_status st = check_volume_device(v);
+    if (st != GEO_OK) return st;
+    if (polls == 0 || polls > (1u << 20)) return GEO_ERR_INVALID_ARG;
+    return cuda_status(launch_wait_selftest(v->status, polls, static_cast<cudaStream_t>(stream)));
+}
+
+geo_status geo_debug_fail_alloc(int32_t nth) {
+    if (nth < 0) return GEO_ERR_INVALID_ARG;
+    g_fail_alloc.store(nth);
+    return GEO_OK;
 }
 
 geo_status geo_check_device_status(geo_volume v, uint32_t* word, void* stream) {

@@ -2,6 +2,7 @@
 // CUDA translation units of the navigator library (not part of the C ABI).
 #pragma once
 #include <cstdint>
+#include <new>
 #include <cuda_runtime.h>
 #include "../../include/geo.h"
 
@@ -123,7 +124,7 @@ struct BatchView {
     unsigned int* counter;    // next tile to claim (reset before every launch)
     unsigned int* status;     // device error word of the batch
     int32_t segs;             // 1 if a volume holds a tube segment or a polycone
-    int32_t pad;
+    int32_t nvols;            // entries of vols
     const int64_t* idx;       // track indices of packed tiles (count < 0), or null
 };
 
@@ -132,6 +133,8 @@ constexpr unsigned ST_TMA_TIMEOUT = 1u;
 constexpr unsigned ST_BAD_INDEX = 2u;
 constexpr unsigned ST_SYNC_TIMEOUT = 4u;
 
+// the failure path of a bounded wait, run on purpose (tests)
+cudaError_t launch_wait_selftest(unsigned int* status, uint32_t polls, cudaStream_t s);
 // shared memory of the refine kernel's two stage buffers (host)
 size_t refine_stage_bytes();
 // the refine kernel in its latency configuration (small baskets)
@@ -148,6 +151,15 @@ cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, 
 bool small_basket(const VolView& v, int64_t n, int num_sms);
 cudaError_t launch_dist_warp(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                              cudaStream_t s, int num_sms);
+// small baskets in volumes of 33..64 daughters (no voxels), FP32-filter mode:
+// one warp per track with the daughters' FP32 bounds split over its lanes
+#ifndef GEO_SMALL_FILTER_TRACKS_PER_SM
+#define GEO_SMALL_FILTER_TRACKS_PER_SM 8
+#endif
+constexpr int kSmallFilterTracksPerSm = GEO_SMALL_FILTER_TRACKS_PER_SM;
+bool small_basket_filter(const VolView& v, int64_t n, int num_sms);
+cudaError_t launch_dist_warp_filter(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
+                                    cudaStream_t s, int num_sms);
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit,
@@ -177,6 +189,20 @@ size_t adjoint_workspace_bytes(int nd, int64_t n, int num_sms);
 cudaError_t launch_adjoint(const VolView& v, const Basket& b, const int32_t* hit, const double* gstep, double* gp,
                            double* gd, double* gtrans, double* gparams, double* workspace, cudaStream_t s,
                            int num_sms);
+
+// The library's allocations go through these, so that geo_debug_fail_alloc()
+// (host-side fault injection for the tests) can make one of them fail as if
+// memory had run out (defined in geo_abi.cu).
+bool lib_alloc_fails();
+cudaError_t lib_malloc_raw(void** p, size_t bytes);
+template <class T>
+inline cudaError_t lib_malloc(T** p, size_t bytes) {
+    return lib_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline T* lib_new() {
+    return lib_alloc_fails() ? nullptr : new (std::nothrow) T;
+}
 
 // accessors of the opaque volume handle (defined in geo_abi.cu)
 const VolView* volume_view(geo_volume v);

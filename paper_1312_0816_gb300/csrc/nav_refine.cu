@@ -96,8 +96,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 const int count = packed ? -hd.count : hd.count;
                 producer_barrier<kProd>();
                 const VolView& v = hd.vol;
-                const bool live = t < count;
-                const int64_t i = live ? (packed ? bv.idx[base + t] : base + t) : 0;
+                bool live = t < count;
+                int64_t i = live ? (packed ? bv.idx[base + t] : base + t) : 0;
+                if (live && (i < 0 || i >= b.n)) {   // a stale or corrupt tile list: skip, and say so
+                    atomicOr(bv.status, ST_BAD_INDEX);
+                    atomicOr(v.status, ST_BAD_INDEX);
+                    live = false;
+                    i = 0;
+                }
                 cur_i = i;
                 cur_live = live;
                 double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
@@ -188,6 +194,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
             if (lane == 0) mbar_arrive(&done[k & 1]);
         }
     }
+    // a wait that ran out is also reported in every volume's status word,
+    // which geo_check_device_status reads
+    if (!healthy)
+        for (int q = 0; q < bv.nvols; ++q) atomicOr(bv.vols[q].status, ST_SYNC_TIMEOUT);
+}
+
+// A bounded wait that runs out: one warp waits, with `polls` polls, on an
+// mbarrier that no thread arrives at, then records ST_SYNC_TIMEOUT in the
+// status word and returns (the failure path of every wait of the pipeline,
+// exercised on purpose by the tests).
+__global__ void k_wait_selftest(unsigned int* status, uint32_t polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    for (uint32_t it = 0; it < polls; ++it)
+        if (mbar_try_wait(&bar, 0)) return;
+    if (threadIdx.x == 0) atomicOr(status, ST_SYNC_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(unsigned int* status, uint32_t polls, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status, polls);
+    return cudaGetLastError();
 }
 
 template <bool SEGS>
@@ -250,6 +278,7 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
 cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                                cudaStream_t s, int num_sms) {
     if (small_basket(v, b.n, num_sms)) return launch_dist_warp(v, b, step, hit, bpoint, s, num_sms);
+    if (small_basket_filter(v, b.n, num_sms)) return launch_dist_warp_filter(v, b, step, hit, bpoint, s, num_sms);
     return launch_dist_refine_stats(v, b, step, hit, bpoint, nullptr, s, num_sms);
 }
 

@@ -3,10 +3,9 @@
 //
 // Some programs cannot let a library call cudaMalloc once they are running:
 // an application whose framework owns all device memory through its own
-// allocator, a real-time pipeline that forbids allocation after start-up so
-// that a step can neither fail for lack of memory nor stall (cudaMalloc and
-// cudaFree synchronise the device), or code recorded while a stream is being
-// captured in global mode, where cudaMalloc is not permitted.  For them,
+// allocator, or a real-time pipeline that forbids allocation after start-up
+// so that a step can neither fail for lack of memory nor stall the device
+// (cudaMalloc and cudaFree synchronise it).  For them,
 // geo_dist_to_boundary_batched_noalloc runs the batched persistent launch
 // with its scratch -- the tile list, the per-volume views, the tile counter
 // and the status word -- in one fixed array of device memory that belongs to
@@ -118,7 +117,11 @@ extern "C" geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vol
     });
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
-    // pageable sources: each copy has read its source when the call returns
+    // Copies from pageable host memory: the runtime has read the source (into
+    // its staging memory) when such a call returns, so the shared host tile
+    // list can be rewritten by the next call; it also waits for the work
+    // already queued on the stream before it starts the copy, so this call may
+    // block the host until then.
     for (int i = 0; i < n_vols && e == cudaSuccess; ++i)
         e = cudaMemcpyAsync(&d->vols[i], volume_view(vols[i]), sizeof(VolView), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
@@ -133,7 +136,7 @@ extern "C" geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vol
     bv.counter = &d->words[0];
     bv.status = &d->words[1];
     bv.segs = 0;
-    bv.pad = 0;
+    bv.nvols = n_vols;
     bv.idx = nullptr;   // plain tiles only
     for (int i = 0; i < n_vols; ++i) bv.segs = bv.segs || volume_view(vols[i])->segs;
     const Basket bk{x, y, z, dx, dy, dz, n_total};

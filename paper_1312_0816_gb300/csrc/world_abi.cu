@@ -133,7 +133,7 @@ geo_status geo_build_world(const geo_volume* volumes, int32_t n_volumes, const i
             xf.insert(xf.end(), tc, tc + 3);
         }
     }
-    geo_world w = new (std::nothrow) geo_world_s;
+    geo_world w = lib_new<geo_world_s>();
     if (!w) return GEO_ERR_OOM;
     w->device = dev;
     w->nlv = n_volumes;
@@ -152,9 +152,9 @@ geo_status geo_build_world(const geo_volume* volumes, int32_t n_volumes, const i
     std::copy(first.begin(), first.end(), node.begin() + 3 * size_t(w->nnodes));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if ((e = cudaMalloc(&w->d_vols, sizeof(VolView) * views.size())) != cudaSuccess ||
-        (e = cudaMalloc(&w->d_node, sizeof(int32_t) * node.size())) != cudaSuccess ||
-        (e = cudaMalloc(&w->d_xf, sizeof(double) * xf.size())) != cudaSuccess ||
+    if ((e = lib_malloc(&w->d_vols, sizeof(VolView) * views.size())) != cudaSuccess ||
+        (e = lib_malloc(&w->d_node, sizeof(int32_t) * node.size())) != cudaSuccess ||
+        (e = lib_malloc(&w->d_xf, sizeof(double) * xf.size())) != cudaSuccess ||
         (e = cudaMemcpyAsync(w->d_vols, views.data(), sizeof(VolView) * views.size(), cudaMemcpyHostToDevice, s)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(w->d_node, node.data(), sizeof(int32_t) * node.size(), cudaMemcpyHostToDevice, s)) !=
@@ -239,8 +239,8 @@ geo_status geo_world_step(geo_world w, const double* x, const double* y, const d
         w->d_perm = nullptr;
         w->d_cnt = nullptr;
         w->perm_cap = 0;
-        if ((e = cudaMalloc(&w->d_perm, sizeof(int32_t) * size_t(n))) != cudaSuccess ||
-            (e = cudaMalloc(&w->d_cnt, sizeof(int32_t) * (size_t(w->nlv) + 1))) != cudaSuccess)
+        if ((e = lib_malloc(&w->d_perm, sizeof(int32_t) * size_t(n))) != cudaSuccess ||
+            (e = lib_malloc(&w->d_cnt, sizeof(int32_t) * (size_t(w->nlv) + 1))) != cudaSuccess)
             return world_cuda_status(e);
         w->perm_cap = n;
     }

@@ -57,7 +57,8 @@ EXPORTS = ("geo_build_volume", "geo_destroy_volume", "geo_volume_info", "geo_dis
            "geo_check_device_status", "geo_probe_pipe", "geo_build_batch", "geo_destroy_batch",
            "geo_dist_to_boundary_batched", "geo_dist_to_boundary_batched_noalloc", "geo_adjoint_workspace_size",
            "geo_dist_to_boundary_adjoint", "geo_shape_query", "geo_build_world", "geo_destroy_world",
-           "geo_world_info", "geo_world_nodes", "geo_world_locate", "geo_world_step", "geo_status_string")
+           "geo_world_info", "geo_world_nodes", "geo_world_locate", "geo_world_step", "geo_selftest_wait_timeout",
+           "geo_debug_fail_alloc", "geo_status_string")
 
 
 def library_path() -> str:
@@ -103,6 +104,8 @@ def load(build_if_stale: bool = True):
     L.geo_adjoint_workspace_size.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_uint64)]
     L.geo_dist_to_boundary_adjoint.argtypes = [vp, dp, dp, dp, dp, dp, dp, i64, ip, dp, dp, dp, dp, dp, vp,
                                                ctypes.c_uint64, vp]
+    L.geo_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint32, vp]
+    L.geo_debug_fail_alloc.argtypes = [i32]
     L.geo_status_string.argtypes = [ctypes.c_int]
     L.geo_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -455,6 +458,18 @@ def geo_check_device_status(vol: Volume, stream=None) -> int:
     if st == 5:
         raise GeoError(st, f"device status word 0x{w.value:x}")
     return w.value
+
+
+def geo_selftest_wait_timeout(vol: Volume, polls: int = 256, stream=None):
+    """Runs the failure path of a bounded wait (a barrier nobody arrives at);
+    the volume's status word then holds bit 4 (see geo.h)."""
+    _check(load().geo_selftest_wait_timeout(vol.handle, int(polls), _stream(stream)), "geo_selftest_wait_timeout")
+
+
+def geo_debug_fail_alloc(nth: int):
+    """Host-side fault injection: the nth allocation of the library from now
+    on fails as out of memory (0: off).  See geo.h."""
+    _check(load().geo_debug_fail_alloc(int(nth)), "geo_debug_fail_alloc")
 
 
 def geo_probe_pipe(what: int, iters: int = 1 << 16, blocks: int = 0, stream=None) -> float:

@@ -160,3 +160,27 @@ def test_polycone_validation(shape, status):
     L = geonav.load()
     s = shape()
     assert L.geo_shape_query(ctypes.byref(s), 0, None, None, None, None, None, None, 0, None, None, None) == status
+
+
+def test_allocation_failure_returns_oom_on_the_host():
+    """Host-side fault injection (geo_debug_fail_alloc): the library's first
+    allocation of a build fails as if memory had run out, and the build
+    returns GEO_ERR_OOM before it touches the GPU; with the hook off the same
+    call goes on (here, without a GPU, to the device query)."""
+    L = geonav.load()
+    mother = _shape(0, (100, 100, 100))
+    daughter = _shape(0, (10, 10, 10))
+    assert L.geo_debug_fail_alloc(-1) == 1
+    assert L.geo_debug_fail_alloc(1) == 0
+    try:
+        st, out = _build(mother, [daughter])
+        assert st == 3 and out.value is None          # GEO_ERR_OOM, no handle
+    finally:
+        assert L.geo_debug_fail_alloc(0) == 0
+    st, out = _build(mother, [daughter])
+    assert st != 3
+
+
+def test_selftest_rejects_bad_arguments():
+    L = geonav.load()
+    assert L.geo_selftest_wait_timeout(None, 16, None) == 1
