@@ -50,13 +50,16 @@ FP64_OPS = {
     ("out", 0): (30, 0, 1), ("out", 1): (23, 2, 3), ("out", 2): (33, 2, 3),
     ("in", 0): (3, 0, 3), ("in", 1): (12, 1, 2), ("in", 2): (17, 1, 2),
 }
-FP64_TRANSFORM = 21
+FP64_TRANSFORM = 21          # rotated placement: 3 subtractions + 18 multiply/FMA
+FP64_TRANSFORM_IDENTITY = 3  # identity rotation: the 3 subtractions alone
 FP64_BPOINT = 3
 # FP32 instructions of the filter per daughter: bounding-sphere test,
 # transform, and the bound of each kind (MUFU reciprocal / square root
 # counted as 4)
-FP32_SPHERE, FP32_TRANSFORM = 16, 18
+FP32_SPHERE, FP32_TRANSFORM = 16, 18   # the rotation is skipped for identity placements
 FP32_SHAPE = {0: 45, 1: 90, 2: 110}
+FP32_DDA_STEP = 12     # one grid step: pick the axis, advance index and boundary, test the range
+FP32_MOTHER = 100      # the mother's two FP32 exits (shrunk and grown copy)
 KERNEL_SOURCES = ("nav_refine.cu", "refine_kernel.cuh", "nav_refine.cuh", "shapes32.cuh", "shapes64.cuh", "nav_common.cuh",
                   "stage.cuh", "geo_internal.h")
 
@@ -134,37 +137,60 @@ class Clocks:
 
 
 def algorithmic_ops(sc, hit):
-    """Algorithmic work per track of the step (shared by both modes):
-    HBM bytes 48 in + 12 out; FP64 = one evaluation of the winning solid (its
-    transform and DistFromOutside, or the mother's DistFromInside) and the
-    boundary point; FP32 (filter) = one bound per daughter whose bounding
-    sphere the track's line meets, plus the sphere tests."""
+    """Share of the tracks whose winner is the mother, and per (kind, identity
+    placement) the share whose winner is such a daughter."""
     kinds = sc.kinds
+    eye = sc.identity_mask()
     w = hit[hit >= -1]
     m = (w == -1).mean()
     ops_d = {}
+    wd = np.maximum(w, 0)
     for k in (0, 1, 2):
-        ops_d[k] = ((w >= 0) & (np.where(w >= 0, kinds[np.maximum(w, 0)], -1) == k)).mean()
+        for ident in (False, True):
+            ops_d[(k, ident)] = ((w >= 0) & (kinds[wd] == k) & (eye[wd] == ident)).mean()
     return m, ops_d
 
 
 def fp64_ops_per_track(sc, frac_mother, frac_kind, q_sqrt, q_div):
     """Algorithmic FP64 work of the filter+refine step per track, in DFMA
-    equivalents: the mother's DistFromInside (always), the transform and
-    DistFromOutside of the winning daughter, and the boundary point."""
+    equivalents: the mother's DistFromInside (always), the transform (3
+    operations for an identity rotation, 21 otherwise) and DistFromOutside of
+    the winning daughter, and the boundary point."""
     def cost(key):
         a, s, d = FP64_OPS[key]
         return a + s * q_sqrt + d * q_div
 
     ops = cost(("in", sc.mother_kind))
-    for k, f in frac_kind.items():
-        ops += f * (FP64_TRANSFORM + cost(("out", k)))
+    for (k, ident), f in frac_kind.items():
+        ops += f * ((FP64_TRANSFORM_IDENTITY if ident else FP64_TRANSFORM) + cost(("out", k)))
     return ops + FP64_BPOINT
 
 
+def fp64_cost_per_track(sc, hit, q_sqrt, q_div, with_mother=True):
+    """Per-track algorithmic FP64 work (DFMA equivalents) of a step in scene
+    sc given its winners `hit`: the mother's DistFromInside (always, with
+    with_mother), the winning daughter's transform (3 or 21) and
+    DistFromOutside, and the boundary point.  Tracks outside the mother or
+    invalid count 0."""
+    def cost(key):
+        a, s_, d = FP64_OPS[key]
+        return a + s_ * q_sqrt + d * q_div
+
+    eye = sc.identity_mask()
+    per_d = np.array([(FP64_TRANSFORM_IDENTITY if e else FP64_TRANSFORM) + cost(("out", int(k)))
+                      for k, e in zip(sc.kinds, eye)] + [0.0])
+    hit = np.asarray(hit)
+    c = np.where(hit >= 0, per_d[np.maximum(hit, 0)], 0.0)
+    if with_mother:
+        c = c + np.where(hit >= -1, cost(("in", sc.mother_kind)) + FP64_BPOINT, 0.0)
+    return c
+
+
 def fp32_ops_per_track(sc):
-    """Algorithmic FP32 work: every daughter bounded in FP32."""
-    return float(sum(FP32_SPHERE + FP32_TRANSFORM + FP32_SHAPE[int(k)] for k in sc.kinds))
+    """Algorithmic FP32 work: every daughter bounded in FP32 (the rotation
+    only for rotated placements)."""
+    eye = sc.identity_mask()
+    return float(sum(FP32_SPHERE + (0 if e else FP32_TRANSFORM) + FP32_SHAPE[int(k)] for k, e in zip(sc.kinds, eye)))
 
 
 def sources_sha():
@@ -198,8 +224,8 @@ def run_reference(args):
         return
     cores = len(os.sched_getaffinity(0))
     sc = scenes.toy40(1)
-    sample = 1 << 18
-    tr = scenes.sample_tracks(sc, sample, 1)
+    sample = args.n
+    tr = scenes.sample_tracks(sc, sample, 1)   # the GPU arm's basket (rank 0)
     for _ in range(args.warmup):
         oracle.navigate(sc, tr.slice(0, 1024), nthreads=cores)
     t0 = time.perf_counter()
@@ -210,29 +236,145 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tracks/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_tracks": sample},
+            "config": {"workload": WORKLOAD, "tracks_per_gpu": sample, "mode": "the FP64 oracle",
+                       "same_config": sample == N_TRACKS},
             "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{sample} tracks of the toy-detector basket per step"},
+                             "sample": f"the whole {sample}-track toy-detector basket per step"},
             "e2e": {"value": value, "unit": "tracks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(sc, tr):
+# Samples of the side legs' GPU answers, checked against the oracle in the
+# CPU-baseline leg (the one place the benchmark runs the oracle).
+SAMPLES = {}
+SAMPLES_WORLD = {}
+Q_RATES = [8.6, 5.7]       # sqrt, div in DFMA equivalents (the probe's values replace these)
+PEAK_HBM = [6760.9]        # GB/s (MEASURED_PEAKS.json replaces this)
+MOVE = 1e-9   # mm: a start-point move that defines "decided by rounding"
+
+
+def _moved(scenes, tr, k, sign):
+    f = [tr.x.copy(), tr.y.copy(), tr.z.copy()]
+    f[k] = f[k] + sign * MOVE
+    return scenes.Tracks(*f, tr.dx, tr.dy, tr.dz)
+
+
+def accuracy(oracle, scenes, sc, tr, ref, step, hit, cores):
+    """Per-result error of GPU answers against the FP64 oracle, every track:
+    |dstep| within max(1e-9 mm, err) (err the oracle's a-priori FP64 bound),
+    hit equal outside the tie band; a track outside that counts as decided by
+    rounding if its answer is the oracle's for a start moved by 1e-9 mm, else
+    as a violation (must be 0)."""
+    dn = np.sqrt(tr.dx ** 2 + tr.dy ** 2 + tr.dz ** 2)
+    ok = ~np.isnan(ref["step"])
+    tol = np.maximum(1e-9 / dn, ref["err"])
+    d = np.where(ok, np.abs(step - ref["step"]), 0.0)
+    tie = ok & ((ref["second"] - ref["step"]) < tol)
+    cond = ok & (ref["err"] > 1e-9)
+    nan_mismatch = int((np.isnan(step) != ~ok).sum())
+    off = ok & (~(d <= tol) | (~tie & (hit != ref["hit"])))
+    graze = np.zeros(tr.n, dtype=bool)
+    idx = np.nonzero(off)[0]
+    if idx.size:
+        sub = scenes.Tracks(*(f[idx] for f in tr.fields()))
+        m = np.zeros(idx.size, dtype=bool)
+        for k in range(3):
+            for sg in (-1.0, 1.0):
+                r = oracle.navigate(sc, _moved(scenes, sub, k, sg), nthreads=cores)
+                t2 = np.maximum(1e-6 / dn[idx], r["err"])
+                m |= (np.abs(step[idx] - r["step"]) <= t2) & ((hit[idx] == r["hit"]) | (r["second"] - r["step"] < t2))
+        graze[idx] = m
+    viol = off & ~graze
+    return {"tracks": int(ok.sum()), "max_abs_dstep_mm": float((d * dn)[ok & ~cond & ~graze].max(initial=0.0)),
+            "max_abs_dstep_cond_band_mm": float((d * dn)[cond & ~graze].max(initial=0.0)),
+            "tie_banded": int(tie.sum()), "cond_banded": int(cond.sum()),
+            "hit_mismatch_outside_tie_band": int((ok & ~tie & (hit != ref["hit"]) & ~graze).sum()),
+            "rounding_decided": int(graze.sum()), "violations": int(viol.sum()) + nan_mismatch,
+            "bar": "|dstep| <= max(1e-9 mm, err) on every track; hit exact outside the tie band"}
+
+
+def cpu_baseline(sc, tr, step, hit):
     """The oracle as it stands on all host cores, over the whole basket (about
-    1 s wall on 16 cores), plus a single-thread rate on its first 8192 tracks."""
+    1 s wall on 16 cores), plus a single-thread rate on its first 8192 tracks;
+    then, untimed, the per-result error of the GPU answers on that basket and
+    on the side legs' samples against the oracle's."""
     import oracle
+    from paper_1312_0816_gb300 import scenes
 
     cores = len(os.sched_getaffinity(0))
     t0 = time.perf_counter()
-    oracle.navigate(sc, tr, nthreads=cores)
+    ref = oracle.navigate(sc, tr, nthreads=cores)
     dt = time.perf_counter() - t0
     one = tr.slice(0, 8192)
     t1 = time.perf_counter()
     oracle.navigate(sc, one, nthreads=1)
     dt1 = time.perf_counter() - t1
+    acc = {"headline": accuracy(oracle, scenes, sc, tr, ref, step, hit, cores)}
+    for name, (ssc, str_, sstep, shit) in SAMPLES.items():
+        if isinstance(ssc, list):   # batched: one scene per track
+            parts = []
+            for v in sorted(set(id(x) for x in ssc)):
+                sel = np.array([id(x) == v for x in ssc])
+                vs = next(x for x in ssc if id(x) == v)
+                sub = scenes.Tracks(*(f[sel] for f in str_.fields()))
+                r = oracle.navigate(vs, sub, nthreads=cores)
+                parts.append(accuracy(oracle, scenes, vs, sub, r, sstep[sel], shit[sel], cores))
+            agg = {k: sum(p_[k] for p_ in parts) for k in ("tracks", "tie_banded", "cond_banded",
+                                                             "hit_mismatch_outside_tie_band", "rounding_decided",
+                                                             "violations")}
+            agg["max_abs_dstep_mm"] = max(p_["max_abs_dstep_mm"] for p_ in parts)
+            agg["max_abs_dstep_cond_band_mm"] = max(p_["max_abs_dstep_cond_band_mm"] for p_ in parts)
+            acc[name] = agg
+        else:
+            r = oracle.navigate(ssc, str_, nthreads=cores)
+            acc[name] = accuracy(oracle, scenes, ssc, str_, r, sstep, shit, cores)
+    for name, (w, wt, nd, fl, wstep, wnode, wflag) in SAMPLES_WORLD.items():
+        acc[name] = world_accuracy(oracle, scenes, w, wt, nd, fl, wstep, wnode, wflag)
     return {"value": tr.n / dt, "unit": "tracks/s", "cores": cores, "kind": "oracle",
             "sample": f"the whole {tr.n}-track basket once, {cores} threads ({dt:.2f} s wall)",
-            "single_thread_value": 8192 / dt1}
+            "single_thread_value": 8192 / dt1}, acc
+
+
+def world_accuracy(oracle, scenes, w, tr, node, flag, step, node_out, flag_out):
+    """The tree step against the oracle's: |dstep| within max(1e-9 mm, err)
+    (err with the placements' rounding), node and flag equal unless the
+    oracle's own answer changes for a start moved by 1e-9 mm."""
+    s, nn, ff, info = oracle.world_step(w, tr, node, flag, info=True)
+    alive = node >= 0
+    tol = np.maximum(1e-9, info["err"])
+    d = np.where(alive, np.abs(step - s), 0.0)
+    diff = alive & ((node_out != nn) | (flag_out != ff))
+    unstable = np.zeros(tr.n, dtype=bool)
+    if diff.any():
+        for k in range(3):
+            for sg in (-1.0, 1.0):
+                _, n2, f2 = oracle.world_step(w, _moved(scenes, tr, k, sg), node, flag)
+                unstable |= (n2 != nn) | (f2 != ff)
+    cond = alive & (info["err"] > 1e-9)
+    return {"tracks": int(alive.sum()), "max_abs_dstep_mm": float(d[alive & ~cond].max(initial=0.0)),
+            "max_abs_dstep_cond_band_mm": float(d[cond].max(initial=0.0)), "cond_banded": int(cond.sum()),
+            "node_or_flag_differs": int(diff.sum()), "of_which_rounding_decided": int((diff & unstable).sum()),
+            "violations": int((alive & ~(d <= tol)).sum() + (diff & ~unstable).sum()),
+            "bar": "|dstep| <= max(1e-9 mm, err); node and flag exact unless a 1e-9 mm move changes the oracle's"}
+
+
+def roof_block(fp64_dfma, fp32_instr, hbm_bytes, seconds, kernel, note, peak_hbm_gbs):
+    """Binding roofline of a launch from its algorithmic work: T_roof =
+    max(HBM bytes / measured copy bandwidth, FP32 / nominal FP32, FP64 /
+    nominal FP64); frac = T_roof / measured time, reported against the
+    binding term's own peak."""
+    t = {"hbm": hbm_bytes / (peak_hbm_gbs * 1e9), "fp64": fp64_dfma * 2 / (PEAK_FP64_TFLOPS * 1e12),
+         "fp32": fp32_instr * 2 / (PEAK_FP32_TFLOPS * 1e12)}
+    bind = max(t, key=t.get)
+    if bind == "hbm":
+        ach, peak, unit, bound = hbm_bytes / seconds / 1e9, peak_hbm_gbs, "GB/s", "hbm"
+    else:
+        work = fp64_dfma if bind == "fp64" else fp32_instr
+        peak = PEAK_FP64_TFLOPS if bind == "fp64" else PEAK_FP32_TFLOPS
+        ach, unit, bound = work * 2 / seconds / 1e12, "TFLOP/s", "alu"
+    return {"bound": bound, "pipe": bind, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "t_roof_us": {k: v * 1e6 for k, v in t.items()}, "kernel": kernel, "algorithmic": note,
+            "peak_source": "FP32/FP64 nominal from unit counts x 2.07 GHz; HBM measured copy bandwidth"}
 
 
 def batched_leg(pkg, scenes, rank, steps):
@@ -249,15 +391,81 @@ def batched_leg(pkg, scenes, rank, steps):
     x = [torch.from_numpy(f).cuda() for f in tr.fields()]
     step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
     hit = torch.empty(tr.n, dtype=torch.int32, device="cuda")
-    order, bps, timings = autotune.tune_batch(volh, rows, x, step, hit)
-    batch = pkg.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps)
+    order, bps, tile, timings = autotune.tune_batch(volh, rows, x, step, hit)
+    batch = pkg.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps, tile_tracks=tile)
     ms = autotune.time_graph(batch, x, step, hit, reps=steps)
     batch.close()
+    # a sample of the last launch's answers for the accuracy check
+    owner = np.repeat(np.arange(len(rows)), rows[:, 2].astype(np.int64))
+    idx = np.sort(np.random.default_rng(31).choice(tr.n, 20000, replace=False))
+    s_np, h_np = step.cpu().numpy(), hit.cpu().numpy()
+    SAMPLES["batched"] = ([vols[int(rows[owner[i], 0])] for i in idx], scenes.Tracks(*(f[idx] for f in tr.fields())),
+                          s_np[idx], h_np[idx])
+    # algorithmic work of the launch: per basket, its volume's mother, winner
+    # and FP32 bounds of every daughter
+    f64 = f32 = 0.0
+    for v, off, cnt in rows:
+        sc_v = vols[int(v)]
+        f64 += float(fp64_cost_per_track(sc_v, h_np[off:off + cnt], Q_RATES[0], Q_RATES[1]).sum())
+        f32 += fp32_ops_per_track(sc_v) * int(cnt)
+    roof = roof_block(f64, f32, 60.0 * tr.n, ms * 1e-3, "k_dist_batched (one launch per step)",
+                      "per track: its volume's mother exit, winning daughter and boundary point in FP64; "
+                      "every daughter bounded in FP32; 60 B of HBM", PEAK_HBM[0])
     return {"workload": "64 volumes (box/tube mothers, 4..200 mixed daughters), %d baskets of 16..65536 "
                         "tracks, %d tracks, FP32+refine, one persistent launch per step as a CUDA graph"
                         % (len(rows), tr.n),
             "value": tr.n / (ms * 1e-3), "unit": "tracks/s", "ms_per_launch": ms, "steps": steps,
-            "schedule": {"tile_order": order, "blocks_per_sm": bps}, "autotune_ms": timings}
+            "schedule": {"tile_order": order, "blocks_per_sm": bps, "tile_tracks": tile,
+                         "warps": "12 producer + 2 consumer" if tile == 384 else "8 producer + 4 consumer"},
+            "autotune_ms": timings, "roofline": roof}
+
+
+def voxel_counts(sc, grid, tr, step):
+    """Instrumented walk of the uniform grid (counting only; not the
+    navigator): for each track, the distinct daughters listed in the cells
+    its line crosses from its start up to its step, and the grid steps taken.
+    The cells list the daughters whose world bounding box overlaps them, as
+    the library's grid does.  Returns (candidates, dda_steps) per track."""
+    mp = sc.mother_params
+    half = np.array(mp[:3], dtype=float)
+    g = np.array(grid, dtype=int)
+    lo, cell = -half, 2.0 * half / g
+    lists = [[] for _ in range(int(g.prod()))]
+    for j in range(sc.n_daughters):
+        k, p = int(sc.kinds[j]), sc.params[j]
+        he = np.array(p[:3]) if k == 0 else np.array([p[1], p[1], p[2]])
+        R = sc.rot[j].reshape(3, 3)
+        ext = np.abs(R) @ he
+        a = np.clip(np.floor((sc.trans[j] - ext - lo) / cell), 0, g - 1).astype(int)
+        b = np.clip(np.floor((sc.trans[j] + ext - lo) / cell), 0, g - 1).astype(int)
+        for i0 in range(a[0], b[0] + 1):
+            for i1 in range(a[1], b[1] + 1):
+                for i2 in range(a[2], b[2] + 1):
+                    lists[(i0 * g[1] + i1) * g[2] + i2].append(j)
+    cand, steps = np.zeros(tr.n, dtype=int), np.zeros(tr.n, dtype=int)
+    for t in range(tr.n):
+        p = np.array([tr.x[t], tr.y[t], tr.z[t]])
+        d = np.array([tr.dx[t], tr.dy[t], tr.dz[t]])
+        ii = np.clip(np.floor((p - lo) / cell).astype(int), 0, g - 1)
+        st = np.sign(d).astype(int)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            nxt = np.where(d > 0, lo + (ii + 1) * cell, lo + ii * cell)
+            tm = np.where(d != 0, (nxt - p) / d, np.inf)
+            te = np.where(d != 0, cell / np.abs(d), np.inf)
+        seen = set()
+        n = 0
+        while True:
+            seen.update(lists[(ii[0] * g[1] + ii[1]) * g[2] + ii[2]])
+            k = int(np.argmin(tm))
+            if not tm[k] <= step[t]:
+                break
+            ii[k] += st[k]
+            if ii[k] < 0 or ii[k] >= g[k]:
+                break
+            tm[k] += te[k]
+            n += 1
+        cand[t], steps[t] = len(seen), n
+    return cand, steps
 
 
 def voxel_leg(pkg, scenes, rank, steps):
@@ -286,6 +494,24 @@ def voxel_leg(pkg, scenes, rank, steps):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / k
         out[name] = {"value": tr.n / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "steps": k}
+        if mode == 1:   # a sample of the answers for the accuracy check and the work count
+            idx = np.sort(np.random.default_rng(37).choice(tr.n, 20000, replace=False))
+            s_np, h_np = step.cpu().numpy(), hit.cpu().numpy()
+            SAMPLES["voxel_512"] = (sc, scenes.Tracks(*(f[idx] for f in tr.fields())), s_np[idx], h_np[idx])
+            sub = idx[:4000]
+            cand, dda = voxel_counts(sc, pkg.geo_volume_info(vol)["grid"], scenes.Tracks(*(f[sub] for f in tr.fields())),
+                                     s_np[sub])
+            eye = sc.identity_mask()
+            per_cand = np.mean([FP32_SPHERE + (0 if e else FP32_TRANSFORM) + FP32_SHAPE[int(k)]
+                                for k, e in zip(sc.kinds, eye)])
+            f32_track = float(cand.mean() * per_cand + dda.mean() * FP32_DDA_STEP + FP32_MOTHER)
+            f64_track = float(fp64_cost_per_track(sc, h_np, Q_RATES[0], Q_RATES[1]).mean())
+            out["roofline"] = roof_block(f64_track * tr.n, f32_track * tr.n, 60.0 * tr.n, ms * 1e-3,
+                                         "k_dist_refine, grid traversal (one launch per step)",
+                                         "per track: FP32 bounds of the distinct daughters listed in the cells "
+                                         "the line crosses up to its step (%.2f on average, instrumented walk of "
+                                         "4000 tracks) and %.2f grid steps; FP64 mother, winner and boundary point"
+                                         % (cand.mean(), dda.mean()), PEAK_HBM[0])
     info = pkg.geo_volume_info(vol)
     vol.close()
     out["workload"] = ("box mother half 800 mm, 512 rotated boxes/tubes on an 8x8x8 grid, uniform grid %s, "
@@ -461,11 +687,24 @@ def adjoint_leg(pkg, scenes, rank, steps):
             pkg.geo_dist_to_boundary_adjoint(vol, *c, h, w)
 
         ms_fb = _event_time(fwd_bwd, steps)
+        h0 = hits[0].cpu().numpy()
+        eye = sc.identity_mask()
+        rot = np.where(h0 >= 0, ~eye[np.maximum(h0, 0)], False)
+        # the winner's routine again, then the gradient: crossing point 3, surface
+        # gradient 8, g.u 5, R g 9 (rotated placements), one division, the per-track
+        # outputs 17, the owner sums 8
+        f64 = fp64_cost_per_track(sc, h0, Q_RATES[0], Q_RATES[1], with_mother=False)
+        f64 = f64 + np.where(h0 == -1, fp64_cost_per_track(sc, np.full_like(h0, -1), Q_RATES[0], Q_RATES[1])
+                             - FP64_BPOINT, 0.0)
+        f64 = f64 + np.where(h0 >= -1, 3 + 8 + 5 + 17 + 8 + Q_RATES[1] + 9 * rot, 0.0)
+        roof = roof_block(float(f64.sum()), 0.0, 108.0 * n, ms_adj * 1e-3, "k_adjoint + k_adjoint_reduce",
+                          "per track: the winning surface's routine again (transform, distance with its face) "
+                          "and the implicit-function gradient, in FP64", PEAK_HBM[0])
         vol.close()
         # algorithmic bytes of the adjoint: p, d, hit, dL/dstep in; dL/dp, dL/dd out
         gbs = 108.0 * n / (ms_adj * 1e-3) / 1e9
         out[name] = {"adjoint": {"value": n / (ms_adj * 1e-3), "unit": "tracks/s", "ms_per_step": ms_adj,
-                                 "algorithmic_gb_s": gbs},
+                                 "algorithmic_gb_s": gbs, "roofline": roof},
                      "forward_plus_adjoint": {"value": n / (ms_fb * 1e-3), "unit": "tracks/s",
                                               "ms_per_step": ms_fb}}
     out["workload"] = ("2^18 tracks; box mother half 100 mm with 4 boxes, and box mother with one rotated box, "
@@ -511,8 +750,8 @@ def shapes_leg(pkg, steps, q_sqrt, q_div):
     and a six-plane bobbin), for baskets of 1024 tracks (launch-bound:
     microseconds per call) and 2^20 tracks (8 rotating copies, 403 MB > L2);
     for box, tube and cone the FP64 work per track from the routines'
-    instruction mix (placement transform included), as a fraction of the
-    FP64 peak."""
+    instruction mix (the identity placement's 3 subtractions included), as a
+    fraction of the FP64 peak."""
     import torch
     from paper_1312_0816_gb300.scenes import Pcon
 
@@ -547,7 +786,7 @@ def shapes_leg(pkg, steps, q_sqrt, q_div):
                 rec = {"value": n / (ms * 1e-3), "unit": "tracks/s", "us_per_call": ms * 1e3}
                 if (key, kind) in FP64_OPS:   # instruction mixes are counted for box, tube, cone
                     a, sq, dv = FP64_OPS[(key, kind)]
-                    ops = FP64_TRANSFORM + a + sq * q_sqrt + dv * q_div
+                    ops = FP64_TRANSFORM_IDENTITY + a + sq * q_sqrt + dv * q_div
                     rec["fp64_dfma_equiv_per_track"] = ops
                     rec["fp64_frac"] = n * ops * 2 / (ms * 1e-3) / 1e12 / PEAK_FP64_TFLOPS
                 row[f"dist_{key}_{n}"] = rec
@@ -595,6 +834,13 @@ def world_leg(pkg, scenes, rank, steps):
                                                        mode=mode, step=step, node_out=no, flag_out=fo), k)
         out[key] = {"value": n / (ms * 1e-3), "unit": "tracks/s", "ms_per_step": ms, "steps": k}
     out["speedup_of_refine"] = out["fp64_plain"]["ms_per_step"] / out["fp32_refine"]["ms_per_step"]
+    # a sample of the answers (state after one transport step) for the accuracy check
+    xs, nd, fl = states[1]
+    pkg.geo_world_step(W, *xs, nd, fl, mode=1, step=step, node_out=no, flag_out=fo)
+    idx = np.sort(np.random.default_rng(41).choice(n, 20000, replace=False))
+    pick = lambda t: t.cpu().numpy()[idx]
+    SAMPLES_WORLD["world"] = (w, scenes.Tracks(*(pick(t) for t in xs)), pick(nd), pick(fl), pick(step), pick(no),
+                              pick(fo))
     W.close()
     for v in vols:
         v.close()
@@ -660,6 +906,10 @@ def main():
         pkg.geo_dist_to_boundary(vol, *c, mode=mode, step=o[0], hit=o[1])
 
     def timed(mode, steps, warmup, clocks=None):
+        """K steps bracketed by a barrier and synchronisation, timed with CUDA
+        events on the launching stream (the mean over the K steps).  With clocks, nvidia-smi
+        samples the timed region and, so that a short region still has its
+        samples, one more second of the same launches right after it."""
         for k in range(warmup):
             step(k, mode)
         torch.cuda.synchronize()
@@ -678,8 +928,28 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1) / steps
-        clk = clocks.stop() if clocks else None
+        clk = None
+        if clocks:
+            t_end, k = time.time() + 1.0, 0
+            while time.time() < t_end:
+                step(k, mode)
+                k += 1
+                if k % 64 == 0:
+                    torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            clk["sampled_over"] = "the timed region and 1 s of the same launches right after it"
         return max_over_ranks(ms), clk
+
+    def median_ms(mode, reps):
+        """Median over `reps` launches, each between its own pair of events."""
+        per = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for k in range(reps):
+            per[k][0].record(stream)
+            step(k, mode)
+            per[k][1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in per)
 
     # correctness guard: both modes agree before anything is timed
     step(0, 1)
@@ -691,6 +961,10 @@ def main():
 
     clocks = Clocks(local)
     ms_ref, clk = timed(1, args.steps, args.warmup, clocks)
+    # the median of at least 30 launches, each between its own events, after
+    # the timed region (events between the timed launches would perturb them)
+    n_med = max(30, min(args.steps, 400))
+    ms_median = median_ms(1, n_med)
     ms_f64, _ = timed(0, max(3, args.steps // 20), 3)
     pkg.geo_check_device_status(vol)
 
@@ -712,6 +986,7 @@ def main():
     hit0 = np.asarray(hit)
     fm, fk = algorithmic_ops(sc, hit0)
     ops64 = fp64_ops_per_track(sc, fm, fk, q_sqrt, q_div)        # DFMA equivalents per track
+    Q_RATES[0], Q_RATES[1] = q_sqrt, q_div
     ops32 = fp32_ops_per_track(sc)                                # FP32 instructions per track
     hbm_bytes = 60.0
     peak_hbm = 6760.9
@@ -719,6 +994,7 @@ def main():
         peak_hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except Exception:
         pass
+    PEAK_HBM[0] = peak_hbm
     t_hbm = n * hbm_bytes / (peak_hbm * 1e9)
     t_f64 = n * ops64 * 2 / (PEAK_FP64_TFLOPS * 1e12)
     t_f32 = n * ops32 * 2 / (PEAK_FP32_TFLOPS * 1e12)
@@ -765,14 +1041,17 @@ def main():
     segments = None if args.no_segments else segments_leg(pkg, scenes, rank, max(10, args.steps // 100))
     sweep = None if args.no_sweep else sweep_leg(pkg, scenes, rank, max(10, args.steps // 100), vol, base)
 
-    cpu = None
+    cpu, acc = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(sc, tr)
+        cpu, acc = cpu_baseline(sc, tr, st_s.cpu().numpy(), hit0)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": ws * n / (ms_ref * 1e-3), "unit": "tracks/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ref, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_ref,
+            "ms_median": {"value": ms_median, "launches": n_med,
+                          "of": "per-launch CUDA events around each of these launches, after the timed region"},
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "tracks_per_gpu": n, "mode": "GEO_FP32_REFINE",
                        "l2": f"{N_COPIES} rotating basket copies ({N_COPIES * n * 60 / 1e6:.0f} MB > L2)",
@@ -782,6 +1061,7 @@ def main():
             "modes_bit_identical": agree,
             "refine": {"fp64_evals_per_track": evals, "fallback_tracks": fallback},
             "roofline": roof,
+            "accuracy": acc,
             "e2e": {"value": ws * n / e2e_s, "unit": "tracks/s", "h2d_bytes_per_step": 48 * n,
                     "d2h_bytes_per_step": 12 * n,
                     "api": "geo_dist_to_boundary_host on pinned host buffers (the step reads the tracks and writes "

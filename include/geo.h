@@ -245,17 +245,20 @@ typedef struct {
 /* tile_order: 0 = largest estimated cost first (tracks x daughters), 1 = in
  * basket order (the packed tiles of ragged tails after the baskets' full
  * tiles, volume by volume).  blocks_per_sm: resident blocks of the persistent launch
- * (0 = as many as fit).  Values other than these give GEO_ERR_INVALID_ARG. */
+ * (0 = as many as fit).  tile_tracks: the tile shape, 0 or GEO_TILE_TRACKS
+ * (384 tracks per tile, 12 producer and 2 consumer warps) or 256 (8 producer
+ * and 4 consumer warps).  Values other than these give GEO_ERR_INVALID_ARG. */
 typedef struct {
     int32_t tile_order;
     int32_t blocks_per_sm;
+    int32_t tile_tracks;
 } geo_batch_opts;
 
 typedef struct geo_batch_s* geo_batch;
 
 /* Builds a batch: copies the baskets, splits them into tiles of
- * GEO_TILE_TRACKS consecutive tracks, gathers the ragged remainders of each
- * volume's baskets into packed tiles of up to GEO_TILE_TRACKS tracks (listing
+ * tile_tracks (default GEO_TILE_TRACKS) consecutive tracks, gathers the ragged
+ * remainders of each volume's baskets into packed tiles of up to that many tracks (listing
  * their indices), orders the
  * tiles, and uploads the per-volume views, the tile list, the packed
  * indices and a tile counter to the device (the batch owns them).  The volumes must

@@ -1,8 +1,10 @@
 """Autotuner of the batched persistent launch.
 
-The launch has two schedule knobs (geo_batch_opts): the order in which tiles
-are claimed (largest estimated cost first, or basket order) and the number of
-resident blocks per SM.  tune_batch() builds one batch per candidate, times
+The launch has three schedule knobs (geo_batch_opts): the order in which tiles
+are claimed (largest estimated cost first, or basket order), the number of
+resident blocks per SM, and the tile shape (tiles of 384 tracks with 12
+producer + 2 consumer warps, or of 256 with 8 + 4: two instantiations of the
+kernel).  tune_batch() builds one batch per candidate, times
 each as a CUDA graph of the one launch (CUDA events, after warm-up), and keeps
 the fastest.  Results are cached in paper_1312_0816_gb300/_build/autotune.json
 keyed by GPU name, a hash of the kernel sources and a size class of the batch
@@ -18,7 +20,8 @@ import os
 
 from . import build_lib, geonav
 
-CANDIDATES = [(0, 2), (0, 1), (1, 2), (1, 1)]   # (tile_order, blocks_per_sm)
+# (tile_order, blocks_per_sm, tile_tracks)
+CANDIDATES = [(o, b, t) for t in (384, 256) for o in (0, 1) for b in (2, 1)]
 CACHE = os.path.join(build_lib.OUT, "autotune.json")
 
 
@@ -78,21 +81,21 @@ def time_graph(batch, x, step, hit, reps: int = 20) -> float:
 
 
 def tune_batch(volumes, baskets, x, step, hit, use_cache: bool = True, reps: int = 20):
-    """Returns (tile_order, blocks_per_sm, timings) for this batch; x = the
-    six device SoA tensors, step/hit preallocated outputs."""
+    """Returns (tile_order, blocks_per_sm, tile_tracks, timings) for this
+    batch; x = the six device SoA tensors, step/hit preallocated outputs."""
     key = _key(volumes, baskets)
     tab = _load() if use_cache else {}
-    if key in tab:
+    if key in tab and "tile_tracks" in tab[key]:
         c = tab[key]
-        return c["tile_order"], c["blocks_per_sm"], c.get("timings_ms", {})
+        return c["tile_order"], c["blocks_per_sm"], c["tile_tracks"], c.get("timings_ms", {})
     timings = {}
-    for order, bps in CANDIDATES:
-        b = geonav.geo_build_batch(volumes, baskets, tile_order=order, blocks_per_sm=bps)
-        timings[f"{order},{bps}"] = time_graph(b, x, step, hit, reps)
+    for order, bps, tile in CANDIDATES:
+        b = geonav.geo_build_batch(volumes, baskets, tile_order=order, blocks_per_sm=bps, tile_tracks=tile)
+        timings[f"{order},{bps},{tile}"] = time_graph(b, x, step, hit, reps)
         b.close()
     best = min(timings, key=timings.get)
-    order, bps = (int(v) for v in best.split(","))
+    order, bps, tile = (int(v) for v in best.split(","))
     tab = _load()
-    tab[key] = {"tile_order": order, "blocks_per_sm": bps, "timings_ms": timings}
+    tab[key] = {"tile_order": order, "blocks_per_sm": bps, "tile_tracks": tile, "timings_ms": timings}
     _save(tab)
-    return order, bps, timings
+    return order, bps, tile, timings

@@ -44,6 +44,7 @@ struct geo_batch_s {
     int device = 0;
     int32_t n_vols = 0;
     int blocks_per_sm = 0;
+    int tile_tracks = kTileTracks;
     int64_t ntiles = 0;
     int64_t max_end = 0;
     int32_t segs = 0;
@@ -877,12 +878,13 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     if (!vols || n_vols <= 0 || n_baskets < 0 || (n_baskets > 0 && !baskets)) return GEO_ERR_INVALID_ARG;
     const int order = opts ? opts->tile_order : 0;
     const int bps = opts ? opts->blocks_per_sm : 0;
-    if ((order != 0 && order != 1) || bps < 0) return GEO_ERR_INVALID_ARG;
+    const int T = (opts && opts->tile_tracks != 0) ? opts->tile_tracks : kTileTracks;
+    if ((order != 0 && order != 1) || bps < 0 || (T != kTileTracks && T != 256)) return GEO_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
     for (int i = 0; i < n_vols; ++i)
         if (!vols[i] || vols[i]->device != dev) return GEO_ERR_INVALID_ARG;
-    // Every basket's full kTileTracks-track stretches become tiles of
+    // Every basket's full T-track stretches become tiles of
     // consecutive tracks; the ragged tails of a volume's baskets are
     // gathered, in basket order, into packed tiles that list their tracks'
     // indices, so that baskets of a few tracks still fill the producer
@@ -896,22 +898,22 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
         if (bk.reserved != 0 || bk.volume < 0 || bk.volume >= n_vols || bk.offset < 0 || bk.count < 0)
             return GEO_ERR_INVALID_ARG;
         max_end = std::max(max_end, bk.offset + bk.count);
-        const int64_t full = bk.count / kTileTracks * kTileTracks;
-        for (int64_t off = 0; off < full; off += kTileTracks) {
+        const int64_t full = bk.count / T * T;
+        for (int64_t off = 0; off < full; off += T) {
             BatchTile t;
             t.vol = bk.volume;
-            t.count = kTileTracks;
+            t.count = T;
             t.base = bk.offset + off;
             tiles.push_back(t);
-            cost.push_back(int64_t(kTileTracks) * (vols[bk.volume]->view.nd + 1));
+            cost.push_back(int64_t(T) * (vols[bk.volume]->view.nd + 1));
         }
         for (int64_t q = bk.offset + full; q < bk.offset + bk.count; ++q) tails[size_t(bk.volume)].push_back(q);
     }
     std::vector<int64_t> idx;
     for (int v = 0; v < n_vols; ++v) {
         const std::vector<int64_t>& tv = tails[size_t(v)];
-        for (size_t a = 0; a < tv.size(); a += kTileTracks) {
-            const size_t m = std::min<size_t>(kTileTracks, tv.size() - a);
+        for (size_t a = 0; a < tv.size(); a += size_t(T)) {
+            const size_t m = std::min<size_t>(size_t(T), tv.size() - a);
             BatchTile t;
             t.vol = v;
             t.count = -int32_t(m);
@@ -936,6 +938,7 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     b->device = dev;
     b->n_vols = n_vols;
     b->blocks_per_sm = bps;
+    b->tile_tracks = T;
     b->ntiles = int64_t(tiles.size());
     b->max_end = max_end;
     for (int i = 0; i < n_vols; ++i) b->segs = b->segs || vols[i]->view.segs;
@@ -999,7 +1002,8 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
     bv.nvols = b->n_vols;
     bv.idx = b->d_idx;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
-    return cuda_status(launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, s, num_sms_of(b->device)));
+    return cuda_status(
+        launch_dist_batched(bv, bk, step, hit, b->blocks_per_sm, b->tile_tracks, s, num_sms_of(b->device)));
 }
 
 geo_status geo_adjoint_workspace_size(geo_volume v, int64_t n, uint64_t* bytes) {

@@ -151,20 +151,10 @@ cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, 
 bool small_basket(const VolView& v, int64_t n, int num_sms);
 cudaError_t launch_dist_warp(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                              cudaStream_t s, int num_sms);
-// small baskets in volumes of 33..64 daughters (no voxels), FP32-filter mode:
-// one warp per track with the daughters' FP32 bounds split over its lanes
-#ifndef GEO_SMALL_FILTER_TRACKS_PER_SM
-#define GEO_SMALL_FILTER_TRACKS_PER_SM 8
-#endif
-constexpr int kSmallFilterTracksPerSm = GEO_SMALL_FILTER_TRACKS_PER_SM;
-bool small_basket_filter(const VolView& v, int64_t n, int num_sms);
-cudaError_t launch_dist_warp_filter(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
-                                    cudaStream_t s, int num_sms);
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit,
-                                int blocks_per_sm, cudaStream_t s, int num_sms);
-int batched_max_blocks_per_sm(bool segs);
+                                int blocks_per_sm, int tile_tracks, cudaStream_t s, int num_sms);
 cudaError_t launch_contains(const VolView& v, const Basket& b, int32_t* where, int mode, cudaStream_t s,
                             int num_sms);
 cudaError_t launch_safety(const VolView& v, const Basket& b, double* saf, int mode, cudaStream_t s,

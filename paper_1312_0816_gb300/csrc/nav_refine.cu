@@ -45,31 +45,32 @@ struct __align__(16) TileHdr {
 };
 
 // SEGS = false: no volume of the batch holds a tube segment or a polycone.
-template <bool SEGS>
-__global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
+// P producer threads (one track each of a tile of P) and C consumer threads.
+template <bool SEGS, int P, int C>
+__global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
                                                               int32_t* __restrict__ hit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t full[2], done[2];
-    Stage<kProd>* S = reinterpret_cast<Stage<kProd>*>(smem_raw);
-    TileHdr* H = reinterpret_cast<TileHdr*>(smem_raw + 2 * sizeof(Stage<kProd>));
+    Stage<P>* S = reinterpret_cast<Stage<P>*>(smem_raw);
+    TileHdr* H = reinterpret_cast<TileHdr*>(smem_raw + 2 * sizeof(Stage<P>));
     const int t = threadIdx.x;
     const int lane = t & 31;
     bool healthy = true;
     if (t == 0) {
-        mbar_init(&full[0], kProd / 32);
-        mbar_init(&full[1], kProd / 32);
-        mbar_init(&done[0], kCons / 32);
-        mbar_init(&done[1], kCons / 32);
+        mbar_init(&full[0], P / 32);
+        mbar_init(&full[1], P / 32);
+        mbar_init(&done[0], C / 32);
+        mbar_init(&done[1], C / 32);
     }
     __syncthreads();
     constexpr int kWords = int(sizeof(VolView) / sizeof(int4));
 
-    if (t < kProd) {
+    if (t < P) {
         // ------------------------------------------------------ producers --
         int64_t prev_i = 0;      // this thread's track in the previous tile
         bool prev_live = false;
         for (int k = 0;; ++k) {
-            Stage<kProd>& st_ = S[k & 1];
+            Stage<P>& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
             if (t == 0) {
                 const unsigned q = atomicAdd(bv.counter, 1u);
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 }
                 st_.cnt[0] = st_.cnt[1] = st_.cnt[2] = st_.cnt[3] = 0;
             }
-            producer_barrier<kProd>();
+            producer_barrier<P>();
             const int tile = hd.tile;
             int64_t cur_i = 0;
             bool cur_live = false;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                 const int64_t base = hd.base;
                 const bool packed = hd.count < 0;
                 const int count = packed ? -hd.count : hd.count;
-                producer_barrier<kProd>();
+                producer_barrier<P>();
                 const VolView& v = hd.vol;
                 bool live = t < count;
                 int64_t i = live ? (packed ? bv.idx[base + t] : base + t) : 0;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
                     bin = task < 0 ? 0 : kind_bin(v.d64[task].kind);
                 }
                 const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
-                producer_barrier<kProd>();
+                producer_barrier<P>();
                 int start = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
             if (lane == 0) mbar_arrive(&full[k & 1]);
             if (k >= 1) {
                 const int kp = k - 1;
-                Stage<kProd>& sp = S[kp & 1];
+                Stage<P>& sp = S[kp & 1];
                 const VolView& vp = H[kp & 1].vol;
                 mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), bv.status, healthy);
                 if (prev_live && sp.n[t] >= 0) {
@@ -176,15 +177,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_dist_batched(BatchView bv, Bask
         }
     } else {
         // ------------------------------------------------------ consumers --
-        const int c = t - kProd;
+        const int c = t - P;
         for (int k = 0;; ++k) {
-            Stage<kProd>& st_ = S[k & 1];
+            Stage<P>& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), bv.status, healthy);
             if (!healthy || hd.tile < 0) break;
             const VolView& v = hd.vol;
             const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
-            for (int q = c; q < total; q += kCons) {
+            for (int q = c; q < total; q += C) {
                 const int e = st_.task[q];
                 const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
                 st_.res[o] = eval64<SEGS>(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
@@ -218,15 +219,15 @@ cudaError_t launch_wait_selftest(unsigned int* status, uint32_t polls, cudaStrea
     return cudaGetLastError();
 }
 
-template <bool SEGS>
+template <bool SEGS, int P, int C>
 static int batched_blocks_per_sm() {
     static int cached = 0;
     if (cached == 0) {
-        const int smem = 2 * int(sizeof(Stage<kProd>) + sizeof(TileHdr));
+        const int smem = 2 * int(sizeof(Stage<P>) + sizeof(TileHdr));
         int per_sm = 0;
-        if (cudaFuncSetAttribute(k_dist_batched<SEGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        if (cudaFuncSetAttribute(k_dist_batched<SEGS, P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched<SEGS>, kThreads, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched<SEGS, P, C>, P + C, smem) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -237,27 +238,29 @@ static int batched_blocks_per_sm() {
     return cached;
 }
 
-int batched_max_blocks_per_sm(bool segs) {
-    return segs ? batched_blocks_per_sm<true>() : batched_blocks_per_sm<false>();
-}
-
-template <bool SEGS>
+template <bool SEGS, int P, int C>
 static cudaError_t launch_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
                                   cudaStream_t s, int num_sms) {
-    const int smem = 2 * int(sizeof(Stage<kProd>) + sizeof(TileHdr));
-    const int maxb = batched_blocks_per_sm<SEGS>();
+    const int smem = 2 * int(sizeof(Stage<P>) + sizeof(TileHdr));
+    const int maxb = batched_blocks_per_sm<SEGS, P, C>();
     const int per_sm = (blocks_per_sm <= 0 || blocks_per_sm > maxb) ? maxb : blocks_per_sm;
-    cudaError_t e = cudaFuncSetAttribute(k_dist_batched<SEGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dist_batched<SEGS, P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_dist_batched<SEGS><<<per_sm * num_sms, kThreads, smem, s>>>(bv, b, step, hit);
+    k_dist_batched<SEGS, P, C><<<per_sm * num_sms, P + C, smem, s>>>(bv, b, step, hit);
     return cudaGetLastError();
 }
 
+// Two tile shapes, the autotuner's choice per batch: tiles of kTileTracks =
+// 384 tracks with 12 producer + 2 consumer warps, or tiles of 256 with 8 + 4.
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
-                                cudaStream_t s, int num_sms) {
+                                int tile_tracks, cudaStream_t s, int num_sms) {
     static_assert(sizeof(TileHdr) % 16 == 0 && sizeof(VolView) % 16 == 0, "16-byte copies");
-    return bv.segs ? launch_batched<true>(bv, b, step, hit, blocks_per_sm, s, num_sms)
-                   : launch_batched<false>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+    if (tile_tracks == kLatProd)
+        return bv.segs ? launch_batched<true, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms)
+                       : launch_batched<false, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+    return bv.segs ? launch_batched<true, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms)
+                   : launch_batched<false, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
 }
 
 // A basket of at most two tiles of 256 tracks per resident block (two blocks
@@ -278,7 +281,6 @@ cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* 
 cudaError_t launch_dist_refine(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                                cudaStream_t s, int num_sms) {
     if (small_basket(v, b.n, num_sms)) return launch_dist_warp(v, b, step, hit, bpoint, s, num_sms);
-    if (small_basket_filter(v, b.n, num_sms)) return launch_dist_warp_filter(v, b, step, hit, bpoint, s, num_sms);
     return launch_dist_refine_stats(v, b, step, hit, bpoint, nullptr, s, num_sms);
 }
 

@@ -140,6 +140,6 @@ extern "C" geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vol
     bv.idx = nullptr;   // plain tiles only
     for (int i = 0; i < n_vols; ++i) bv.segs = bv.segs || volume_view(vols[i])->segs;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
-    e = launch_dist_batched(bv, bk, step, hit, 0, s, sm_count(dev));
+    e = launch_dist_batched(bv, bk, step, hit, 0, kTileTracks, s, sm_count(dev));
     return e == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
 }

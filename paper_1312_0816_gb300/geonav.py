@@ -48,7 +48,7 @@ class geo_basket(ctypes.Structure):
 
 
 class geo_batch_opts(ctypes.Structure):
-    _fields_ = [("tile_order", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+    _fields_ = [("tile_order", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile_tracks", ctypes.c_int32)]
 
 
 _lib = None
@@ -505,8 +505,10 @@ class Batch:
             pass
 
 
-def geo_build_batch(volumes, baskets, tile_order: int = 0, blocks_per_sm: int = 0, stream=None) -> Batch:
-    """volumes: list of Volume; baskets: (volume index, offset, count) rows."""
+def geo_build_batch(volumes, baskets, tile_order: int = 0, blocks_per_sm: int = 0, tile_tracks: int = 0,
+                    stream=None) -> Batch:
+    """volumes: list of Volume; baskets: (volume index, offset, count) rows;
+    tile_tracks: 0 / GEO_TILE_TRACKS (384) or 256 (see geo.h)."""
     L = load()
     nv = len(volumes)
     handles = (ctypes.c_void_p * max(nv, 1))(*[v.handle for v in volumes])
@@ -515,7 +517,7 @@ def geo_build_batch(volumes, baskets, tile_order: int = 0, blocks_per_sm: int = 
     for k, (v, off, cnt) in enumerate(rows):
         arr[k].volume, arr[k].reserved, arr[k].offset, arr[k].count = int(v), 0, int(off), int(cnt)
     opts = geo_batch_opts()
-    opts.tile_order, opts.blocks_per_sm = int(tile_order), int(blocks_per_sm)
+    opts.tile_order, opts.blocks_per_sm, opts.tile_tracks = int(tile_order), int(blocks_per_sm), int(tile_tracks)
     out = ctypes.c_void_p()
     _check(L.geo_build_batch(handles, nv, arr, len(rows), ctypes.byref(opts), _stream(stream), ctypes.byref(out)),
            "geo_build_batch")

@@ -43,11 +43,13 @@ def per_basket(g, vols, volh, tr, rows, mode):
     return step, hit
 
 
-@pytest.mark.parametrize("order,bps", [(0, 0), (1, 0), (0, 1)])
-def test_batched_equals_per_basket(g, small_batch, order, bps):
+@pytest.mark.parametrize("order,bps,tile", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 256), (1, 1, 256)])
+def test_batched_equals_per_basket(g, small_batch, order, bps, tile):
+    """Every schedule and both tile shapes (384 tracks, 12 + 2 warps; 256, 8 +
+    4) give the per-basket plain FP64 bits."""
     vols, tr, rows = small_batch
     volh = [g.geo_build_volume(v) for v in vols]
-    batch = g.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps)
+    batch = g.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps, tile_tracks=tile)
     s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
     torch.cuda.synchronize()
     s, h = s.cpu().numpy(), h.cpu().numpy()
@@ -134,13 +136,13 @@ def test_autotuner_picks_a_candidate_and_caches(g, small_batch, tmp_path, monkey
     x = dev(tr)
     step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
     hit = torch.empty(tr.n, dtype=torch.int32, device="cuda")
-    order, bps, timings = autotune.tune_batch(volh, rows, x, step, hit, reps=3)
-    assert (order, bps) in autotune.CANDIDATES
+    order, bps, tile, timings = autotune.tune_batch(volh, rows, x, step, hit, reps=3)
+    assert (order, bps, tile) in autotune.CANDIDATES
     assert len(timings) == len(autotune.CANDIDATES) and all(t > 0 for t in timings.values())
     again = autotune.tune_batch(volh, rows, x, step, hit, reps=3)
-    assert again[:2] == (order, bps)
+    assert again[:3] == (order, bps, tile)
     # the tuned schedule gives the same answers
-    batch = g.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps)
+    batch = g.geo_build_batch(volh, rows, tile_order=order, blocks_per_sm=bps, tile_tracks=tile)
     s, h = g.geo_dist_to_boundary_batched(batch, *x)
     ref = g.geo_build_batch(volh, rows)
     s0, h0 = g.geo_dist_to_boundary_batched(ref, *x)
@@ -157,8 +159,8 @@ def test_batched_segments_and_polycones(g):
     baskets = [(int(rng.integers(0, 4)), int(rng.integers(1, 700))) for _ in range(60)]
     tr, rows = scenes.batched_tracks(vols, baskets, 12)
     volh = [g.geo_build_volume(v) for v in vols]
-    for order in (0, 1):
-        batch = g.geo_build_batch(volh, rows, tile_order=order)
+    for order, tile in ((0, 0), (1, 0), (0, 256)):
+        batch = g.geo_build_batch(volh, rows, tile_order=order, tile_tracks=tile)
         s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
         torch.cuda.synchronize()
         s, h = s.cpu().numpy(), h.cpu().numpy()

@@ -352,38 +352,3 @@ def test_full_size_toy_detector_sampled(g, orc):
     sub = scenes.Tracks(*(f[idx] for f in tr.fields()))
     ref = orc.navigate(sc, sub, nthreads=8)
     compare(ref, step[idx], hit[idx], sub, sc, orc, max_graze=1e-4)
-
-
-def _many_daughter_scenes():
-    """The toy detector (40 daughters) and the batched workload's volumes of
-    33..64 mixed, rotated daughters under box and tube mothers."""
-    out = [scene("toy40")]
-    vols, _ = scenes.batched64(seed=3)
-    out += [v for v in vols if 32 < v.n_daughters <= 64][:3]
-    return out
-
-
-@pytest.mark.parametrize("which", range(4))
-def test_small_basket_filter_path(g, which):
-    """Baskets of a few tracks per SM in volumes of 33..64 daughters take, in
-    FP32-filter mode, the warp-per-track filter kernel (the lanes split the
-    daughters' FP32 bounds, then refine in FP64 round by round): the same bits
-    as the plain FP64 mode and as the large-basket kernel give the same tracks,
-    random and adversarial, at 1, 16, 1000 tracks and at the switch."""
-    vols = _many_daughter_scenes()
-    if which >= len(vols):
-        pytest.skip("fewer volumes of 33..64 daughters")
-    sc = vols[which]
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    tr = scenes.sample_tracks(sc, 40000, 41)
-    adv = scenes.adversarial_tracks(sc, 3000, 42)
-    joined = scenes.Tracks(*(np.concatenate([a, b]) for a, b in zip(adv.fields(), tr.fields())))
-    s_big, h_big, b_big = run_nav(g, sc, joined, 1, bpoint=True)
-    for n_small in (1, 16, 1000, 8 * sms, 8 * sms + 1):
-        for start in (0, 3000):   # adversarial rays first, then random ones
-            small = scenes.Tracks(*(f[start:start + n_small].copy() for f in joined.fields()))
-            for mode in (0, 1):
-                s_sm, h_sm, b_sm = run_nav(g, sc, small, mode, bpoint=True)
-                assert np.array_equal(s_sm.view(np.int64), s_big[start:start + n_small].view(np.int64)), (n_small, mode)
-                assert np.array_equal(h_sm, h_big[start:start + n_small]), (n_small, mode)
-                assert np.array_equal(b_sm.view(np.int64), b_big[:, start:start + n_small].view(np.int64))
