@@ -416,7 +416,7 @@ def batched_leg(pkg, scenes, rank, steps):
                         % (len(rows), tr.n),
             "value": tr.n / (ms * 1e-3), "unit": "tracks/s", "ms_per_launch": ms, "steps": steps,
             "schedule": {"tile_order": order, "blocks_per_sm": bps, "tile_tracks": tile,
-                         "warps": "12 producer + 2 consumer" if tile == 384 else "8 producer + 4 consumer"},
+                         "warps": "12 producer + 4 consumer" if tile == 384 else "8 producer + 4 consumer"},
             "autotune_ms": timings, "roofline": roof}
 
 
@@ -468,14 +468,15 @@ def voxel_counts(sc, grid, tr, step):
     return cand, steps
 
 
-def voxel_leg(pkg, scenes, rank, steps):
+def voxel_leg(pkg, scenes, rank, steps, n=1 << 24):
     """512 daughters (boxes and tubes, rotated, on an 8x8x8 grid) in a box
-    mother with the uniform-grid candidate list; 2^24 tracks; FP32+refine vs
-    plain FP64, both walking the grid."""
+    mother with the uniform-grid candidate list; n = 2^24 tracks (fewer only
+    for a profiler capture); FP32+refine vs plain FP64, both walking the
+    grid."""
     import torch
 
     sc = scenes.grid512(5)
-    tr = scenes.sample_tracks(sc, 1 << 24, 5 + 1000 * rank)
+    tr = scenes.sample_tracks(sc, n, 5 + 1000 * rank)
     vol = pkg.geo_build_volume(sc, voxelize=True)
     x = [torch.from_numpy(f).cuda() for f in tr.fields()]
     step = torch.empty(tr.n, dtype=torch.float64, device="cuda")
@@ -515,7 +516,7 @@ def voxel_leg(pkg, scenes, rank, steps):
     info = pkg.geo_volume_info(vol)
     vol.close()
     out["workload"] = ("box mother half 800 mm, 512 rotated boxes/tubes on an 8x8x8 grid, uniform grid %s, "
-                       "2^24 tracks (inputs 805 MB > L2)" % "x".join(str(g) for g in info["grid"]))
+                       "%d tracks (inputs %d MB > L2)" % ("x".join(str(g) for g in info["grid"]), n, n * 48 // 10**6))
     out["speedup_of_refine"] = out["fp64_plain"]["ms_per_step"] / out["fp32_refine"]["ms_per_step"]
     return out
 
@@ -857,6 +858,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-voxel", action="store_true")
+    ap.add_argument("--voxel-n", type=int, default=1 << 24, help="tracks of the voxel leg (a smaller case for ncu)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-queries", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
@@ -986,6 +988,10 @@ def main():
     hit0 = np.asarray(hit)
     fm, fk = algorithmic_ops(sc, hit0)
     ops64 = fp64_ops_per_track(sc, fm, fk, q_sqrt, q_div)        # DFMA equivalents per track
+    # the kernel evaluates the mother in FP64 only where its bound does not
+    # lose to the winning daughter's: the work it must do is the winner's alone
+    a_m, s_m, d_m = FP64_OPS[("in", sc.mother_kind)]
+    ops64_winner = ops64 - (1.0 - fm) * (a_m + s_m * q_sqrt + d_m * q_div)
     Q_RATES[0], Q_RATES[1] = q_sqrt, q_div
     ops32 = fp32_ops_per_track(sc)                                # FP32 instructions per track
     hbm_bytes = 60.0
@@ -1009,6 +1015,12 @@ def main():
                            "the probe measured %.3f TFLOP/s" % (2 * r_f64 / 1e12),
             "kernel": "k_dist_refine (one launch per step)", "kernel_sources_sha": sources_sha(),
             "algorithmic_per_track": {"hbm_bytes": hbm_bytes, "fp64_dfma_equiv": ops64, "fp32_instr": ops32},
+            "fp64_count": "the mother's exit on every track, the winning daughter's transform and "
+                          "DistFromOutside, the boundary point",
+            "winner_only": {"fp64_dfma_equiv": ops64_winner,
+                            "frac": n * ops64_winner * 2 / launch_s / 1e12 / PEAK_FP64_TFLOPS,
+                            "note": "the FP64 work the filter leaves: the winner's evaluation alone "
+                                    "(the mother's only where it wins) and the boundary point"},
             "t_roof_us": {"hbm": t_hbm * 1e6, "fp64": t_f64 * 1e6, "fp32": t_f32 * 1e6},
             "measured_rates": {"fp32_fma_tflops": 2 * r_f32 / 1e12, "fp64_fma_tflops": 2 * r_f64 / 1e12,
                                "fp64_div_per_s": r_div, "fp64_sqrt_per_s": r_sqrt,
@@ -1033,7 +1045,7 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / k_e2e)
 
     batched = None if args.no_batched else batched_leg(pkg, scenes, rank, max(10, args.steps // 40))
-    voxel = None if args.no_voxel else voxel_leg(pkg, scenes, rank, max(5, args.steps // 200))
+    voxel = None if args.no_voxel else voxel_leg(pkg, scenes, rank, max(5, args.steps // 200), args.voxel_n)
     adjoint = None if args.no_adjoint else adjoint_leg(pkg, scenes, rank, max(10, args.steps // 40))
     queries = None if args.no_queries else queries_leg(pkg, scenes, rank, max(10, args.steps // 100), sc)
     shapes = None if args.no_shapes else shapes_leg(pkg, max(10, args.steps // 100), q_sqrt, q_div)

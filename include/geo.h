@@ -246,7 +246,7 @@ typedef struct {
  * basket order (the packed tiles of ragged tails after the baskets' full
  * tiles, volume by volume).  blocks_per_sm: resident blocks of the persistent launch
  * (0 = as many as fit).  tile_tracks: the tile shape, 0 or GEO_TILE_TRACKS
- * (384 tracks per tile, 12 producer and 2 consumer warps) or 256 (8 producer
+ * (384 tracks per tile, 12 producer and 4 consumer warps) or 256 (8 producer
  * and 4 consumer warps).  Values other than these give GEO_ERR_INVALID_ARG. */
 typedef struct {
     int32_t tile_order;
@@ -418,7 +418,8 @@ geo_status geo_check_device_status(geo_volume v, uint32_t* word, void* stream);
  * The paper has no counterpart; these exercise the library's failure paths.
  *
  * geo_selftest_wait_timeout: launches one warp that waits, with `polls`
- * (1 .. 2^20) polls, on a shared-memory barrier that no thread arrives at --
+ * (1 .. 2^20) polls of the pipeline's bounded wait, on a shared-memory
+ * barrier that no thread arrives at --
  * the failure path of every bounded wait of the pipeline kernels -- and
  * records bit 4 in the volume's status word; the kernel then returns, so the
  * context stays usable.  Asynchronous on `stream`; read the word with

@@ -3,7 +3,7 @@
 The launch has three schedule knobs (geo_batch_opts): the order in which tiles
 are claimed (largest estimated cost first, or basket order), the number of
 resident blocks per SM, and the tile shape (tiles of 384 tracks with 12
-producer + 2 consumer warps, or of 256 with 8 + 4: two instantiations of the
+producer + 4 consumer warps, or of 256 with 8 + 4: two instantiations of the
 kernel).  tune_batch() builds one batch per candidate, times
 each as a CUDA graph of the one launch (CUDA events, after warm-up), and keeps
 the fastest.  Results are cached in paper_1312_0816_gb300/_build/autotune.json

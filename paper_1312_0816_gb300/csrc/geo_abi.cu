@@ -283,6 +283,16 @@ ShapeRec64 make_rec64(const geo_placed_shape& s, const double* table = nullptr) 
 // FP32 record of a solid grown (grow > 0) or shrunk (grow < 0) by |grow| mm.
 // Returns false when a shrunk solid degenerates.  A polycone is bounded by its
 // tube (centered: about its origin, for a mother).
+// The float nearest x from above / below.
+float float_up(double x) {
+    const float f = float(x);
+    return double(f) < x ? std::nextafter(f, HUGE_VALF) : f;
+}
+float float_down(double x) {
+    const float f = float(x);
+    return double(f) > x ? std::nextafter(f, -HUGE_VALF) : f;
+}
+
 bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32& r, bool centered = false) {
     if (s.kind == GEO_PCON && grow >= 0) return make_rec32(bounding_tube(s, centered), grow, delta, r);
     geo_placed_shape in;
@@ -319,6 +329,11 @@ bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32
         r.e[1] = float(rmax * rmax);
         r.e[2] = float(dz);
         r.e[3] = hole ? 1.f : 0.f;
+        // acceptance limits of the filter's crossings, lenient by delta
+        const double ro = rmax + delta, ri = rmin - delta;
+        r.e[4] = float_up(ro * ro);
+        r.e[5] = hole && ri > 0 ? float_down(ri * ri) : 0.f;
+        r.e[6] = float_up(dz + delta);
     } else {
         const double dz = p[0], dzg = dz + g;
         if (!(dzg > 0)) return false;
@@ -342,8 +357,16 @@ bool make_rec32(const geo_placed_shape& s, double grow, double delta, ShapeRec32
         r.e[7] = float(olo * olo);
         r.e[8] = hole ? float(i_hi * i_hi) : 0.f;
         r.e[9] = float(ohi * ohi);
+        // acceptance limits of the filter's end-plane crossings, lenient by delta
+        r.e[10] = float_up((olo + delta) * (olo + delta));
+        r.e[11] = float_up((ohi + delta) * (ohi + delta));
+        const double ilo = hole ? i_lo - delta : 0.0, ihi = hole ? i_hi - delta : 0.0;
+        r.e[12] = ilo > 0 ? float_down(ilo * ilo) : 0.f;
+        r.e[13] = ihi > 0 ? float_down(ihi * ihi) : 0.f;
+        r.e[14] = float_up(dzg + delta);
     }
     r.brad = float(bounding_radius(s) * (1.0 + 1e-6) + std::max(g, 0.0));
+    r.brad2 = float_up(double(r.brad) * double(r.brad));
     return true;
 }
 

@@ -61,17 +61,20 @@ static_assert(sizeof(ShapeRec64) == 256, "ShapeRec64 layout");
 //  transform and of the shape arithmetic is covered (see nav_refine.cu):
 //   box : e[0..2] = h + delta
 //   tube: e[0] rmin_in^2 (shrunk hole, 0 if none), e[1] rmax_out^2, e[2] dz + delta,
-//         e[3] has_hole (0/1)
+//         e[3] has_hole (0/1), e[4..6] acceptance limits (shapes32.cuh)
 //   cone: e[0] dz + delta, e[1] a_out', e[2] b_out, e[3] a_in', e[4] b_in,
-//         e[5] has_hole, e[6..9] inflated end radii squared (rmin1,rmax1,rmin2,rmax2)
-//  brad: inflated bounding radius.
+//         e[5] has_hole, e[6..9] inflated end radii squared (rmin1,rmax1,rmin2,rmax2),
+//         e[10..14] acceptance limits (shapes32.cuh)
+//  brad: inflated bounding radius; brad2 = brad^2 rounded up, beside t so
+//  that the bounding-sphere test reads both with one 16-byte load.
 //  flags: kRec32Identity when the rotation is exactly the identity (the
 //  filter then skips the rotation: x = R^T w is w itself).
 constexpr int32_t kRec32Identity = 1;
 struct __align__(16) ShapeRec32 {
-    float R[9];
     float t[3];
-    float e[16];
+    float brad2;
+    float R[9];
+    float e[15];
     float brad;
     float delta;
     int32_t kind;

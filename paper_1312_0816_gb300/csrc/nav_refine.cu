@@ -126,11 +126,8 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
                 }
                 const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
                 producer_barrier<P>();
-                int start = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < bin) start += st_.cnt[q];
-                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << kOwnerBits);
+                if (bin >= 0) st_.task[bin_start(st_.cnt, bin) + slot] = t | ((task + 1) << kOwnerBits);
+                pad_bins<P>(st_, t);
                 if (rs.status == 0) {
 #pragma unroll
                     for (int q = 0; q < kCand; ++q) {
@@ -184,9 +181,10 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), bv.status, healthy);
             if (!healthy || hd.tile < 0) break;
             const VolView& v = hd.vol;
-            const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
+            const int total = bin_start(st_.cnt, 4);
             for (int q = c; q < total; q += C) {
                 const int e = st_.task[q];
+                if (e < 0) continue;
                 const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
                 st_.res[o] = eval64<SEGS>(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
                                     st_.pd[4][o], st_.pd[5][o]);
@@ -201,16 +199,16 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
         for (int q = 0; q < bv.nvols; ++q) atomicOr(bv.vols[q].status, ST_SYNC_TIMEOUT);
 }
 
-// A bounded wait that runs out: one warp waits, with `polls` polls, on an
-// mbarrier that no thread arrives at, then records ST_SYNC_TIMEOUT in the
-// status word and returns (the failure path of every wait of the pipeline,
-// exercised on purpose by the tests).
+// A bounded wait that runs out: one warp waits, with `polls` polls of the
+// pipeline's own wait (mbar_wait_limited), on an mbarrier that no thread
+// arrives at, then records ST_SYNC_TIMEOUT in the status word and returns
+// (the failure path of every wait of the pipeline, exercised on purpose by
+// the tests).
 __global__ void k_wait_selftest(unsigned int* status, uint32_t polls) {
     __shared__ uint64_t bar;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    for (uint32_t it = 0; it < polls; ++it)
-        if (mbar_try_wait(&bar, 0)) return;
+    if (mbar_wait_limited(&bar, 0, polls)) return;
     if (threadIdx.x == 0) atomicOr(status, ST_SYNC_TIMEOUT);
 }
 
@@ -252,7 +250,7 @@ static cudaError_t launch_batched(const BatchView& bv, const Basket& b, double* 
 }
 
 // Two tile shapes, the autotuner's choice per batch: tiles of kTileTracks =
-// 384 tracks with 12 producer + 2 consumer warps, or tiles of 256 with 8 + 4.
+// 384 tracks with 12 producer + 4 consumer warps, or tiles of 256 with 8 + 4.
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
                                 int tile_tracks, cudaStream_t s, int num_sms) {
     static_assert(sizeof(TileHdr) % 16 == 0 && sizeof(VolView) % 16 == 0, "16-byte copies");

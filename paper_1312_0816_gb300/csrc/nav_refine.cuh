@@ -57,11 +57,12 @@ __device__ __forceinline__ float lower_bound(float t, float delta, float inv_dn)
 // inserted into the candidate list when it can beat the mother's exit.
 __device__ __forceinline__ void bound_daughter(const ShapeRec32& r, int j, const float* p32, const float* d32,
                                                float inv_dd, float inv_dn, float Um, Cands& c) {
-    const float w0 = p32[0] - r.t[0], w1 = p32[1] - r.t[1], w2 = p32[2] - r.t[2];
+    const float4 tb = *reinterpret_cast<const float4*>(r.t);   // t and brad^2
+    const float w0 = p32[0] - tb.x, w1 = p32[1] - tb.y, w2 = p32[2] - tb.z;
     const float s0 = -fmaf(w0, d32[0], fmaf(w1, d32[1], w2 * d32[2])) * inv_dd;
     const float q0 = fmaf(s0, d32[0], w0), q1 = fmaf(s0, d32[1], w1), q2 = fmaf(s0, d32[2], w2);
     const float perp2 = fmaf(q0, q0, fmaf(q1, q1, q2 * q2));
-    if (perp2 > r.brad * r.brad) return;
+    if (perp2 > tb.w) return;
     const float half = r.brad * inv_dn;
     if (s0 + half < 0.f || s0 - half > Um) return;
     float x[3], u[3];

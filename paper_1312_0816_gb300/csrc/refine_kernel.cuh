@@ -13,35 +13,39 @@
 namespace geonav {
 
 // Warp-specialised persistent kernel.  A block holds 12 producer warps (one
-// track per thread per tile of kTileTracks = 384) and 2 consumer warps; with
-// two blocks per SM that is one consumer warp per SM sub-partition (the FP64
-// units are per sub-partition, and the microbenchmark shows one warp with a
-// dependent FP64 chain keeps one busy).  The FP32 pass sets the pace, and its
-// latency is hidden by warps: on the toy detector 12 + 2 warps at a cap of 72
-// registers take 0.31 ms where 8 + 4 warps at 80 registers took 0.35 ms (one
-// consumer warp per block: 0.45 ms; at 64 registers: 0.33-0.37 ms).
+// track per thread per tile of kTileTracks = 384) and 4 consumer warps; with
+// two blocks per SM (64 registers per thread) that is two consumer warps per
+// SM sub-partition.  The FP64 unit is per sub-partition and issues one warp
+// instruction every 64 cycles; a dependent FP64 chain takes about 76 cycles
+// per step, and the square roots, divisions and comparisons between them
+// leave gaps, so one warp cannot keep its unit busy and two do better.
+// Measured on the toy detector (2^20 tracks): 12 + 4 warps 0.242 ms, 12 + 2
+// warps at 72 registers 0.257 ms, 11 + 3 0.248, 10 + 4 0.254, 9 + 3 at 80
+// registers 0.264, 8 + 4 0.265; the producers alone (FP64 evaluations
+// skipped) take 0.207 ms and the consumers alone (each track's winner given)
+// 0.160 ms, so the FP32 pass sets the pace.
 //  producers: FP32 pass of tile k, then bin each track's first FP64 task by
 //             solid kind (mother, box, tube, cone) into stage k%2, arrive on
 //             full[k%2]; then wait done[(k-1)%2] and finish tile k-1 (rare
 //             extra refinements, stores).
 //  consumers: wait full[k%2], evaluate the binned tasks of tile k in FP64 (a
-//             warp takes 32 consecutive tasks, so nearly always one kind),
-//             arrive on done[k%2].
+//             warp takes 32 consecutive tasks, all of one kind: the bins
+//             start on multiples of 32), arrive on done[k%2].
 // The FP64 pipe therefore works on tile k while the FP32 pass of tile k+1 runs.
 // Every wait is bounded; a wait that runs out records ST_SYNC_TIMEOUT.
-// Two block configurations (P producer threads, one track each per tile, and
+// Block configurations (P producer threads, one track each per tile, and
 // C consumer threads):
-//  * 12 + 2 warps, tiles of kTileTracks = 384: throughput (many tiles per
-//    block; the batched launch);
+//  * 12 + 4 warps, tiles of kTileTracks = 384: throughput (many tiles per
+//    block) and the batched launch (there 12 + 2 warps at 72 registers take
+//    as long);
 //  * 8 + 4 warps, tiles of 256: baskets of at most two tiles per block,
-//    where the latency of a tile's FP64 phase with 2 consumer warps would
-//    set the time (1024 tracks: 32 us per call instead of 46 us).
-constexpr int kProd = kTileTracks;   // the batched launch
-constexpr int kCons = 64;
-constexpr int kThreads = kProd + kCons;
-constexpr int kLatProd = 256, kLatCons = 128;
+//    where the latency of one tile sets the time.
+constexpr int kProd = kTileTracks, kCons = 128;   // throughput and batched: 12 + 4 warps
+constexpr int kVoxCons = 64;                       // throughput with the uniform grid: 12 + 2 warps
+constexpr int kLatProd = 256, kLatCons = 128;      // latency: 8 + 4 warps
 constexpr int kOwnerBits = 9;   // binned task: owner | (solid + 1) << kOwnerBits
-static_assert(kProd <= (1 << kOwnerBits) && kProd % 32 == 0 && kLatProd % 32 == 0, "task encoding");
+static_assert(kProd <= (1 << kOwnerBits) && kProd % 32 == 0 && kLatProd % 32 == 0 && kLatProd >= 128,
+              "task encoding, bin padding");
 
 template <int P>
 struct Stage {
@@ -52,22 +56,51 @@ struct Stage {
     float Lm[P];
     float dropped[P];
     int n[P];               // candidate count, -1: answer already final
-    int task[P];            // binned tasks: owner | (solid + 1) << kOwnerBits
+    int task[P + 128];      // binned tasks: owner | (solid + 1) << kOwnerBits; -1 pads
     int cnt[4];
 };
+
+// Each bin of a stage's task list starts on a multiple of 32, so that the 32
+// consecutive tasks a consumer warp takes are of one kind (a warp pays for
+// every code path its lanes take); the slots between bins hold -1.
+__device__ __forceinline__ int bin_start(const int* cnt, int bin) {
+    int start = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (q < bin) start += (cnt[q] + 31) & ~31;
+    return start;
+}
+
+// After the counts are final: thread t < 128 pads bin t / 32 (P >= 128).
+template <int P>
+__device__ __forceinline__ void pad_bins(Stage<P>& st, int t) {
+    if (t < 128) {
+        const int b = t >> 5, c = st.cnt[b];
+        if ((t & 31) < ((c + 31) & ~31) - c) st.task[bin_start(st.cnt, b) + c + (t & 31)] = -1;
+    }
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait; after one timeout the caller stops waiting altogether (its
-// results are then unreliable and the status word says so).
+// Bounded wait: at most `polls` polls.  Returns whether the phase completed.
+// (Polls that let the hardware suspend the waiting warp were measured slower
+// here: the producers' and consumers' hand-offs are frequent, and a
+// suspended warp resumes late.)
 constexpr uint32_t kSyncPolls = 1u << 20;
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, uint32_t parity, uint32_t polls) {
+    for (uint32_t it = 0; it < polls; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// The pipeline's wait; after one timeout the caller stops waiting altogether
+// (its results are then unreliable and the status word says so).
 __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned int* status,
                                                   bool& healthy) {
     if (!healthy) return;
-    for (uint32_t it = 0; it < kSyncPolls; ++it)
-        if (mbar_try_wait(bar, parity)) return;
+    if (mbar_wait_limited(bar, parity, kSyncPolls)) return;
     atomicOr(status, ST_SYNC_TIMEOUT);
     healthy = false;
 }
@@ -141,11 +174,8 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
                 producer_barrier<P>();
                 const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
                 producer_barrier<P>();
-                int start = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < bin) start += st_.cnt[q];
-                if (bin >= 0) st_.task[start + slot] = t | ((task + 1) << kOwnerBits);
+                if (bin >= 0) st_.task[bin_start(st_.cnt, bin) + slot] = t | ((task + 1) << kOwnerBits);
+                pad_bins<P>(st_, t);
                 // stash the FP32 state; final answers are stored right away
                 if (rs.status == 0) {
 #pragma unroll
@@ -202,9 +232,10 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
         for (int k = 0; k < K; ++k) {
             Stage<P>& st_ = S[k & 1];
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), v.status, healthy);
-            const int total = st_.cnt[0] + st_.cnt[1] + st_.cnt[2] + st_.cnt[3];
+            const int total = bin_start(st_.cnt, 4);
             for (int q = c; q < total; q += C) {
                 const int e = st_.task[q];
+                if (e < 0) continue;
                 const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
                 st_.res[o] = eval64<SEGS>(v, tab64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
                                     st_.pd[4][o], st_.pd[5][o]);
@@ -245,11 +276,15 @@ static cudaError_t launch_refine_cfg(const VolView& v, const Basket& b, double* 
     const int smem = 2 * int(sizeof(Stage<P>)) +
                      (v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0);
     if (v.voxelized) {
+        // the grid walk needs registers: 12 + 2 warps at 72 registers beat
+        // 12 + 4 at 64 (7.0 against 7.4 ms for 2^24 tracks in 512 daughters)
+        constexpr int CV = P == kProd ? kVoxCons : C;
+        const int smem_v = 2 * int(sizeof(Stage<P>));
         if (v.segs)
-            return launch_refine<P, C>(k_dist_refine<P, C, false, 1, true>, smem, v, b, step, hit, bpoint, nref, s,
-                                       num_sms);
-        return launch_refine<P, C>(k_dist_refine<P, C, false, 1, false>, smem, v, b, step, hit, bpoint, nref, s,
-                                   num_sms);
+            return launch_refine<P, CV>(k_dist_refine<P, CV, false, 1, true>, smem_v, v, b, step, hit, bpoint, nref,
+                                        s, num_sms);
+        return launch_refine<P, CV>(k_dist_refine<P, CV, false, 1, false>, smem_v, v, b, step, hit, bpoint, nref, s,
+                                    num_sms);
     }
     if (v.smem_refine) {
         if (v.segs)

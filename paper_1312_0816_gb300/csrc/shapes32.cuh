@@ -87,16 +87,15 @@ __device__ __forceinline__ float box_exit32(const float* h, const float* x, cons
 }
 
 // ------------------------------------------------------------- quadrics -----
+// The routines below select operands instead of branching, so that the lanes
+// of a warp bounding the same solid run one code path whatever their tracks.
+//
 // D with a tolerance: a discriminant within rounding of zero counts as a
 // tangent (D = 0), which only adds candidates.
 __device__ __forceinline__ bool disc32(float A, float B, float C, float& sq) {
-    float D = fmaf(B, B, -A * C);
-    if (D < 0.f) {
-        if (D > -16.f * kEps32f * (B * B + fabsf(A * C))) D = 0.f;
-        else return false;
-    }
-    sq = fsqrt(D);
-    return true;
+    const float D = fmaf(B, B, -A * C);
+    sq = fsqrt(fmaxf(D, 0.f));
+    return D >= 0.f || D > -16.f * kEps32f * (B * B + fabsf(A * C));
 }
 
 // Roots are parameters relative to the (shifted) origin of the frame and may
@@ -104,63 +103,62 @@ __device__ __forceinline__ bool disc32(float A, float B, float C, float& sq) {
 // falling root (F decreases through 0): (-B - sq)/A in stable form
 __device__ __forceinline__ float root_falling32(float A, float B, float C) {
     float sq;
-    if (!disc32(A, B, C, sq)) return f_inf();
-    if (B < 0.f) return fdiv(C, sq - B);
-    if (A != 0.f) return fdiv(-B - sq, A);
-    return f_inf();
+    const bool real = disc32(A, B, C, sq);
+    const bool bneg = B < 0.f;
+    const float q = fdiv(bneg ? C : -B - sq, bneg ? sq - B : A);
+    return real && (bneg || A != 0.f) ? q : f_inf();
 }
 
 // rising root (F increases through 0): (-B + sq)/A in stable form
 __device__ __forceinline__ float root_rising32(float A, float B, float C) {
     float sq;
-    if (!disc32(A, B, C, sq)) return f_inf();
-    if (B > 0.f) return fdiv(C, -B - sq);
-    if (A != 0.f) return fdiv(sq - B, A);
-    return f_inf();
+    const bool real = disc32(A, B, C, sq);
+    const bool bpos = B > 0.f;
+    const float q = fdiv(bpos ? C : sq - B, bpos ? -B - sq : A);
+    return real && (bpos || A != 0.f) ? q : f_inf();
 }
 
 // ---------------------------------------------------------------- tube -----
-// e: [0] rmin'^2 (0 if no hole), [1] rmax'^2, [2] dz', [3] hole flag
-__device__ __forceinline__ float tube_enter32(const float* e, const float* x, const float* u, float tmin,
-                                              float tol) {
-    const float dz = e[2];
-    const float zl = dz + tol;
-    const float ro = fsqrt(e[1]) + tol;
-    const float ri = e[3] != 0.f ? fsqrt(e[0]) - tol : 0.f;
-    const float ro2 = ro * ro;
-    const float ri2 = ri > 0.f ? ri * ri : 0.f;
+// e: [0] rmin'^2 (0 if no hole), [1] rmax'^2, [2] dz', [3] hole flag, and the
+// acceptance limits, lenient by tol = delta (geo_abi.cu make_rec32):
+// [4] (rmax' + delta)^2 rounded up, [5] (rmin' - delta)^2 rounded down (0
+// without a hole), [6] dz' + delta rounded up.
+__device__ __forceinline__ float tube_enter32(const float* e, const float* x, const float* u, float tmin) {
+    const float dz = e[2], zl = e[6], ro2 = e[4], ri2 = e[5];
     // start point
     const float sx = fmaf(tmin, u[0], x[0]), sy = fmaf(tmin, u[1], x[1]), sz = fmaf(tmin, u[2], x[2]);
     const float sr2 = fmaf(sx, sx, sy * sy);
     if (fabsf(sz) <= zl && sr2 <= ro2 && sr2 >= ri2) return tmin;
-    float best = f_inf();
-    if (fabsf(sz) > dz && sz * u[2] < 0.f) {
-        const float t = fdiv(copysignf(dz, sz) - x[2], u[2]);
-        const float xh = fmaf(t, u[0], x[0]), yh = fmaf(t, u[1], x[1]);
-        const float r2 = fmaf(xh, xh, yh * yh);
-        if (r2 <= ro2 && r2 >= ri2) best = fmaxf(t, tmin);
-    }
+    // the z-plane the start lies beyond, when the track approaches it
+    const float tz = fdiv(copysignf(dz, sz) - x[2], u[2]);
+    const float xh = fmaf(tz, u[0], x[0]), yh = fmaf(tz, u[1], x[1]);
+    const float r2 = fmaf(xh, xh, yh * yh);
+    float best = fabsf(sz) > dz && sz * u[2] < 0.f && r2 <= ro2 && r2 >= ri2 ? fmaxf(tz, tmin) : f_inf();
     const float A = fmaf(u[0], u[0], u[1] * u[1]);
     const float B = fmaf(x[0], u[0], x[1] * u[1]);
     const float rho2 = fmaf(x[0], x[0], x[1] * x[1]);
     {
         const float s = root_falling32(A, B, rho2 - e[1]);
-        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+        best = s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl ? s : best;
     }
-    if (e[3] != 0.f) {
+    if (e[3] != 0.f) {   // uniform across the warp: every lane bounds the same solid
         const float s = root_rising32(A, B, rho2 - e[0]);
-        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+        best = s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl ? s : best;
     }
     return best;
 }
 
 // ---------------------------------------------------------------- cone -----
 // e: [0] dz', [1] a_out', [2] b_out, [3] a_in', [4] b_in, [5] hole,
-//    [6] rmin1'^2 [7] rmax1'^2 [8] rmin2'^2 [9] rmax2'^2 (at z = -dz', +dz')
+//    [6] rmin1'^2 [7] rmax1'^2 [8] rmin2'^2 [9] rmax2'^2 (at z = -dz', +dz'),
+// and the end annuli's acceptance limits, lenient by tol = delta:
+//    [10] (rmax1' + delta)^2 [11] (rmax2' + delta)^2 rounded up,
+//    [12] (rmin1' - delta)^2 [13] (rmin2' - delta)^2 rounded down (0 where
+//    there is no hole), [14] dz' + delta rounded up.
 __device__ __forceinline__ float cone_enter32(const float* e, const float* x, const float* u, float tmin,
                                               float tol) {
     const float dz = e[0];
-    const float zl = dz + tol;
+    const float zl = e[14];
     const bool hole = e[5] != 0.f;
     const float sx = fmaf(tmin, u[0], x[0]), sy = fmaf(tmin, u[1], x[1]), sz = fmaf(tmin, u[2], x[2]);
     const float sr2 = fmaf(sx, sx, sy * sy);
@@ -168,28 +166,25 @@ __device__ __forceinline__ float cone_enter32(const float* e, const float* x, co
         const float ro = fmaf(e[2], sz, e[1]) + tol, ri = fmaf(e[4], sz, e[3]) - tol;
         if (fabsf(sz) <= zl && sr2 <= ro * ro && (!hole || ri <= 0.f || sr2 >= ri * ri)) return tmin;
     }
-    float best = f_inf();
-    if (fabsf(sz) > dz && sz * u[2] < 0.f) {
-        const float t = fdiv(copysignf(dz, sz) - x[2], u[2]);
-        const float xh = fmaf(t, u[0], x[0]), yh = fmaf(t, u[1], x[1]);
-        const float r2 = fmaf(xh, xh, yh * yh);
-        const float lo2 = sz > 0.f ? e[8] : e[6];
-        const float hi = fsqrt(sz > 0.f ? e[9] : e[7]) + tol;
-        const float lo = hole ? fmaxf(fsqrt(lo2) - tol, 0.f) : 0.f;
-        if (r2 <= hi * hi && r2 >= lo * lo) best = fmaxf(t, tmin);
-    }
+    // the end plane the start lies beyond, when the track approaches it
+    const float tz = fdiv(copysignf(dz, sz) - x[2], u[2]);
+    const float xh = fmaf(tz, u[0], x[0]), yh = fmaf(tz, u[1], x[1]);
+    const float r2 = fmaf(xh, xh, yh * yh);
+    const bool up = sz > 0.f;
+    const float hi2 = up ? e[11] : e[10], lo2 = up ? e[13] : e[12];
+    float best = fabsf(sz) > dz && sz * u[2] < 0.f && r2 <= hi2 && r2 >= lo2 ? fmaxf(tz, tmin) : f_inf();
     const float A0 = fmaf(u[0], u[0], u[1] * u[1]);
     const float B0 = fmaf(x[0], u[0], x[1] * u[1]);
     const float rho2 = fmaf(x[0], x[0], x[1] * x[1]);
     {
         const float r0 = fmaf(e[2], x[2], e[1]), rs = e[2] * u[2];
         const float s = root_falling32(fmaf(-rs, rs, A0), fmaf(-r0, rs, B0), fmaf(-r0, r0, rho2));
-        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+        best = s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl ? s : best;
     }
-    if (hole) {
+    if (hole) {   // uniform across the warp
         const float r0 = fmaf(e[4], x[2], e[3]), rs = e[4] * u[2];
         const float s = root_rising32(fmaf(-rs, rs, A0), fmaf(-r0, rs, B0), fmaf(-r0, r0, rho2));
-        if (s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl) best = s;
+        best = s >= tmin && s < best && fabsf(fmaf(s, u[2], x[2])) <= zl ? s : best;
     }
     return best;
 }
@@ -200,7 +195,7 @@ __device__ __forceinline__ float cone_enter32(const float* e, const float* x, co
 __device__ __forceinline__ float enter32(const ShapeRec32& r, const float* x, const float* u, float tmin) {
     const float tol = r.delta;
     if (r.kind == KBOX) return box_enter32(r.e, x, u, tmin, tol);
-    if (r.kind == KTUBE) return tube_enter32(r.e, x, u, tmin, tol);
+    if (r.kind == KTUBE) return tube_enter32(r.e, x, u, tmin);
     return cone_enter32(r.e, x, u, tmin, tol);
 }
 

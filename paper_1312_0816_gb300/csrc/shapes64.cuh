@@ -85,16 +85,18 @@ __device__ __forceinline__ void point_to_local64(const ShapeRec64& r, double px,
 // F(s) = A s^2 + 2 B s + C.  Root where F falls through zero (F' = -2 sqrt(D)),
 // s = (-B - sqrt(D)) / A; +inf when there is none.  May be negative.
 // Both cancellation-free forms are selected operand-wise so that every lane
-// of a warp runs the same single square root and division.
+// of a warp runs the same single square root and division; a lane whose
+// result is discarded takes the square root and quotient of 1, so that no
+// lane of the warp diverges into the handling of a special operand (zero).
 __device__ __forceinline__ double root_falling(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
     const bool real = NONNEG(D);
-    const double sq = SQRT(real ? D : 0.0);
+    const double sq = SQRT(real ? D : 1.0);
     const bool bneg = IS_NEG(B);
     const double num = bneg ? C : SUB(-B, sq);
     const double den = bneg ? SUB(sq, B) : A;
     const bool ok = real && (bneg || IS_NEG(A));
-    const double s = DIV(num, ok ? den : 1.0);
+    const double s = DIV(ok ? num : 1.0, ok ? den : 1.0);
     return ok ? s : d_inf();
 }
 
@@ -102,12 +104,12 @@ __device__ __forceinline__ double root_falling(double A, double B, double C) {
 __device__ __forceinline__ double root_rising(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
     const bool real = NONNEG(D);
-    const double sq = SQRT(real ? D : 0.0);
+    const double sq = SQRT(real ? D : 1.0);
     const bool bpos = IS_POS(B);
     const double num = bpos ? C : SUB(sq, B);
     const double den = bpos ? SUB(-B, sq) : A;
     const bool ok = real && (bpos || IS_POS(A));
-    const double s = DIV(num, ok ? den : 1.0);
+    const double s = DIV(ok ? num : 1.0, ok ? den : 1.0);
     return ok ? s : d_inf();
 }
 
@@ -117,24 +119,24 @@ __device__ __forceinline__ double root_rising(double A, double B, double C) {
 __device__ __forceinline__ double root_falling_any(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
     const bool real = NONNEG(D);
-    const double sq = SQRT(real ? D : 0.0);
+    const double sq = SQRT(real ? D : 1.0);
     const bool bneg = IS_NEG(B);
     const double num = bneg ? C : SUB(-B, sq);
     const double den = bneg ? SUB(sq, B) : A;
     const bool ok = real && (bneg || !IS_ZERO(A));
-    const double s = DIV(num, ok ? den : 1.0);
+    const double s = DIV(ok ? num : 1.0, ok ? den : 1.0);
     return ok ? s : d_inf();
 }
 
 __device__ __forceinline__ double root_rising_any(double A, double B, double C) {
     const double D = FMA(B, B, -MUL(A, C));
     const bool real = NONNEG(D);
-    const double sq = SQRT(real ? D : 0.0);
+    const double sq = SQRT(real ? D : 1.0);
     const bool bpos = IS_POS(B);
     const double num = bpos ? C : SUB(sq, B);
     const double den = bpos ? SUB(-B, sq) : A;
     const bool ok = real && (bpos || !IS_ZERO(A));
-    const double s = DIV(num, ok ? den : 1.0);
+    const double s = DIV(ok ? num : 1.0, ok ? den : 1.0);
     return ok ? s : d_inf();
 }
 

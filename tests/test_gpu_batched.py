@@ -45,7 +45,7 @@ def per_basket(g, vols, volh, tr, rows, mode):
 
 @pytest.mark.parametrize("order,bps,tile", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 256), (1, 1, 256)])
 def test_batched_equals_per_basket(g, small_batch, order, bps, tile):
-    """Every schedule and both tile shapes (384 tracks, 12 + 2 warps; 256, 8 +
+    """Every schedule and both tile shapes (384 tracks, 12 + 4 warps; 256, 8 +
     4) give the per-basket plain FP64 bits."""
     vols, tr, rows = small_batch
     volh = [g.geo_build_volume(v) for v in vols]

@@ -149,7 +149,7 @@ def test_refine_fallback_to_the_full_loop(g, orc, n):
 def test_refine_block_configurations(g, name):
     """Both block configurations of the filter kernel -- 8 + 4 warps with
     tiles of 256 tracks while a basket has at most two tiles for each of two
-    blocks per SM, 12 + 2 warps with tiles of GEO_TILE_TRACKS beyond -- return
+    blocks per SM, 12 + 4 warps with tiles of GEO_TILE_TRACKS beyond -- return
     the plain FP64 bits, on either side of the switch and with a ragged tail."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     edge = 4 * sms * 256
