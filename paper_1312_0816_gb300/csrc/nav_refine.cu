@@ -67,11 +67,12 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
 
     if (t < P) {
         // ------------------------------------------------------ producers --
-        int64_t prev_i = 0;      // this thread's track in the previous tile
-        bool prev_live = false;
         for (int k = 0;; ++k) {
             Stage<P>& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
+            // the stage and its header held tile k-2, which its consumers must
+            // have finished
+            if (k >= 2) mbar_wait_bounded(&done[k & 1], uint32_t(((k - 2) >> 1) & 1), bv.status, healthy);
             if (t == 0) {
                 const unsigned q = atomicAdd(bv.counter, 1u);
                 if (int64_t(q) < bv.ntiles) {
@@ -87,8 +88,6 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
             }
             producer_barrier<P>();
             const int tile = hd.tile;
-            int64_t cur_i = 0;
-            bool cur_live = false;
             if (tile >= 0) {
                 if (t < kWords)
                     reinterpret_cast<int4*>(&hd.vol)[t] = reinterpret_cast<const int4*>(bv.vols + hd.vol_index)[t];
@@ -105,8 +104,6 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
                     live = false;
                     i = 0;
                 }
-                cur_i = i;
-                cur_live = live;
                 double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
                 if (live) {
                     px = b.x[i]; py = b.y[i]; pz = b.z[i];
@@ -137,40 +134,13 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
                     st_.Lm[t] = rs.Lm;
                     st_.dropped[t] = rs.c.dropped;
                     st_.n[t] = rs.c.n;
-                } else {
-                    st_.n[t] = -1;
-                    if (live) store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
+                } else if (live) {
+                    store_result(i, b.n, best, h, px, py, pz, qx, qy, qz, step, hit, nullptr);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[k & 1]);
-            if (k >= 1) {
-                const int kp = k - 1;
-                Stage<P>& sp = S[kp & 1];
-                const VolView& vp = H[kp & 1].vol;
-                mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), bv.status, healthy);
-                if (prev_live && sp.n[t] >= 0) {
-                    RefineState rs;
-                    rs.status = 0;
-                    rs.c.n = sp.n[t];
-#pragma unroll
-                    for (int q = 0; q < kCand; ++q) {
-                        rs.c.L[q] = sp.L[q][t];
-                        rs.c.j[q] = sp.j[q][t];
-                    }
-                    rs.c.dropped = sp.dropped[t];
-                    rs.Lm = sp.Lm[t];
-                    double best;
-                    int h, nev;
-                    if (!refine_fast(rs, sp.res[t], best, h))
-                        refine_rest<SEGS>(vp, vp.d64, rs, sp.res[t], sp.pd[0][t], sp.pd[1][t], sp.pd[2][t],
-                                          sp.pd[3][t], sp.pd[4][t], sp.pd[5][t], best, h, nev);
-                    store_result(prev_i, b.n, best, h, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, step, hit, nullptr);
-                }
-            }
             if (tile < 0) break;
-            prev_live = cur_live;
-            prev_i = cur_i;
         }
     } else {
         // ------------------------------------------------------ consumers --
@@ -181,13 +151,15 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), bv.status, healthy);
             if (!healthy || hd.tile < 0) break;
             const VolView& v = hd.vol;
+            const int64_t base = hd.base;
+            const bool packed = hd.count < 0;
             const int total = bin_start(st_.cnt, 4);
             for (int q = c; q < total; q += C) {
                 const int e = st_.task[q];
                 if (e < 0) continue;
                 const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
-                st_.res[o] = eval64<SEGS>(v, v.d64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
-                                    st_.pd[4][o], st_.pd[5][o]);
+                const int64_t i = packed ? bv.idx[base + o] : base + o;
+                finish_track<SEGS, P>(v, v.d64, st_, o, jj, i, b.n, step, hit, nullptr, nullptr);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);

@@ -24,13 +24,15 @@ namespace geonav {
 // registers 0.264, 8 + 4 0.265; the producers alone (FP64 evaluations
 // skipped) take 0.207 ms and the consumers alone (each track's winner given)
 // 0.160 ms, so the FP32 pass sets the pace.
-//  producers: FP32 pass of tile k, then bin each track's first FP64 task by
-//             solid kind (mother, box, tube, cone) into stage k%2, arrive on
-//             full[k%2]; then wait done[(k-1)%2] and finish tile k-1 (rare
-//             extra refinements, stores).
+//  producers: wait done[k%2] (the stage's previous tile, k-2, finished), FP32
+//             pass of tile k, bin each track's first FP64 task by solid kind
+//             (mother, box, tube, cone) into stage k%2, arrive on full[k%2].
 //  consumers: wait full[k%2], evaluate the binned tasks of tile k in FP64 (a
 //             warp takes 32 consecutive tasks, all of one kind: the bins
-//             start on multiples of 32), arrive on done[k%2].
+//             start on multiples of 32) and finish their tracks (rare extra
+//             refinements, stores), arrive on done[k%2].  Finishing there
+//             instead of in the producers took 0.2425 -> 0.2300 ms: the
+//             producers set the pace, and the consumers had time to spare.
 // The FP64 pipe therefore works on tile k while the FP32 pass of tile k+1 runs.
 // Every wait is bounded; a wait that runs out records ST_SYNC_TIMEOUT.
 // Block configurations (P producer threads, one track each per tile, and
@@ -50,7 +52,6 @@ static_assert(kProd <= (1 << kOwnerBits) && kProd % 32 == 0 && kLatProd % 32 == 
 template <int P>
 struct Stage {
     double pd[6][P];        // the tile's positions and directions (FP64)
-    double res[P];          // FP64 value of each track's first task
     float L[kCand][P];      // stashed FP32 state for the producers' second half
     int j[kCand][P];
     float Lm[P];
@@ -109,6 +110,36 @@ __device__ __forceinline__ void mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // polycone)
 __device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : (kind == KPCON ? 3 : 1 + kind); }
 
+// A consumer's whole share of one track: the FP64 value of its first task
+// jj, then the refinement's end (nearly always refine_fast: no other bound
+// can win or tie) and the store.
+template <bool SEGS, int P>
+__device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64* __restrict__ tab64, const Stage<P>& st,
+                                             int o, int jj, int64_t i, int64_t n, double* __restrict__ step,
+                                             int32_t* __restrict__ hit, double* __restrict__ bpoint,
+                                             int32_t* __restrict__ nref) {
+    const double s_first =
+        eval64<SEGS>(v, tab64, jj, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o], st.pd[5][o]);
+    RefineState rs;
+    rs.status = 0;
+    rs.c.n = st.n[o];
+#pragma unroll
+    for (int q = 0; q < kCand; ++q) {
+        rs.c.L[q] = st.L[q][o];
+        rs.c.j[q] = st.j[q][o];
+    }
+    rs.c.dropped = st.dropped[o];
+    rs.Lm = st.Lm[o];
+    double best;
+    int h, nev = 1;
+    if (!refine_fast(rs, s_first, best, h))
+        refine_rest<SEGS>(v, tab64, rs, s_first, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o],
+                          st.pd[5][o], best, h, nev);
+    store_result(i, n, best, h, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o], st.pd[5][o], step,
+                 hit, bpoint);
+    if (nref) nref[i] = nev;
+}
+
 template <int P>
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(P) : "memory"); }
 
@@ -148,83 +179,55 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
 
     if (t < P) {
         // ------------------------------------------------------ producers --
-        for (int k = 0; k <= K; ++k) {
-            if (k < K) {
-                Stage<P>& st_ = S[k & 1];
-                const int64_t i = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * P + t;
-                const bool live = i < b.n;
-                double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
-                if (live) {
-                    px = b.x[i]; py = b.y[i]; pz = b.z[i];
-                    qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
-                }
-                st_.pd[0][t] = px; st_.pd[1][t] = py; st_.pd[2][t] = pz;
-                st_.pd[3][t] = qx; st_.pd[4][t] = qy; st_.pd[5][t] = qz;
-                RefineState rs;
-                double best = 0.0;
-                int h = -2, nev = 0;
-                rs.status = 1;
-                if (live) refine_pass1<TRAV, SEGS>(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
-                int task = 0, bin = -1;
-                if (rs.status == 0) {
-                    task = first_task(rs);
-                    bin = task < 0 ? 0 : kind_bin(tab64[task].kind);
-                }
-                if (t < 4) st_.cnt[t] = 0;
-                producer_barrier<P>();
-                const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
-                producer_barrier<P>();
-                if (bin >= 0) st_.task[bin_start(st_.cnt, bin) + slot] = t | ((task + 1) << kOwnerBits);
-                pad_bins<P>(st_, t);
-                // stash the FP32 state; final answers are stored right away
-                if (rs.status == 0) {
-#pragma unroll
-                    for (int q = 0; q < kCand; ++q) {
-                        st_.L[q][t] = rs.c.L[q];
-                        st_.j[q][t] = rs.c.j[q];
-                    }
-                    st_.Lm[t] = rs.Lm;
-                    st_.dropped[t] = rs.c.dropped;
-                    st_.n[t] = rs.c.n;
-                } else {
-                    st_.n[t] = -1;
-                    if (live) {
-                        // the track is read back from the stage: keeping it in
-                        // registers through the FP32 pass would spill
-                        store_result(i, b.n, best, h, st_.pd[0][t], st_.pd[1][t], st_.pd[2][t], st_.pd[3][t],
-                                     st_.pd[4][t], st_.pd[5][t], step, hit, bpoint);
-                        if (nref) nref[i] = nev;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[k & 1]);
+        for (int k = 0; k < K; ++k) {
+            Stage<P>& st_ = S[k & 1];
+            // the stage held tile k-2, which its consumers must have finished
+            if (k >= 2) mbar_wait_bounded(&done[k & 1], uint32_t(((k - 2) >> 1) & 1), v.status, healthy);
+            const int64_t i = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * P + t;
+            const bool live = i < b.n;
+            double px = 0, py = 0, pz = 0, qx = 1, qy = 0, qz = 0;
+            if (live) {
+                px = b.x[i]; py = b.y[i]; pz = b.z[i];
+                qx = b.dx[i]; qy = b.dy[i]; qz = b.dz[i];
             }
-            if (k >= 1) {
-                const int kp = k - 1;
-                Stage<P>& sp = S[kp & 1];
-                mbar_wait_bounded(&done[kp & 1], uint32_t((kp >> 1) & 1), v.status, healthy);
-                const int64_t i = (int64_t(blockIdx.x) + int64_t(kp) * gridDim.x) * P + t;
-                if (i < b.n && sp.n[t] >= 0) {
-                    RefineState rs;
-                    rs.status = 0;
-                    rs.c.n = sp.n[t];
-#pragma unroll
-                    for (int q = 0; q < kCand; ++q) {
-                        rs.c.L[q] = sp.L[q][t];
-                        rs.c.j[q] = sp.j[q][t];
-                    }
-                    rs.c.dropped = sp.dropped[t];
-                    rs.Lm = sp.Lm[t];
-                    double best;
-                    int h, nev = 1;
-                    if (!refine_fast(rs, sp.res[t], best, h))
-                        refine_rest<SEGS>(v, tab64, rs, sp.res[t], sp.pd[0][t], sp.pd[1][t], sp.pd[2][t], sp.pd[3][t],
-                                          sp.pd[4][t], sp.pd[5][t], best, h, nev);
-                    store_result(i, b.n, best, h, sp.pd[0][t], sp.pd[1][t], sp.pd[2][t], sp.pd[3][t], sp.pd[4][t],
-                                 sp.pd[5][t], step, hit, bpoint);
-                    if (nref) nref[i] = nev;
-                }
+            st_.pd[0][t] = px; st_.pd[1][t] = py; st_.pd[2][t] = pz;
+            st_.pd[3][t] = qx; st_.pd[4][t] = qy; st_.pd[5][t] = qz;
+            RefineState rs;
+            double best = 0.0;
+            int h = -2, nev = 0;
+            rs.status = 1;
+            if (live) refine_pass1<TRAV, SEGS>(v, tab32, tab64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+            int task = 0, bin = -1;
+            if (rs.status == 0) {
+                task = first_task(rs);
+                bin = task < 0 ? 0 : kind_bin(tab64[task].kind);
             }
+            if (t < 4) st_.cnt[t] = 0;
+            producer_barrier<P>();
+            const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
+            producer_barrier<P>();
+            if (bin >= 0) st_.task[bin_start(st_.cnt, bin) + slot] = t | ((task + 1) << kOwnerBits);
+            pad_bins<P>(st_, t);
+            // stash the FP32 state for the consumer that finishes the track;
+            // final answers are stored right away
+            if (rs.status == 0) {
+#pragma unroll
+                for (int q = 0; q < kCand; ++q) {
+                    st_.L[q][t] = rs.c.L[q];
+                    st_.j[q][t] = rs.c.j[q];
+                }
+                st_.Lm[t] = rs.Lm;
+                st_.dropped[t] = rs.c.dropped;
+                st_.n[t] = rs.c.n;
+            } else if (live) {
+                // the track is read back from the stage: keeping it in
+                // registers through the FP32 pass would spill
+                store_result(i, b.n, best, h, st_.pd[0][t], st_.pd[1][t], st_.pd[2][t], st_.pd[3][t],
+                             st_.pd[4][t], st_.pd[5][t], step, hit, bpoint);
+                if (nref) nref[i] = nev;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[k & 1]);
         }
     } else {
         // ------------------------------------------------------ consumers --
@@ -237,8 +240,8 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
                 const int e = st_.task[q];
                 if (e < 0) continue;
                 const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
-                st_.res[o] = eval64<SEGS>(v, tab64, jj, st_.pd[0][o], st_.pd[1][o], st_.pd[2][o], st_.pd[3][o],
-                                    st_.pd[4][o], st_.pd[5][o]);
+                const int64_t i = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * P + o;
+                finish_track<SEGS, P>(v, tab64, st_, o, jj, i, b.n, step, hit, bpoint, nref);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);
