@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
                     hd.tile = -1;
                 }
                 st_.cnt[0] = st_.cnt[1] = st_.cnt[2] = st_.cnt[3] = 0;
+                st_.next = 0;
             }
             producer_barrier<P>();
             const int tile = hd.tile;
@@ -140,27 +141,34 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[k & 1]);
-            if (tile < 0) break;
+            if (tile < 0) {
+                // the queue is empty: help the consumers with this block's
+                // last tile (k - 1), whose stage every producer has filled
+                if (k >= 1 && __all_sync(0xffffffffu, healthy)) {
+                    const TileHdr& hl = H[(k - 1) & 1];
+                    const int64_t base = hl.base;
+                    const bool packed = hl.count < 0;
+                    const int64_t* idx = bv.idx;
+                    drain_tasks<SEGS, P>(hl.vol, hl.vol.d64, S[(k - 1) & 1],
+                                         [=](int o) { return packed ? idx[base + o] : base + o; }, b.n, step, hit,
+                                         nullptr, nullptr);
+                }
+                break;
+            }
         }
     } else {
         // ------------------------------------------------------ consumers --
-        const int c = t - P;
         for (int k = 0;; ++k) {
             Stage<P>& st_ = S[k & 1];
             TileHdr& hd = H[k & 1];
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), bv.status, healthy);
-            if (!healthy || hd.tile < 0) break;
+            if (!__all_sync(0xffffffffu, healthy) || hd.tile < 0) break;   // warp-uniform
             const VolView& v = hd.vol;
             const int64_t base = hd.base;
             const bool packed = hd.count < 0;
-            const int total = bin_start(st_.cnt, 4);
-            for (int q = c; q < total; q += C) {
-                const int e = st_.task[q];
-                if (e < 0) continue;
-                const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
-                const int64_t i = packed ? bv.idx[base + o] : base + o;
-                finish_track<SEGS, P>(v, v.d64, st_, o, jj, i, b.n, step, hit, nullptr, nullptr);
-            }
+            const int64_t* idx = bv.idx;
+            drain_tasks<SEGS, P>(v, v.d64, st_, [=](int o) { return packed ? idx[base + o] : base + o; }, b.n, step,
+                                 hit, nullptr, nullptr);
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);
         }

@@ -59,6 +59,8 @@ struct Stage {
     int n[P];               // candidate count, -1: answer already final
     int task[P + 128];      // binned tasks: owner | (solid + 1) << kOwnerBits; -1 pads
     int cnt[4];
+    int next;               // the next chunk of 32 tasks to claim
+    int pad_[3];
 };
 
 // Each bin of a stage's task list starts on a multiple of 32, so that the 32
@@ -140,6 +142,30 @@ __device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64*
     if (nref) nref[i] = nev;
 }
 
+// A warp's share of a stage's FP64 tasks: it claims chunks of 32 tasks (one
+// bin-aligned chunk, so one solid kind) from the stage's counter until none
+// is left, and finishes their tracks; index(o) is the basket index of the
+// tile's track o.  Every lane of the warp takes part.
+template <bool SEGS, int P, typename Index>
+__device__ __forceinline__ void drain_tasks(const VolView& v, const ShapeRec64* __restrict__ tab64, Stage<P>& st,
+                                            Index index, int64_t n, double* __restrict__ step,
+                                            int32_t* __restrict__ hit, double* __restrict__ bpoint,
+                                            int32_t* __restrict__ nref) {
+    const int total = bin_start(st.cnt, 4);   // a multiple of 32
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int q0 = 0;
+        if (lane == 0) q0 = atomicAdd(&st.next, 32);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        if (q0 >= total) break;
+        const int e = st.task[q0 + lane];
+        if (e >= 0) {
+            const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
+            finish_track<SEGS, P>(v, tab64, st, o, jj, index(o), n, step, hit, bpoint, nref);
+        }
+    }
+}
+
 template <int P>
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(P) : "memory"); }
 
@@ -203,6 +229,7 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
                 bin = task < 0 ? 0 : kind_bin(tab64[task].kind);
             }
             if (t < 4) st_.cnt[t] = 0;
+            if (t == 4) st_.next = 0;
             producer_barrier<P>();
             const int slot = bin >= 0 ? atomicAdd(&st_.cnt[bin], 1) : 0;
             producer_barrier<P>();
@@ -229,20 +256,24 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[k & 1]);
         }
+        // with nothing left to filter, the producers help the consumers
+        // with the last tile's FP64 tasks
+        if (K >= 1) {
+            const int kl = K - 1;
+            mbar_wait_bounded(&full[kl & 1], uint32_t((kl >> 1) & 1), v.status, healthy);
+            const int64_t base = (int64_t(blockIdx.x) + int64_t(kl) * gridDim.x) * P;
+            if (__all_sync(0xffffffffu, healthy))   // a stage that was never filled is not read
+                drain_tasks<SEGS, P>(v, tab64, S[kl & 1], [base](int o) { return base + o; }, b.n, step, hit, bpoint,
+                                     nref);
+        }
     } else {
         // ------------------------------------------------------ consumers --
-        const int c = t - P;
         for (int k = 0; k < K; ++k) {
-            Stage<P>& st_ = S[k & 1];
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), v.status, healthy);
-            const int total = bin_start(st_.cnt, 4);
-            for (int q = c; q < total; q += C) {
-                const int e = st_.task[q];
-                if (e < 0) continue;
-                const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
-                const int64_t i = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * P + o;
-                finish_track<SEGS, P>(v, tab64, st_, o, jj, i, b.n, step, hit, bpoint, nref);
-            }
+            const int64_t base = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * P;
+            if (__all_sync(0xffffffffu, healthy))   // a stage that was never filled is not read
+                drain_tasks<SEGS, P>(v, tab64, S[k & 1], [base](int o) { return base + o; }, b.n, step, hit, bpoint,
+                                     nref);
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);
         }
