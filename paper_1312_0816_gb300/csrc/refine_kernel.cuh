@@ -63,6 +63,15 @@ struct Stage {
     int pad_[3];
 };
 
+// The answers of one tile, gathered for stores by consecutive lanes (the
+// single-volume kernel: its outputs may be host memory read over the link).
+template <int P>
+struct Answers {
+    double best[P];         // the step ...
+    int h[P];               // ... and hit, kNoStore for a lane without a track
+    int nev[P];             // FP64 evaluations (statistics)
+};
+
 // Each bin of a stage's task list starts on a multiple of 32, so that the 32
 // consecutive tasks a consumer warp takes are of one kind (a warp pays for
 // every code path its lanes take); the slots between bins hold -1.
@@ -114,12 +123,15 @@ __device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : (
 
 // A consumer's whole share of one track: the FP64 value of its first task
 // jj, then the refinement's end (nearly always refine_fast: no other bound
-// can win or tie) and the store.
-template <bool SEGS, int P>
-__device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64* __restrict__ tab64, const Stage<P>& st,
-                                             int o, int jj, int64_t i, int64_t n, double* __restrict__ step,
-                                             int32_t* __restrict__ hit, double* __restrict__ bpoint,
-                                             int32_t* __restrict__ nref) {
+// can win or tie).  The answer goes to the stage (STAGED), from where the
+// tile's answers are stored together, consecutive tracks by consecutive
+// lanes (the tasks themselves are in kind order: their own stores would
+// scatter, which outputs in host memory read over the host link pay for);
+// or it is stored right away to index(o).
+template <bool SEGS, int P, bool STAGED, typename Index>
+__device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64* __restrict__ tab64,
+                                             const Stage<P>& st, Answers<P>* ans, int o, int jj, Index index,
+                                             int64_t n, double* __restrict__ step, int32_t* __restrict__ hit) {
     const double s_first =
         eval64<SEGS>(v, tab64, jj, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o], st.pd[5][o]);
     RefineState rs;
@@ -137,20 +149,41 @@ __device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64*
     if (!refine_fast(rs, s_first, best, h))
         refine_rest<SEGS>(v, tab64, rs, s_first, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o],
                           st.pd[5][o], best, h, nev);
-    store_result(i, n, best, h, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o], st.pd[5][o], step,
-                 hit, bpoint);
-    if (nref) nref[i] = nev;
+    if (STAGED) {
+        ans->best[o] = best;
+        ans->h[o] = h;
+        ans->nev[o] = nev;
+    } else {
+        store_result(index(o), n, best, h, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, step, hit, nullptr);
+    }
+}
+
+constexpr int kNoStore = -0x7fffffff;   // a stage lane without a track
+
+// The tile's answers from the stage to the outputs, consecutive tracks by
+// consecutive lanes of the C threads that call it; index(o) is the basket
+// index of the tile's track o.
+template <int P, int C, typename Index>
+__device__ __forceinline__ void store_tile(const Stage<P>& st, const Answers<P>& ans, int c, Index index, int64_t n,
+                                           double* __restrict__ step, int32_t* __restrict__ hit,
+                                           double* __restrict__ bpoint, int32_t* __restrict__ nref) {
+    for (int o = c; o < P; o += C) {
+        const int h = ans.h[o];
+        if (h == kNoStore) continue;
+        const int64_t i = index(o);
+        store_result(i, n, ans.best[o], h, st.pd[0][o], st.pd[1][o], st.pd[2][o], st.pd[3][o], st.pd[4][o],
+                     st.pd[5][o], step, hit, bpoint);
+        if (nref) nref[i] = ans.nev[o];
+    }
 }
 
 // A warp's share of a stage's FP64 tasks: it claims chunks of 32 tasks (one
 // bin-aligned chunk, so one solid kind) from the stage's counter until none
-// is left, and finishes their tracks; index(o) is the basket index of the
-// tile's track o.  Every lane of the warp takes part.
-template <bool SEGS, int P, typename Index>
+// is left, and finishes their tracks.  Every lane of the warp takes part.
+template <bool SEGS, int P, bool STAGED, typename Index>
 __device__ __forceinline__ void drain_tasks(const VolView& v, const ShapeRec64* __restrict__ tab64, Stage<P>& st,
-                                            Index index, int64_t n, double* __restrict__ step,
-                                            int32_t* __restrict__ hit, double* __restrict__ bpoint,
-                                            int32_t* __restrict__ nref) {
+                                            Answers<P>* ans, Index index, int64_t n, double* __restrict__ step,
+                                            int32_t* __restrict__ hit) {
     const int total = bin_start(st.cnt, 4);   // a multiple of 32
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -161,13 +194,15 @@ __device__ __forceinline__ void drain_tasks(const VolView& v, const ShapeRec64* 
         const int e = st.task[q0 + lane];
         if (e >= 0) {
             const int o = e & ((1 << kOwnerBits) - 1), jj = (e >> kOwnerBits) - 1;
-            finish_track<SEGS, P>(v, tab64, st, o, jj, index(o), n, step, hit, bpoint, nref);
+            finish_track<SEGS, P, STAGED>(v, tab64, st, ans, o, jj, index, n, step, hit);
         }
     }
 }
 
 template <int P>
 __device__ __forceinline__ void producer_barrier() { asm volatile("bar.sync 1, %0;" ::"r"(P) : "memory"); }
+template <int C>
+__device__ __forceinline__ void consumer_barrier() { asm volatile("bar.sync 2, %0;" ::"r"(C) : "memory"); }
 
 template <int P, int C, bool SMEM, int TRAV, bool SEGS>
 __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, double* __restrict__ step,
@@ -179,7 +214,8 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
     __shared__ uint64_t bar;
     __shared__ uint64_t full[2], done[2];
     Stage<P>* S = reinterpret_cast<Stage<P>*>(smem_raw);
-    unsigned char* tables = smem_raw + 2 * sizeof(Stage<P>);
+    Answers<P>* A = reinterpret_cast<Answers<P>*>(smem_raw + 2 * sizeof(Stage<P>));
+    unsigned char* tables = smem_raw + 2 * (sizeof(Stage<P>) + sizeof(Answers<P>));
     const ShapeRec32* tab32 = v.d32;
     const ShapeRec64* tab64 = v.d64;
     if (SMEM) {
@@ -246,34 +282,25 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
                 st_.Lm[t] = rs.Lm;
                 st_.dropped[t] = rs.c.dropped;
                 st_.n[t] = rs.c.n;
-            } else if (live) {
-                // the track is read back from the stage: keeping it in
-                // registers through the FP32 pass would spill
-                store_result(i, b.n, best, h, st_.pd[0][t], st_.pd[1][t], st_.pd[2][t], st_.pd[3][t],
-                             st_.pd[4][t], st_.pd[5][t], step, hit, bpoint);
-                if (nref) nref[i] = nev;
+            } else {   // a final answer, or no track
+                A[k & 1].best[t] = best;
+                A[k & 1].h[t] = live ? h : kNoStore;
+                A[k & 1].nev[t] = nev;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[k & 1]);
         }
-        // with nothing left to filter, the producers help the consumers
-        // with the last tile's FP64 tasks
-        if (K >= 1) {
-            const int kl = K - 1;
-            mbar_wait_bounded(&full[kl & 1], uint32_t((kl >> 1) & 1), v.status, healthy);
-            const int64_t base = (int64_t(blockIdx.x) + int64_t(kl) * gridDim.x) * P;
-            if (__all_sync(0xffffffffu, healthy))   // a stage that was never filled is not read
-                drain_tasks<SEGS, P>(v, tab64, S[kl & 1], [base](int o) { return base + o; }, b.n, step, hit, bpoint,
-                                     nref);
-        }
     } else {
         // ------------------------------------------------------ consumers --
+        const int c = t - P;
         for (int k = 0; k < K; ++k) {
             mbar_wait_bounded(&full[k & 1], uint32_t((k >> 1) & 1), v.status, healthy);
             const int64_t base = (int64_t(blockIdx.x) + int64_t(k) * gridDim.x) * P;
-            if (__all_sync(0xffffffffu, healthy))   // a stage that was never filled is not read
-                drain_tasks<SEGS, P>(v, tab64, S[k & 1], [base](int o) { return base + o; }, b.n, step, hit, bpoint,
-                                     nref);
+            const bool ok = __all_sync(0xffffffffu, healthy);   // a stage never filled is not read
+            auto index = [base](int o) { return base + o; };
+            if (ok) drain_tasks<SEGS, P, true>(v, tab64, S[k & 1], &A[k & 1], index, b.n, step, hit);
+            consumer_barrier<C>();   // every answer of the tile is in the stage
+            if (ok) store_tile<P, C>(S[k & 1], A[k & 1], c, index, b.n, step, hit, bpoint, nref);
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);
         }
@@ -306,14 +333,14 @@ static cudaError_t launch_refine(K kernel, int smem, const VolView& v, const Bas
 template <int P, int C>
 static cudaError_t launch_refine_cfg(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                                      int32_t* nref, cudaStream_t s, int num_sms) {
-    static_assert(sizeof(Stage<P>) % 16 == 0, "stage size keeps the tables 16-byte aligned");
-    const int smem = 2 * int(sizeof(Stage<P>)) +
+    static_assert(sizeof(Stage<P>) % 16 == 0 && sizeof(Answers<P>) % 16 == 0, "the tables stay 16-byte aligned");
+    const int smem = 2 * int(sizeof(Stage<P>) + sizeof(Answers<P>)) +
                      (v.smem_refine ? v.nd * int(sizeof(ShapeRec64) + sizeof(ShapeRec32)) : 0);
     if (v.voxelized) {
         // the grid walk needs registers: 12 + 2 warps at 72 registers beat
         // 12 + 4 at 64 (7.0 against 7.4 ms for 2^24 tracks in 512 daughters)
         constexpr int CV = P == kProd ? kVoxCons : C;
-        const int smem_v = 2 * int(sizeof(Stage<P>));
+        const int smem_v = 2 * int(sizeof(Stage<P>) + sizeof(Answers<P>));
         if (v.segs)
             return launch_refine<P, CV>(k_dist_refine<P, CV, false, 1, true>, smem_v, v, b, step, hit, bpoint, nref,
                                         s, num_sms);
