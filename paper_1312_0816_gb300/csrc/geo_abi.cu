@@ -48,6 +48,7 @@ struct geo_batch_s {
     int64_t ntiles = 0;
     int64_t max_end = 0;
     int32_t segs = 0;
+    int32_t vox = 0;            // a volume has a uniform grid
     int64_t* d_idx = nullptr;   // track indices of packed tiles
     VolView* d_vols = nullptr;
     BatchTile* d_tiles = nullptr;
@@ -964,7 +965,10 @@ geo_status geo_build_batch(const geo_volume* vols, int32_t n_vols, const geo_bas
     b->tile_tracks = T;
     b->ntiles = int64_t(tiles.size());
     b->max_end = max_end;
-    for (int i = 0; i < n_vols; ++i) b->segs = b->segs || vols[i]->view.segs;
+    for (int i = 0; i < n_vols; ++i) {
+        b->segs = b->segs || vols[i]->view.segs;
+        b->vox = b->vox || vols[i]->view.voxelized;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if ((e = lib_malloc(&b->d_vols, sizeof(VolView) * n_vols)) != cudaSuccess ||
@@ -1023,6 +1027,8 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
     bv.status = b->d_words + 1;
     bv.segs = b->segs;
     bv.nvols = b->n_vols;
+    bv.vox = b->vox;
+    bv.pad_ = 0;
     bv.idx = b->d_idx;
     const Basket bk{x, y, z, dx, dy, dz, n_total};
     return cuda_status(

@@ -128,6 +128,8 @@ struct BatchView {
     unsigned int* status;     // device error word of the batch
     int32_t segs;             // 1 if a volume holds a tube segment or a polycone
     int32_t nvols;            // entries of vols
+    int32_t vox;              // 1 if a volume has a uniform grid
+    int32_t pad_;
     const int64_t* idx;       // track indices of packed tiles (count < 0), or null
 };
 

@@ -45,8 +45,11 @@ struct __align__(16) TileHdr {
 };
 
 // SEGS = false: no volume of the batch holds a tube segment or a polycone.
-// P producer threads (one track each of a tile of P) and C consumer threads.
-template <bool SEGS, int P, int C>
+// VOX = false: no volume has a uniform grid, and the kernel carries only the
+// all-daughter FP32 pass (10 % faster on the 64-volume batch than with the
+// grid walk's code beside it).  P producer threads (one track each of a tile
+// of P) and C consumer threads.
+template <bool SEGS, bool VOX, int P, int C>
 __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket b, double* __restrict__ step,
                                                               int32_t* __restrict__ hit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_batched(BatchView bv, Basket 
                 double best = 0.0;
                 int h = -2, nev = 0;
                 rs.status = 1;
-                if (live) refine_pass1<2>(v, v.d32, v.d64, px, py, pz, qx, qy, qz, rs, best, h, nev);
+                if (live) refine_pass1<VOX ? 2 : 0>(v, v.d32, v.d64, px, py, pz, qx, qy, qz, rs, best, h, nev);
                 int task = 0, bin = -1;
                 if (rs.status == 0) {
                     task = first_task(rs);
@@ -187,15 +190,15 @@ cudaError_t launch_wait_selftest(unsigned int* status, uint32_t polls, cudaStrea
     return cudaGetLastError();
 }
 
-template <bool SEGS, int P, int C>
+template <bool SEGS, bool VOX, int P, int C>
 static int batched_blocks_per_sm() {
     static int cached = 0;
     if (cached == 0) {
         const int smem = 2 * int(sizeof(Stage<P>) + sizeof(TileHdr));
         int per_sm = 0;
-        if (cudaFuncSetAttribute(k_dist_batched<SEGS, P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        if (cudaFuncSetAttribute(k_dist_batched<SEGS, VOX, P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched<SEGS, P, C>, P + C, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dist_batched<SEGS, VOX, P, C>, P + C, smem) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -206,16 +209,16 @@ static int batched_blocks_per_sm() {
     return cached;
 }
 
-template <bool SEGS, int P, int C>
+template <bool SEGS, bool VOX, int P, int C>
 static cudaError_t launch_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
                                   cudaStream_t s, int num_sms) {
     const int smem = 2 * int(sizeof(Stage<P>) + sizeof(TileHdr));
-    const int maxb = batched_blocks_per_sm<SEGS, P, C>();
+    const int maxb = batched_blocks_per_sm<SEGS, VOX, P, C>();
     const int per_sm = (blocks_per_sm <= 0 || blocks_per_sm > maxb) ? maxb : blocks_per_sm;
     cudaError_t e =
-        cudaFuncSetAttribute(k_dist_batched<SEGS, P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_dist_batched<SEGS, VOX, P, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_dist_batched<SEGS, P, C><<<per_sm * num_sms, P + C, smem, s>>>(bv, b, step, hit);
+    k_dist_batched<SEGS, VOX, P, C><<<per_sm * num_sms, P + C, smem, s>>>(bv, b, step, hit);
     return cudaGetLastError();
 }
 
@@ -224,11 +227,21 @@ static cudaError_t launch_batched(const BatchView& bv, const Basket& b, double* 
 cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* step, int32_t* hit, int blocks_per_sm,
                                 int tile_tracks, cudaStream_t s, int num_sms) {
     static_assert(sizeof(TileHdr) % 16 == 0 && sizeof(VolView) % 16 == 0, "16-byte copies");
-    if (tile_tracks == kLatProd)
-        return bv.segs ? launch_batched<true, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms)
-                       : launch_batched<false, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
-    return bv.segs ? launch_batched<true, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms)
-                   : launch_batched<false, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+    const int code = (bv.segs ? 1 : 0) + (bv.vox ? 2 : 0);
+    if (tile_tracks == kLatProd) {
+        switch (code) {
+            case 0: return launch_batched<false, false, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+            case 1: return launch_batched<true, false, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+            case 2: return launch_batched<false, true, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+            default: return launch_batched<true, true, kLatProd, kLatCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+        }
+    }
+    switch (code) {
+        case 0: return launch_batched<false, false, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+        case 1: return launch_batched<true, false, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+        case 2: return launch_batched<false, true, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+        default: return launch_batched<true, true, kProd, kCons>(bv, b, step, hit, blocks_per_sm, s, num_sms);
+    }
 }
 
 // A basket of at most two tiles of 256 tracks per resident block (two blocks

@@ -137,8 +137,13 @@ extern "C" geo_status geo_dist_to_boundary_batched_noalloc(const geo_volume* vol
     bv.status = &d->words[1];
     bv.segs = 0;
     bv.nvols = n_vols;
+    bv.vox = 0;
+    bv.pad_ = 0;
     bv.idx = nullptr;   // plain tiles only
-    for (int i = 0; i < n_vols; ++i) bv.segs = bv.segs || volume_view(vols[i])->segs;
+    for (int i = 0; i < n_vols; ++i) {
+        bv.segs = bv.segs || volume_view(vols[i])->segs;
+        bv.vox = bv.vox || volume_view(vols[i])->voxelized;
+    }
     const Basket bk{x, y, z, dx, dy, dz, n_total};
     e = launch_dist_batched(bv, bk, step, hit, 0, kTileTracks, s, sm_count(dev));
     return e == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;

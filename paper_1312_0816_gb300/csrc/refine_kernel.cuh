@@ -28,18 +28,20 @@ namespace geonav {
 //             pass of tile k, bin each track's first FP64 task by solid kind
 //             (mother, box, tube, cone) into stage k%2, arrive on full[k%2].
 //  consumers: wait full[k%2], evaluate the binned tasks of tile k in FP64 (a
-//             warp takes 32 consecutive tasks, all of one kind: the bins
-//             start on multiples of 32) and finish their tracks (rare extra
-//             refinements, stores), arrive on done[k%2].  Finishing there
-//             instead of in the producers took 0.2425 -> 0.2300 ms: the
-//             producers set the pace, and the consumers had time to spare.
+//             warp claims chunks of 32 consecutive tasks, all of one kind:
+//             the bins start on multiples of 32) and finish their tracks
+//             (rare extra refinements), gather the tile's answers in its
+//             answer buffer, then store them by consecutive lanes; arrive on
+//             done[k%2].  Finishing there instead of in the producers took
+//             0.2425 -> 0.2300 ms: the producers set the pace, and the
+//             consumers had time to spare.
 // The FP64 pipe therefore works on tile k while the FP32 pass of tile k+1 runs.
 // Every wait is bounded; a wait that runs out records ST_SYNC_TIMEOUT.
 // Block configurations (P producer threads, one track each per tile, and
 // C consumer threads):
 //  * 12 + 4 warps, tiles of kTileTracks = 384: throughput (many tiles per
-//    block) and the batched launch (there 12 + 2 warps at 72 registers take
-//    as long);
+//    block) and the batched launch (there 12 + 2 warps at 72 registers took
+//    1.292 against 1.248 ms);
 //  * 8 + 4 warps, tiles of 256: baskets of at most two tiles per block,
 //    where the latency of one tile sets the time.
 constexpr int kProd = kTileTracks, kCons = 128;   // throughput and batched: 12 + 4 warps

@@ -169,3 +169,31 @@ def test_batched_segments_and_polycones(g):
         assert np.array_equal(s.view(np.int64), s64.view(np.int64))
         batch.close()
 
+
+
+@pytest.mark.parametrize("segs", [False, True], ids=["plain", "segments"])
+def test_batched_with_voxelised_volumes(g, segs):
+    """A batch holding volumes with a uniform grid (the batched kernel's
+    instantiation with the grid walk) beside plain ones, with and without
+    tube segments and polycones: the same bits as one call per basket, both
+    tile shapes."""
+    vols = [scenes.grid512(5), scenes.toy40(1), scenes.box4(0)]
+    vox = [True, True, False]
+    if segs:
+        vols.append(scenes.pcon4())
+        vox.append(False)
+    rng = np.random.default_rng(21)
+    baskets = [(int(rng.integers(0, len(vols))), int(rng.integers(1, 900))) for _ in range(50)]
+    tr, rows = scenes.batched_tracks(vols, baskets, 13)
+    volh = [g.geo_build_volume(v, voxelize=x) for v, x in zip(vols, vox)]
+    for tile in (0, 256):
+        batch = g.geo_build_batch(volh, rows, tile_order=0, tile_tracks=tile)
+        s, h = g.geo_dist_to_boundary_batched(batch, *dev(tr))
+        torch.cuda.synchronize()
+        s, h = s.cpu().numpy(), h.cpu().numpy()
+        s64, h64 = per_basket(g, vols, volh, tr, rows, 0)
+        assert np.array_equal(h, h64)
+        assert np.array_equal(s.view(np.int64), s64.view(np.int64))
+        batch.close()
+    for v in volh:
+        v.close()
