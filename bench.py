@@ -923,6 +923,10 @@ def main():
             clocks.mark()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        # a spin of about a millisecond ahead of the first event, so that the
+        # timed launches are queued before the device reaches it: the events
+        # then bracket device time, not the host's latency to the first launch
+        torch.cuda._sleep(2_000_000)
         e0.record(stream)
         for k in range(steps):
             step(k, mode)
