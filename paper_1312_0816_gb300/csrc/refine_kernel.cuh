@@ -54,11 +54,11 @@ static_assert(kProd <= (1 << kOwnerBits) && kProd % 32 == 0 && kLatProd % 32 == 
 template <int P>
 struct Stage {
     double pd[6][P];        // the tile's positions and directions (FP64)
-    float L[kCand][P];      // stashed FP32 state for the producers' second half
-    int j[kCand][P];
+    float L[kCand][P];      // FP32 state stashed by the producers for the consumer
+    int j[kCand][P];        //   that finishes the track (tracks with an FP64 task)
     float Lm[P];
     float dropped[P];
-    int n[P];               // candidate count, -1: answer already final
+    int n[P];               // candidate count
     int task[P + 128];      // binned tasks: owner | (solid + 1) << kOwnerBits; -1 pads
     int cnt[4];
     int next;               // the next chunk of 32 tasks to claim
@@ -125,11 +125,11 @@ __device__ __forceinline__ int kind_bin(int kind) { return kind == KTUBS ? 2 : (
 
 // A consumer's whole share of one track: the FP64 value of its first task
 // jj, then the refinement's end (nearly always refine_fast: no other bound
-// can win or tie).  The answer goes to the stage (STAGED), from where the
-// tile's answers are stored together, consecutive tracks by consecutive
-// lanes (the tasks themselves are in kind order: their own stores would
-// scatter, which outputs in host memory read over the host link pay for);
-// or it is stored right away to index(o).
+// can win or tie).  The answer goes to the tile's answer buffer (STAGED),
+// from where the tile's answers are stored together, consecutive tracks by
+// consecutive lanes (the tasks themselves are in kind order: their own
+// stores would scatter, which outputs in host memory written over the host
+// link pay for); or it is stored right away to index(o).
 template <bool SEGS, int P, bool STAGED, typename Index>
 __device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64* __restrict__ tab64,
                                              const Stage<P>& st, Answers<P>* ans, int o, int jj, Index index,
@@ -160,11 +160,11 @@ __device__ __forceinline__ void finish_track(const VolView& v, const ShapeRec64*
     }
 }
 
-constexpr int kNoStore = -0x7fffffff;   // a stage lane without a track
+constexpr int kNoStore = -0x7fffffff;   // an answer-buffer lane without a track
 
-// The tile's answers from the stage to the outputs, consecutive tracks by
-// consecutive lanes of the C threads that call it; index(o) is the basket
-// index of the tile's track o.
+// The tile's answers from its answer buffer to the outputs, consecutive
+// tracks by consecutive lanes of the C threads that call it; index(o) is the
+// basket index of the tile's track o.
 template <int P, int C, typename Index>
 __device__ __forceinline__ void store_tile(const Stage<P>& st, const Answers<P>& ans, int c, Index index, int64_t n,
                                            double* __restrict__ step, int32_t* __restrict__ hit,
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
             if (bin >= 0) st_.task[bin_start(st_.cnt, bin) + slot] = t | ((task + 1) << kOwnerBits);
             pad_bins<P>(st_, t);
             // stash the FP32 state for the consumer that finishes the track;
-            // final answers are stored right away
+            // a final answer goes to the tile's answer buffer
             if (rs.status == 0) {
 #pragma unroll
                 for (int q = 0; q < kCand; ++q) {
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(P + C, 2) k_dist_refine(VolView v, Basket b, d
             const bool ok = __all_sync(0xffffffffu, healthy);   // a stage never filled is not read
             auto index = [base](int o) { return base + o; };
             if (ok) drain_tasks<SEGS, P, true>(v, tab64, S[k & 1], &A[k & 1], index, b.n, step, hit);
-            consumer_barrier<C>();   // every answer of the tile is in the stage
+            consumer_barrier<C>();   // every answer of the tile is in its answer buffer
             if (ok) store_tile<P, C>(S[k & 1], A[k & 1], c, index, b.n, step, hit, bpoint, nref);
             __syncwarp();
             if (lane == 0) mbar_arrive(&done[k & 1]);
