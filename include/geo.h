@@ -297,7 +297,7 @@ geo_status geo_dist_to_boundary_batched(geo_batch b, const double* x, const doub
  * geo_build_batch.  x..dz, step, hit: device arrays as for
  * geo_dist_to_boundary_batched, n_total covering every basket.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and caches it.
  * Every call reuses the same array, so calls that overlap on the GPU (on
  * different streams, or from different host threads) race: serialise them.
  * The counter and status word are cleared by each call; the rest keeps the

@@ -1,7 +1,6 @@
 """The no-allocation entry point, for callers that cannot let a library
 allocate device memory while they run (their allocator owns all device memory,
-allocation is forbidden after start-up, or the call is recorded under a
-global-mode stream capture).  It must give the same answers as the regular
+or allocation is forbidden after start-up).  It must give the same answers as the regular
 batched entry point, call after call, while its scratch lives in the
 library's fixed device array.  This file is collected last on purpose."""
 import numpy as np
