@@ -193,12 +193,27 @@ def fp32_ops_per_track(sc):
     return float(sum(FP32_SPHERE + (0 if e else FP32_TRANSFORM) + FP32_SHAPE[int(k)] for k, e in zip(sc.kinds, eye)))
 
 
-def sources_sha():
+def code_only(text: str) -> str:
+    """A source file without its comments and with its blank space collapsed,
+    so that an edit of comments alone keeps the kernel's captured counters."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def sources_sha(read=None):
+    """Hash of the refine kernel's code (comments excluded); read(name) gives
+    a source's text (default: the file in the package)."""
     import hashlib
 
+    if read is None:
+        def read(f):
+            return open(os.path.join(ROOT, "paper_1312_0816_gb300", "csrc", f)).read()
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1312_0816_gb300", "csrc", f), "rb").read())
+        h.update(code_only(read(f)).encode())
     return h.hexdigest()[:16]
 
 
