@@ -146,6 +146,12 @@ size_t refine_stage_bytes();
 cudaError_t launch_dist_refine_latency(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                        double* bpoint, int32_t* nref, cudaStream_t s, int num_sms);
 
+// small baskets in volumes of many daughters: the FP32 pass of a track split
+// over the warps of a block
+bool split_basket(const VolView& v, int64_t n, int num_sms);
+cudaError_t launch_dist_refine_split(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
+                                     int32_t* nref, cudaStream_t s);
+
 // launchers (host), each returns cudaGetLastError() of its launch
 cudaError_t launch_dist_fp64(const VolView& v, const Basket& b, double* step, int32_t* hit,
                              double* bpoint, cudaStream_t s, int num_sms);

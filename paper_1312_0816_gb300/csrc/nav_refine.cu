@@ -244,13 +244,16 @@ cudaError_t launch_dist_batched(const BatchView& bv, const Basket& b, double* st
     }
 }
 
-// A basket of at most two tiles of 256 tracks per resident block (two blocks
-// per SM) takes the latency configuration, larger ones the throughput
-// configuration (toy detector, one call: 65536 tracks 43.8 us instead of
-// 59.1 us, 131072 tracks 66.5 us instead of 78.5 us; from 196608 tracks on
-// the two are equal, and at 2^20 the throughput configuration is 13 % faster).
+// A small basket in a volume of many daughters takes the split kernel
+// (split_basket()); otherwise a basket of at most two tiles of 256 tracks per
+// resident block (two blocks per SM) takes the latency configuration, larger
+// ones the throughput configuration (toy detector, one call: 65536 tracks
+// 43.8 us instead of 59.1 us, 131072 tracks 66.5 us instead of 78.5 us; from
+// 196608 tracks on the two are equal, and at 2^20 the throughput
+// configuration is 13 % faster).
 cudaError_t launch_dist_refine_stats(const VolView& v, const Basket& b, double* step, int32_t* hit,
                                      double* bpoint, int32_t* nref, cudaStream_t s, int num_sms) {
+    if (split_basket(v, b.n, num_sms)) return launch_dist_refine_split(v, b, step, hit, bpoint, nref, s);
     if (b.n <= int64_t(4) * num_sms * kLatProd)
         return launch_dist_refine_latency(v, b, step, hit, bpoint, nref, s, num_sms);
     return launch_refine_cfg<kProd, kCons>(v, b, step, hit, bpoint, nref, s, num_sms);

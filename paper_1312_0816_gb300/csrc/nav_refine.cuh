@@ -167,11 +167,13 @@ struct RefineState {
 // FP32 pass: bounds of the mother and of every daughter.  When status == 1
 // on return, best/h already hold the final answer.  TRAVERSAL: 0 = every
 // daughter, 1 = the uniform grid, 2 = chosen per volume at run time.
+// (TRAVERSAL 0 only) j_first, j_step: bound daughters j_first, j_first +
+// j_step, ... alone (a share of the volume's daughters).
 template <int TRAVERSAL, bool SEGS = true>
 __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32* __restrict__ tab32,
                                              const ShapeRec64* __restrict__ tab64, double px, double py,
                                              double pz, double qx, double qy, double qz, RefineState& st,
-                                             double& best, int& h, int& nev) {
+                                             double& best, int& h, int& nev, int j_first = 0, int j_step = 1) {
     nev = 0;
     st.status = 1;
     st.c.n = 0;
@@ -219,7 +221,7 @@ __device__ __forceinline__ void refine_pass1(const VolView& v, const ShapeRec32*
     const float Um = e_hi + 16.f * kEps32f * e_hi + v.m32u.delta * inv_dn;
     const bool grid = TRAVERSAL == 1 || (TRAVERSAL == 2 && v.voxelized);
     if (!grid) {
-        for (int j = 0; j < v.nd; ++j) bound_daughter(tab32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
+        for (int j = j_first; j < v.nd; j += j_step) bound_daughter(tab32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
     } else {
         // only daughters listed in the cells the track crosses before the
         // mother's exit (upper bound Um); a daughter met again is skipped

@@ -352,3 +352,64 @@ def test_full_size_toy_detector_sampled(g, orc):
     sub = scenes.Tracks(*(f[idx] for f in tr.fields()))
     ref = orc.navigate(sc, sub, nthreads=8)
     compare(ref, step[idx], hit[idx], sub, sc, orc, max_graze=1e-4)
+
+
+def many_solids_scene():
+    """36 small solids of every kind (boxes, tubes, cones, tube segments,
+    polycones), rotated, on a 4 x 3 x 3 grid of pitch 200 mm in a box mother:
+    the split kernel's instantiation with the segment and polycone code."""
+    rng = np.random.default_rng(41)
+    rows = []
+    k = 0
+    for ix in range(4):
+        for iy in range(3):
+            for iz in range(3):
+                c = (-300.0 + 200.0 * ix, -200.0 + 200.0 * iy, -200.0 + 200.0 * iz)
+                rot = scenes.haar_rotation(rng)
+                kind = k % 5
+                if kind == scenes.BOX:
+                    spec = tuple(rng.uniform(15.0, 40.0, 3))
+                elif kind == scenes.TUBE:
+                    spec = (rng.uniform(0.0, 15.0), rng.uniform(25.0, 45.0), rng.uniform(15.0, 45.0))
+                elif kind == scenes.CONE:
+                    spec = (rng.uniform(20.0, 40.0), 5.0, 30.0, 0.0, 40.0)
+                elif kind == scenes.TUBS:
+                    spec = (rng.uniform(0.0, 10.0), rng.uniform(25.0, 45.0), rng.uniform(15.0, 40.0),
+                            rng.uniform(-3.0, 3.0), rng.uniform(0.5, 6.0))
+                else:
+                    spec = scenes.Pcon((-30.0, -5.0, 5.0, 30.0), (0.0, 8.0, 8.0, 0.0), (30.0, 40.0, 40.0, 25.0),
+                                       rng.uniform(-3.0, 3.0), rng.uniform(1.0, 2.0 * math.pi))
+                rows.append((kind, spec, rot, c))
+                k += 1
+    return scenes._scene("many36", scenes.BOX, (450.0, 350.0, 350.0), rows)
+
+
+@pytest.mark.parametrize("name", ["toy40", "grid512", "many36"])
+def test_split_small_baskets(g, orc, name):
+    """Small baskets in volumes of more than 32 daughters (no uniform grid)
+    take the split kernel (a track's FP32 pass spread over the warps of a
+    block by daughter): the plain FP64 bits and boundary points, the same
+    bits as the pipelined kernel gives the same tracks in a large basket, on
+    either side of the switch and on ragged block tails; the oracle on the
+    smallest baskets."""
+    sc = many_solids_scene() if name == "many36" else scene(name)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    edge = 4 * sms * 32 * (2 if sc.n_daughters >= 128 else 1)
+    big = scenes.sample_tracks(sc, max(edge + 100, 200000), 51)
+    s_big, h_big, b_big = run_nav(g, sc, big, 1, bpoint=True)
+    for n in (1, 31, 33, 1000, edge, edge + 1):
+        tr = big.slice(0, n)
+        s1, h1, b1 = run_nav(g, sc, tr, 1, bpoint=True)
+        s0, h0, b0 = run_nav(g, sc, tr, 0, bpoint=True)
+        assert np.array_equal(h1, h0) and np.array_equal(s1.view(np.int64), s0.view(np.int64)), (name, n)
+        assert np.array_equal(b1.view(np.int64), b0.view(np.int64)), (name, n)
+        assert np.array_equal(h1, h_big[:n]) and np.array_equal(s1.view(np.int64), s_big[:n].view(np.int64)), n
+        if n <= 1000:
+            compare(orc.navigate(sc, tr, nthreads=8), s1, h1, tr, sc, orc, max_banded=None)
+    # adversarial rays (grazing, edges, apexes) in a small basket
+    adv = scenes.adversarial_tracks(sc, 2000, 52)
+    s1, h1 = run_nav(g, sc, adv, 1)
+    s0, h0 = run_nav(g, sc, adv, 0)
+    assert np.array_equal(h1, h0) and np.array_equal(s1.view(np.int64), s0.view(np.int64))
+    _, _, nref = g.geo_dist_to_boundary_stats(vol(g, sc), *dev(big.slice(0, 1000)))
+    assert np.all(nref.cpu().numpy() >= 0)
