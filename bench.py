@@ -568,7 +568,10 @@ def segments_leg(pkg, scenes, rank, steps):
     return out
 
 
-def sweep_leg(pkg, scenes, rank, steps, vol, base):
+SWEEP_SIZES = (16, 64, 256, 1024, 4096, 65536, 1 << 20)
+
+
+def sweep_leg(pkg, scenes, rank, steps, vol, base, sizes=SWEEP_SIZES):
     """Fig. 3's axis, time per track against basket size, on the toy detector:
     baskets of N = 16 .. 2^20 consecutive tracks of the 2^20-track basket;
     per N the tracks/s of one geo_dist_to_boundary call per basket (32 calls
@@ -594,7 +597,7 @@ def sweep_leg(pkg, scenes, rank, steps, vol, base):
     bstep = torch.empty(nb, dtype=torch.float64, device="cuda")
     bhit = torch.empty(nb, dtype=torch.int32, device="cuda")
     sweep = {}
-    for N in (16, 64, 256, 1024, 4096, 65536, 1 << 20):
+    for N in sizes:
         offs = rng.integers(0, n - N + 1, size=32)
         calls = 32 if N < (1 << 20) else 1
         args = [[f[int(o): int(o) + N] for f in base] for o in offs[:calls]]
@@ -880,6 +883,8 @@ def main():
     ap.add_argument("--no-world", action="store_true")
     ap.add_argument("--no-segments", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-sizes", default=",".join(str(v) for v in SWEEP_SIZES),
+                    help="basket sizes of the sweep leg, comma-separated (one size for an ncu capture)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -1070,7 +1075,8 @@ def main():
     shapes = None if args.no_shapes else shapes_leg(pkg, max(10, args.steps // 100), q_sqrt, q_div)
     world = None if args.no_world else world_leg(pkg, scenes, rank, max(10, args.steps // 100))
     segments = None if args.no_segments else segments_leg(pkg, scenes, rank, max(10, args.steps // 100))
-    sweep = None if args.no_sweep else sweep_leg(pkg, scenes, rank, max(10, args.steps // 100), vol, base)
+    sizes = tuple(int(v) for v in args.sweep_sizes.split(",") if v)
+    sweep = None if args.no_sweep else sweep_leg(pkg, scenes, rank, max(10, args.steps // 100), vol, base, sizes)
 
     cpu, acc = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
