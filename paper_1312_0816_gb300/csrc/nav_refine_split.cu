@@ -120,17 +120,21 @@ __global__ void __launch_bounds__(kSplitWarps * 32, kSplitBlocksPerSm)
     if (nref) nref[i] = nev;
 }
 
-// Volumes of more than 32 daughters without a uniform grid (smaller volumes
-// keep the warp-per-track kernel or the pipelined one), baskets that fill at
-// most one wave of blocks (four 256-thread blocks per SM at 64 registers), two
-// waves from 128 daughters on.  Measured per call (CUDA graph of one call),
-// pipelined kernel -> this one: toy detector (40 daughters) 16 tracks 21.8 ->
-// 16.3 us, 1024 28.7 -> 18.3, 16384 30.7 -> 26.5, 32768 32.7 -> 40.9; 512
-// daughters without the grid 16 tracks 126.9 -> 30.0 us, 16384 118.8 ->
-// 34.8, 32768 118.8 -> 59.3, 65536 124.9 -> 100.3.
+// Volumes of more than 32 daughters (smaller volumes keep the warp-per-track
+// kernel or the pipelined one), baskets that fill at most one wave of blocks
+// (four 256-thread blocks per SM at 64 registers), two waves from 128
+// daughters on in a volume without a uniform grid.  A volume with a grid is
+// walked here daughter by daughter all the same: for a small basket the
+// shared walk beats each lane's own walk through the cells.  Measured per
+// call (CUDA graph of one call), pipelined kernel -> this one: toy detector
+// (40 daughters) 16 tracks 21.8 -> 16.3 us, 1024 28.7 -> 18.3, 16384 30.7 ->
+// 26.5, 32768 32.7 -> 40.9; 512 daughters without the grid 16 tracks 126.9
+// -> 30.0 us, 16384 118.8 -> 34.8, 32768 118.8 -> 59.3, 65536 124.9 ->
+// 100.3; the same with the grid (the pipelined kernel walking it) 16 tracks
+// 45.0 -> 28.6 us, 16384 55.2 -> 34.8, 32768 55.3 -> 59.3.
 bool split_basket(const VolView& v, int64_t n, int num_sms) {
     const int64_t wave = int64_t(kSplitBlocksPerSm) * num_sms * 32;
-    return !v.voxelized && v.nd > 32 && n <= (v.nd >= 128 ? 2 : 1) * wave;
+    return v.nd > 32 && n <= (v.nd >= 128 && !v.voxelized ? 2 : 1) * wave;
 }
 
 cudaError_t launch_dist_refine_split(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,

@@ -384,23 +384,31 @@ def many_solids_scene():
     return scenes._scene("many36", scenes.BOX, (450.0, 350.0, 350.0), rows)
 
 
-@pytest.mark.parametrize("name", ["toy40", "grid512", "many36"])
+@pytest.mark.parametrize("name", ["toy40", "grid512", "grid512_vox", "many36"])
 def test_split_small_baskets(g, orc, name):
-    """Small baskets in volumes of more than 32 daughters (no uniform grid)
-    take the split kernel (a track's FP32 pass spread over the warps of a
-    block by daughter): the plain FP64 bits and boundary points, the same
-    bits as the pipelined kernel gives the same tracks in a large basket, on
-    either side of the switch and on ragged block tails; the oracle on the
-    smallest baskets."""
-    sc = many_solids_scene() if name == "many36" else scene(name)
+    """Small baskets in volumes of more than 32 daughters take the split
+    kernel (a track's FP32 pass spread over the warps of a block by daughter;
+    a volume's uniform grid is not walked there): the plain FP64 bits and
+    boundary points, the same bits as the pipelined kernel gives the same
+    tracks in a large basket, on either side of the switch and on ragged
+    block tails; the oracle on the smallest baskets."""
+    sc = many_solids_scene() if name == "many36" else scene(name.replace("_vox", ""))
+    voxelize = name.endswith("_vox")
+    volh = g.geo_build_volume(sc, voxelize=voxelize) if voxelize else vol(g, sc)
+
+    def nav(tr, mode):
+        out = g.geo_dist_to_boundary(volh, *dev(tr), mode=mode, want_bpoint=True)
+        torch.cuda.synchronize()
+        return [o.cpu().numpy() for o in out]
+
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    edge = 4 * sms * 32 * (2 if sc.n_daughters >= 128 else 1)
+    edge = 4 * sms * 32 * (2 if sc.n_daughters >= 128 and not voxelize else 1)
     big = scenes.sample_tracks(sc, max(edge + 100, 200000), 51)
-    s_big, h_big, b_big = run_nav(g, sc, big, 1, bpoint=True)
+    s_big, h_big, b_big = nav(big, 1)
     for n in (1, 31, 33, 1000, edge, edge + 1):
         tr = big.slice(0, n)
-        s1, h1, b1 = run_nav(g, sc, tr, 1, bpoint=True)
-        s0, h0, b0 = run_nav(g, sc, tr, 0, bpoint=True)
+        s1, h1, b1 = nav(tr, 1)
+        s0, h0, b0 = nav(tr, 0)
         assert np.array_equal(h1, h0) and np.array_equal(s1.view(np.int64), s0.view(np.int64)), (name, n)
         assert np.array_equal(b1.view(np.int64), b0.view(np.int64)), (name, n)
         assert np.array_equal(h1, h_big[:n]) and np.array_equal(s1.view(np.int64), s_big[:n].view(np.int64)), n
@@ -408,8 +416,9 @@ def test_split_small_baskets(g, orc, name):
             compare(orc.navigate(sc, tr, nthreads=8), s1, h1, tr, sc, orc, max_banded=None)
     # adversarial rays (grazing, edges, apexes) in a small basket
     adv = scenes.adversarial_tracks(sc, 2000, 52)
-    s1, h1 = run_nav(g, sc, adv, 1)
-    s0, h0 = run_nav(g, sc, adv, 0)
+    s1, h1, _ = nav(adv, 1)
+    s0, h0, _ = nav(adv, 0)
     assert np.array_equal(h1, h0) and np.array_equal(s1.view(np.int64), s0.view(np.int64))
-    _, _, nref = g.geo_dist_to_boundary_stats(vol(g, sc), *dev(big.slice(0, 1000)))
+    _, _, nref = g.geo_dist_to_boundary_stats(volh, *dev(big.slice(0, 1000)))
     assert np.all(nref.cpu().numpy() >= 0)
+    assert g.geo_check_device_status(volh) == 0
