@@ -1,6 +1,7 @@
 // world.cu -- kernels of the geometry tree: Locate, and the step followed by
-// final localisation (the per-track routines are in world.cuh).  One thread
-// per track, grid-stride; the volumes' tables are read through L1.
+// final localisation (the per-track routines are in world.cuh).  Grid-stride
+// over the tracks (the filtered step by tiles of 256); the volumes' tables
+// are read through L1.
 //
 // Before a step the tracks are grouped by the logical volume of their node
 // (a counting sort of track indices: histogram, scan, scatter), and the step
@@ -14,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "launch.cuh"
+#include "refine_kernel.cuh"
 #include "world.cuh"
 
 namespace geonav {
@@ -92,10 +94,10 @@ __global__ void __launch_bounds__(256) k_world_scatter(WorldView w, int64_t n, c
     }
 }
 
-// One thread per track over the grouped order.  Three resident blocks per SM
-// (80 registers, some spills) instead of two at 124: the toy world's
-// filtered step 0.44 -> 0.41 ms.
-template <int MODE>
+// The plain FP64 step (GEO_FP64), one thread per track over the grouped
+// order.  Three resident blocks per SM (80 registers, some spills) instead of
+// two at 124 (measured on the filtered step when it ran this way: 0.44 ->
+// 0.41 ms on the toy world).
 __global__ void __launch_bounds__(256, 3) k_world_step(WorldView w, Basket b, const int32_t* __restrict__ perm,
                                                     const int32_t* __restrict__ node_in,
                                                     const int32_t* __restrict__ flag_in, double* __restrict__ step,
@@ -114,8 +116,7 @@ __global__ void __launch_bounds__(256, 3) k_world_step(WorldView w, Basket b, co
             const int skip = flag >= 0 && flag < v.nd ? flag : -1;
             const bool entered = flag == -2;
             int h;
-            if (MODE == GEO_FP64) world_nav64(v, x, u, skip, entered, best, h);
-            else world_refine(v, x, u, skip, entered, best, h);
+            world_nav64(v, x, u, skip, entered, best, h);
             if (h >= -1) {
                 double bp[3] = {FMA(best, u[0], x[0]), FMA(best, u[1], x[1]), FMA(best, u[2], x[2])};
                 world_relocate(w, node, h, bp, nout, fout);
@@ -124,6 +125,169 @@ __global__ void __launch_bounds__(256, 3) k_world_step(WorldView w, Basket b, co
         step[i] = best;
         node_out[i] = nout;
         if (flag_out) flag_out[i] = fout;
+    }
+}
+
+// The filtered step (GEO_FP32_REFINE) by tiles of 256 tracks of the grouped
+// order, with the FP64 evaluations every track needs binned by solid kind:
+// the FP32 pass per track; then each track's first FP64 task and, after it
+// left a daughter, that daughter's re-entry distance, run by whole warps over
+// the binned list (32 tasks of one kind each: a warp pays for every code path
+// its lanes take); then per track the rest of the refinement, the merge of
+// the re-entry and the relocation.  The same answers as one thread per track
+// (the same routines on the same values).  Toy world, the bench's four
+// states: 0.366 ms per step with one thread per track, 0.350 with the first
+// tasks binned, 0.332 with the re-entries binned too (two blocks per SM
+// instead of three: 0.401).
+constexpr int kWorldTile = 256;
+struct WorldTile {
+    double x[3][kWorldTile];   // the track in its node's frame
+    double u[3][kWorldTile];
+    double s1[kWorldTile];     // the first task's FP64 value (a final answer's step)
+    float L[kCand][kWorldTile];
+    int j[kCand][kWorldTile];
+    float Lm[kWorldTile];
+    float dropped[kWorldTile];
+    int n[kWorldTile];         // candidate count; -1: the FP32 pass's answer is final
+    int h[kWorldTile];         // a final answer's hit
+    int lv[kWorldTile];        // logical volume
+    double sre[kWorldTile];    // the re-entry distance of the daughter just left
+    int task[2 * kWorldTile + 256];
+    int cnt[8];
+    int next;
+};
+
+__device__ __forceinline__ int bin_start8(const int* cnt, int bin) {
+    int start = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (q < bin) start += (cnt[q] + 31) & ~31;
+    return start;
+}
+constexpr int kReentryTask = 1 << 30;
+
+__global__ void __launch_bounds__(kWorldTile, 3)
+    k_world_step_binned(WorldView w, Basket b, const int32_t* __restrict__ perm, const int32_t* __restrict__ node_in,
+                        const int32_t* __restrict__ flag_in, double* __restrict__ step,
+                        int32_t* __restrict__ node_out, int32_t* __restrict__ flag_out) {
+    __shared__ WorldTile T;
+    const int t = threadIdx.x, lane = t & 31;
+    const int64_t ntiles = (b.n + kWorldTile - 1) / kWorldTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t q = tile * kWorldTile + t;
+        int bin = -1, task = 0, bin2 = -1, task2 = 0;
+        {
+            // FP32 pass of this thread's track
+            const bool live = q < b.n;
+            const int64_t i = live ? (perm ? perm[q] : q) : 0;
+            const int node = live ? node_in[i] : -1;
+            const int flag = live && flag_in ? flag_in[i] : -1;
+            RefineState st;
+            st.status = 1;
+            double best = d_nan(), x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+            int h = -2, lvi = 0;
+            if (live && node >= 0 && node < w.nnodes) {
+                world_to_node(w.xf + 12 * size_t(node), b.x[i], b.y[i], b.z[i], b.dx[i], b.dy[i], b.dz[i], x, u);
+                lvi = w.lv[node];
+                const VolView& v = w.vols[lvi];
+                world_pass1(v, x, u, flag >= 0 && flag < v.nd ? flag : -1, flag == -2, st, best, h);
+                if (st.status == 0) {
+                    task = first_task(st);
+                    bin = task < 0 ? 0 : kind_bin(v.d64[task].kind);
+                    if (flag >= 0 && flag < v.nd) {
+                        task2 = flag;
+                        bin2 = 4 + kind_bin(v.d64[flag].kind);
+                    }
+                }
+            }
+            __syncthreads();   // the previous tile's tracks are done with the tile's memory
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T.x[k][t] = x[k];
+                T.u[k][t] = u[k];
+            }
+#pragma unroll
+            for (int c = 0; c < kCand; ++c) {
+                T.L[c][t] = st.c.L[c];
+                T.j[c][t] = st.c.j[c];
+            }
+            T.Lm[t] = st.Lm;
+            T.dropped[t] = st.c.dropped;
+            T.n[t] = st.status == 0 ? st.c.n : -1;
+            T.s1[t] = best;
+            T.h[t] = h;
+            T.lv[t] = lvi;
+            if (t < 8) T.cnt[t] = 0;
+            if (t == 8) T.next = 0;
+        }
+        __syncthreads();
+        const int slot = bin >= 0 ? atomicAdd(&T.cnt[bin], 1) : 0;
+        const int slot2 = bin2 >= 0 ? atomicAdd(&T.cnt[bin2], 1) : 0;
+        __syncthreads();
+        if (bin >= 0) T.task[bin_start8(T.cnt, bin) + slot] = t | ((task + 1) << kOwnerBits);
+        if (bin2 >= 0) T.task[bin_start8(T.cnt, bin2) + slot2] = kReentryTask | t | ((task2 + 1) << kOwnerBits);
+        {   // -1 between the bins (each starts on a multiple of 32)
+            const int bb = t >> 5, c = T.cnt[bb];
+            if ((t & 31) < ((c + 31) & ~31) - c) T.task[bin_start8(T.cnt, bb) + c + (t & 31)] = -1;
+        }
+        __syncthreads();
+        // the first FP64 tasks and the re-entries, 32 of one kind per warp
+        const int total = bin_start8(T.cnt, 8);
+        for (;;) {
+            int q0 = 0;
+            if (lane == 0) q0 = atomicAdd(&T.next, 32);
+            q0 = __shfl_sync(0xffffffffu, q0, 0);
+            if (q0 >= total) break;
+            const int e = T.task[q0 + lane];
+            if (e >= 0) {
+                const int o = e & ((1 << kOwnerBits) - 1), jj = ((e & ~kReentryTask) >> kOwnerBits) - 1;
+                const VolView& v = w.vols[T.lv[o]];
+                if (e & kReentryTask) {
+                    const ShapeRec64& r = v.d64[jj];
+                    double xl[3], ul[3];
+                    to_local64(r, T.x[0][o], T.x[1][o], T.x[2][o], T.u[0][o], T.u[1][o], T.u[2][o], xl, ul);
+                    T.sre[o] = reentry64(r, xl, ul);
+                } else {
+                    T.s1[o] = eval64(v, v.d64, jj, T.x[0][o], T.x[1][o], T.x[2][o], T.u[0][o], T.u[1][o], T.u[2][o]);
+                }
+            }
+        }
+        __syncthreads();
+        // the rest of each track: refinement, re-entry, relocation
+        if (q < b.n) {
+            const int64_t i = perm ? perm[q] : q;
+            const int node = node_in[i];
+            const int flag = flag_in ? flag_in[i] : -1;
+            double best = d_nan();
+            int nout = -2, fout = -1;
+            if (node >= 0 && node < w.nnodes) {
+                const double x[3] = {T.x[0][t], T.x[1][t], T.x[2][t]}, u[3] = {T.u[0][t], T.u[1][t], T.u[2][t]};
+                int h = T.h[t];
+                best = T.s1[t];
+                if (T.n[t] >= 0) {
+                    const VolView& v = w.vols[T.lv[t]];
+                    RefineState st;
+                    st.status = 0;
+                    st.c.n = T.n[t];
+#pragma unroll
+                    for (int c = 0; c < kCand; ++c) {
+                        st.c.L[c] = T.L[c][t];
+                        st.c.j[c] = T.j[c][t];
+                    }
+                    st.c.dropped = T.dropped[t];
+                    st.Lm = T.Lm[t];
+                    const double s1 = best;
+                    world_finish(v, x, u, flag >= 0 && flag < v.nd ? flag : -1, flag == -2, st, s1, best, h, &T.sre[t]);
+                }
+                if (h >= -1) {
+                    double bp[3] = {FMA(best, u[0], x[0]), FMA(best, u[1], x[1]), FMA(best, u[2], x[2])};
+                    world_relocate(w, node, h, bp, nout, fout);
+                }
+            }
+            step[i] = best;
+            node_out[i] = nout;
+            if (flag_out) flag_out[i] = fout;
+        }
     }
 }
 
@@ -167,10 +331,10 @@ cudaError_t launch_world_step(const WorldView& w, const Basket& b, const int32_t
                               const int32_t* flag_in, double* step, int32_t* node_out, int32_t* flag_out, int mode,
                               cudaStream_t s, int num_sms) {
     if (mode == GEO_FP64)
-        k_world_step<GEO_FP64><<<blocks_for(k_world_step<GEO_FP64>, b.n, 0, num_sms), 256, 0, s>>>(
-            w, b, perm, node_in, flag_in, step, node_out, flag_out);
+        k_world_step<<<blocks_for(k_world_step, b.n, 0, num_sms), 256, 0, s>>>(w, b, perm, node_in, flag_in, step,
+                                                                            node_out, flag_out);
     else
-        k_world_step<GEO_FP32_REFINE><<<blocks_for(k_world_step<GEO_FP32_REFINE>, b.n, 0, num_sms), 256, 0, s>>>(
+        k_world_step_binned<<<blocks_for(k_world_step_binned, b.n, 0, num_sms), kWorldTile, 0, s>>>(
             w, b, perm, node_in, flag_in, step, node_out, flag_out);
     return cudaGetLastError();
 }

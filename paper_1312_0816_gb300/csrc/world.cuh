@@ -197,9 +197,22 @@ static __device__ __noinline__ void world_nav64(const VolView& v, const double* 
 // The same answer with the FP32 filter: bounds for every daughter but
 // `skip`, FP64 refinement of the candidates, then `skip`'s re-entry distance
 // merged with the order of the sequential loop.  A track whose candidate
-// list overflowed takes the FP64 loop.
-static __device__ void world_refine(const VolView& v, const double* x, const double* u, int skip, bool entered,
-                             double& best, int& h) {
+// list overflowed takes the FP64 loop.  In three parts, so that the kernel can
+// run the first FP64 evaluation of many tracks binned by solid kind:
+// world_pass1 (FP32; st.status 1: best/h final), the first task's FP64 value
+// (eval64 of first_task(st)), world_finish (s_re: the re-entry distance of
+// `skip` when the caller has it already).
+static __device__ __forceinline__ void world_pass1(const VolView& v, const double* x, const double* u, int skip,
+                                                   bool entered, RefineState& st, double& best, int& h) {
+    st.status = 1;
+    st.c.n = 0;
+    st.c.dropped = f_inf();
+#pragma unroll
+    for (int k = 0; k < kCand; ++k) {
+        st.c.L[k] = f_inf();
+        st.c.j[k] = 0;
+    }
+    st.Lm = 0.f;
     if (!valid_track(x[0], x[1], x[2], u[0], u[1], u[2])) {
         best = d_nan();
         h = -2;
@@ -214,14 +227,6 @@ static __device__ void world_refine(const VolView& v, const double* x, const dou
     }
     const float inv_dd = __frcp_rn(dd);
     const float inv_dn = rsqrtf(dd) * (1.f + 4.f * kEps32f);
-    RefineState st;
-    st.c.n = 0;
-    st.c.dropped = f_inf();
-#pragma unroll
-    for (int k = 0; k < kCand; ++k) {
-        st.c.L[k] = f_inf();
-        st.c.j[k] = 0;
-    }
     bool in_shrunk;
     const float e_lo = exit32(v.m32, p32, d32, in_shrunk);
     const bool inside = in_shrunk || entered || contains64_cold<true>(v.m64, x[0], x[1], x[2]);
@@ -237,18 +242,29 @@ static __device__ void world_refine(const VolView& v, const double* x, const dou
     for (int j = 0; j < v.nd; ++j)
         if (j != skip) bound_daughter(v.d32[j], j, p32, d32, inv_dd, inv_dn, Um, st.c);
     st.status = 0;
-    const double s1 = eval64(v, v.d64, first_task(st), x[0], x[1], x[2], u[0], u[1], u[2]);
-    int nev;
-    refine_rest(v, v.d64, st, s1, x[0], x[1], x[2], u[0], u[1], u[2], best, h, nev);
-    if (nev >= 1000) {   // the candidate list overflowed: the loop over every daughter
-        world_nav64(v, x, u, skip, entered, best, h);
-        return;
+}
+
+static __device__ __forceinline__ void world_finish(const VolView& v, const double* x, const double* u, int skip,
+                                                    bool entered, const RefineState& st, double s1, double& best,
+                                                    int& h, const double* s_re = nullptr) {
+    if (!refine_fast(st, s1, best, h)) {
+        int nev;
+        refine_rest(v, v.d64, st, s1, x[0], x[1], x[2], u[0], u[1], u[2], best, h, nev);
+        if (nev >= 1000) {   // the candidate list overflowed: the loop over every daughter
+            world_nav64(v, x, u, skip, entered, best, h);
+            return;
+        }
     }
     if (skip >= 0) {
-        const ShapeRec64& r = v.d64[skip];
-        double xl[3], ul[3];
-        to_local64(r, x[0], x[1], x[2], u[0], u[1], u[2], xl, ul);
-        const double s = reentry64(r, xl, ul);
+        double s;
+        if (s_re) {
+            s = *s_re;
+        } else {
+            const ShapeRec64& r = v.d64[skip];
+            double xl[3], ul[3];
+            to_local64(r, x[0], x[1], x[2], u[0], u[1], u[2], xl, ul);
+            s = reentry64(r, xl, ul);
+        }
         if (LT(s, best) || (BITS(s) == BITS(best) && h >= 0 && skip < h)) {
             best = s;
             h = skip;
