@@ -139,6 +139,7 @@ bool split_basket(const VolView& v, int64_t n, int num_sms) {
 
 cudaError_t launch_dist_refine_split(const VolView& v, const Basket& b, double* step, int32_t* hit, double* bpoint,
                                      int32_t* nref, cudaStream_t s) {
+    if (b.n <= 0) return cudaSuccess;
     const unsigned blocks = unsigned((b.n + 31) / 32);
     if (v.segs)
         k_dist_split<true><<<blocks, kSplitWarps * 32, 0, s>>>(v, b, step, hit, bpoint, nref);
