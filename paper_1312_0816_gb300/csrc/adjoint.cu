@@ -15,11 +15,12 @@
 // in the volume's device status word.
 //
 // Geometry gradients are sums over tracks; they are reduced deterministically.
-// Every block owns a fixed set of tiles of 256 tracks.  Within a tile each warp
-// groups its lanes by owner (the winning daughter, or the mother's parameters)
-// and sums every group with a fixed butterfly of shuffles; the warps then add
-// their group sums into the block's shared accumulators one warp after the
-// other (a warp's groups have distinct owners).  Block partials go to a
+// Every block owns a fixed set of tiles of 256 tracks, ordered within the
+// tile by their hit (a stable sort).  Within a tile each warp groups its
+// lanes by owner (the winning daughter, or the mother's parameters) and sums
+// every group in lane order; the warps then add their group sums into the
+// block's shared accumulators one warp after the other (a warp's groups have
+// distinct owners).  Block partials go to a
 // caller-provided workspace and a second kernel adds them in block order.  No
 // step depends on timing, so repeated calls give the same bits.
 #include <cuda_runtime.h>
@@ -135,12 +136,50 @@ __global__ void __launch_bounds__(kAdjTile) k_adjoint(VolView v, Basket b, const
     double* tval = gsum + kAdjWarps * 32 * kGeo;     // [kGeo][kTval] per-track contributions
     int* gown = reinterpret_cast<int*>(tval + kGeo * kTval);   // [kAdjWarps][32] group owners
     int* town = gown + kAdjWarps * 32;                // [kAdjTile] per-track owners
+    int* skey = town + kAdjTile;                      // [kAdjTile] sort keys
+    int* sidx = skey + kAdjTile;                      // [kAdjTile] the tile's track order
+    int* wzero = sidx + kAdjTile;                     // [kAdjWarps] zeros of one radix pass
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nbits = 32 - __clz(v.nd + 2);           // keys 0 .. nd + 2
     for (int q = t; q < nown * kGeo; q += kAdjTile) acc[q] = 0.0;
     __syncthreads();
     const int64_t ntiles = (b.n + kAdjTile - 1) / kAdjTile;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t i = tile * kAdjTile + t;
+        // The tile's tracks ordered by their hit (a stable LSD radix sort,
+        // one ballot per bit): the lanes of a warp then mostly run one
+        // solid's FP64 routine, and a warp's owner groups are few.  Key 0:
+        // no surface (outside, inside a daughter, past the basket's end), 1
+        // the mother, j + 2 daughter j, nd + 2 a hit index out of range.
+        int key = 0, idx = t;
+        {
+            const int64_t i0 = tile * kAdjTile + t;
+            if (i0 < b.n) {
+                const int h = hit[i0];
+                key = h < -1 ? 0 : (h >= v.nd ? v.nd + 2 : h + 2);
+            }
+        }
+        for (int bit = 0; bit < nbits; ++bit) {
+            const bool one = (key >> bit) & 1;
+            const unsigned ones = __ballot_sync(0xffffffffu, one);
+            if (lane == 0) wzero[warp] = 32 - __popc(ones);
+            __syncthreads();
+            int before = 0, total = 0;   // zeros in the warps before this one, in the tile
+            for (int w = 0; w < kAdjWarps; ++w) {
+                const int z = wzero[w];
+                total += z;
+                if (w < warp) before += z;
+            }
+            const unsigned below = (1u << lane) - 1u;
+            const int pos = one ? total + (warp * 32 - before) + __popc(ones & below)
+                                : before + __popc(~ones & below);
+            skey[pos] = key;
+            sidx[pos] = idx;
+            __syncthreads();
+            key = skey[t];
+            idx = sidx[t];
+            __syncthreads();
+        }
+        const int64_t i = tile * kAdjTile + idx;
         int o = -1;
         double c[kGeo] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (i < b.n) {
@@ -266,7 +305,7 @@ __global__ void __launch_bounds__(256) k_adjoint_reduce(int nblocks, int nd, con
 
 size_t adjoint_smem_bytes(int nd) {
     return (size_t(nd + 1) * kGeo + size_t(kAdjWarps) * 32 * kGeo + size_t(kGeo) * kTval) * sizeof(double) +
-           (size_t(kAdjWarps) * 32 + kAdjTile) * sizeof(int);
+           (size_t(kAdjWarps) * 32 + 3 * size_t(kAdjTile) + kAdjWarps) * sizeof(int);
 }
 
 int adjoint_blocks(int64_t n, int num_sms) {
