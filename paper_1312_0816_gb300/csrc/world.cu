@@ -152,11 +152,12 @@ struct WorldTile {
     int h[kWorldTile];         // a final answer's hit
     int lv[kWorldTile];        // logical volume
     double sre[kWorldTile];    // the re-entry distance of the daughter just left
-    int task[2 * kWorldTile + 256];
-    int cnt[8];
-    int next;
+    int task[2 * kWorldTile + 256];   // binned tasks (8 bins, each padded to a multiple of 32)
+    int cnt[8];                       // bins 0-3: first tasks by kind, 4-7: re-entries by kind
+    int next;                         // the next chunk of 32 tasks to claim
 };
 
+// start of bin `bin` of the tile's task list
 __device__ __forceinline__ int bin_start8(const int* cnt, int bin) {
     int start = 0;
 #pragma unroll
@@ -164,7 +165,7 @@ __device__ __forceinline__ int bin_start8(const int* cnt, int bin) {
         if (q < bin) start += (cnt[q] + 31) & ~31;
     return start;
 }
-constexpr int kReentryTask = 1 << 30;
+constexpr int kReentryTask = 1 << 30;   // task flag: the re-entry of the daughter just left
 
 __global__ void __launch_bounds__(kWorldTile, 3)
     k_world_step_binned(WorldView w, Basket b, const int32_t* __restrict__ perm, const int32_t* __restrict__ node_in,
